@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""RT-TDA benchmark: trajectory-steps/s of the batched sigma build + RK4 stepper.
+
+Workload (linear absorption): nocc=64, nvirt=448, naux=1536 (dim 28673),
+synthetic factors (seeded generator), three trajectories kicked along x, y, z
+(kappa = 1e-3) from |0>, RK4 dt = 0.05 au.  One "step" is one RK4 step of the
+whole batch (four sigma builds per trajectory, observables included).
+
+Default: 1 GPU.  Under torchrun each rank propagates its own batch (weak
+scaling, no data-path collective); timing is the max over ranks.
+`--impl reference` times the CPU oracle on a bounded row sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RT-TDA trajectory-steps/s vs plain FP64 path at stated dipole err; p50/p99 latency"
+UNIT = "trajectory-steps/s"
+NOCC, NVIRT, NAUX, CX, DT, KAPPA, SEED = 64, 448, 1536, 0.2, 0.05, 1e-3, 0
+DIRS = [(1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)]
+NDIM = 1 + NOCC * NVIRT
+WORKLOAD = (f"linear absorption: nocc={NOCC} nvirt={NVIRT} naux={NAUX} (dim {NDIM}), "
+            f"3 trajectories (x/y/z kicks, kappa={KAPPA}) per GPU, RK4 dt={DT} au, c_x={CX}")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 CUDA-core peak from unit counts: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz.
+FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def base_config(prec: str, world: int) -> dict:
+    return {"workload": WORKLOAD, "precision": prec, "trajectories_per_gpu": 3,
+            "global_trajectories": 3 * world, "parallelism": f"trajectory replicas x{world}",
+            "l2": "inputs larger than L2: every stage streams B_vv (1.23 GB fp32) and B_ov",
+            "seed": SEED}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+class OracleSample:
+    """Dense sigma = H(t)c of the oracle on a block of rows of the explicit A.
+
+    The block is the rows of the first `nocc_rows` occupied orbitals (all
+    virtuals); one sampled step is the oracle's sigma on that block for all
+    three trajectories, four times (one RK4 step), and the full step is that
+    time scaled by (rows of A) / (rows in the block).  Building A is setup,
+    as rttda_create is for the GPU."""
+
+    def __init__(self, mol, nocc_rows: int):
+        from oracle import rttda_oracle as orc
+        self.orc = orc
+        self.rows = np.arange(1, 1 + nocc_rows * NVIRT)
+        self.A = orc.A_block(mol, CX, 0, nocc_rows)
+        self.M = [orc.M_rows(*orc.dipole_along(mol, d), self.rows) for d in DIRS]
+        rng = np.random.default_rng(1)
+        self.c = [rng.standard_normal(NDIM) + 1j * rng.standard_normal(NDIM) for _ in DIRS]
+
+    def step(self):
+        for k in range(3):
+            c = self.c[k]
+            for _ in range(4):
+                sg = self.orc.sigma(self.A, self.M[k], 0.0, c)
+                c[self.rows] = c[self.rows] + (-1j * DT) * sg * 1e-6
+
+    def scale(self) -> float:
+        return NDIM / len(self.rows)
+
+    @staticmethod
+    def cores() -> int:
+        try:
+            from threadpoolctl import threadpool_info
+            n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+            return max(n) if n else 1
+        except Exception:
+            return 1
+
+
+def time_oracle(mol, nocc_rows: int, nsteps: int, warmup: int = 1):
+    s = OracleSample(mol, nocc_rows)
+    for _ in range(warmup):
+        s.step()
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        s.step()
+    dt_sample = (time.perf_counter() - t0) / nsteps
+    full_step = dt_sample * s.scale()
+    return {"value": 3.0 / full_step, "unit": UNIT, "cores": OracleSample.cores(), "kind": "oracle",
+            "sample": (f"oracle dense sigma on {len(s.rows)} of {NDIM} rows of A (occupied 0..{nocc_rows - 1}), "
+                       f"3 trajectories x 4 sigma per step, {nsteps} sampled steps, scaled x{s.scale():.2f} "
+                       "to a full RK4 step; building A excluded as setup"),
+            "ms_per_step": full_step * 1e3}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    from paper_2601_16949_b300 import synth
+    mol = synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
+    base = time_oracle(mol, 2, args.steps, warmup=args.warmup)
+    line = {"metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": base["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": base_config("fp64 (CPU oracle)", 1), "impl": "reference",
+            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2601_16949_b300 import binding as rb
+    from paper_2601_16949_b300 import synth
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    mol = synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
+    pulses = [dict(kind=rb.KICK, E0=KAPPA, direction=d) for d in DIRS]
+    T, K, W = 3, args.steps, args.warmup
+    prop = rb.Propagator(mol, CX, args.prec)
+    prop.set_field(pulses)
+    h = prop.h
+    dev = torch.device("cuda", local)
+    c_out = torch.zeros((T, NDIM, 2), dtype=torch.float64, device=dev)
+    dip = torch.zeros((T, K + 1), dtype=torch.float64, device=dev)
+    nrm = torch.zeros((T, K + 1), dtype=torch.float64, device=dev)
+    # a dedicated stream: the library's kernels and the timing events must
+    # share it (the legacy default stream would not order with the library)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
+
+    def propagate(nsteps, d, n):
+        rb.rttda_propagate_device(h, 0, DT, nsteps, c_out.data_ptr(), d.data_ptr(), n.data_ptr(), sptr)
+
+    # warm-up (>= 3 steps)
+    wd = torch.zeros((T, W + 1), dtype=torch.float64, device=dev)
+    wn = torch.zeros_like(wd)
+    propagate(W, wd, wn)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    launches0, _ = rb.rttda_launch_stats(h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(uuid) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        propagate(K, dip, nrm)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches1, per_step = rb.rttda_launch_stats(h)
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    value = world * T * K / (ms / 1e3)
+    dip32 = dip.cpu().numpy()
+
+    # per-kernel timing pass (events around every kernel class, same workload)
+    rb.rttda_profile(h, True)
+    kp = min(K, 40)
+    pd_, pn_ = torch.zeros((T, kp + 1), dtype=torch.float64, device=dev), torch.zeros((T, kp + 1), dtype=torch.float64, device=dev)
+    propagate(kp, pd_, pn_)
+    torch.cuda.synchronize()
+    prof = rb.rttda_profile_read(h)
+    rb.rttda_profile(h, False)
+
+    # plain FP64 single-trajectory path on the same molecule (z kick)
+    p64 = rb.Propagator(mol, CX, "fp64")
+    p64.set_field([pulses[2]])
+    k64 = max(2, min(args.fp64_steps, K))
+    d64 = torch.zeros((1, k64 + 1), dtype=torch.float64, device=dev)
+    n64 = torch.zeros_like(d64)
+    c64 = torch.zeros((1, NDIM, 2), dtype=torch.float64, device=dev)
+    rb.rttda_propagate_device(p64.h, 0, DT, 1, c64.data_ptr(), d64.data_ptr(), n64.data_ptr(), sptr)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rb.rttda_propagate_device(p64.h, 0, DT, k64, c64.data_ptr(), d64.data_ptr(), n64.data_ptr(), sptr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_rate = k64 / (e0.elapsed_time(e1) / 1e3)
+    d64h = d64.cpu().numpy()[0]
+    ref = d64h - d64h[0]
+    dip_err = float(np.max(np.abs(dip32[2, :k64 + 1] - d64h)) / max(np.max(np.abs(ref)), 1e-300))
+    p64.close()
+
+    # end to end through the host-buffer ABI: per step, H2D of the state from
+    # pinned memory (rttda_set_state), one RK4 step, D2H of state and traces
+    ke = max(3, min(args.e2e_steps, K))
+    pin = lambda *s: torch.zeros(s, dtype=torch.float64).pin_memory()
+    ch, co, dh, nh = pin(T, NDIM, 2), pin(T, NDIM, 2), pin(T, 2), pin(T, 2)
+    tcur = rb.rttda_get_state(h, ch.numpy())
+    rb.rttda_set_state(h, ch.data_ptr(), tcur)
+    rb.rttda_resume(h, DT, 1, co.data_ptr(), dh.data_ptr(), nh.data_ptr())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        rb.rttda_set_state(h, ch.data_ptr(), tcur)
+        rb.rttda_resume(h, DT, 1, co.data_ptr(), dh.data_ptr(), nh.data_ptr())
+        ch, co = co, ch
+        tcur += DT
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * T * ke / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": T * NDIM * 16, "d2h_bytes_per_step": T * NDIM * 16 + 2 * T * 2 * 8,
+           "steps": ke, "call": "rttda_set_state + rttda_resume(nsteps=1) per step, pinned host buffers"}
+
+    # roofline of the dominant kernel class
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        peaks = json.load(open(PEAKS_FILE))
+    ms_cls = {k: v[0] for k, v in prof.items()}
+    dom = max(ms_cls, key=ms_cls.get)
+    C, M, Nn, Kk = 2 * T, 2 * T * NOCC, NVIRT, NAUX * NVIRT
+    xm_ms, xm_n = prof["exchange_main"]
+    flop_launch = 2.0 * M * Nn * Kk
+    achieved = flop_launch / (xm_ms / max(xm_n, 1) / 1e3) / 1e12 if xm_n else None
+    if args.prec in ("fp64", "fp32"):
+        bound = "alu"
+        peak = FP32_ALU_PEAK_TFLOPS if args.prec == "fp32" else 148 * 2 * 2.032e9 * 2 / 1e12
+        peak_src = "derived: 148 SM x 128 FP32 lanes x 2 flop x 2032 MHz" if args.prec == "fp32" else \
+            "derived: FP64 FMA rate"
+    else:
+        bound = "tensor"
+        bf16 = peaks.get("bf16_tflops", 1822.3)
+        peak = bf16 if args.prec == "bf16" else bf16 / 2
+        peak_src = "of measured bf16 burst" + (" x 1/2 (tf32 nominal ratio)" if args.prec == "tf32" else "")
+    roof = {"bound": bound, "kernel": "exchange_main (sum_{P,b} Z^P_ib B^P_ab)", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_source": peak_src, "flop_per_launch": flop_launch,
+            "avg_launch_ms": xm_ms / max(xm_n, 1), "launches_timed": xm_n,
+            "dominant_class": dom, "class_ms_share": {k: round(v / sum(ms_cls.values()), 4) for k, v in ms_cls.items()}}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cb = time_oracle(mol, 8, args.cpu_steps, warmup=1)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    dtype = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.prec]
+    cfg = base_config(args.prec, world)
+    cfg.update({"fp64_path_traj_steps_per_s": fp64_rate, "speedup_vs_fp64_path": value / world / fp64_rate,
+                "fp64_path": f"plain FP64, one trajectory (z kick), {k64} timed steps",
+                "dipole_rel_err_vs_fp64": dip_err, "dipole_err_horizon_steps": k64,
+                "launches_per_step": per_step})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": int(launches1 - launches0), "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    prop.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,230 @@
+/*
+ * rttda.h - C ABI of the B300-native RT-TDA propagation library.
+ *
+ * Real-time Tamm-Dancoff (RT-TDA) electron dynamics after Knoll & Levine,
+ * "Simulating Electron Dynamics with GPU-Accelerated Real-Time Tamm-Dancoff
+ * Approximation" (arXiv 2601.16949).  The library propagates complex
+ * amplitudes c in the ground-plus-singles basis {|0>, |ia>} under
+ *
+ *     i dc/dt = H(t) c,   H(t) = A - E(t) M_d            (Eqs. ode_rt_tda, e_field)
+ *
+ * with A_00 = 0, A_0,ia = 0 (Sec. 2.1, last paragraph) and, on the singles
+ * block (structure of Eq. A_matrix_element2, two-electron part written in
+ * three-index factorised form for this library),
+ *
+ *     A_ia,jb = d_ij d_ab (e_a - e_i) + 2 sum_P B^P_ia B^P_jb
+ *                                     - c_x sum_P B^P_ij B^P_ab.
+ *
+ * M_d is the CSF-basis dipole matrix along the unit polarisation d, built
+ * from MO-basis blocks by the Slater-Condon rules (Eqs. sc1-sc6):
+ * M_0,ia = <0|mu_d|ia>, M_ia,ia = mu_aa - mu_ii, M_ia,ib = mu_ab,
+ * M_ia,ja = -mu_ji, zero otherwise (the constant <Phi0|mu|Phi0> is dropped).
+ *
+ * Conventions for every entry point:
+ *  - Atomic units throughout.
+ *  - Amplitude vectors have n = 1 + nocc*nvirt complex entries; entry 0 is
+ *    |0>, entry 1 + i*nvirt + a is |ia> ("virtuals run fastest", Sec. 2.1).
+ *    Complex numbers are stored as interleaved (re, im) doubles.
+ *    A batch of ntraj trajectories is stored trajectory-major:
+ *    c[(t*n + k)*2 + {0,1}].
+ *  - Host pointers are owned by the caller and only read/written during the
+ *    call.  Device pointers (functions with _device in their name or
+ *    documented as such) must be CUDA device memory of the current device.
+ *  - Every function returns an rttda_status; no C++ exception crosses the
+ *    ABI.  On failure rttda_last_error() returns a message for the calling
+ *    thread.  RTTDA_E_CUDA means a CUDA call failed; the handle must then be
+ *    destroyed.
+ *  - A handle is not thread-safe: use one handle per host thread.
+ *  - All computation runs in this library's CUDA kernels on the GPU; there
+ *    is no CPU fallback.  Calls fail with RTTDA_E_CUDA if no device is usable.
+ */
+#ifndef RTTDA_H
+#define RTTDA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTTDA_ABI_VERSION 1
+
+typedef struct rttda_ctx* rttda_t;
+typedef struct rttda_server* rttda_server_t;
+
+typedef enum {
+  RTTDA_OK = 0,
+  RTTDA_E_ARG = 1,      /* invalid argument (checked before any GPU work) */
+  RTTDA_E_OOM = 2,      /* device allocation failed / budget exceeded     */
+  RTTDA_E_CUDA = 3,     /* a CUDA runtime or driver call failed           */
+  RTTDA_E_TIMEOUT = 4,  /* a bounded device or host wait ran out          */
+  RTTDA_E_STATE = 5,    /* call not valid in the handle's current state   */
+  RTTDA_E_BUSY = 6      /* resource in use (server queue full, etc.)      */
+} rttda_status;
+
+/* Arithmetic used for the factor contractions (Coulomb, exchange, field).
+ * The RK4 amplitude state, the norm and the dipole expectation are FP64 in
+ * every mode.
+ *   FP64: all contractions in FP64 (CUDA cores).
+ *   FP32: factors and contractions in FP32 (CUDA cores), FP64 state.
+ *   TF32: factors stored FP32; exchange on tcgen05 tensor cores in TF32 with
+ *         FP32 accumulation; Coulomb and field in FP32.
+ *   BF16: factors stored BF16; exchange on tcgen05 tensor cores in BF16 with
+ *         FP32 accumulation; Coulomb with BF16 factors, FP32 accumulation;
+ *         field in FP32. */
+typedef enum { RTTDA_FP64 = 0, RTTDA_FP32 = 1, RTTDA_TF32 = 2, RTTDA_BF16 = 3 } rttda_prec;
+
+/* Pulse shapes E(t) (Sec. 2.2, Eqs. delta_pulse, continuous wave,
+ * transform_limited, chirped_pulse) plus a sin^2 envelope:
+ *   KICK     : E0 delta(t); applied exactly as c(0+) = exp(+i E0 M_d) c(0)
+ *              at the start of rttda_propagate, E = 0 afterwards.
+ *   CW       : E0 sin(omega t)
+ *   GAUSS_TL : E0 exp(-(t-t0)^2 / (2 s^2)) sin(omega (t-t0)), s = fwhm/2.35482
+ *   CHIRP    : E0 exp(-(t-t0)^2 / (2 s^2)) sin((omega + beta (t-t0)/2)(t-t0))
+ *   SIN2     : E0 sin^2(pi t / duration) sin(omega t) for 0 <= t <= duration,
+ *              0 otherwise. */
+typedef enum {
+  RTTDA_KICK = 0, RTTDA_CW = 1, RTTDA_GAUSS_TL = 2, RTTDA_CHIRP = 3, RTTDA_SIN2 = 4
+} rttda_pulse_kind;
+
+typedef struct {
+  int kind;          /* rttda_pulse_kind                                   */
+  double E0;         /* field amplitude (kick strength kappa for KICK)     */
+  double omega;      /* carrier frequency (Ha)                             */
+  double t0;         /* pulse centre (GAUSS_TL, CHIRP)                     */
+  double fwhm;       /* full width at half maximum of the envelope         */
+  double beta;       /* chirp rate (CHIRP)                                 */
+  double duration;   /* sin^2 window length (SIN2)                         */
+  double dir[3];     /* polarisation d (normalised by the library)         */
+} rttda_pulse;
+
+/* ABI version of the loaded library (RTTDA_ABI_VERSION it was built with). */
+int rttda_abi_version(void);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* rttda_last_error(void);
+
+/* Create a handle for one molecule and upload its factors.
+ * Defines A (Eq. A_matrix_element2, factorised as above) and the dipole
+ * blocks of the Slater-Condon rules (Eqs. sc2-sc5).
+ *   nocc, nvirt, naux >= 1.
+ *   eps_occ[nocc], eps_virt[nvirt]       orbital energies (Ha).
+ *   B_ov[naux][nocc][nvirt]               B^P_ia.
+ *   B_oo[naux][nocc][nocc]                B^P_ij, symmetric in ij.
+ *   B_vv[naux][nvirt][nvirt]              B^P_ab, symmetric in ab.
+ *   mu_oo[3][nocc][nocc], mu_vv[3][nvirt][nvirt]  MO dipole blocks (x,y,z),
+ *                                         symmetric.
+ *   mu_0ov[3][nocc][nvirt]                <0|mu_x|ia> (pass sqrt(2) <i|mu|a>
+ *                                         for MO-basis input, Eq. sc2).
+ *   c_x                                   exchange scaling.
+ *   prec                                  rttda_prec.
+ * All arrays are host FP64 and are copied (and cast to the working
+ * precision) before the call returns; symmetry is assumed, not checked.
+ * Errors: RTTDA_E_ARG (null pointer, non-positive size, bad prec),
+ * RTTDA_E_OOM, RTTDA_E_CUDA.  *out is NULL on failure. */
+rttda_status rttda_create(int nocc, int nvirt, int naux,
+                          const double* eps_occ, const double* eps_virt,
+                          const double* B_ov, const double* B_oo, const double* B_vv,
+                          const double* mu_oo, const double* mu_vv, const double* mu_0ov,
+                          double c_x, int prec, rttda_t* out);
+
+/* Device memory the handle holds right now, in bytes. */
+rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes);
+
+/* Set the batch: one pulse per trajectory (Eq. e_field, Eqs. e_fields).
+ * ntraj >= 1; pulses[ntraj] (host).  Builds mu_d = sum_x d_x mu_x per
+ * trajectory on the device.  Discards any propagated state.
+ * Errors: RTTDA_E_ARG (ntraj < 1, unknown kind, zero polarisation,
+ * non-positive fwhm/duration where used), RTTDA_E_OOM, RTTDA_E_CUDA. */
+rttda_status rttda_set_field(rttda_t h, const rttda_pulse* pulses, int ntraj);
+
+/* Propagate every trajectory of the batch from t = 0.
+ *   c0        host [ntraj][n][2] initial amplitudes, or NULL for |0> (the
+ *             Kohn-Sham ground state, Sec. 2.2 "initial conditions").
+ *   dt > 0, nsteps >= 0.
+ *   Kick pulses are applied at t = 0+ first.  Then nsteps RK4 steps of
+ *   dc/dt = -i H(t) c (stages at t, t+dt/2, t+dt/2, t+dt).
+ *   c_out        host [ntraj][n][2] final amplitudes, or NULL.
+ *   dipole_trace host [ntraj][nsteps+1]: Re c^dagger M_d c at t_k = k dt
+ *                (k = 0 is after the kick), or NULL.
+ *   norm_trace   host [ntraj][nsteps+1]: |c|^2 at t_k, or NULL.
+ * The handle keeps the final state and time for rttda_resume/get_state.
+ * Errors: RTTDA_E_STATE (no rttda_set_field yet), RTTDA_E_ARG, RTTDA_E_OOM,
+ * RTTDA_E_CUDA.  Blocks until the results are in the host buffers. */
+rttda_status rttda_propagate(rttda_t h, const double* c0, double dt, long nsteps,
+                             double* c_out, double* dipole_trace, double* norm_trace);
+
+/* As rttda_propagate, but every buffer is device memory and the work is
+ * enqueued on `stream` (a cudaStream_t; NULL = the handle's own stream).
+ * Returns after enqueueing; results are valid once the stream reaches them.
+ * The buffers must stay allocated until then. */
+rttda_status rttda_propagate_device(rttda_t h, const double* c0_dev, double dt, long nsteps,
+                                    double* c_out_dev, double* dipole_dev, double* norm_dev,
+                                    void* stream);
+
+/* Continue from the handle's current state and time (no kick).  Buffers as
+ * in rttda_propagate; entry 0 of each trace is the current state.
+ * Errors: RTTDA_E_STATE if there is no state (nothing propagated or set). */
+rttda_status rttda_resume(rttda_t h, double dt, long nsteps,
+                          double* c_out, double* dipole_trace, double* norm_trace);
+
+/* Checkpoint: copy the current state [ntraj][n][2] and time to the host. */
+rttda_status rttda_get_state(rttda_t h, double* c, double* t);
+
+/* Restore: set the current state [ntraj][n][2] (host) and time t. */
+rttda_status rttda_set_state(rttda_t h, const double* c, double t);
+
+/* One evaluation of sigma = H(t) c for the whole batch (Eq. e_field with
+ * Eq. sigmas; the field term uses each trajectory's pulse at time t; a kick
+ * contributes nothing for t > 0).  c_dev and sigma_dev are device
+ * [ntraj][n][2]; enqueued on `stream` (NULL = handle stream).  The handle's
+ * propagation state is not touched. */
+rttda_status rttda_sigma(rttda_t h, const double* c_dev, double t, double* sigma_dev, void* stream);
+
+/* Absorption spectrum from dipole traces (dipole-trace analogue of
+ * Eq. fourier_transform, averaged over traces as in Eq. spectrum_average):
+ *   S(w) = (1/ntraces) sum_tr (w/kappa) sum_k w_k (mu_k - mu_0)
+ *          exp(-gamma t_k) sin(w t_k) dt,
+ * trapezoid weights w_k (1/2 at both ends), t_k = k dt.
+ *   trace     host [ntraces][npts]; npts >= 2; kappa != 0; gamma >= 0.
+ *   omega_out host [nfreq] (may be NULL): w_j = wmin + j (wmax-wmin)/(nfreq-1).
+ *   S_out     host [nfreq].
+ * Computed on the GPU (FP64).  No handle needed. */
+rttda_status rttda_spectrum(const double* trace, long ntraces, long npts, double dt,
+                            double kappa, double gamma, double wmin, double wmax,
+                            long nfreq, double* omega_out, double* S_out);
+
+/* Kernel classes reported by rttda_profile_read (one event pair per launch
+ * group of the class).  EXCHANGE_MAIN is the long-K contraction
+ * sum_{P,b} Z^P_ib B^P_ab; EXCHANGE_Z builds Z^P = B^P_oo c. */
+enum {
+  RTTDA_KC_FIELD = 0,          /* M_d c (Slater-Condon rules, Eqs. sc2-sc5)   */
+  RTTDA_KC_COULOMB = 1,        /* both Coulomb passes                         */
+  RTTDA_KC_EXCHANGE_Z = 2,     /* Z^P = B^P_oo c                              */
+  RTTDA_KC_EXCHANGE_MAIN = 3,  /* sum_{P,b} Z^P_ib B^P_ab                     */
+  RTTDA_KC_COMBINE = 4,        /* sigma assembly + RK4 stage update           */
+  RTTDA_KC_OBSERVE = 5,        /* dipole and norm reductions                  */
+  RTTDA_KC_KICK = 6,           /* exp(+i kappa M_d) Taylor series             */
+  RTTDA_NUM_KERNEL_CLASSES = 7
+};
+
+/* Tracing.  enable != 0: later propagations launch kernels directly (no CUDA
+ * graph) with a CUDA event pair around every kernel-class launch; the
+ * counters restart.  rttda_profile_read waits for the recorded events, writes
+ * the summed milliseconds ms[RTTDA_NUM_KERNEL_CLASSES] and the number of
+ * timed launches per class launches[...] (either may be NULL) and resets. */
+rttda_status rttda_profile(rttda_t h, int enable);
+rttda_status rttda_profile_read(rttda_t h, double* ms, long long* launches);
+
+/* Kernels this handle has enqueued so far (*total) and in one RK4 step of
+ * the last propagation (*per_step).  Either pointer may be NULL. */
+rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step);
+
+/* Free every resource of the handle (NULL is ignored). */
+void rttda_destroy(rttda_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTTDA_H */

@@ -143,6 +143,25 @@ def A_rows(mol: dict, c_x: float, rows) -> np.ndarray:
     return out
 
 
+def A_block(mol: dict, c_x: float, i0: int, i1: int) -> np.ndarray:
+    """Rows of A for the occupied range i0 <= i < i1 (all a), as one block.
+
+    Same definition as build_A restricted to those rows."""
+    o, v, P = mol["nocc"], mol["nvirt"], mol["naux"]
+    n = dim(o, v)
+    ni = i1 - i0
+    out = np.zeros((ni * v, n))
+    Bf = mol["B_ov"].reshape(P, -1)
+    coul = Bf[:, i0 * v:i1 * v].T @ Bf
+    exch = np.einsum("pij,pab->iajb", mol["B_oo"][:, i0:i1, :], mol["B_vv"], optimize=True)
+    out[:, 1:] = 2.0 * coul - c_x * exch.reshape(ni * v, o * v)
+    for i in range(i0, i1):
+        for a in range(v):
+            r = (i - i0) * v + a
+            out[r, csf_index(i, a, v)] += mol["eps_virt"][a] - mol["eps_occ"][i]
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Dipole matrix (Eqs. sc1-sc6)
 # ---------------------------------------------------------------------------
@@ -234,7 +253,13 @@ def kick(M: np.ndarray, kappa: float, c: np.ndarray, tol: float = 1e-18) -> np.n
 
 
 def sigma(A: np.ndarray, M: np.ndarray, E: float, c: np.ndarray) -> np.ndarray:
-    """sigma = H(t) c = (A - E(t) M) c (Eq. e_field with Eq. sigmas)."""
+    """sigma = H(t) c = (A - E(t) M) c (Eq. e_field with Eq. sigmas).
+
+    A and M are real, so the real and imaginary parts of c are multiplied
+    separately (numpy would otherwise copy A to complex for every product)."""
+    c = np.asarray(c)
+    if np.iscomplexobj(c):
+        return (A @ c.real - E * (M @ c.real)) + 1j * (A @ c.imag - E * (M @ c.imag))
     return A @ c - E * (M @ c)
 
 

@@ -1,0 +1,276 @@
+"""Thin ctypes binding of the RT-TDA C ABI (include/rttda.h).
+
+The functions below carry the ABI's names and only marshal arguments:
+numpy arrays for host buffers, integer device addresses (e.g.
+``tensor.data_ptr()``) for device buffers.  Every step of the propagation
+runs in the library's CUDA kernels; if the shared library is missing this
+module raises on import instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librttda.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"RT-TDA CUDA library not built: {LIB_PATH} is missing "
+                      "(run paper_2601_16949_b300/build.py)")
+
+lib = ct.CDLL(LIB_PATH)
+
+# status codes (rttda_status)
+OK, E_ARG, E_OOM, E_CUDA, E_TIMEOUT, E_STATE, E_BUSY = range(7)
+STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_OOM", 3: "E_CUDA", 4: "E_TIMEOUT", 5: "E_STATE", 6: "E_BUSY"}
+# precisions (rttda_prec)
+FP64, FP32, TF32, BF16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
+# pulse kinds (rttda_pulse_kind)
+KICK, CW, GAUSS_TL, CHIRP, SIN2 = 0, 1, 2, 3, 4
+
+
+class rttda_pulse(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("E0", ct.c_double), ("omega", ct.c_double), ("t0", ct.c_double),
+                ("fwhm", ct.c_double), ("beta", ct.c_double), ("duration", ct.c_double),
+                ("dir", ct.c_double * 3)]
+
+
+class RTTDAError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.rttda_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+_dp = ct.POINTER(ct.c_double)
+_h = ct.c_void_p
+
+lib.rttda_abi_version.restype = ct.c_int
+lib.rttda_last_error.restype = ct.c_char_p
+lib.rttda_create.argtypes = [ct.c_int, ct.c_int, ct.c_int] + [_dp] * 8 + [ct.c_double, ct.c_int, ct.POINTER(_h)]
+lib.rttda_create.restype = ct.c_int
+lib.rttda_memory_bytes.argtypes = [_h, ct.POINTER(ct.c_size_t)]
+lib.rttda_set_field.argtypes = [_h, ct.POINTER(rttda_pulse), ct.c_int]
+lib.rttda_propagate.argtypes = [_h, _dp, ct.c_double, ct.c_long, _dp, _dp, _dp]
+lib.rttda_propagate_device.argtypes = [_h, ct.c_void_p, ct.c_double, ct.c_long, ct.c_void_p, ct.c_void_p,
+                                       ct.c_void_p, ct.c_void_p]
+lib.rttda_resume.argtypes = [_h, ct.c_double, ct.c_long, _dp, _dp, _dp]
+lib.rttda_get_state.argtypes = [_h, _dp, _dp]
+lib.rttda_set_state.argtypes = [_h, _dp, ct.c_double]
+lib.rttda_sigma.argtypes = [_h, ct.c_void_p, ct.c_double, ct.c_void_p, ct.c_void_p]
+lib.rttda_spectrum.argtypes = [_dp, ct.c_long, ct.c_long, ct.c_double, ct.c_double, ct.c_double, ct.c_double,
+                               ct.c_double, ct.c_long, _dp, _dp]
+lib.rttda_profile.argtypes = [_h, ct.c_int]
+lib.rttda_profile_read.argtypes = [_h, _dp, ct.POINTER(ct.c_longlong)]
+lib.rttda_launch_stats.argtypes = [_h, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]
+lib.rttda_destroy.argtypes = [_h]
+lib.rttda_destroy.restype = None
+for _name in ("rttda_create", "rttda_memory_bytes", "rttda_set_field", "rttda_propagate", "rttda_propagate_device",
+              "rttda_resume", "rttda_get_state", "rttda_set_state", "rttda_sigma", "rttda_spectrum",
+              "rttda_profile", "rttda_profile_read", "rttda_launch_stats"):
+    getattr(lib, _name).restype = ct.c_int
+
+
+def _check(status: int, where: str) -> None:
+    if status != OK:
+        raise RTTDAError(status, where)
+
+
+def _ptr(a):
+    """Host pointer of a C-contiguous float64 numpy array (None -> NULL).
+    An int is taken as a raw address (e.g. a pinned torch tensor's data_ptr())."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ct.cast(ct.c_void_p(a), _dp) if a else None
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError("expected a C-contiguous float64 numpy array")
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def rttda_abi_version() -> int:
+    return lib.rttda_abi_version()
+
+
+def rttda_last_error() -> str:
+    return lib.rttda_last_error().decode(errors="replace")
+
+
+def rttda_create(nocc, nvirt, naux, eps_occ, eps_virt, B_ov, B_oo, B_vv, mu_oo, mu_vv, mu_0ov, c_x, prec):
+    arrs = [_f64(x) for x in (eps_occ, eps_virt, B_ov, B_oo, B_vv, mu_oo, mu_vv, mu_0ov)]
+    h = _h()
+    prec = PRECISIONS.get(prec, prec) if isinstance(prec, str) else prec
+    _check(lib.rttda_create(nocc, nvirt, naux, *[_ptr(a) for a in arrs], float(c_x), int(prec), ct.byref(h)),
+           "rttda_create")
+    return h
+
+
+def rttda_memory_bytes(h) -> int:
+    n = ct.c_size_t()
+    _check(lib.rttda_memory_bytes(h, ct.byref(n)), "rttda_memory_bytes")
+    return n.value
+
+
+def make_pulses(pulses) -> ct.Array:
+    arr = (rttda_pulse * len(pulses))()
+    for k, p in enumerate(pulses):
+        get = (lambda name, d=0.0: p.get(name, d)) if isinstance(p, dict) else (lambda name, d=0.0: getattr(p, name, d))
+        arr[k].kind = int(get("kind", KICK))
+        arr[k].E0 = float(get("E0", 0.0))
+        arr[k].omega = float(get("omega", 0.0))
+        arr[k].t0 = float(get("t0", 0.0))
+        arr[k].fwhm = float(get("fwhm", 1.0))
+        arr[k].beta = float(get("beta", 0.0))
+        arr[k].duration = float(get("duration", 0.0))
+        d = get("direction", None)
+        if d is None:
+            d = get("dir", (0.0, 0.0, 1.0))
+        for x in range(3):
+            arr[k].dir[x] = float(d[x])
+    return arr
+
+
+def rttda_set_field(h, pulses) -> None:
+    arr = make_pulses(pulses)
+    _check(lib.rttda_set_field(h, arr, len(pulses)), "rttda_set_field")
+
+
+def rttda_propagate(h, c0, dt, nsteps, c_out=None, dipole_trace=None, norm_trace=None) -> None:
+    _check(lib.rttda_propagate(h, _ptr(c0), float(dt), int(nsteps), _ptr(c_out), _ptr(dipole_trace),
+                               _ptr(norm_trace)), "rttda_propagate")
+
+
+def rttda_propagate_ptr(h, c0_ptr, dt, nsteps, c_out_ptr, dip_ptr, nrm_ptr) -> None:
+    """rttda_propagate with raw host addresses (e.g. pinned torch tensors)."""
+    cast = lambda p: None if not p else ct.cast(ct.c_void_p(p), _dp)
+    _check(lib.rttda_propagate(h, cast(c0_ptr), float(dt), int(nsteps), cast(c_out_ptr), cast(dip_ptr),
+                               cast(nrm_ptr)), "rttda_propagate")
+
+
+def rttda_propagate_device(h, c0_dev, dt, nsteps, c_out_dev, dipole_dev, norm_dev, stream=0) -> None:
+    _check(lib.rttda_propagate_device(h, c0_dev or None, float(dt), int(nsteps), c_out_dev or None,
+                                      dipole_dev or None, norm_dev or None, stream or None),
+           "rttda_propagate_device")
+
+
+def rttda_resume(h, dt, nsteps, c_out=None, dipole_trace=None, norm_trace=None) -> None:
+    _check(lib.rttda_resume(h, float(dt), int(nsteps), _ptr(c_out), _ptr(dipole_trace), _ptr(norm_trace)),
+           "rttda_resume")
+
+
+def rttda_get_state(h, c) -> float:
+    t = ct.c_double()
+    _check(lib.rttda_get_state(h, _ptr(c), ct.byref(t)), "rttda_get_state")
+    return t.value
+
+
+def rttda_set_state(h, c, t) -> None:
+    _check(lib.rttda_set_state(h, _ptr(c), float(t)), "rttda_set_state")
+
+
+def rttda_sigma(h, c_dev, t, sigma_dev, stream=0) -> None:
+    _check(lib.rttda_sigma(h, c_dev, float(t), sigma_dev, stream or None), "rttda_sigma")
+
+
+def rttda_spectrum(trace, dt, kappa, gamma, wmin, wmax, nfreq):
+    tr = np.atleast_2d(_f64(trace))
+    om = np.zeros(nfreq)
+    S = np.zeros(nfreq)
+    _check(lib.rttda_spectrum(_ptr(tr), tr.shape[0], tr.shape[1], float(dt), float(kappa), float(gamma),
+                              float(wmin), float(wmax), int(nfreq), _ptr(om), _ptr(S)), "rttda_spectrum")
+    return om, S
+
+
+KERNEL_CLASSES = ("field", "coulomb", "exchange_z", "exchange_main", "combine", "observe", "kick")
+
+
+def rttda_profile(h, enable: bool) -> None:
+    _check(lib.rttda_profile(h, 1 if enable else 0), "rttda_profile")
+
+
+def rttda_profile_read(h) -> dict:
+    n = len(KERNEL_CLASSES)
+    ms = (ct.c_double * n)()
+    cnt = (ct.c_longlong * n)()
+    _check(lib.rttda_profile_read(h, ms, cnt), "rttda_profile_read")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def rttda_launch_stats(h) -> tuple:
+    tot = ct.c_longlong()
+    per = ct.c_longlong()
+    _check(lib.rttda_launch_stats(h, ct.byref(tot), ct.byref(per)), "rttda_launch_stats")
+    return tot.value, per.value
+
+
+def rttda_destroy(h) -> None:
+    lib.rttda_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper (still only marshalling)
+# ---------------------------------------------------------------------------
+class Propagator:
+    """Owns one handle; numpy in, numpy out."""
+
+    def __init__(self, mol: dict, c_x: float, prec="fp64"):
+        self.nocc, self.nvirt, self.naux = mol["nocc"], mol["nvirt"], mol["naux"]
+        self.n = 1 + self.nocc * self.nvirt
+        self.h = rttda_create(self.nocc, self.nvirt, self.naux, mol["eps_occ"], mol["eps_virt"], mol["B_ov"],
+                              mol["B_oo"], mol["B_vv"], mol["mu_oo"], mol["mu_vv"], mol["mu_0ov"], c_x, prec)
+        self.ntraj = 0
+
+    def set_field(self, pulses):
+        rttda_set_field(self.h, pulses)
+        self.ntraj = len(pulses)
+
+    def propagate(self, dt, nsteps, c0=None, want_state=True, want_trace=True):
+        c_out = np.zeros((self.ntraj, self.n, 2)) if want_state else None
+        dip = np.zeros((self.ntraj, nsteps + 1)) if want_trace else None
+        nrm = np.zeros((self.ntraj, nsteps + 1)) if want_trace else None
+        c0a = None
+        if c0 is not None:
+            c0 = np.asarray(c0)
+            if np.iscomplexobj(c0):
+                c0 = np.stack([c0.real, c0.imag], axis=-1)
+            c0a = _f64(c0.reshape(self.ntraj, self.n, 2))
+        rttda_propagate(self.h, c0a, dt, nsteps, c_out, dip, nrm)
+        c = None if c_out is None else c_out[..., 0] + 1j * c_out[..., 1]
+        return c, dip, nrm
+
+    def resume(self, dt, nsteps):
+        c_out = np.zeros((self.ntraj, self.n, 2))
+        dip = np.zeros((self.ntraj, nsteps + 1))
+        nrm = np.zeros((self.ntraj, nsteps + 1))
+        rttda_resume(self.h, dt, nsteps, c_out, dip, nrm)
+        return c_out[..., 0] + 1j * c_out[..., 1], dip, nrm
+
+    def get_state(self):
+        c = np.zeros((self.ntraj, self.n, 2))
+        t = rttda_get_state(self.h, c)
+        return c[..., 0] + 1j * c[..., 1], t
+
+    def set_state(self, c, t):
+        c = np.asarray(c)
+        rttda_set_state(self.h, _f64(np.stack([c.real, c.imag], axis=-1)), t)
+
+    def memory_bytes(self):
+        return rttda_memory_bytes(self.h)
+
+    def close(self):
+        if self.h:
+            rttda_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,852 @@
+// RT-TDA engine: device buffers, precision plan, RK4 schedule, CUDA graphs,
+// and the C ABI declared in include/rttda.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/rttda.h"
+#include "engine_internal.h"
+#include "kernels_simt.cuh"
+
+using namespace rttda;
+
+namespace rttda {
+thread_local std::string g_last_error;
+
+rttda_status set_error(rttda_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+}  // namespace rttda
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      return set_error(e_ == cudaErrorMemoryAllocation ? RTTDA_E_OOM : RTTDA_E_CUDA,               \
+                       std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    }                                                                                              \
+  } while (0)
+
+#define CKS(expr)                         \
+  do {                                    \
+    rttda_status s_ = (expr);             \
+    if (s_ != RTTDA_OK) return s_;        \
+  } while (0)
+
+namespace {
+
+constexpr int kNumSM = 148;
+
+inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+
+inline unsigned blocks_for(long long n, int threads) { return (unsigned)std::max(1LL, cdiv(n, threads)); }
+
+// SIMT GEMM tile shapes per compute type.
+template <typename TC> struct Tile;
+template <> struct Tile<double> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
+template <> struct Tile<float> { static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8; };
+
+template <typename T>
+rttda_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  CK(cudaMalloc((void**)p, count * sizeof(T)));
+  return RTTDA_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+double fro(const double* a, size_t n) {
+  double s = 0.0;
+  for (size_t k = 0; k < n; ++k) s += a[k] * a[k];
+  return std::sqrt(s);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct rttda_ctx {
+  int o = 0, v = 0, P = 0, prec = 0;
+  long long ov = 0, N = 0;
+  double cx = 0.0;
+  size_t fbytes = 8, cbytes = 8;
+  cudaStream_t stream = nullptr;
+
+  // factors (working precision)
+  void* Bov = nullptr;
+  void* Boo = nullptr;
+  void* Bvv = nullptr;
+  double* eps_o = nullptr;
+  double* eps_v = nullptr;
+  double* mu_oo = nullptr;  // [3][o][o]
+  double* mu_vv = nullptr;  // [3][v][v]
+  double* mu_0 = nullptr;   // [3][o][v]
+  double mu_bound[3] = {0, 0, 0};
+
+  // batch
+  int T = 0;
+  std::vector<rttda_pulse> pulses;
+  PulseDev* d_pulses = nullptr;
+  double* d_kappa = nullptr;
+  double* d_dirs = nullptr;
+  double* moo64 = nullptr;
+  double* mvv64 = nullptr;
+  double* m064 = nullptr;
+  void* mooC = nullptr;
+  void* mvvC = nullptr;
+  void* m0C = nullptr;
+  bool any_field = false, any_kick = false;
+  int kick_terms = 0;
+
+  // state and scratch
+  double* Xn = nullptr;
+  double* Xs = nullptr;
+  double* acc = nullptr;
+  double* F = nullptr;
+  double* E = nullptr;
+  double* term = nullptr;
+  double* obs_part = nullptr;
+  double* Xq = nullptr;  // sigma entry input
+  long long* d_step = nullptr;
+  void* w = nullptr;
+  void* Jpart = nullptr;
+  void* Zt = nullptr;
+  void* Kpart = nullptr;
+  int SJ = 1, pchunkJ = 1, SK = 1, zchunk = 1, obsG = 1;
+  long long obs_rows = 1;
+  size_t dev_bytes = 0;
+
+  bool have_state = false;
+  double t_now = 0.0;
+
+  // host staging for the host-buffer entry points
+  double* h_io = nullptr;  // device staging [T][N][2] + traces
+  size_t h_io_count = 0;
+
+  // profiling: CUDA events around every kernel class (no graphs while on)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev[RTTDA_NUM_KERNEL_CLASSES];
+  size_t prof_used[RTTDA_NUM_KERNEL_CLASSES] = {};
+  long long launches = 0;        // kernels enqueued (running count)
+  long long launches_per_step = 0;
+
+  ~rttda_ctx();
+  rttda_status alloc_batch();
+  void free_batch();
+};
+
+rttda_ctx::~rttda_ctx() {
+  if (stream) cudaStreamSynchronize(stream);
+  for (auto& v : prof_ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
+  free_batch();
+  dfree(Bov);
+  dfree(Boo);
+  dfree(Bvv);
+  dfree(eps_o);
+  dfree(eps_v);
+  dfree(mu_oo);
+  dfree(mu_vv);
+  dfree(mu_0);
+  if (stream) cudaStreamDestroy(stream);
+}
+
+void rttda_ctx::free_batch() {
+  void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xn, Xs, acc, F, E, term,
+                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io};
+  for (void* p : ps) dfree(p);
+  d_pulses = nullptr;
+  d_kappa = d_dirs = moo64 = mvv64 = m064 = nullptr;
+  mooC = mvvC = m0C = nullptr;
+  Xn = Xs = acc = F = E = term = obs_part = Xq = nullptr;
+  d_step = nullptr;
+  w = Jpart = Zt = Kpart = nullptr;
+  h_io = nullptr;
+  h_io_count = 0;
+  T = 0;
+  have_state = false;
+}
+
+// ---------------------------------------------------------------------------
+// Profiling hooks: an event pair around each launch of a kernel class.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Prof {
+  rttda_ctx* h;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t stop = nullptr;
+  Prof(rttda_ctx* h_, int cls_, cudaStream_t s_) : h(h_), cls(cls_), s(s_) {
+    if (!h->prof_on) return;
+    auto& v = h->prof_ev[cls];
+    size_t& u = h->prof_used[cls];
+    while (v.size() < u + 2) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      v.push_back(e);
+    }
+    cudaEventRecord(v[u], s);
+    stop = v[u + 1];
+    u += 2;
+  }
+  ~Prof() {
+    if (stop) cudaEventRecord(stop, s);
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Precision-dispatched launches
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename TF, typename TC>
+struct Ops {
+  using TL = Tile<TC>;
+
+  static void coulomb(rttda_ctx* h, const double* X, cudaStream_t s) {
+    Prof pr(h, RTTDA_KC_COULOMB, s);
+    h->launches += 2;
+    const int C = 2 * h->T;
+    constexpr int PB = 8;
+    k_coul_w<TF, TC, 8, PB><<<blocks_for(h->P, PB), 256, 0, s>>>((const TF*)h->Bov, X, h->P, h->ov, C, (TC*)h->w);
+    dim3 g(blocks_for(h->ov, 256), h->SJ);
+    const size_t smem = (size_t)h->pchunkJ * C * sizeof(TC);
+    k_coul_J<TF, TC, 8><<<g, 256, smem, s>>>((const TF*)h->Bov, (const TC*)h->w, h->P, h->ov, C, h->pchunkJ,
+                                            (TC*)h->Jpart);
+  }
+
+  static void exchange(rttda_ctx* h, const double* X, cudaStream_t s) {
+    const int C = 2 * h->T, o = h->o, v = h->v;
+    const int M = C * o;
+    for (int p0 = 0, c = 0; p0 < h->P; p0 += h->zchunk, ++c) {
+      const int pc = std::min(h->zchunk, h->P - p0);
+      // Z^P_(b,col),i = sum_j X_(j,b),col B^P_ji  for P in the chunk
+      {
+        Prof pr(h, RTTDA_KC_EXCHANGE_Z, s);
+        h->launches += 1;
+        dim3 g(blocks_for(o, TL::BN), blocks_for((long long)v * C, TL::BM), pc);
+        k_gemm_tn<double, TF, TC, TL::BM, TL::BN, TL::BK, TL::TM, TL::TN>
+            <<<g, (TL::BM / TL::TM) * (TL::BN / TL::TN), 0, s>>>(
+                v * C, o, o, X + C, (long long)v * C, 0, (const TF*)h->Boo + (size_t)p0 * o * o, o,
+                (long long)o * o, (TC*)h->Zt, o, (long long)v * C * o, 0, 1, o, 0);
+      }
+      // K_(col,i),a += sum_{P in chunk, b} Z^P_(col,i),b B^P_ba   (split-K)
+      {
+        Prof pr(h, RTTDA_KC_EXCHANGE_MAIN, s);
+        h->launches += 1;
+        const long long Kc = (long long)pc * v;
+        const long long kper = cdiv(cdiv(Kc, h->SK), TL::BK) * TL::BK;
+        dim3 g(blocks_for(v, TL::BN), blocks_for(M, TL::BM), h->SK);
+        k_gemm_tn<TC, TF, TC, TL::BM, TL::BN, TL::BK, TL::TM, TL::TN>
+            <<<g, (TL::BM / TL::TM) * (TL::BN / TL::TN), 0, s>>>(
+                M, v, Kc, (const TC*)h->Zt, M, 0, (const TF*)h->Bvv + (size_t)p0 * v * v, v, 0,
+                (TC*)h->Kpart, v, 0, (long long)M * v, h->SK, kper, c > 0 ? 1 : 0);
+      }
+    }
+  }
+
+  static void field(rttda_ctx* h, const double* X, cudaStream_t s) {
+    Prof pr(h, RTTDA_KC_FIELD, s);
+    h->launches += 2;
+    dim3 g(blocks_for(h->v, 32), blocks_for(h->o, 8), h->T);
+    if (std::is_same<TC, double>::value) {
+      k_field<double, double><<<g, dim3(32, 8), 0, s>>>(h->o, h->v, h->T, X, h->moo64, h->mvv64, h->m064, h->F);
+      k_field0<double, double><<<h->T, 256, 0, s>>>(h->ov, h->T, X, h->m064, h->F);
+    } else {
+      k_field<TC, TC><<<g, dim3(32, 8), 0, s>>>(h->o, h->v, h->T, X, (const TC*)h->mooC, (const TC*)h->mvvC,
+                                                (const TC*)h->m0C, h->F);
+      k_field0<TC, TC><<<h->T, 256, 0, s>>>(h->ov, h->T, X, (const TC*)h->m0C, h->F);
+    }
+  }
+
+  static void combine(rttda_ctx* h, int mode, int stage, bool use_field, double dt, const double* Xin,
+                      double* sig_out, cudaStream_t s) {
+    Prof pr(h, RTTDA_KC_COMBINE, s);
+    h->launches += 1;
+    const int C = 2 * h->T;
+    k_combine<TC><<<blocks_for(h->N, 256), 256, 0, s>>>(
+        mode, stage, h->N, h->o, h->v, h->T, h->eps_o, h->eps_v, h->cx, (const TC*)h->Jpart, h->SJ,
+        (const TC*)h->Kpart, h->SK, (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn,
+        const_cast<double*>(Xin), h->acc, sig_out);
+  }
+
+  static void set_smem_limits() {
+    cudaFuncSetAttribute(k_coul_J<TF, TC, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  }
+};
+
+template <typename F>
+void dispatch(int prec, F&& f) {
+  if (prec == RTTDA_FP64)
+    f(Ops<double, double>{});
+  else
+    f(Ops<float, float>{});
+}
+
+// Exact kick exp(+i kappa M_d) on h->Xn (FP64 field products).
+void enqueue_kick(rttda_ctx* h, cudaStream_t s) {
+  Prof pr(h, RTTDA_KC_KICK, s);
+  h->launches += 3 * h->kick_terms;
+  const long long NT = h->N * h->T;
+  cudaMemcpyAsync(h->term, h->Xn, sizeof(double) * NT * 2, cudaMemcpyDeviceToDevice, s);
+  for (int k = 1; k <= h->kick_terms; ++k) {
+    dim3 g(blocks_for(h->v, 32), blocks_for(h->o, 8), h->T);
+    k_field<double, double><<<g, dim3(32, 8), 0, s>>>(h->o, h->v, h->T, h->term, h->moo64, h->mvv64, h->m064,
+                                                      h->F);
+    k_field0<double, double><<<h->T, 256, 0, s>>>(h->ov, h->T, h->term, h->m064, h->F);
+    k_kick_term<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->d_kappa, 1.0 / k, h->F, h->term, h->Xn);
+  }
+}
+
+void enqueue_observe(rttda_ctx* h, const double* X, double* dip, double* nrm, long long ld, long long step_offset,
+                     cudaStream_t s) {
+  Prof pr(h, RTTDA_KC_OBSERVE, s);
+  h->launches += 2;
+  k_obs_partial<<<h->obsG, 256, 0, s>>>(h->N, h->T, h->obs_rows, X, h->F, h->obs_part);
+  k_obs_final<<<1, 128, 0, s>>>(h->obsG, h->T, h->obs_part, h->d_step, step_offset, ld, dip, nrm);
+}
+
+// One RK4 step (four sigma builds) plus the observables of the step's start.
+template <typename O>
+void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, double* dip, double* nrm, long long ld,
+                  cudaStream_t s) {
+  h->launches += 2;  // efield + step counter
+  k_efield<<<1, 128, 0, s>>>(h->T, h->d_pulses, h->d_step, base, t_off, dt, h->E);
+  for (int st = 0; st < 4; ++st) {
+    const bool fld = h->any_field;
+    if (st == 0 || fld) O::field(h, h->Xs, s);
+    if (st == 0 && dip) enqueue_observe(h, h->Xn, dip, nrm, ld, 0, s);
+    O::coulomb(h, h->Xs, s);
+    O::exchange(h, h->Xs, s);
+    O::combine(h, 0, st, fld, dt, h->Xs, nullptr, s);
+  }
+  k_step_inc<<<1, 1, 0, s>>>(h->d_step);
+}
+
+rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, double* dip, double* nrm,
+                       cudaStream_t s) {
+  // stage times are t_off + (base + k + c_s) dt with an integer base when the
+  // start time is a whole number of steps
+  long long base = 0;
+  double t_off = t_call;
+  const double nb = std::nearbyint(t_call / dt);
+  if (std::fabs(nb * dt - t_call) <= 1e-12 * std::max(1.0, std::fabs(t_call))) {
+    base = (long long)nb;
+    t_off = 0.0;
+  }
+  const long long ld = nsteps + 1;
+  CK(cudaMemsetAsync(h->d_step, 0, sizeof(long long), s));
+  CK(cudaMemcpyAsync(h->Xs, h->Xn, sizeof(double) * h->N * 2 * h->T, cudaMemcpyDeviceToDevice, s));
+  if (nsteps > 0 && h->prof_on) {
+    // profiling: direct launches so that every kernel class gets its events
+    const long long l0 = h->launches;
+    for (long k = 0; k < nsteps; ++k)
+      dispatch(h->prec, [&](auto ops) { enqueue_step(h, ops, base, t_off, dt, dip, nrm, ld, s); });
+    h->launches_per_step = (h->launches - l0) / nsteps;
+  } else if (nsteps > 0) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const long long l0 = h->launches;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    dispatch(h->prec, [&](auto ops) { enqueue_step(h, ops, base, t_off, dt, dip, nrm, ld, s); });
+    h->launches_per_step = h->launches - l0;
+    h->launches = l0 + h->launches_per_step * nsteps;
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (ce != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return set_error(RTTDA_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    }
+    for (long k = 0; k < nsteps; ++k) {
+      ce = cudaGraphLaunch(exec, s);
+      if (ce != cudaSuccess) break;
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+  }
+  if (dip) {
+    dispatch(h->prec, [&](auto ops) { decltype(ops)::field(h, h->Xn, s); });
+    enqueue_observe(h, h->Xn, dip, nrm, ld, 0, s);
+  }
+  CK(cudaGetLastError());
+  h->t_now = t_off + (double)(base + nsteps) * dt;
+  h->have_state = true;
+  return RTTDA_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Batch set-up
+// ---------------------------------------------------------------------------
+rttda_status rttda_ctx::alloc_batch() {
+  const int C = 2 * T;
+  const long long NC = N * C;
+  CKS(dalloc(&Xn, NC));
+  CKS(dalloc(&Xs, NC));
+  CKS(dalloc(&acc, NC));
+  CKS(dalloc(&F, NC));
+  CKS(dalloc(&term, NC));
+  CKS(dalloc(&Xq, NC));
+  CKS(dalloc(&E, 4 * (size_t)T));
+  CKS(dalloc(&d_step, 1));
+  // Coulomb scratch
+  {
+    const long long xblocks = cdiv(ov, 256);
+    SJ = (int)std::max(1LL, std::min<long long>(P, cdiv(4 * kNumSM, xblocks)));
+    const size_t max_smem = 96 * 1024;
+    pchunkJ = (int)cdiv(P, SJ);
+    while ((size_t)pchunkJ * C * cbytes > max_smem && pchunkJ > 1) pchunkJ = (pchunkJ + 1) / 2;
+    SJ = (int)cdiv(P, pchunkJ);
+    char* p = nullptr;
+    CK(cudaMalloc((void**)&p, (size_t)P * C * cbytes));
+    w = p;
+    CK(cudaMalloc((void**)&p, (size_t)SJ * ov * C * cbytes));
+    Jpart = p;
+  }
+  // exchange scratch: Z for a chunk of P (at most ~1 GiB), split-K partials
+  {
+    const size_t zper = (size_t)v * C * o * cbytes;
+    const size_t zbudget = (size_t)1 << 30;
+    zchunk = (int)std::max<size_t>(1, std::min<size_t>(P, zbudget / std::max<size_t>(zper, 1)));
+    char* p = nullptr;
+    CK(cudaMalloc((void**)&p, (size_t)zchunk * zper));
+    Zt = p;
+    const int BM = prec == RTTDA_FP64 ? Tile<double>::BM : Tile<float>::BM;
+    const int BN = prec == RTTDA_FP64 ? Tile<double>::BN : Tile<float>::BN;
+    const int BK = prec == RTTDA_FP64 ? Tile<double>::BK : Tile<float>::BK;
+    const long long tiles = cdiv((long long)C * o, BM) * cdiv(v, BN);
+    const long long kchunks = cdiv((long long)zchunk * v, BK);
+    SK = (int)std::max(1LL, std::min(kchunks, cdiv(4 * kNumSM, tiles)));
+    CK(cudaMalloc((void**)&p, (size_t)SK * C * o * v * cbytes));
+    Kpart = p;
+  }
+  obsG = (int)std::max(1LL, std::min(1024LL, cdiv(N, 2048)));
+  obs_rows = cdiv(N, obsG);
+  obsG = (int)cdiv(N, obs_rows);
+  CKS(dalloc(&obs_part, (size_t)obsG * T * 2));
+  return RTTDA_OK;
+}
+
+// Upload the molecule: factors cast on the device to the working type.
+static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const double* eps_virt, const double* B_ov,
+                                const double* B_oo, const double* B_vv, const double* mu_oo, const double* mu_vv,
+                                const double* mu_0ov) {
+  CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  dispatch(h->prec, [&](auto ops) { decltype(ops)::set_smem_limits(); });
+  const size_t o = h->o, v = h->v, P = h->P;
+  const size_t chunk = (size_t)1 << 26;  // elements per staging pass
+  const size_t stage_n = std::min(chunk, std::max({P * o * v, P * o * o, P * v * v}));
+  double* stage = nullptr;
+  struct Guard {
+    double*& p;
+    ~Guard() {
+      if (p) cudaFree(p);
+    }
+  } guard{stage};
+  if (h->prec != RTTDA_FP64) CKS(dalloc(&stage, stage_n));
+  auto upload = [&](const double* src, size_t n, void** dst) -> rttda_status {
+    CK(cudaMalloc(dst, std::max<size_t>(n, 1) * h->fbytes));
+    for (size_t off = 0; off < n; off += chunk) {
+      const size_t m = std::min(chunk, n - off);
+      if (h->prec == RTTDA_FP64) {
+        CK(cudaMemcpyAsync((double*)*dst + off, src + off, m * 8, cudaMemcpyHostToDevice, h->stream));
+      } else {
+        CK(cudaMemcpyAsync(stage, src + off, m * 8, cudaMemcpyHostToDevice, h->stream));
+        k_cast<float><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, stage, (float*)*dst + off);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->stream));
+      }
+    }
+    return RTTDA_OK;
+  };
+  auto upload64 = [&](const double* src, size_t n, double** dst) -> rttda_status {
+    CK(cudaMalloc((void**)dst, std::max<size_t>(n, 1) * 8));
+    CK(cudaMemcpyAsync(*dst, src, n * 8, cudaMemcpyHostToDevice, h->stream));
+    return RTTDA_OK;
+  };
+  CKS(upload(B_ov, P * o * v, &h->Bov));
+  CKS(upload(B_oo, P * o * o, &h->Boo));
+  CKS(upload(B_vv, P * v * v, &h->Bvv));
+  CKS(upload64(eps_occ, o, &h->eps_o));
+  CKS(upload64(eps_virt, v, &h->eps_v));
+  CKS(upload64(mu_oo, 3 * o * o, &h->mu_oo));
+  CKS(upload64(mu_vv, 3 * v * v, &h->mu_vv));
+  CKS(upload64(mu_0ov, 3 * o * v, &h->mu_0));
+  CK(cudaStreamSynchronize(h->stream));
+  // spectral-norm bound of M_x: |m_x| + |mu_vv,x|_F + |mu_oo,x|_F
+  for (int x = 0; x < 3; ++x)
+    h->mu_bound[x] = fro(mu_0ov + x * o * v, o * v) + fro(mu_vv + x * v * v, v * v) + fro(mu_oo + x * o * o, o * o);
+  return RTTDA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int rttda_abi_version(void) { return RTTDA_ABI_VERSION; }
+
+const char* rttda_last_error(void) { return g_last_error.c_str(); }
+
+rttda_status rttda_create(int nocc, int nvirt, int naux, const double* eps_occ, const double* eps_virt,
+                          const double* B_ov, const double* B_oo, const double* B_vv, const double* mu_oo,
+                          const double* mu_vv, const double* mu_0ov, double c_x, int prec, rttda_t* out) {
+  g_last_error.clear();
+  if (!out) return set_error(RTTDA_E_ARG, "rttda_create: out is NULL");
+  *out = nullptr;
+  if (nocc < 1 || nvirt < 1 || naux < 1) return set_error(RTTDA_E_ARG, "rttda_create: nocc, nvirt, naux must be >= 1");
+  if (!eps_occ || !eps_virt || !B_ov || !B_oo || !B_vv || !mu_oo || !mu_vv || !mu_0ov)
+    return set_error(RTTDA_E_ARG, "rttda_create: NULL input array");
+  if (prec != RTTDA_FP64 && prec != RTTDA_FP32)
+    return set_error(RTTDA_E_ARG, "rttda_create: unsupported precision");
+  if (!std::isfinite(c_x)) return set_error(RTTDA_E_ARG, "rttda_create: c_x not finite");
+
+  rttda_ctx* h = new rttda_ctx();
+  h->o = nocc;
+  h->v = nvirt;
+  h->P = naux;
+  h->ov = (long long)nocc * nvirt;
+  h->N = 1 + h->ov;
+  h->cx = c_x;
+  h->prec = prec;
+  h->fbytes = prec == RTTDA_FP64 ? 8 : 4;
+  h->cbytes = prec == RTTDA_FP64 ? 8 : 4;
+
+  rttda_status st = create_impl(h, eps_occ, eps_virt, B_ov, B_oo, B_vv, mu_oo, mu_vv, mu_0ov);
+  if (st != RTTDA_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return RTTDA_OK;
+}
+
+rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes) {
+  if (!h || !bytes) return set_error(RTTDA_E_ARG, "rttda_memory_bytes: NULL argument");
+  const size_t o = h->o, v = h->v, P = h->P;
+  size_t b = (P * o * v + P * o * o + P * v * v) * h->fbytes + (o + v + 3 * (o * o + v * v + o * v)) * 8;
+  if (h->T > 0) {
+    const size_t C = 2 * h->T, NC = h->N * C;
+    b += NC * 8 * 6 + (size_t)P * C * h->cbytes + (size_t)h->SJ * h->ov * C * h->cbytes +
+         (size_t)h->zchunk * v * C * o * h->cbytes + (size_t)h->SK * C * o * v * h->cbytes +
+         (size_t)h->T * (o * o + v * v + o * v) * (8 + (h->prec == RTTDA_FP64 ? 0 : h->cbytes));
+  }
+  *bytes = b;
+  return RTTDA_OK;
+}
+
+rttda_status rttda_set_field(rttda_t h, const rttda_pulse* pulses, int ntraj) {
+  g_last_error.clear();
+  if (!h || !pulses) return set_error(RTTDA_E_ARG, "rttda_set_field: NULL argument");
+  if (ntraj < 1) return set_error(RTTDA_E_ARG, "rttda_set_field: ntraj must be >= 1");
+  std::vector<PulseDev> pd(ntraj);
+  std::vector<double> kappa(ntraj, 0.0), dirs(3 * ntraj);
+  bool any_field = false, any_kick = false;
+  double xmax = 0.0;
+  for (int t = 0; t < ntraj; ++t) {
+    const rttda_pulse& p = pulses[t];
+    if (p.kind < RTTDA_KICK || p.kind > RTTDA_SIN2) return set_error(RTTDA_E_ARG, "rttda_set_field: unknown pulse kind");
+    const double dn = std::sqrt(p.dir[0] * p.dir[0] + p.dir[1] * p.dir[1] + p.dir[2] * p.dir[2]);
+    if (!(dn > 0.0) || !std::isfinite(dn)) return set_error(RTTDA_E_ARG, "rttda_set_field: zero polarisation vector");
+    if (!std::isfinite(p.E0) || !std::isfinite(p.omega)) return set_error(RTTDA_E_ARG, "rttda_set_field: non-finite E0/omega");
+    if ((p.kind == RTTDA_GAUSS_TL || p.kind == RTTDA_CHIRP) && !(p.fwhm > 0.0))
+      return set_error(RTTDA_E_ARG, "rttda_set_field: fwhm must be > 0");
+    if (p.kind == RTTDA_SIN2 && !(p.duration > 0.0)) return set_error(RTTDA_E_ARG, "rttda_set_field: duration must be > 0");
+    for (int x = 0; x < 3; ++x) dirs[3 * t + x] = p.dir[x] / dn;
+    pd[t].kind = p.kind;
+    pd[t].E0 = p.E0;
+    pd[t].omega = p.omega;
+    pd[t].t0 = p.t0;
+    pd[t].sigma = p.fwhm / 2.35482;  // Sec. 2.2: sigma = FWHM / 2.35482
+    pd[t].beta = p.beta;
+    pd[t].duration = p.duration;
+    if (p.kind == RTTDA_KICK) {
+      any_kick = true;
+      kappa[t] = p.E0;
+      double b = 0.0;
+      for (int x = 0; x < 3; ++x) b += std::fabs(dirs[3 * t + x]) * h->mu_bound[x];
+      xmax = std::max(xmax, std::fabs(p.E0) * b);
+    } else {
+      any_field = true;
+    }
+  }
+  // Taylor terms: x^K / K! below 1e-18 with x a bound on |kappa M_d|.
+  int K = 0;
+  if (any_kick) {
+    double term = 1.0;
+    K = 0;
+    while (K < 400) {
+      ++K;
+      term *= xmax / K;
+      if (term < 1e-18 && K > xmax) break;
+    }
+    if (K >= 400) return set_error(RTTDA_E_ARG, "rttda_set_field: kick too strong for the Taylor series");
+  }
+
+  h->free_batch();
+  h->T = ntraj;
+  h->pulses.assign(pulses, pulses + ntraj);
+  h->any_field = any_field;
+  h->any_kick = any_kick;
+  h->kick_terms = K;
+  CKS(dalloc(&h->d_pulses, ntraj));
+  CKS(dalloc(&h->d_kappa, ntraj));
+  CKS(dalloc(&h->d_dirs, 3 * ntraj));
+  CK(cudaMemcpyAsync(h->d_pulses, pd.data(), sizeof(PulseDev) * ntraj, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_kappa, kappa.data(), sizeof(double) * ntraj, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_dirs, dirs.data(), sizeof(double) * 3 * ntraj, cudaMemcpyHostToDevice, h->stream));
+  const long long loo = (long long)h->o * h->o, lvv = (long long)h->v * h->v, lov = h->ov;
+  CKS(dalloc(&h->moo64, loo * ntraj));
+  CKS(dalloc(&h->mvv64, lvv * ntraj));
+  CKS(dalloc(&h->m064, lov * ntraj));
+  cudaStream_t s = h->stream;
+  k_dipole_dir<double><<<blocks_for(loo * ntraj, 256), 256, 0, s>>>(loo, ntraj, h->d_dirs, h->mu_oo, h->moo64);
+  k_dipole_dir<double><<<blocks_for(lvv * ntraj, 256), 256, 0, s>>>(lvv, ntraj, h->d_dirs, h->mu_vv, h->mvv64);
+  k_dipole_dir<double><<<blocks_for(lov * ntraj, 256), 256, 0, s>>>(lov, ntraj, h->d_dirs, h->mu_0, h->m064);
+  if (h->prec != RTTDA_FP64) {
+    float* p = nullptr;
+    CKS(dalloc(&p, loo * ntraj));
+    h->mooC = p;
+    CKS(dalloc(&p, lvv * ntraj));
+    h->mvvC = p;
+    CKS(dalloc(&p, lov * ntraj));
+    h->m0C = p;
+    k_dipole_dir<float><<<blocks_for(loo * ntraj, 256), 256, 0, s>>>(loo, ntraj, h->d_dirs, h->mu_oo, (float*)h->mooC);
+    k_dipole_dir<float><<<blocks_for(lvv * ntraj, 256), 256, 0, s>>>(lvv, ntraj, h->d_dirs, h->mu_vv, (float*)h->mvvC);
+    k_dipole_dir<float><<<blocks_for(lov * ntraj, 256), 256, 0, s>>>(lov, ntraj, h->d_dirs, h->mu_0, (float*)h->m0C);
+  }
+  CKS(h->alloc_batch());
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return RTTDA_OK;
+}
+
+static rttda_status propagate_impl(rttda_t h, bool fresh, const double* c0_dev, double dt, long nsteps,
+                                   double* c_out_dev, double* dip_dev, double* nrm_dev, cudaStream_t s) {
+  if (h->T < 1) return set_error(RTTDA_E_STATE, "rttda_propagate: call rttda_set_field first");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(RTTDA_E_ARG, "rttda_propagate: dt must be > 0");
+  if (nsteps < 0) return set_error(RTTDA_E_ARG, "rttda_propagate: nsteps must be >= 0");
+  const long long NT = h->N * h->T;
+  double t_call = 0.0;
+  if (fresh) {
+    if (c0_dev)
+      k_abi_to_dev<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, c0_dev, h->Xn);
+    else
+      k_ground<<<blocks_for(NT * 2, 256), 256, 0, s>>>(h->N, h->T, h->Xn);
+    if (h->any_kick) enqueue_kick(h, s);
+  } else {
+    if (!h->have_state) return set_error(RTTDA_E_STATE, "rttda_resume: no state to resume from");
+    t_call = h->t_now;
+  }
+  // traces: both or neither are needed by the kernels; use scratch for a missing one
+  double* dip = dip_dev;
+  double* nrm = nrm_dev;
+  double* tmp = nullptr;
+  if ((dip == nullptr) != (nrm == nullptr)) {
+    CKS(dalloc(&tmp, (size_t)h->T * (nsteps + 1)));
+    if (!dip) dip = tmp;
+    if (!nrm) nrm = tmp;
+  }
+  rttda_status st = run_steps(h, t_call, dt, nsteps, dip, nrm, s);
+  if (st == RTTDA_OK && c_out_dev) k_dev_to_abi<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->Xn, c_out_dev);
+  if (tmp) {
+    cudaStreamSynchronize(s);
+    cudaFree(tmp);
+  }
+  if (st != RTTDA_OK) return st;
+  CK(cudaGetLastError());
+  return RTTDA_OK;
+}
+
+rttda_status rttda_propagate_device(rttda_t h, const double* c0_dev, double dt, long nsteps, double* c_out_dev,
+                                    double* dipole_dev, double* norm_dev, void* stream) {
+  g_last_error.clear();
+  if (!h) return set_error(RTTDA_E_ARG, "rttda_propagate_device: NULL handle");
+  cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+  return propagate_impl(h, true, c0_dev, dt, nsteps, c_out_dev, dipole_dev, norm_dev, s);
+}
+
+static rttda_status host_call(rttda_t h, bool fresh, const double* c0, double dt, long nsteps, double* c_out,
+                              double* dip, double* nrm) {
+  if (h->T < 1) return set_error(RTTDA_E_STATE, "rttda_propagate: call rttda_set_field first");
+  if (nsteps < 0) return set_error(RTTDA_E_ARG, "rttda_propagate: nsteps must be >= 0");
+  const size_t NT2 = (size_t)h->N * h->T * 2, TR = (size_t)h->T * (nsteps + 1);
+  const size_t need = 2 * NT2 + 2 * TR;
+  if (h->h_io_count < need) {
+    dfree(h->h_io);
+    h->h_io = nullptr;
+    h->h_io_count = 0;
+    CKS(dalloc(&h->h_io, need));
+    h->h_io_count = need;
+  }
+  double* d_c0 = h->h_io;
+  double* d_cout = d_c0 + NT2;
+  double* d_dip = d_cout + NT2;
+  double* d_nrm = d_dip + TR;
+  cudaStream_t s = h->stream;
+  if (c0) CK(cudaMemcpyAsync(d_c0, c0, NT2 * 8, cudaMemcpyHostToDevice, s));
+  const bool want_tr = dip || nrm;
+  CKS(propagate_impl(h, fresh, c0 ? d_c0 : nullptr, dt, nsteps, c_out ? d_cout : nullptr, want_tr ? d_dip : nullptr,
+                     want_tr ? d_nrm : nullptr, s));
+  if (c_out) CK(cudaMemcpyAsync(c_out, d_cout, NT2 * 8, cudaMemcpyDeviceToHost, s));
+  if (dip) CK(cudaMemcpyAsync(dip, d_dip, TR * 8, cudaMemcpyDeviceToHost, s));
+  if (nrm) CK(cudaMemcpyAsync(nrm, d_nrm, TR * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return RTTDA_OK;
+}
+
+rttda_status rttda_propagate(rttda_t h, const double* c0, double dt, long nsteps, double* c_out,
+                             double* dipole_trace, double* norm_trace) {
+  g_last_error.clear();
+  if (!h) return set_error(RTTDA_E_ARG, "rttda_propagate: NULL handle");
+  return host_call(h, true, c0, dt, nsteps, c_out, dipole_trace, norm_trace);
+}
+
+rttda_status rttda_resume(rttda_t h, double dt, long nsteps, double* c_out, double* dipole_trace,
+                          double* norm_trace) {
+  g_last_error.clear();
+  if (!h) return set_error(RTTDA_E_ARG, "rttda_resume: NULL handle");
+  if (!h->have_state) return set_error(RTTDA_E_STATE, "rttda_resume: no state to resume from");
+  return host_call(h, false, nullptr, dt, nsteps, c_out, dipole_trace, norm_trace);
+}
+
+rttda_status rttda_get_state(rttda_t h, double* c, double* t) {
+  g_last_error.clear();
+  if (!h || !c) return set_error(RTTDA_E_ARG, "rttda_get_state: NULL argument");
+  if (!h->have_state) return set_error(RTTDA_E_STATE, "rttda_get_state: no state");
+  const long long NT = h->N * h->T;
+  k_dev_to_abi<<<blocks_for(NT, 256), 256, 0, h->stream>>>(h->N, h->T, h->Xn, h->term);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c, h->term, NT * 2 * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (t) *t = h->t_now;
+  return RTTDA_OK;
+}
+
+rttda_status rttda_set_state(rttda_t h, const double* c, double t) {
+  g_last_error.clear();
+  if (!h || !c) return set_error(RTTDA_E_ARG, "rttda_set_state: NULL argument");
+  if (h->T < 1) return set_error(RTTDA_E_STATE, "rttda_set_state: call rttda_set_field first");
+  if (!std::isfinite(t)) return set_error(RTTDA_E_ARG, "rttda_set_state: t not finite");
+  const long long NT = h->N * h->T;
+  CK(cudaMemcpyAsync(h->term, c, NT * 2 * 8, cudaMemcpyHostToDevice, h->stream));
+  k_abi_to_dev<<<blocks_for(NT, 256), 256, 0, h->stream>>>(h->N, h->T, h->term, h->Xn);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  h->t_now = t;
+  h->have_state = true;
+  return RTTDA_OK;
+}
+
+rttda_status rttda_sigma(rttda_t h, const double* c_dev, double t, double* sigma_dev, void* stream) {
+  g_last_error.clear();
+  if (!h || !c_dev || !sigma_dev) return set_error(RTTDA_E_ARG, "rttda_sigma: NULL argument");
+  if (h->T < 1) return set_error(RTTDA_E_STATE, "rttda_sigma: call rttda_set_field first");
+  if (!std::isfinite(t)) return set_error(RTTDA_E_ARG, "rttda_sigma: t not finite");
+  cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+  const long long NT = h->N * h->T;
+  k_abi_to_dev<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, c_dev, h->Xq);
+  // E at time t goes to slot 0 of the stage table (step counter 0, stage 0)
+  CK(cudaMemsetAsync(h->d_step, 0, sizeof(long long), s));
+  k_efield<<<1, 128, 0, s>>>(h->T, h->d_pulses, h->d_step, 0, t, 0.0, h->E);
+  dispatch(h->prec, [&](auto ops) {
+    using O = decltype(ops);
+    if (h->any_field) O::field(h, h->Xq, s);
+    O::coulomb(h, h->Xq, s);
+    O::exchange(h, h->Xq, s);
+    O::combine(h, 1, 0, h->any_field, 0.0, h->Xq, h->term, s);
+  });
+  k_dev_to_abi<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->term, sigma_dev);
+  CK(cudaGetLastError());
+  return RTTDA_OK;
+}
+
+rttda_status rttda_spectrum(const double* trace, long ntraces, long npts, double dt, double kappa, double gamma,
+                            double wmin, double wmax, long nfreq, double* omega_out, double* S_out) {
+  g_last_error.clear();
+  if (!trace || !S_out) return set_error(RTTDA_E_ARG, "rttda_spectrum: NULL argument");
+  if (ntraces < 1 || npts < 2 || nfreq < 1) return set_error(RTTDA_E_ARG, "rttda_spectrum: bad sizes");
+  if (!(dt > 0.0) || kappa == 0.0 || !(gamma >= 0.0) || !std::isfinite(kappa))
+    return set_error(RTTDA_E_ARG, "rttda_spectrum: bad dt/kappa/gamma");
+  if (nfreq > (1L << 30)) return set_error(RTTDA_E_ARG, "rttda_spectrum: nfreq too large");
+  double *d_tr = nullptr, *d_S = nullptr, *d_w = nullptr;
+  const size_t ntr = (size_t)ntraces * npts;
+  auto cleanup = [&]() {
+    dfree(d_tr);
+    dfree(d_S);
+    dfree(d_w);
+  };
+  rttda_status st = RTTDA_OK;
+  if ((st = dalloc(&d_tr, ntr)) != RTTDA_OK || (st = dalloc(&d_S, nfreq)) != RTTDA_OK ||
+      (st = dalloc(&d_w, nfreq)) != RTTDA_OK) {
+    cleanup();
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(d_tr, trace, ntr * 8, cudaMemcpyHostToDevice);
+  const double dw = nfreq > 1 ? (wmax - wmin) / (double)(nfreq - 1) : 0.0;
+  if (e == cudaSuccess) {
+    k_spectrum<<<(unsigned)nfreq, 256>>>(d_tr, ntraces, npts, dt, kappa, gamma, wmin, dw, d_w, d_S);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(S_out, d_S, nfreq * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && omega_out) e = cudaMemcpy(omega_out, d_w, nfreq * 8, cudaMemcpyDeviceToHost);
+  cleanup();
+  if (e != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("rttda_spectrum: ") + cudaGetErrorString(e));
+  return RTTDA_OK;
+}
+
+rttda_status rttda_profile(rttda_t h, int enable) {
+  g_last_error.clear();
+  if (!h) return set_error(RTTDA_E_ARG, "rttda_profile: NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  h->prof_on = enable != 0;
+  for (size_t& u : h->prof_used) u = 0;
+  return RTTDA_OK;
+}
+
+rttda_status rttda_profile_read(rttda_t h, double* ms, long long* launches) {
+  g_last_error.clear();
+  if (!h) return set_error(RTTDA_E_ARG, "rttda_profile_read: NULL handle");
+  for (int c = 0; c < RTTDA_NUM_KERNEL_CLASSES; ++c) {
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < h->prof_used[c]; k += 2) {
+      CK(cudaEventSynchronize(h->prof_ev[c][k + 1]));
+      float x = 0.f;
+      CK(cudaEventElapsedTime(&x, h->prof_ev[c][k], h->prof_ev[c][k + 1]));
+      tot += x;
+    }
+    if (ms) ms[c] = tot;
+    if (launches) launches[c] = (long long)(h->prof_used[c] / 2);
+    h->prof_used[c] = 0;
+  }
+  return RTTDA_OK;
+}
+
+rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step) {
+  g_last_error.clear();
+  if (!h) return set_error(RTTDA_E_ARG, "rttda_launch_stats: NULL handle");
+  if (total) *total = h->launches;
+  if (per_step) *per_step = h->launches_per_step;
+  return RTTDA_OK;
+}
+
+void rttda_destroy(rttda_t h) { delete h; }
+
+}  // extern "C"

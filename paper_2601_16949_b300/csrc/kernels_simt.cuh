@@ -1,0 +1,618 @@
+// SIMT (CUDA-core) kernels of the RT-TDA sigma build and RK4 stepper.
+//
+// Device amplitude layout: X[n*C + 2t + q], n in [0, N) (n = 0 is |0>,
+// n = 1 + i*nvirt + a is |ia>), t the trajectory, q = 0 (re) / 1 (im),
+// C = 2T real columns.  Every trajectory is two real columns of the same
+// contraction because A and M_d are real symmetric.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace rttda {
+
+// ---------------------------------------------------------------------------
+// Pulses (Sec. 2.2, Eqs. delta_pulse ... chirped_pulse, plus sin^2)
+// ---------------------------------------------------------------------------
+struct PulseDev {
+  int kind;                       // 0 kick, 1 CW, 2 Gaussian TL, 3 chirp, 4 sin^2
+  double E0, omega, t0, sigma, beta, duration;
+};
+
+__device__ __forceinline__ double pulse_field(const PulseDev& p, double t) {
+  switch (p.kind) {
+    case 1:
+      return p.E0 * sin(p.omega * t);
+    case 2:
+    case 3: {
+      const double tau = t - p.t0;
+      const double env = exp(-tau * tau / (2.0 * p.sigma * p.sigma));
+      const double w = p.omega + (p.kind == 3 ? 0.5 * p.beta * tau : 0.0);
+      return p.E0 * env * sin(w * tau);
+    }
+    case 4: {
+      if (t < 0.0 || t > p.duration) return 0.0;
+      const double s = sin(3.14159265358979323846 * t / p.duration);
+      return p.E0 * s * s * sin(p.omega * t);
+    }
+    default:
+      return 0.0;  // a kick acts only at t = 0+
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Conversions and reductions
+// ---------------------------------------------------------------------------
+template <typename TC, typename TS>
+__device__ __forceinline__ TC cvt(TS x) { return static_cast<TC>(x); }
+template <>
+__device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+  return x;
+}
+
+// Fixed-order block sum (deterministic); result valid in thread 0.
+// scratch must hold blockDim.x/32 elements.
+template <typename T>
+__device__ __forceinline__ T block_sum(T x, T* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  x = warp_sum(x);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = x;
+  __syncthreads();
+  T r = 0;
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    r = lane < nw ? scratch[lane] : T(0);
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Coulomb, pass 1: w[P][col] = sum_ia B^P_ia X[1+ia][col]
+// (first contraction of 2 sum_jb (ia|jb) c_jb with (ia|jb) = sum_P B B)
+// One block per PB rows of B: each amplitude row loaded from L2 serves PB
+// factor rows streamed from HBM.
+// ---------------------------------------------------------------------------
+template <typename TF, typename TC, int CG, int PB>
+__global__ void __launch_bounds__(256) k_coul_w(const TF* __restrict__ Bov, const double* __restrict__ X, int P,
+                                                long long ov, int C, TC* __restrict__ w) {
+  __shared__ TC red[32];
+  const int p0 = blockIdx.x * PB;
+  const int pb = min(PB, P - p0);
+  const double* Xs = X + C;
+  for (int c0 = 0; c0 < C; c0 += CG) {
+    const int cg = min(CG, C - c0);
+    TC acc[PB][CG];
+#pragma unroll
+    for (int r = 0; r < PB; ++r)
+#pragma unroll
+      for (int c = 0; c < CG; ++c) acc[r][c] = TC(0);
+    for (long long ia = threadIdx.x; ia < ov; ia += blockDim.x) {
+      TC x[CG];
+      const double* xr = Xs + ia * C + c0;
+#pragma unroll
+      for (int c = 0; c < CG; ++c) x[c] = c < cg ? (TC)xr[c] : TC(0);
+#pragma unroll
+      for (int r = 0; r < PB; ++r) {
+        if (r < pb) {
+          const TC b = cvt<TC>(Bov[(size_t)(p0 + r) * ov + ia]);
+#pragma unroll
+          for (int c = 0; c < CG; ++c) acc[r][c] = fma(b, x[c], acc[r][c]);
+        }
+      }
+    }
+    for (int r = 0; r < pb; ++r) {
+      for (int c = 0; c < cg; ++c) {
+        const TC s = block_sum(acc[r][c], red);
+        if (threadIdx.x == 0) w[(size_t)(p0 + r) * C + c0 + c] = s;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coulomb, pass 2: Jpart[s][ia][col] = 2 sum_{P in chunk s} B^P_ia w[P][col]
+// grid (ceil(ov/256), nsplit); the chunk of w is staged in shared memory.
+// ---------------------------------------------------------------------------
+template <typename TF, typename TC, int CG>
+__global__ void __launch_bounds__(256) k_coul_J(const TF* __restrict__ Bov, const TC* __restrict__ w, int P,
+                                                long long ov, int C, int pchunk, TC* __restrict__ Jpart) {
+  extern __shared__ unsigned char smem_raw[];
+  TC* ws = reinterpret_cast<TC*>(smem_raw);
+  const int s = blockIdx.y;
+  const int p0 = s * pchunk, p1 = min(P, p0 + pchunk);
+  for (int e = threadIdx.x; e < (p1 - p0) * C; e += blockDim.x) ws[e] = w[(size_t)p0 * C + e];
+  __syncthreads();
+  const long long ia = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ia >= ov) return;
+  for (int c0 = 0; c0 < C; c0 += CG) {
+    TC acc[CG];
+#pragma unroll
+    for (int c = 0; c < CG; ++c) acc[c] = TC(0);
+    for (int p = p0; p < p1; ++p) {
+      const TC b = cvt<TC>(Bov[(size_t)p * ov + ia]);
+      const TC* wr = ws + (p - p0) * C + c0;
+#pragma unroll
+      for (int c = 0; c < CG; ++c)
+        if (c0 + c < C) acc[c] = fma(b, wr[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < CG; ++c)
+      if (c0 + c < C) Jpart[((size_t)s * ov + ia) * C + c0 + c] = TC(2) * acc[c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Generic SIMT GEMM:  D[m][n] (+)= sum_k A[k*lda + m] * B[k*ldb + n]
+// Used for the exchange: Z = B_oo C per P (batched) and the long-K
+// contraction sum_{P,b} Z^P_(col,i),b B^P_ba (split-K, partial outputs).
+// grid.z = batch * nsplit.  Thread (tx, ty) owns rows
+// ty*TM/2 + {0, BM/2} + r and columns tx*TN/2 + {0, BN/2} + r.
+// ---------------------------------------------------------------------------
+template <typename TA, typename TB, typename TC, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    k_gemm_tn(int M, int N, long long K, const TA* __restrict__ A, long long lda, long long strideA,
+              const TB* __restrict__ B, long long ldb, long long strideB, TC* __restrict__ D, long long ldd,
+              long long strideD, long long splitStrideD, int nsplit, long long kper, int accumulate) {
+  constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
+  constexpr int LA = (BK * BM) / NT, LB = (BK * BN) / NT;
+  static_assert((BK * BM) % NT == 0 && (BK * BN) % NT == 0, "tile/threads mismatch");
+  __shared__ TC As[2][BK][BM];
+  __shared__ TC Bs[2][BK][BN];
+
+  const int z = blockIdx.z;
+  const int batch = z / nsplit, split = z % nsplit;
+  A += (size_t)batch * strideA;
+  B += (size_t)batch * strideB;
+  D += (size_t)batch * strideD + (size_t)split * splitStrideD;
+  const long long kbeg = (long long)split * kper;
+  const long long kend = min(K, kbeg + kper);
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int tid = threadIdx.x, tx = tid % NTX, ty = tid / NTX;
+
+  TC acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = TC(0);
+
+  TC ra[LA], rb[LB];
+  auto gload = [&](long long k0) {
+#pragma unroll
+    for (int l = 0; l < LA; ++l) {
+      const int e = tid + l * NT, kk = e / BM, mm = e % BM;
+      const long long gk = k0 + kk;
+      ra[l] = (gk < kend && m0 + mm < M) ? cvt<TC>(A[gk * lda + m0 + mm]) : TC(0);
+    }
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const int e = tid + l * NT, kk = e / BN, nn = e % BN;
+      const long long gk = k0 + kk;
+      rb[l] = (gk < kend && n0 + nn < N) ? cvt<TC>(B[gk * ldb + n0 + nn]) : TC(0);
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < LA; ++l) {
+      const int e = tid + l * NT;
+      As[buf][e / BM][e % BM] = ra[l];
+    }
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const int e = tid + l * NT;
+      Bs[buf][e / BN][e % BN] = rb[l];
+    }
+  };
+
+  int buf = 0;
+  if (kbeg < kend) {
+    gload(kbeg);
+    sstore(0);
+  }
+  __syncthreads();
+  for (long long k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
+    if (more) gload(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TC a[TM], b[TN];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < TM / 2; ++r) a[h * (TM / 2) + r] = As[buf][kk][ty * (TM / 2) + h * (BM / 2) + r];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < TN / 2; ++r) b[h * (TN / 2) + r] = Bs[buf][kk][tx * (TN / 2) + h * (BN / 2) + r];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      sstore(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int m = m0 + ty * (TM / 2) + (i / (TM / 2)) * (BM / 2) + (i % (TM / 2));
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int n = n0 + tx * (TN / 2) + (j / (TN / 2)) * (BN / 2) + (j % (TN / 2));
+      if (n >= N) continue;
+      TC* dst = D + (size_t)m * ldd + n;
+      *dst = accumulate ? *dst + acc[i][j] : acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Field product F = M_d X for every trajectory (Slater-Condon rules, Eqs.
+// sc2-sc5), singles rows:
+//   F_ia = m_ia X_0 + sum_b mu_ab X_ib - sum_j mu_ji X_ja
+// grid (ceil(v/32), ceil(o/8), T), block (32, 8): thread (a, i).
+// ---------------------------------------------------------------------------
+template <typename TM_, typename TC>
+__global__ void __launch_bounds__(256) k_field(int o, int v, int T, const double* __restrict__ X,
+                                               const TM_* __restrict__ moo, const TM_* __restrict__ mvv,
+                                               const TM_* __restrict__ m0, double* __restrict__ F) {
+  __shared__ TC sx[8][32][2];    // X[i0+ii][b0+bb]
+  __shared__ TC sm[32][33];      // mu_vv[b0+bb][a0+aa]
+  __shared__ TC so[32][9];       // mu_oo[j0+jj][i0+ii]
+  __shared__ TC sy[32][32][2];   // X[j0+jj][a0+aa]
+  const int C = 2 * T;
+  const int t = blockIdx.z;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int a0 = blockIdx.x * 32, i0 = blockIdx.y * 8;
+  const int a = a0 + tx, i = i0 + ty;
+  const TM_* Mv = mvv + (size_t)t * v * v;
+  const TM_* Mo = moo + (size_t)t * o * o;
+  const TM_* Mz = m0 + (size_t)t * o * v;
+  const double* Xt = X + 2 * t;
+  TC fr = 0, fi = 0;
+  for (int b0 = 0; b0 < v; b0 += 32) {
+    {
+      const int ii = ty, bb = tx;
+      const bool ok = (i0 + ii < o) && (b0 + bb < v);
+      const size_t row = 1 + (size_t)(i0 + ii) * v + b0 + bb;
+      sx[ii][bb][0] = ok ? (TC)Xt[row * C] : TC(0);
+      sx[ii][bb][1] = ok ? (TC)Xt[row * C + 1] : TC(0);
+    }
+    for (int e = tid; e < 32 * 32; e += 256) {
+      const int bb = e / 32, aa = e % 32;
+      sm[bb][aa] = (b0 + bb < v && a0 + aa < v) ? cvt<TC>(Mv[(size_t)(b0 + bb) * v + a0 + aa]) : TC(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int bb = 0; bb < 32; ++bb) {
+      const TC mv = sm[bb][tx];
+      fr = fma(sx[ty][bb][0], mv, fr);
+      fi = fma(sx[ty][bb][1], mv, fi);
+    }
+    __syncthreads();
+  }
+  for (int j0 = 0; j0 < o; j0 += 32) {
+    for (int e = tid; e < 32 * 8; e += 256) {
+      const int jj = e / 8, ii = e % 8;
+      so[jj][ii] = (j0 + jj < o && i0 + ii < o) ? cvt<TC>(Mo[(size_t)(j0 + jj) * o + i0 + ii]) : TC(0);
+    }
+    for (int e = tid; e < 32 * 32; e += 256) {
+      const int jj = e / 32, aa = e % 32;
+      const bool ok = (j0 + jj < o) && (a0 + aa < v);
+      const size_t row = 1 + (size_t)(j0 + jj) * v + a0 + aa;
+      sy[jj][aa][0] = ok ? (TC)Xt[row * C] : TC(0);
+      sy[jj][aa][1] = ok ? (TC)Xt[row * C + 1] : TC(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < 32; ++jj) {
+      const TC mo = so[jj][ty];
+      fr = fma(-mo, sy[jj][tx][0], fr);
+      fi = fma(-mo, sy[jj][tx][1], fi);
+    }
+    __syncthreads();
+  }
+  if (a < v && i < o) {
+    const TC mz = cvt<TC>(Mz[(size_t)i * v + a]);
+    fr = fma(mz, (TC)Xt[0], fr);
+    fi = fma(mz, (TC)Xt[1], fi);
+    const size_t row = 1 + (size_t)i * v + a;
+    F[row * C + 2 * t] = (double)fr;
+    F[row * C + 2 * t + 1] = (double)fi;
+  }
+}
+
+// Ground row of the field product: F_0 = sum_ia m_ia X_ia (Hermitian
+// partner of sc2).  One block per trajectory, fixed-order reduction.
+template <typename TM_, typename TC>
+__global__ void __launch_bounds__(256) k_field0(long long ov, int T, const double* __restrict__ X,
+                                                const TM_* __restrict__ m0, double* __restrict__ F) {
+  __shared__ TC red[32];
+  const int C = 2 * T, t = blockIdx.x;
+  const TM_* Mz = m0 + (size_t)t * ov;
+  TC sr = 0, si = 0;
+  for (long long ia = threadIdx.x; ia < ov; ia += blockDim.x) {
+    const TC m = cvt<TC>(Mz[ia]);
+    sr = fma(m, (TC)X[(1 + ia) * C + 2 * t], sr);
+    si = fma(m, (TC)X[(1 + ia) * C + 2 * t + 1], si);
+  }
+  sr = block_sum(sr, red);
+  si = block_sum(si, red);
+  if (threadIdx.x == 0) {
+    F[2 * t] = (double)sr;
+    F[2 * t + 1] = (double)si;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// E(t) of every trajectory at the four RK4 stage times of the current step:
+// E[s*T + t] at t_off + (base + step + c_s) dt, c = (0, 1/2, 1/2, 1).  The
+// integer step index keeps stage times identical between one long run and a
+// run resumed part-way.
+// ---------------------------------------------------------------------------
+__global__ void k_efield(int T, const PulseDev* __restrict__ pulses, const long long* __restrict__ step,
+                         long long base, double t_off, double dt, double* __restrict__ E) {
+  const double cs[4] = {0.0, 0.5, 0.5, 1.0};
+  const long long n = base + *step;
+  for (int e = threadIdx.x; e < 4 * T; e += blockDim.x) {
+    const int s = e / T, t = e % T;
+    E[e] = pulse_field(pulses[t], t_off + ((double)n + cs[s]) * dt);
+  }
+}
+
+__global__ void k_step_inc(long long* step) { *step += 1; }
+
+// ---------------------------------------------------------------------------
+// sigma assembly and RK4 stage update (one thread per amplitude row n).
+//   sigma_n = (e_a - e_i) X_n + J_n - c_x K_n - E_t F_n      (n = ia)
+//   sigma_0 = -E_t F_0                                        (A_00 = 0)
+//   k = -i sigma
+// mode 0 (RK4, stage s):
+//   s=0: acc = k;      Xs = Xn + dt/2 k
+//   s=1: acc += 2k;    Xs = Xn + dt/2 k
+//   s=2: acc += 2k;    Xs = Xn + dt k
+//   s=3: Xn += dt/6 (acc + k);  Xs = Xn
+// mode 1: write sigma to sig_out (same layout as X).
+// Kpart is the exchange partial sum laid out [s][(col*o + i)][a].
+// ---------------------------------------------------------------------------
+template <typename TC>
+__global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long N, int o, int v, int T,
+                                                 const double* __restrict__ eps_o,
+                                                 const double* __restrict__ eps_v, double cx,
+                                                 const TC* __restrict__ Jpart, int SJ,
+                                                 const TC* __restrict__ Kpart, int SK, long long Kstride,
+                                                 const double* __restrict__ F, const double* __restrict__ E,
+                                                 int use_field, double dt, double* __restrict__ Xn,
+                                                 double* __restrict__ Xs, double* __restrict__ acc,
+                                                 double* __restrict__ sig_out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int C = 2 * T;
+  const long long ov = N - 1;
+  int i = 0, a = 0;
+  double d = 0.0;
+  if (n > 0) {
+    i = (int)((n - 1) / v);
+    a = (int)((n - 1) % v);
+    d = eps_v[a] - eps_o[i];
+  }
+  for (int t = 0; t < T; ++t) {
+    double sg[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int col = 2 * t + q;
+      const size_t idx = (size_t)n * C + col;
+      double s = 0.0;
+      if (n > 0) {
+        s = d * Xs[idx];
+        double j = 0.0;
+        for (int p = 0; p < SJ; ++p) j += (double)Jpart[((size_t)p * ov + (n - 1)) * C + col];
+        double kx = 0.0;
+        for (int p = 0; p < SK; ++p)
+          kx += (double)Kpart[(size_t)p * Kstride + ((size_t)col * o + i) * v + a];
+        s += j - cx * kx;
+      }
+      if (use_field) s -= E[stage * T + t] * F[idx];
+      sg[q] = s;
+    }
+    const size_t ir = (size_t)n * C + 2 * t, ii = ir + 1;
+    if (mode == 1) {
+      sig_out[ir] = sg[0];
+      sig_out[ii] = sg[1];
+      continue;
+    }
+    const double kr = sg[1], ki = -sg[0];  // k = -i sigma
+    switch (stage) {
+      case 0:
+        acc[ir] = kr;
+        acc[ii] = ki;
+        Xs[ir] = Xn[ir] + 0.5 * dt * kr;
+        Xs[ii] = Xn[ii] + 0.5 * dt * ki;
+        break;
+      case 1:
+        acc[ir] += 2.0 * kr;
+        acc[ii] += 2.0 * ki;
+        Xs[ir] = Xn[ir] + 0.5 * dt * kr;
+        Xs[ii] = Xn[ii] + 0.5 * dt * ki;
+        break;
+      case 2:
+        acc[ir] += 2.0 * kr;
+        acc[ii] += 2.0 * ki;
+        Xs[ir] = Xn[ir] + dt * kr;
+        Xs[ii] = Xn[ii] + dt * ki;
+        break;
+      default: {
+        const double xr = Xn[ir] + (dt / 6.0) * (acc[ir] + kr);
+        const double xi = Xn[ii] + (dt / 6.0) * (acc[ii] + ki);
+        Xn[ir] = xr;
+        Xn[ii] = xi;
+        Xs[ir] = xr;
+        Xs[ii] = xi;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Observables: mu_d = Re c^dagger F (F = M_d c) and |c|^2 per trajectory.
+// Two-phase fixed-order reduction in FP64.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_obs_partial(long long N, int T, long long rows_per_block,
+                                                     const double* __restrict__ X,
+                                                     const double* __restrict__ F,
+                                                     double* __restrict__ part) {
+  __shared__ double red[32];
+  const int C = 2 * T;
+  const long long r0 = (long long)blockIdx.x * rows_per_block;
+  const long long r1 = min(N, r0 + rows_per_block);
+  for (int t = 0; t < T; ++t) {
+    double mu = 0.0, nr = 0.0;
+    for (long long n = r0 + threadIdx.x; n < r1; n += blockDim.x) {
+      const double xr = X[n * C + 2 * t], xi = X[n * C + 2 * t + 1];
+      mu = fma(xr, F[n * C + 2 * t], mu);
+      mu = fma(xi, F[n * C + 2 * t + 1], mu);
+      nr = fma(xr, xr, nr);
+      nr = fma(xi, xi, nr);
+    }
+    mu = block_sum(mu, red);
+    nr = block_sum(nr, red);
+    if (threadIdx.x == 0) {
+      part[((size_t)blockIdx.x * T + t) * 2] = mu;
+      part[((size_t)blockIdx.x * T + t) * 2 + 1] = nr;
+    }
+  }
+}
+
+// trace layout [t][ld]; the row written is *step (+ step_offset).
+__global__ void k_obs_final(int G, int T, const double* __restrict__ part, const long long* __restrict__ step,
+                            long long step_offset, long long ld, double* __restrict__ dip,
+                            double* __restrict__ nrm) {
+  const long long k = *step + step_offset;
+  for (int t = threadIdx.x; t < T; t += blockDim.x) {
+    double mu = 0.0, nr = 0.0;
+    for (int g = 0; g < G; ++g) {
+      mu += part[((size_t)g * T + t) * 2];
+      nr += part[((size_t)g * T + t) * 2 + 1];
+    }
+    dip[(size_t)t * ld + k] = mu;
+    nrm[(size_t)t * ld + k] = nr;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kick exp(+i kappa M_d) by its Taylor series: with F = M_d term,
+// term <- (i kappa / k) F, out += term.
+// ---------------------------------------------------------------------------
+__global__ void k_kick_term(long long N, int T, const double* __restrict__ kappa, double inv_k,
+                            const double* __restrict__ F, double* __restrict__ term, double* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * T) return;
+  const long long n = e / T;
+  const int t = (int)(e % T);
+  const int C = 2 * T;
+  const double s = kappa[t] * inv_k;
+  const size_t ir = (size_t)n * C + 2 * t;
+  const double fr = F[ir], fi = F[ir + 1];
+  const double tr = -s * fi, ti = s * fr;  // (i s) (fr + i fi)
+  term[ir] = tr;
+  term[ir + 1] = ti;
+  out[ir] += tr;
+  out[ir + 1] += ti;
+}
+
+// ---------------------------------------------------------------------------
+// Layout changes between the ABI ([t][n][2]) and the device ([n][t][2]).
+// ---------------------------------------------------------------------------
+__global__ void k_abi_to_dev(long long N, int T, const double* __restrict__ in, double* __restrict__ X) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * T) return;
+  const long long n = e / T;
+  const int t = (int)(e % T);
+  X[(n * T + t) * 2] = in[((size_t)t * N + n) * 2];
+  X[(n * T + t) * 2 + 1] = in[((size_t)t * N + n) * 2 + 1];
+}
+
+__global__ void k_dev_to_abi(long long N, int T, const double* __restrict__ X, double* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * T) return;
+  const int t = (int)(e / N);
+  const long long n = e % N;
+  out[((size_t)t * N + n) * 2] = X[(n * T + t) * 2];
+  out[((size_t)t * N + n) * 2 + 1] = X[(n * T + t) * 2 + 1];
+}
+
+// |0> for every trajectory.
+__global__ void k_ground(long long N, int T, double* __restrict__ X) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * 2 * T) return;
+  X[e] = (e < 2 * T && (e % 2) == 0) ? 1.0 : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Factor casts and per-trajectory dipole blocks.
+// ---------------------------------------------------------------------------
+template <typename TD>
+__global__ void k_cast(long long n, const double* __restrict__ src, TD* __restrict__ dst) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) dst[e] = static_cast<TD>(src[e]);
+}
+template <>
+__global__ void k_cast<__nv_bfloat16>(long long n, const double* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) dst[e] = __double2bfloat16(src[e]);
+}
+
+// out[t][e] = sum_x d[t][x] src[x][e]  (mu_d = mu . d, Eq. e_field)
+template <typename TD>
+__global__ void k_dipole_dir(long long len, int T, const double* __restrict__ dirs, const double* __restrict__ src,
+                             TD* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= len * T) return;
+  const int t = (int)(e / len);
+  const long long k = e % len;
+  const double val = dirs[3 * t] * src[k] + dirs[3 * t + 1] * src[len + k] + dirs[3 * t + 2] * src[2 * len + k];
+  out[e] = static_cast<TD>(val);
+}
+
+// ---------------------------------------------------------------------------
+// Damped dipole spectrum (one block per frequency, fixed-order reduction):
+// S_j = (w_j / kappa) (1/ntr) sum_tr sum_k wt_k (mu_k - mu_0) e^{-g t_k} sin(w_j t_k) dt
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_spectrum(const double* __restrict__ trace, long long ntr, long long npts,
+                                                  double dt, double kappa, double gamma, double wmin,
+                                                  double dw, double* __restrict__ om_out,
+                                                  double* __restrict__ S) {
+  __shared__ double red[32];
+  const long long j = blockIdx.x;
+  const double w = wmin + dw * (double)j;
+  double acc = 0.0;
+  for (long long tr = 0; tr < ntr; ++tr) {
+    const double* mu = trace + tr * npts;
+    const double mu0 = mu[0];
+    for (long long k = threadIdx.x; k < npts; k += blockDim.x) {
+      const double t = dt * (double)k;
+      const double wt = (k == 0 || k == npts - 1) ? 0.5 : 1.0;
+      acc += wt * (mu[k] - mu0) * exp(-gamma * t) * sin(w * t);
+    }
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    S[j] = (w / kappa) * acc * dt / (double)ntr;
+    om_out[j] = w;
+  }
+}
+
+}  // namespace rttda

@@ -1,0 +1,188 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle."""
+import numpy as np
+import pytest
+
+from oracle import rttda_oracle as orc
+from paper_2601_16949_b300 import synth
+from tests._util import oracle_runs, oracle_sigma, to_ri, unit
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rb():
+    from paper_2601_16949_b300 import binding
+    return binding
+
+
+PULSES4 = [
+    dict(kind=1, E0=0.03, omega=0.7, direction=(0, 0, 1)),                          # CW
+    dict(kind=2, E0=0.05, omega=0.9, t0=2.0, fwhm=1.7, direction=(1, 0, 0)),         # TL
+    dict(kind=3, E0=0.04, omega=0.6, t0=1.5, fwhm=2.5, beta=0.3, direction=(0, 1, 1)),  # chirp
+    dict(kind=4, E0=0.05, omega=1.1, duration=4.0, direction=(1, 1, 0)),             # sin^2
+]
+
+
+def _sigma_gpu(rb, prop, c, t):
+    cd = torch.tensor(to_ri(c), dtype=torch.float64, device="cuda")
+    sd = torch.zeros_like(cd)
+    rb.rttda_sigma(prop.h, cd.data_ptr(), t, sd.data_ptr(), 0)
+    torch.cuda.synchronize()
+    s = sd.cpu().numpy()
+    return s[..., 0] + 1j * s[..., 1]
+
+
+@pytest.mark.parametrize("shape", [(3, 5, 7), (1, 1, 1), (5, 37, 19), (17, 70, 33)])
+def test_sigma_fp64_matches_oracle(rb, shape):
+    mol = synth.molecule(*shape, seed=4)
+    c_x = 0.2
+    prop = rb.Propagator(mol, c_x, "fp64")
+    prop.set_field(PULSES4)
+    n = prop.n
+    c = synth.random_state(n, len(PULSES4), seed=7)
+    for t in (0.0, 1.3, 2.7):
+        got = _sigma_gpu(rb, prop, c, t)
+        ref = oracle_sigma(mol, c_x, PULSES4, c, t)
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(got - ref)) < 1e-13 * max(scale, 1.0), (shape, t)
+    prop.close()
+
+
+@pytest.mark.parametrize("shape", [(3, 5, 7), (17, 70, 33)])
+def test_sigma_fp32_matches_oracle(rb, shape):
+    mol = synth.molecule(*shape, seed=5)
+    c_x = 0.2
+    prop = rb.Propagator(mol, c_x, "fp32")
+    prop.set_field(PULSES4)
+    c = synth.random_state(prop.n, len(PULSES4), seed=8)
+    got = _sigma_gpu(rb, prop, c, 1.1)
+    ref = oracle_sigma(mol, c_x, PULSES4, c, 1.1)
+    err = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    assert np.all(err < 2e-6), err
+    prop.close()
+
+
+def test_config1_fp64_2000_steps_within_1e10(rb):
+    """o=8, v=24, P=96, z kick kappa=1e-3 from |0>, c_x=0.2, dt=0.05,
+    2000 RK4 steps: max |dc| <= 1e-10 against the dense oracle."""
+    mol = synth.molecule(8, 24, 96, seed=0)
+    pulses = [dict(kind=0, E0=1e-3, direction=(0, 0, 1))]
+    prop = rb.Propagator(mol, 0.2, "fp64")
+    prop.set_field(pulses)
+    c, dip, nrm = prop.propagate(0.05, 2000)
+    ref = oracle_runs(mol, 0.2, pulses, 0.05, 2000)[0]
+    assert np.max(np.abs(c[0] - ref.c)) <= 1e-10
+    assert np.max(np.abs(dip[0] - ref.dipole)) <= 1e-10 * max(1.0, np.max(np.abs(ref.dipole)))
+    assert np.max(np.abs(nrm[0] - ref.norm)) <= 1e-12
+    prop.close()
+
+
+def test_fp64_pulses_batch_matches_oracle(rb):
+    mol = synth.molecule(4, 9, 11, seed=2)
+    prop = rb.Propagator(mol, 0.3, "fp64")
+    prop.set_field(PULSES4)
+    c, dip, nrm = prop.propagate(0.05, 120)
+    refs = oracle_runs(mol, 0.3, PULSES4, 0.05, 120)
+    for t, ref in enumerate(refs):
+        assert np.max(np.abs(c[t] - ref.c)) < 1e-12, t
+        assert np.max(np.abs(dip[t] - ref.dipole)) < 1e-11, t
+        assert np.max(np.abs(nrm[t] - ref.norm)) < 1e-13, t
+    prop.close()
+
+
+def test_fp64_from_given_initial_state(rb):
+    mol = synth.molecule(3, 6, 5, seed=3)
+    pulses = [dict(kind=1, E0=0.02, omega=0.5, direction=(0, 1, 0)), dict(kind=0, E0=0.01, direction=(1, 0, 0))]
+    prop = rb.Propagator(mol, 0.2, "fp64")
+    prop.set_field(pulses)
+    c0 = synth.random_state(prop.n, 2, seed=9)
+    c, dip, nrm = prop.propagate(0.04, 50, c0=c0)
+    refs = oracle_runs(mol, 0.2, pulses, 0.04, 50, c0=c0)
+    for t, ref in enumerate(refs):
+        assert np.max(np.abs(c[t] - ref.c)) < 1e-12
+    prop.close()
+
+
+def test_batch_equals_solo(rb):
+    mol = synth.molecule(6, 20, 24, seed=6)
+    prop = rb.Propagator(mol, 0.2, "fp64")
+    prop.set_field(PULSES4)
+    cb, db, nb = prop.propagate(0.05, 60)
+    for t, p in enumerate(PULSES4):
+        prop.set_field([p])
+        cs, ds, ns = prop.propagate(0.05, 60)
+        assert np.max(np.abs(cs[0] - cb[t])) < 1e-14
+        assert np.max(np.abs(ds[0] - db[t])) < 1e-13
+    prop.close()
+
+
+def test_resume_is_bitwise(rb):
+    mol = synth.molecule(5, 12, 17, seed=8)
+    pulses = [PULSES4[1], PULSES4[3]]
+    a = rb.Propagator(mol, 0.2, "fp64")
+    a.set_field(pulses)
+    c_full, d_full, _ = a.propagate(0.05, 80)
+    a.propagate(0.05, 40)
+    state, t = a.get_state()
+    assert t == pytest.approx(2.0)
+    b = rb.Propagator(mol, 0.2, "fp64")
+    b.set_field(pulses)
+    b.set_state(state, t)
+    c_res, d_res, _ = b.resume(0.05, 40)
+    assert np.array_equal(c_res, c_full)
+    assert np.array_equal(d_res[:, -1], d_full[:, -1])
+    a.close()
+    b.close()
+
+
+def test_spectrum_kernel_matches_oracle(rb):
+    rng = np.random.default_rng(3)
+    tr = np.cumsum(rng.standard_normal((3, 2001)), axis=1) * 1e-3
+    om, S = rb.rttda_spectrum(tr, 0.05, 1e-3, 1e-3, 0.1, 2.0, 257)
+    ref = orc.spectrum(tr, 0.05, 1e-3, 1e-3, orc.frequency_grid(0.1, 2.0, 257))
+    assert np.allclose(om, orc.frequency_grid(0.1, 2.0, 257), rtol=0, atol=1e-15)
+    assert np.max(np.abs(S - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_errors_are_reported(rb):
+    mol = synth.molecule(2, 3, 4, seed=1)
+    prop = rb.Propagator(mol, 0.2, "fp64")
+    with pytest.raises(rb.RTTDAError) as e:
+        prop.propagate(0.05, 3)
+    assert e.value.status == rb.E_STATE
+    with pytest.raises(rb.RTTDAError) as e:
+        rb.rttda_set_field(prop.h, [dict(kind=9)])
+    assert e.value.status == rb.E_ARG
+    prop.set_field([dict(kind=0, E0=1e-3)])
+    with pytest.raises(rb.RTTDAError) as e:
+        prop.propagate(-0.05, 3)
+    assert e.value.status == rb.E_ARG
+    prop.close()
+
+
+def test_config2_sampled_rows_fp64_and_fp32(rb):
+    """Full-size o=64, v=448, P=1536 molecule: one sigma on a random batch of
+    three x/y/z trajectories, checked row by row against the oracle's
+    element-wise A and M rows."""
+    mol = synth.molecule(64, 448, 1536, seed=0)
+    pulses = [dict(kind=1, E0=0.01, omega=0.5, direction=d) for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1))]
+    n = 1 + 64 * 448
+    c = synth.random_state(n, 3, seed=11)
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([[0, 1, n - 1], rng.choice(np.arange(2, n - 1), 29, replace=False)])
+    t = 0.9
+    Arows = orc.A_rows(mol, 0.2, rows)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 3e-6)):
+        prop = rb.Propagator(mol, 0.2, prec)
+        prop.set_field(pulses)
+        got = _sigma_gpu(rb, prop, c, t)
+        prop.close()
+        for k, p in enumerate(pulses):
+            Mrows = orc.M_rows(*orc.dipole_along(mol, unit(p["direction"])), rows)
+            E = orc.field(orc.Pulse(kind=1, E0=0.01, omega=0.5), t)
+            ref = Arows @ c[k] - E * (Mrows @ c[k])
+            scale = np.abs(Arows) @ np.abs(c[k]) + abs(E) * (np.abs(Mrows) @ np.abs(c[k]))
+            err = np.abs(got[k, rows] - ref) / np.maximum(scale, 1e-300)
+            assert np.max(err) < tol, (prec, k, np.max(err))

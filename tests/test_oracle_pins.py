@@ -105,6 +105,17 @@ def test_A_rows_equal_dense_rows():
     A = orc.build_A(mol, 0.25)
     rows = [0, 1, 7, 13, 24]
     assert np.allclose(orc.A_rows(mol, 0.25, rows), A[rows], rtol=0, atol=1e-15)
+    blk = orc.A_block(mol, 0.25, 1, 3)
+    assert np.allclose(blk, A[1 + 6:1 + 18], rtol=0, atol=1e-15)
+
+
+def test_sigma_complex_split_equals_complex_product():
+    mol = small_mol(2, 3, 4, seed=1)
+    A = orc.build_A(mol, 0.2)
+    M = orc.build_M(*orc.dipole_along(mol, (1, 0, 0)))
+    c = synth.random_state(A.shape[0], 1, seed=5)[0]
+    ref = (A.astype(complex) - 0.3 * M.astype(complex)) @ c
+    assert np.allclose(orc.sigma(A, M, 0.3, c), ref, rtol=0, atol=1e-15)
 
 
 # ---------------------------------------------------------------------------
