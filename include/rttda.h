@@ -65,14 +65,19 @@ typedef enum {
 /* Arithmetic used for the factor contractions (Coulomb, exchange, field).
  * The RK4 amplitude state, the norm and the dipole expectation are FP64 in
  * every mode.
- *   FP64: all contractions in FP64 (CUDA cores).
- *   FP32: factors and contractions in FP32 (CUDA cores), FP64 state.
- *   TF32: factors stored FP32; exchange on tcgen05 tensor cores in TF32 with
- *         FP32 accumulation; Coulomb and field in FP32.
- *   BF16: factors stored BF16; exchange on tcgen05 tensor cores in BF16 with
- *         FP32 accumulation; Coulomb with BF16 factors, FP32 accumulation;
- *         field in FP32. */
-typedef enum { RTTDA_FP64 = 0, RTTDA_FP32 = 1, RTTDA_TF32 = 2, RTTDA_BF16 = 3 } rttda_prec;
+ *   FP64:   all contractions in FP64 (CUDA cores).
+ *   FP32:   factors and contractions in FP32 (CUDA cores).
+ *   TF32:   reserved (rejected with RTTDA_E_ARG by this version).
+ *   BF16:   exchange on tcgen05 tensor cores with BF16 factors and BF16
+ *           activations, FP32 accumulation; Coulomb with BF16 factors and
+ *           FP32 arithmetic; field in FP32.
+ *   BF16X3: exchange on tcgen05 tensor cores with every operand split into
+ *           BF16 hi + lo parts (x = hi + lo) and the products hi*hi + hi*lo +
+ *           lo*hi accumulated in FP32 (about 16 significant bits per
+ *           operand); Coulomb and field in FP32 on CUDA cores. */
+typedef enum {
+  RTTDA_FP64 = 0, RTTDA_FP32 = 1, RTTDA_TF32 = 2, RTTDA_BF16 = 3, RTTDA_BF16X3 = 4
+} rttda_prec;
 
 /* Pulse shapes E(t) (Sec. 2.2, Eqs. delta_pulse, continuous wave,
  * transform_limited, chirped_pulse) plus a sin^2 envelope:
@@ -161,6 +166,11 @@ rttda_status rttda_propagate(rttda_t h, const double* c0, double dt, long nsteps
 rttda_status rttda_propagate_device(rttda_t h, const double* c0_dev, double dt, long nsteps,
                                     double* c_out_dev, double* dipole_dev, double* norm_dev,
                                     void* stream);
+
+/* Wait for the work enqueued on `stream` (NULL = the handle's stream) and
+ * report device-side failures: RTTDA_E_TIMEOUT if a bounded wait inside a
+ * tensor-core kernel ran out (the results of that call are invalid). */
+rttda_status rttda_sync(rttda_t h, void* stream);
 
 /* Continue from the handle's current state and time (no kick).  Buffers as
  * in rttda_propagate; entry 0 of each trace is the current state.

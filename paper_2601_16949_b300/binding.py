@@ -26,8 +26,8 @@ lib = ct.CDLL(LIB_PATH)
 OK, E_ARG, E_OOM, E_CUDA, E_TIMEOUT, E_STATE, E_BUSY = range(7)
 STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_OOM", 3: "E_CUDA", 4: "E_TIMEOUT", 5: "E_STATE", 6: "E_BUSY"}
 # precisions (rttda_prec)
-FP64, FP32, TF32, BF16 = 0, 1, 2, 3
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
+FP64, FP32, TF32, BF16, BF16X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
 # pulse kinds (rttda_pulse_kind)
 KICK, CW, GAUSS_TL, CHIRP, SIN2 = 0, 1, 2, 3, 4
 
@@ -63,6 +63,7 @@ lib.rttda_set_state.argtypes = [_h, _dp, ct.c_double]
 lib.rttda_sigma.argtypes = [_h, ct.c_void_p, ct.c_double, ct.c_void_p, ct.c_void_p]
 lib.rttda_spectrum.argtypes = [_dp, ct.c_long, ct.c_long, ct.c_double, ct.c_double, ct.c_double, ct.c_double,
                                ct.c_double, ct.c_long, _dp, _dp]
+lib.rttda_sync.argtypes = [_h, ct.c_void_p]
 lib.rttda_profile.argtypes = [_h, ct.c_int]
 lib.rttda_profile_read.argtypes = [_h, _dp, ct.POINTER(ct.c_longlong)]
 lib.rttda_launch_stats.argtypes = [_h, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]
@@ -70,7 +71,7 @@ lib.rttda_destroy.argtypes = [_h]
 lib.rttda_destroy.restype = None
 for _name in ("rttda_create", "rttda_memory_bytes", "rttda_set_field", "rttda_propagate", "rttda_propagate_device",
               "rttda_resume", "rttda_get_state", "rttda_set_state", "rttda_sigma", "rttda_spectrum",
-              "rttda_profile", "rttda_profile_read", "rttda_launch_stats"):
+              "rttda_profile", "rttda_profile_read", "rttda_launch_stats", "rttda_sync"):
     getattr(lib, _name).restype = ct.c_int
 
 
@@ -173,6 +174,10 @@ def rttda_get_state(h, c) -> float:
 
 def rttda_set_state(h, c, t) -> None:
     _check(lib.rttda_set_state(h, _ptr(c), float(t)), "rttda_set_state")
+
+
+def rttda_sync(h, stream=0) -> None:
+    _check(lib.rttda_sync(h, stream or None), "rttda_sync")
 
 
 def rttda_sigma(h, c_dev, t, sigma_dev, stream=0) -> None:

@@ -1,5 +1,7 @@
 // RT-TDA engine: device buffers, precision plan, RK4 schedule, CUDA graphs,
 // and the C ABI declared in include/rttda.h.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,6 +15,7 @@
 #include "../../include/rttda.h"
 #include "engine_internal.h"
 #include "kernels_simt.cuh"
+#include "tc_gemm.cuh"
 
 using namespace rttda;
 
@@ -130,6 +133,19 @@ struct rttda_ctx {
   bool have_state = false;
   double t_now = 0.0;
 
+  // tensor-core exchange (BF16 / BF16X3): padded BF16 planes and TMA maps
+  bool tc = false;
+  int nplanes = 1, nprod = 1, vp = 0, op = 0, tc_bn = 256;
+  __nv_bfloat16* Bvv_tc = nullptr;  // [plane][P][vp][vp]
+  __nv_bfloat16* Boo_tc = nullptr;  // [plane][P*o][op]
+  __nv_bfloat16* Xt = nullptr;      // [plane][C*vp][op]
+  __nv_bfloat16* Zk = nullptr;      // [plane][C*o][zchunk*vp]
+  size_t zplane = 0;
+  std::vector<CUtensorMap> tmZA, tmMA, tmMB;
+  CUtensorMap tmZB;
+  std::vector<int> tc_kper;
+  int* d_err = nullptr;
+
   // host staging for the host-buffer entry points
   double* h_io = nullptr;  // device staging [T][N][2] + traces
   size_t h_io_count = 0;
@@ -143,6 +159,7 @@ struct rttda_ctx {
 
   ~rttda_ctx();
   rttda_status alloc_batch();
+  rttda_status alloc_tc(int C);
   void free_batch();
 };
 
@@ -159,12 +176,15 @@ rttda_ctx::~rttda_ctx() {
   dfree(mu_oo);
   dfree(mu_vv);
   dfree(mu_0);
+  dfree(Bvv_tc);
+  dfree(Boo_tc);
+  dfree(d_err);
   if (stream) cudaStreamDestroy(stream);
 }
 
 void rttda_ctx::free_batch() {
   void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xn, Xs, acc, F, E, term,
-                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io};
+                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk};
   for (void* p : ps) dfree(p);
   d_pulses = nullptr;
   d_kappa = d_dirs = moo64 = mvv64 = m064 = nullptr;
@@ -172,6 +192,11 @@ void rttda_ctx::free_batch() {
   Xn = Xs = acc = F = E = term = obs_part = Xq = nullptr;
   d_step = nullptr;
   w = Jpart = Zt = Kpart = nullptr;
+  Xt = Zk = nullptr;
+  tmZA.clear();
+  tmMA.clear();
+  tmMB.clear();
+  tc_kper.clear();
   h_io = nullptr;
   h_io_count = 0;
   T = 0;
@@ -213,7 +238,84 @@ struct Prof {
 // ---------------------------------------------------------------------------
 namespace {
 
-template <typename TF, typename TC>
+// --- tensor-core exchange -------------------------------------------------
+constexpr int kZBN = 256, kZStages = 3;   // Z = B_oo c   (K = nocc, short)
+constexpr int kMStages = 4;               // main contraction over (P, b)
+
+template <int BN, int ST, int BM, int EP>
+void tc_launch(dim3 g, const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s) {
+  tc::k_tc_gemm<BN, ST, BM, EP><<<g, tc::kThreads, tc::smem_bytes<BN, ST>(), s>>>(a, b, prm);
+}
+
+template <int BN, int ST, int BM, int EP>
+void tc_attr() {
+  cudaFuncSetAttribute(tc::k_tc_gemm<BN, ST, BM, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::smem_bytes<BN, ST>());
+}
+
+void set_tc_smem_limits() {
+  tc_attr<kZBN, kZStages, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>();
+  tc_attr<128, kMStages + 2, tc::BMODE_VV, tc::EPI_PARTIAL>();
+  tc_attr<224, kMStages, tc::BMODE_VV, tc::EPI_PARTIAL>();
+  tc_attr<256, kMStages, tc::BMODE_VV, tc::EPI_PARTIAL>();
+}
+
+void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
+  const int C = 2 * h->T, o = h->o, v = h->v, vp = h->vp, op = h->op;
+  {
+    Prof pr(h, RTTDA_KC_EXCHANGE_Z, s);
+    h->launches += 1;
+    const long long tot = (long long)C * vp * op;
+    k_prep_xt<<<blocks_for(tot, 256), 256, 0, s>>>(o, v, vp, op, C, X, h->Xt, h->nplanes > 1 ? h->Xt + tot : nullptr);
+  }
+  for (int c = 0, p0 = 0; p0 < h->P; p0 += h->zchunk, ++c) {
+    const int pc = std::min(h->zchunk, h->P - p0);
+    {
+      // Z^P_(col,i),b = sum_j B^P_ij c_(j,b),col for P in the chunk (BF16 planes out)
+      Prof pr(h, RTTDA_KC_EXCHANGE_Z, s);
+      h->launches += 1;
+      tc::Params prm{};
+      prm.M = pc * o;
+      prm.N = C * vp;
+      prm.kt_total = (int)cdiv(op, tc::kBK);
+      prm.kt_per_split = prm.kt_total;
+      prm.nprod = h->nprod;
+      prm.zhi = h->Zk;
+      prm.zlo = h->nplanes > 1 ? h->Zk + h->zplane : nullptr;
+      prm.o = o;
+      prm.vp = vp;
+      prm.zld = (long long)pc * vp;
+      prm.err = h->d_err;
+      dim3 g(blocks_for((long long)C * vp, kZBN), blocks_for((long long)pc * o, tc::kBM), 1);
+      tc_launch<kZBN, kZStages, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>(g, h->tmZA[c], h->tmZB, prm, s);
+    }
+    {
+      // K_(col,i),a (+)= sum_{P in chunk, b} Z^P_(col,i),b B^P_ab   (split-K)
+      Prof pr(h, RTTDA_KC_EXCHANGE_MAIN, s);
+      h->launches += 1;
+      tc::Params prm{};
+      prm.M = C * o;
+      prm.N = v;
+      prm.kt_total = pc * (vp / tc::kBK);
+      prm.kt_per_split = h->tc_kper[c];
+      prm.nprod = h->nprod;
+      prm.vtiles = vp / tc::kBK;
+      prm.out = (float*)h->Kpart;
+      prm.ldo = v;
+      prm.split_stride = (long long)C * o * v;
+      prm.accum = c > 0 ? 1 : 0;
+      prm.err = h->d_err;
+      dim3 g(blocks_for(v, h->tc_bn), blocks_for((long long)C * o, tc::kBM), h->SK);
+      switch (h->tc_bn) {
+        case 128: tc_launch<128, kMStages + 2, tc::BMODE_VV, tc::EPI_PARTIAL>(g, h->tmMA[c], h->tmMB[c], prm, s); break;
+        case 224: tc_launch<224, kMStages, tc::BMODE_VV, tc::EPI_PARTIAL>(g, h->tmMA[c], h->tmMB[c], prm, s); break;
+        default: tc_launch<256, kMStages, tc::BMODE_VV, tc::EPI_PARTIAL>(g, h->tmMA[c], h->tmMB[c], prm, s); break;
+      }
+    }
+  }
+}
+
+template <typename TF, typename TC, bool XTC>
 struct Ops {
   using TL = Tile<TC>;
 
@@ -230,6 +332,10 @@ struct Ops {
   }
 
   static void exchange(rttda_ctx* h, const double* X, cudaStream_t s) {
+    if (XTC) {
+      exchange_tc(h, X, s);
+      return;
+    }
     const int C = 2 * h->T, o = h->o, v = h->v;
     const int M = C * o;
     for (int p0 = 0, c = 0; p0 < h->P; p0 += h->zchunk, ++c) {
@@ -286,15 +392,18 @@ struct Ops {
 
   static void set_smem_limits() {
     cudaFuncSetAttribute(k_coul_J<TF, TC, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (XTC) set_tc_smem_limits();
   }
 };
 
 template <typename F>
 void dispatch(int prec, F&& f) {
-  if (prec == RTTDA_FP64)
-    f(Ops<double, double>{});
-  else
-    f(Ops<float, float>{});
+  switch (prec) {
+    case RTTDA_FP64: f(Ops<double, double, false>{}); break;
+    case RTTDA_FP32: f(Ops<float, float, false>{}); break;
+    case RTTDA_BF16: f(Ops<__nv_bfloat16, float, true>{}); break;
+    default: f(Ops<float, float, true>{}); break;  // RTTDA_BF16X3
+  }
 }
 
 // Exact kick exp(+i kappa M_d) on h->Xn (FP64 field products).
@@ -395,6 +504,104 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
 // ---------------------------------------------------------------------------
 // Batch set-up
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// TMA tensor maps (driver entry point; no link-time dependency on libcuda)
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+// BF16 tile map with 128-byte swizzle; dims/box innermost first, strides in
+// bytes for dims 1..rank-1.
+static rttda_status bf16_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
+                             const uint64_t* strides, const uint32_t* box) {
+  auto enc = tmap_encoder();
+  if (!enc) return set_error(RTTDA_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base),
+                   reinterpret_cast<const cuuint64_t*>(dims), reinterpret_cast<const cuuint64_t*>(strides),
+                   reinterpret_cast<const cuuint32_t*>(box), es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(RTTDA_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return RTTDA_OK;
+}
+
+// Buffers, split-K plan and TMA maps of the tensor-core exchange for C columns.
+static rttda_status alloc_tc(rttda_ctx* h, int C) {
+  const int o = h->o, v = h->v, P = h->P, vp = h->vp, op = h->op;
+  const size_t xt = (size_t)C * vp * op;
+  CKS(dalloc(&h->Xt, xt * h->nplanes));
+  // Z chunk: C*o rows of zchunk*vp BF16 per plane, at most ~2 GiB in total
+  const size_t zper = (size_t)C * o * vp * 2 * h->nplanes;
+  h->zchunk = (int)std::max<size_t>(1, std::min<size_t>(P, ((size_t)2 << 30) / std::max<size_t>(zper, 1)));
+  h->zplane = (size_t)C * o * h->zchunk * vp;
+  CKS(dalloc(&h->Zk, h->zplane * h->nplanes));
+  // main contraction tile width along a (N = nvirt)
+  int best = 256;
+  long long bestw = -1;
+  for (int bn : {128, 224, 256}) {
+    const long long wasted = cdiv(v, bn) * bn;
+    if (bestw < 0 || wasted < bestw || (wasted == bestw && bn > best)) {
+      best = bn;
+      bestw = wasted;
+    }
+  }
+  h->tc_bn = best;
+  const long long tiles = cdiv((long long)C * o, tc::kBM) * cdiv(v, best);
+  const long long kt_full = (long long)h->zchunk * (vp / tc::kBK);
+  h->SK = (int)std::max(1LL, std::min(kt_full, kNumSM / std::max(1LL, tiles)));
+  char* p = nullptr;
+  CK(cudaMalloc((void**)&p, (size_t)h->SK * C * o * v * sizeof(float)));
+  h->Kpart = p;
+  // maps
+  {
+    const uint64_t dims[3] = {(uint64_t)op, (uint64_t)C * vp, (uint64_t)h->nplanes};
+    const uint64_t str[2] = {(uint64_t)op * 2, (uint64_t)xt * 2};
+    const uint32_t box[3] = {64, (uint32_t)kZBN, 1};
+    CKS(bf16_map(&h->tmZB, h->Xt, 3, dims, str, box));
+  }
+  for (int p0 = 0; p0 < P; p0 += h->zchunk) {
+    const int pc = std::min(h->zchunk, P - p0);
+    CUtensorMap za, ma, mb;
+    {
+      const uint64_t dims[3] = {(uint64_t)op, (uint64_t)pc * o, (uint64_t)h->nplanes};
+      const uint64_t str[2] = {(uint64_t)op * 2, (uint64_t)P * o * op * 2};
+      const uint32_t box[3] = {64, 128, 1};
+      CKS(bf16_map(&za, h->Boo_tc + (size_t)p0 * o * op, 3, dims, str, box));
+    }
+    {
+      const uint64_t dims[3] = {(uint64_t)pc * vp, (uint64_t)C * o, (uint64_t)h->nplanes};
+      const uint64_t str[2] = {(uint64_t)pc * vp * 2, (uint64_t)h->zplane * 2};
+      const uint32_t box[3] = {64, 128, 1};
+      CKS(bf16_map(&ma, h->Zk, 3, dims, str, box));
+    }
+    {
+      const uint64_t dims[4] = {(uint64_t)vp, (uint64_t)vp, (uint64_t)pc, (uint64_t)h->nplanes};
+      const uint64_t str[3] = {(uint64_t)vp * 2, (uint64_t)vp * vp * 2, (uint64_t)P * vp * vp * 2};
+      const uint32_t box[4] = {64, (uint32_t)best, 1, 1};
+      CKS(bf16_map(&mb, h->Bvv_tc + (size_t)p0 * vp * vp, 4, dims, str, box));
+    }
+    h->tmZA.push_back(za);
+    h->tmMA.push_back(ma);
+    h->tmMB.push_back(mb);
+    const long long kt = (long long)pc * (vp / tc::kBK);
+    h->tc_kper.push_back((int)cdiv(kt, h->SK));
+  }
+  return RTTDA_OK;
+}
+
+rttda_status rttda_ctx::alloc_tc(int C) { return ::alloc_tc(this, C); }
+
 rttda_status rttda_ctx::alloc_batch() {
   const int C = 2 * T;
   const long long NC = N * C;
@@ -420,8 +627,8 @@ rttda_status rttda_ctx::alloc_batch() {
     CK(cudaMalloc((void**)&p, (size_t)SJ * ov * C * cbytes));
     Jpart = p;
   }
-  // exchange scratch: Z for a chunk of P (at most ~1 GiB), split-K partials
-  {
+  // exchange scratch: Z for a chunk of P (bounded size), split-K partials
+  if (!tc) {
     const size_t zper = (size_t)v * C * o * cbytes;
     const size_t zbudget = (size_t)1 << 30;
     zchunk = (int)std::max<size_t>(1, std::min<size_t>(P, zbudget / std::max<size_t>(zper, 1)));
@@ -436,6 +643,8 @@ rttda_status rttda_ctx::alloc_batch() {
     SK = (int)std::max(1LL, std::min(kchunks, cdiv(4 * kNumSM, tiles)));
     CK(cudaMalloc((void**)&p, (size_t)SK * C * o * v * cbytes));
     Kpart = p;
+  } else {
+    CKS(alloc_tc(C));
   }
   obsG = (int)std::max(1LL, std::min(1024LL, cdiv(N, 2048)));
   obs_rows = cdiv(N, obsG);
@@ -460,19 +669,45 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
       if (p) cudaFree(p);
     }
   } guard{stage};
-  if (h->prec != RTTDA_FP64) CKS(dalloc(&stage, stage_n));
+  if (h->prec != RTTDA_FP64) CKS(dalloc(&stage, std::max(stage_n, h->tc ? std::max(v * v, o * o) : (size_t)1)));
+  CKS(dalloc(&h->d_err, 1));
+  CK(cudaMemset(h->d_err, 0, sizeof(int)));
   auto upload = [&](const double* src, size_t n, void** dst) -> rttda_status {
     CK(cudaMalloc(dst, std::max<size_t>(n, 1) * h->fbytes));
     for (size_t off = 0; off < n; off += chunk) {
       const size_t m = std::min(chunk, n - off);
-      if (h->prec == RTTDA_FP64) {
+      if (h->fbytes == 8) {
         CK(cudaMemcpyAsync((double*)*dst + off, src + off, m * 8, cudaMemcpyHostToDevice, h->stream));
       } else {
         CK(cudaMemcpyAsync(stage, src + off, m * 8, cudaMemcpyHostToDevice, h->stream));
-        k_cast<float><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, stage, (float*)*dst + off);
+        if (h->fbytes == 4)
+          k_cast<float><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, stage, (float*)*dst + off);
+        else
+          k_cast<__nv_bfloat16><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, stage, (__nv_bfloat16*)*dst + off);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(h->stream));
       }
+    }
+    return RTTDA_OK;
+  };
+  // tensor-core operands: BF16 hi (and lo) planes with zero padding, packed
+  // slab by slab of whole P
+  auto pack = [&](const double* src, size_t slab, size_t out_slab, bool vv, __nv_bfloat16** dst) -> rttda_status {
+    const size_t plane = P * out_slab;
+    CK(cudaMalloc((void**)dst, plane * h->nplanes * 2));
+    const size_t per = std::max<size_t>(1, chunk / std::max<size_t>(slab, 1));
+    for (size_t p0 = 0; p0 < P; p0 += per) {
+      const size_t pc = std::min(per, P - p0);
+      CK(cudaMemcpyAsync(stage, src + p0 * slab, pc * slab * 8, cudaMemcpyHostToDevice, h->stream));
+      __nv_bfloat16* hi = *dst + p0 * out_slab;
+      __nv_bfloat16* lo = h->nplanes > 1 ? hi + plane : nullptr;
+      const long long tot = (long long)(pc * out_slab);
+      if (vv)
+        k_pack_vv<<<blocks_for(tot, 256), 256, 0, h->stream>>>((int)pc, h->v, h->vp, stage, hi, lo);
+      else
+        k_pack_oo<<<blocks_for(tot, 256), 256, 0, h->stream>>>((int)pc, h->o, h->op, stage, hi, lo);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(h->stream));
     }
     return RTTDA_OK;
   };
@@ -482,8 +717,13 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
     return RTTDA_OK;
   };
   CKS(upload(B_ov, P * o * v, &h->Bov));
-  CKS(upload(B_oo, P * o * o, &h->Boo));
-  CKS(upload(B_vv, P * v * v, &h->Bvv));
+  if (h->tc) {
+    CKS(pack(B_oo, o * o, o * (size_t)h->op, false, &h->Boo_tc));
+    CKS(pack(B_vv, v * v, (size_t)h->vp * h->vp, true, &h->Bvv_tc));
+  } else {
+    CKS(upload(B_oo, P * o * o, &h->Boo));
+    CKS(upload(B_vv, P * v * v, &h->Bvv));
+  }
   CKS(upload64(eps_occ, o, &h->eps_o));
   CKS(upload64(eps_virt, v, &h->eps_v));
   CKS(upload64(mu_oo, 3 * o * o, &h->mu_oo));
@@ -514,7 +754,7 @@ rttda_status rttda_create(int nocc, int nvirt, int naux, const double* eps_occ, 
   if (nocc < 1 || nvirt < 1 || naux < 1) return set_error(RTTDA_E_ARG, "rttda_create: nocc, nvirt, naux must be >= 1");
   if (!eps_occ || !eps_virt || !B_ov || !B_oo || !B_vv || !mu_oo || !mu_vv || !mu_0ov)
     return set_error(RTTDA_E_ARG, "rttda_create: NULL input array");
-  if (prec != RTTDA_FP64 && prec != RTTDA_FP32)
+  if (prec != RTTDA_FP64 && prec != RTTDA_FP32 && prec != RTTDA_BF16 && prec != RTTDA_BF16X3)
     return set_error(RTTDA_E_ARG, "rttda_create: unsupported precision");
   if (!std::isfinite(c_x)) return set_error(RTTDA_E_ARG, "rttda_create: c_x not finite");
 
@@ -526,8 +766,13 @@ rttda_status rttda_create(int nocc, int nvirt, int naux, const double* eps_occ, 
   h->N = 1 + h->ov;
   h->cx = c_x;
   h->prec = prec;
-  h->fbytes = prec == RTTDA_FP64 ? 8 : 4;
+  h->fbytes = prec == RTTDA_FP64 ? 8 : prec == RTTDA_BF16 ? 2 : 4;
   h->cbytes = prec == RTTDA_FP64 ? 8 : 4;
+  h->tc = prec == RTTDA_BF16 || prec == RTTDA_BF16X3;
+  h->nplanes = prec == RTTDA_BF16X3 ? 2 : 1;
+  h->nprod = prec == RTTDA_BF16X3 ? 3 : 1;
+  h->vp = (int)cdiv(nvirt, 64) * 64;
+  h->op = (int)cdiv(nocc, 8) * 8;
 
   rttda_status st = create_impl(h, eps_occ, eps_virt, B_ov, B_oo, B_vv, mu_oo, mu_vv, mu_0ov);
   if (st != RTTDA_OK) {
@@ -541,7 +786,11 @@ rttda_status rttda_create(int nocc, int nvirt, int naux, const double* eps_occ, 
 rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes) {
   if (!h || !bytes) return set_error(RTTDA_E_ARG, "rttda_memory_bytes: NULL argument");
   const size_t o = h->o, v = h->v, P = h->P;
-  size_t b = (P * o * v + P * o * o + P * v * v) * h->fbytes + (o + v + 3 * (o * o + v * v + o * v)) * 8;
+  size_t b = P * o * v * h->fbytes + (o + v + 3 * (o * o + v * v + o * v)) * 8;
+  if (h->tc)
+    b += (P * o * (size_t)h->op + P * (size_t)h->vp * h->vp) * 2 * h->nplanes;
+  else
+    b += (P * o * o + P * v * v) * h->fbytes;
   if (h->T > 0) {
     const size_t C = 2 * h->T, NC = h->N * C;
     b += NC * 8 * 6 + (size_t)P * C * h->cbytes + (size_t)h->SJ * h->ov * C * h->cbytes +
@@ -645,6 +894,7 @@ static rttda_status propagate_impl(rttda_t h, bool fresh, const double* c0_dev, 
   if (nsteps < 0) return set_error(RTTDA_E_ARG, "rttda_propagate: nsteps must be >= 0");
   const long long NT = h->N * h->T;
   double t_call = 0.0;
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
   if (fresh) {
     if (c0_dev)
       k_abi_to_dev<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, c0_dev, h->Xn);
@@ -683,6 +933,16 @@ rttda_status rttda_propagate_device(rttda_t h, const double* c0_dev, double dt, 
   return propagate_impl(h, true, c0_dev, dt, nsteps, c_out_dev, dipole_dev, norm_dev, s);
 }
 
+// A bounded device wait that ran out leaves a code in d_err.
+static rttda_status check_device_error(rttda_t h) {
+  int e = 0;
+  CK(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0)
+    return set_error(RTTDA_E_TIMEOUT, "a tensor-core pipeline wait exceeded its time limit (code " +
+                                          std::to_string(e) + ")");
+  return RTTDA_OK;
+}
+
 static rttda_status host_call(rttda_t h, bool fresh, const double* c0, double dt, long nsteps, double* c_out,
                               double* dip, double* nrm) {
   if (h->T < 1) return set_error(RTTDA_E_STATE, "rttda_propagate: call rttda_set_field first");
@@ -709,7 +969,7 @@ static rttda_status host_call(rttda_t h, bool fresh, const double* c0, double dt
   if (dip) CK(cudaMemcpyAsync(dip, d_dip, TR * 8, cudaMemcpyDeviceToHost, s));
   if (nrm) CK(cudaMemcpyAsync(nrm, d_nrm, TR * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  return RTTDA_OK;
+  return check_device_error(h);
 }
 
 rttda_status rttda_propagate(rttda_t h, const double* c0, double dt, long nsteps, double* c_out,
@@ -762,6 +1022,7 @@ rttda_status rttda_sigma(rttda_t h, const double* c_dev, double t, double* sigma
   if (!std::isfinite(t)) return set_error(RTTDA_E_ARG, "rttda_sigma: t not finite");
   cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
   const long long NT = h->N * h->T;
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
   k_abi_to_dev<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, c_dev, h->Xq);
   // E at time t goes to slot 0 of the stage table (step counter 0, stage 0)
   CK(cudaMemsetAsync(h->d_step, 0, sizeof(long long), s));
@@ -810,6 +1071,13 @@ rttda_status rttda_spectrum(const double* trace, long ntraces, long npts, double
   cleanup();
   if (e != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("rttda_spectrum: ") + cudaGetErrorString(e));
   return RTTDA_OK;
+}
+
+rttda_status rttda_sync(rttda_t h, void* stream) {
+  g_last_error.clear();
+  if (!h) return set_error(RTTDA_E_ARG, "rttda_sync: NULL handle");
+  CK(cudaStreamSynchronize(stream ? (cudaStream_t)stream : h->stream));
+  return check_device_error(h);
 }
 
 rttda_status rttda_profile(rttda_t h, int enable) {

@@ -616,3 +616,64 @@ __global__ void __launch_bounds__(256) k_spectrum(const double* __restrict__ tra
 }
 
 }  // namespace rttda
+
+namespace rttda {
+
+// ---------------------------------------------------------------------------
+// Tensor-core operand packing (BF16 planes; lo = bf16(x - hi), zero padding)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __double2bfloat16(x);
+  l = __double2bfloat16(x - (double)__bfloat162float(h));
+}
+
+// B^P_ab [pc][v][v] (FP64) -> planes [plane][P][vp][vp], slab p0..p0+pc
+__global__ void k_pack_vv(int pc, int v, int vp, const double* __restrict__ src, __nv_bfloat16* __restrict__ hi,
+                          __nv_bfloat16* __restrict__ lo) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tot = (long long)pc * vp * vp;
+  if (e >= tot) return;
+  const int b = (int)(e % vp);
+  const int a = (int)((e / vp) % vp);
+  const long long p = e / ((long long)vp * vp);
+  const double x = (a < v && b < v) ? src[(p * v + a) * v + b] : 0.0;
+  __nv_bfloat16 h, l;
+  split_bf16(x, h, l);
+  hi[e] = h;
+  if (lo) lo[e] = l;
+}
+
+// B^P_ij [pc][o][o] (FP64) -> planes [plane][(P, i)][op]
+__global__ void k_pack_oo(int pc, int o, int op, const double* __restrict__ src, __nv_bfloat16* __restrict__ hi,
+                          __nv_bfloat16* __restrict__ lo) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tot = (long long)pc * o * op;
+  if (e >= tot) return;
+  const int j = (int)(e % op);
+  const long long r = e / op;  // (p, i)
+  const double x = j < o ? src[r * o + j] : 0.0;
+  __nv_bfloat16 h, l;
+  split_bf16(x, h, l);
+  hi[e] = h;
+  if (lo) lo[e] = l;
+}
+
+// Amplitudes -> Xt[plane][(col, b)][j] = X[1 + j v + b][col] (K-major B
+// operand of Z^P = B^P_oo c), zero for b >= v or j >= o.
+__global__ void k_prep_xt(int o, int v, int vp, int op, int C, const double* __restrict__ X,
+                          __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tot = (long long)C * vp * op;
+  if (e >= tot) return;
+  const int j = (int)(e % op);
+  const long long r = e / op;
+  const int b = (int)(r % vp);
+  const int col = (int)(r / vp);
+  const double x = (j < o && b < v) ? X[(1 + (size_t)j * v + b) * C + col] : 0.0;
+  __nv_bfloat16 h, l;
+  split_bf16(x, h, l);
+  hi[e] = h;
+  if (lo) lo[e] = l;
+}
+
+}  // namespace rttda

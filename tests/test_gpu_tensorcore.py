@@ -1,0 +1,120 @@
+"""GPU parity of the tcgen05 exchange paths (BF16 and BF16 hi/lo split)."""
+import numpy as np
+import pytest
+
+from oracle import rttda_oracle as orc
+from paper_2601_16949_b300 import synth
+from tests._util import oracle_runs, oracle_sigma, to_ri, unit
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PULSES = [
+    dict(kind=1, E0=0.03, omega=0.7, direction=(0, 0, 1)),
+    dict(kind=2, E0=0.05, omega=0.9, t0=2.0, fwhm=1.7, direction=(1, 0, 0)),
+    dict(kind=4, E0=0.05, omega=1.1, duration=4.0, direction=(1, 1, 0)),
+]
+
+
+@pytest.fixture(scope="module")
+def rb():
+    from paper_2601_16949_b300 import binding
+    return binding
+
+
+def _sigma_gpu(rb, prop, c, t):
+    cd = torch.tensor(to_ri(c), dtype=torch.float64, device="cuda")
+    sd = torch.zeros_like(cd)
+    rb.rttda_sigma(prop.h, cd.data_ptr(), t, sd.data_ptr(), 0)
+    rb.rttda_sync(prop.h)
+    s = sd.cpu().numpy()
+    return s[..., 0] + 1j * s[..., 1]
+
+
+def _two_electron_part(mol, c_x, c):
+    """(A - diag(e_a - e_i)) c: the part computed from the factors."""
+    m0 = dict(mol)
+    m0["eps_occ"] = np.zeros_like(mol["eps_occ"])
+    m0["eps_virt"] = np.zeros_like(mol["eps_virt"])
+    A2 = orc.build_A(m0, c_x)
+    return np.array([A2 @ ck for ck in c])
+
+
+@pytest.mark.parametrize("prec,tol2e", [("bf16x3", 2e-4), ("bf16", 3e-2)])
+@pytest.mark.parametrize("shape", [(3, 5, 7), (17, 70, 33), (64, 128, 40), (9, 192, 130)])
+def test_sigma_tensorcore_matches_oracle(rb, prec, tol2e, shape):
+    mol = synth.molecule(*shape, seed=12)
+    c_x = 0.2
+    prop = rb.Propagator(mol, c_x, prec)
+    prop.set_field(PULSES)
+    c = synth.random_state(prop.n, len(PULSES), seed=3)
+    got = _sigma_gpu(rb, prop, c, 1.4)
+    ref = oracle_sigma(mol, c_x, PULSES, c, 1.4)
+    s2e = np.max(np.abs(_two_electron_part(mol, c_x, c)), axis=1)
+    sall = np.max(np.abs(ref), axis=1)
+    err = np.max(np.abs(got - ref), axis=1)
+    assert np.all(err <= tol2e * s2e + 2e-6 * sall), (err, s2e, sall)
+    prop.close()
+
+
+def test_bf16x3_exchange_only_matches_oracle_tightly(rb):
+    """Isolate the exchange: zero Coulomb factors and orbital energies, no
+    field; the hi/lo split must reproduce the FP64 exchange to ~1e-4."""
+    mol = synth.molecule(32, 128, 64, seed=21)
+    mol["B_ov"][:] = 0.0
+    mol["eps_occ"][:] = 0.0
+    mol["eps_virt"][:] = 0.0
+    prop = rb.Propagator(mol, 1.0, "bf16x3")
+    prop.set_field([dict(kind=0, E0=0.0)])
+    c = synth.random_state(prop.n, 1, seed=4)
+    got = _sigma_gpu(rb, prop, c, 0.5)
+    A = orc.build_A(mol, 1.0)
+    ref = A @ c[0]
+    assert np.max(np.abs(got[0] - ref)) < 1e-4 * np.max(np.abs(ref))
+    prop.close()
+
+
+@pytest.mark.parametrize("prec,dip_tol", [("bf16x3", 2e-4), ("bf16", 5e-2)])
+def test_tensorcore_propagation_against_oracle(rb, prec, dip_tol):
+    mol = synth.molecule(8, 64, 48, seed=5)
+    pulses = [dict(kind=0, E0=1e-3, direction=d) for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1))]
+    prop = rb.Propagator(mol, 0.2, prec)
+    prop.set_field(pulses)
+    c, dip, nrm = prop.propagate(0.05, 400)
+    rb.rttda_sync(prop.h)
+    refs = oracle_runs(mol, 0.2, pulses, 0.05, 400)
+    for t, ref in enumerate(refs):
+        d = ref.dipole - ref.dipole[0]
+        rel = np.max(np.abs(dip[t] - ref.dipole)) / np.max(np.abs(d))
+        assert rel < dip_tol, (prec, t, rel)
+        assert np.max(np.abs(nrm[t] - ref.norm)) < 1e-6, (prec, t)
+    prop.close()
+
+
+def test_bf16x3_config2_sampled_rows(rb):
+    """Full-size o=64, v=448, P=1536: sampled rows of one sigma against the
+    oracle's element-wise rows."""
+    mol = synth.molecule(64, 448, 1536, seed=0)
+    pulses = [dict(kind=1, E0=0.01, omega=0.5, direction=d) for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1))]
+    n = 1 + 64 * 448
+    c = synth.random_state(n, 3, seed=11)
+    rng = np.random.default_rng(1)
+    rows = np.concatenate([[0, 1, n - 1], rng.choice(np.arange(2, n - 1), 21, replace=False)])
+    Arows = orc.A_rows(mol, 0.2, rows)
+    m0 = dict(mol)
+    m0["eps_occ"] = np.zeros(64)
+    m0["eps_virt"] = np.zeros(448)
+    A2rows = orc.A_rows(m0, 0.2, rows)
+    prop = rb.Propagator(mol, 0.2, "bf16x3")
+    prop.set_field(pulses)
+    got = _sigma_gpu(rb, prop, c, 0.9)
+    prop.close()
+    E = orc.field(orc.Pulse(kind=1, E0=0.01, omega=0.5), 0.9)
+    for k, p in enumerate(pulses):
+        Mrows = orc.M_rows(*orc.dipole_along(mol, unit(p["direction"])), rows)
+        ref = Arows @ c[k] - E * (Mrows @ c[k])
+        s2e = np.abs(A2rows) @ np.abs(c[k])
+        sall = np.abs(Arows) @ np.abs(c[k]) + abs(E) * (np.abs(Mrows) @ np.abs(c[k]))
+        err = np.abs(got[k, rows] - ref)
+        assert np.all(err <= 2e-4 * s2e + 2e-6 * sall + 1e-300), (k, np.max(err / np.maximum(s2e, 1e-300)))
