@@ -179,6 +179,71 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# Roofline: algorithmic work per launch of a kernel class
+# ---------------------------------------------------------------------------
+PREC_INFO = {  # factor bytes, exchange planes, tensor products per K tile
+    "fp64": dict(fb=8, planes=1, nprod=1, tensor=False),
+    "fp32": dict(fb=4, planes=1, nprod=1, tensor=False),
+    "bf16": dict(fb=2, planes=1, nprod=1, tensor=True),
+    "bf16x3": dict(fb=4, planes=2, nprod=3, tensor=True),
+}
+
+
+def algorithmic_work(prec: str, cls: str, T: int):
+    """(flop, bytes) of one launch of a kernel class on this workload.
+
+    exchange_main: sum_{P,b} Z^P_(col,i),b B^P_ab, M = 2T*nocc, N = nvirt,
+    K = naux*nvirt; bytes = Z and B_vv read once (all planes).  Flops count
+    every tensor product of the split (nprod x 2MNK)."""
+    pi = PREC_INFO[prec]
+    C = 2 * T
+    o, v, P = NOCC, NVIRT, NAUX
+    if cls == "exchange_main":
+        M, N, K = C * o, v, P * v
+        eb = 2 if pi["tensor"] else pi["fb"]
+        return pi["nprod"] * 2.0 * M * N * K, pi["planes"] * eb * (M * K + P * v * v)
+    if cls == "coulomb":
+        return 2 * 2.0 * P * o * v * C, 2.0 * P * o * v * (pi["fb"] if prec != "bf16x3" else 4)
+    if cls == "exchange_z":
+        eb = 2 if pi["tensor"] else pi["fb"]
+        return pi["nprod"] * 2.0 * P * o * o * v * C, pi["planes"] * eb * (P * o * v * C + P * o * o)
+    return None, None
+
+
+def roofline(prec: str, cls: str, prof_entry, T: int, peaks: dict) -> dict:
+    ms, n = prof_entry
+    flop, byts = algorithmic_work(prec, cls, T)
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    bf16 = peaks.get("bf16_tflops", 1800.0)
+    out = {"kernel": cls, "avg_launch_ms": ms / max(n, 1), "launches_timed": n, "traffic": None,
+           "flop_per_launch": flop, "bytes_per_launch": byts}
+    if flop is None or n == 0:
+        out.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None})
+        return out
+    sec = ms / n / 1e3
+    pi = PREC_INFO[prec]
+    if pi["tensor"]:
+        cpeak, cunit, csrc = bf16, "TFLOP/s", "measured bf16 burst (MEASURED_PEAKS.json)"
+        cbound = "tensor"
+    else:
+        lanes = 128 if prec == "fp32" else 64
+        cpeak = 148 * lanes * 2 * 2.032e9 / 1e12
+        cunit, cbound = "TFLOP/s", "alu"
+        csrc = f"derived: 148 SM x {lanes} {'FP32' if prec == 'fp32' else 'FP64'} FMA/clk x 2 x 2032 MHz"
+    t_comp = flop / (cpeak * 1e12)
+    t_mem = byts / (hbm * 1e9)
+    if t_mem >= t_comp:
+        out.update({"bound": "hbm", "achieved": byts / sec / 1e9, "peak": hbm, "unit": "GB/s",
+                    "peak_source": "measured HBM copy (MEASURED_PEAKS.json)"})
+    else:
+        out.update({"bound": cbound, "achieved": flop / sec / 1e12, "peak": cpeak, "unit": cunit,
+                    "peak_source": csrc})
+    out["frac"] = out["achieved"] / out["peak"]
+    out["other_bound_frac"] = (flop / sec / 1e12 / cpeak) if out["bound"] == "hbm" else (byts / sec / 1e9 / hbm)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args):
@@ -243,9 +308,16 @@ def run_gpu(args):
         torch.cuda.synchronize()
         barrier()
     launches1, per_step = rb.rttda_launch_stats(h)
+    rb.rttda_sync(h, sptr)
     ms = max_over_ranks(ev0.elapsed_time(ev1))
     value = world * T * K / (ms / 1e3)
     dip32 = dip.cpu().numpy()
+    if args.only_timed:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                              "warmup": W, "ms_per_step": ms / K, "mode": "only-timed", "prec": args.prec}))
+        prop.close()
+        return 0
 
     # per-kernel timing pass (events around every kernel class, same workload)
     rb.rttda_profile(h, True)
@@ -297,37 +369,19 @@ def run_gpu(args):
            "steps": ke, "call": "rttda_set_state + rttda_resume(nsteps=1) per step, pinned host buffers"}
 
     # roofline of the dominant kernel class
-    peaks = {}
-    if os.path.exists(PEAKS_FILE):
-        peaks = json.load(open(PEAKS_FILE))
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     ms_cls = {k: v[0] for k, v in prof.items()}
     dom = max(ms_cls, key=ms_cls.get)
-    C, M, Nn, Kk = 2 * T, 2 * T * NOCC, NVIRT, NAUX * NVIRT
-    xm_ms, xm_n = prof["exchange_main"]
-    flop_launch = 2.0 * M * Nn * Kk
-    achieved = flop_launch / (xm_ms / max(xm_n, 1) / 1e3) / 1e12 if xm_n else None
-    if args.prec in ("fp64", "fp32"):
-        bound = "alu"
-        peak = FP32_ALU_PEAK_TFLOPS if args.prec == "fp32" else 148 * 2 * 2.032e9 * 2 / 1e12
-        peak_src = "derived: 148 SM x 128 FP32 lanes x 2 flop x 2032 MHz" if args.prec == "fp32" else \
-            "derived: FP64 FMA rate"
-    else:
-        bound = "tensor"
-        bf16 = peaks.get("bf16_tflops", 1822.3)
-        peak = bf16 if args.prec == "bf16" else bf16 / 2
-        peak_src = "of measured bf16 burst" + (" x 1/2 (tf32 nominal ratio)" if args.prec == "tf32" else "")
-    roof = {"bound": bound, "kernel": "exchange_main (sum_{P,b} Z^P_ib B^P_ab)", "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "peak_source": peak_src, "flop_per_launch": flop_launch,
-            "avg_launch_ms": xm_ms / max(xm_n, 1), "launches_timed": xm_n,
-            "dominant_class": dom, "class_ms_share": {k: round(v / sum(ms_cls.values()), 4) for k, v in ms_cls.items()}}
+    roof = roofline(args.prec, dom, prof[dom], T, peaks)
+    roof["class_ms_share"] = {k: round(v / max(sum(ms_cls.values()), 1e-30), 4) for k, v in ms_cls.items()}
+    roof["class_ms_per_step"] = {k: round(v / kp, 4) for k, v in ms_cls.items()}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cb = time_oracle(mol, 8, args.cpu_steps, warmup=1)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
-    dtype = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.prec]
+    dtype = {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.prec]
     cfg = base_config(args.prec, world)
     cfg.update({"fp64_path_traj_steps_per_s": fp64_rate, "speedup_vs_fp64_path": value / world / fp64_rate,
                 "fp64_path": f"plain FP64, one trajectory (z kick), {k64} timed steps",
@@ -345,21 +399,68 @@ def run_gpu(args):
     return 0
 
 
+def run_accuracy(args):
+    """Long-horizon dipole / norm error of each precision against FP64 on the
+    same molecule, one z-kicked trajectory."""
+    import torch
+    from paper_2601_16949_b300 import binding as rb
+    from paper_2601_16949_b300 import synth
+    torch.cuda.set_device(0)
+    mol = synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
+    pulse = [dict(kind=rb.KICK, E0=KAPPA, direction=(0.0, 0.0, 1.0))]
+    n = args.accuracy
+    res = {}
+    for prec in ["fp64"] + [p for p in args.accuracy_precs.split(",") if p]:
+        pr = rb.Propagator(mol, CX, prec)
+        pr.set_field(pulse)
+        t0 = time.perf_counter()
+        _, dip, nrm = pr.propagate(DT, n, want_state=False)
+        res[prec] = (dip[0], nrm[0], time.perf_counter() - t0)
+        pr.close()
+    d64, n64, _ = res["fp64"]
+    ref = d64 - d64[0]
+    out = {"mode": "accuracy", "workload": WORKLOAD, "steps": n, "horizon_au": n * DT,
+           "fp64_norm_drift": float(np.max(np.abs(n64 - n64[0]))), "results": {}}
+    for prec, (d, nr, sec) in res.items():
+        if prec == "fp64":
+            continue
+        err = np.abs(d - d64) / np.max(np.abs(ref))
+        k = np.arange(len(err))
+        out["results"][prec] = {
+            "dipole_rel_err": float(np.max(err)),
+            "dipole_rel_err_at": {str(int(m)): float(np.max(err[: m + 1])) for m in (n // 8, n // 4, n // 2, n)},
+            "norm_diff_vs_fp64": float(np.max(np.abs(nr - n64))),
+            "seconds": sec}
+        del k
+    out["fp64_seconds"] = res["fp64"][2]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"])
+    ap.add_argument("--accuracy", type=int, default=0,
+                    help="instead of timing: propagate N steps with FP64 and the chosen precisions "
+                         "(z kick) and print their dipole/norm errors against FP64")
+    ap.add_argument("--accuracy-precs", default="fp32,bf16x3,bf16")
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="warm-up and timed steps only (for profiler captures): no per-kernel pass, "
+                         "no FP64 comparison, no end-to-end or CPU legs")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.accuracy:
+        return run_accuracy(args)
     return run_gpu(args)
 
 
