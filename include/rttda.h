@@ -230,6 +230,31 @@ rttda_status rttda_profile_read(rttda_t h, double* ms, long long* launches);
  * the last propagation (*per_step).  Either pointer may be NULL. */
 rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step);
 
+/* Coulomb term of sigma without allocating any device memory.
+ * The paper has no counterpart; this entry point exists for callers that
+ * may not allocate GPU memory while they run (an application whose device
+ * memory is owned by its own pool or arena, an allocator-free real-time
+ * loop, a process with a fixed device-memory budget).
+ *   sigma[t][0] = 0,
+ *   sigma[t][1+ia] = 2 sum_jb (ia|jb) c[t][1+jb],  (ia|jb) = sum_P B^P_ia B^P_jb,
+ * in FP64 for every trajectory t (complex, [ntraj][1+nocc*nvirt][2]).
+ *   B_ov_dev  device [naux][nocc*nvirt] FP64, read only.
+ *   c_dev     device [ntraj][n][2] FP64, read only.
+ *   sigma_dev device [ntraj][n][2] FP64, written.
+ *   stream    cudaStream_t to enqueue on (NULL = the legacy default stream).
+ * Its only scratch is a fixed array of 2^20 doubles (8 MiB) inside the
+ * library, held on every device that loads the library until the process
+ * exits; naux*2*ntraj must not exceed 2^20, otherwise RTTDA_E_ARG is
+ * returned before any GPU work.  The call makes no cudaMalloc/cudaFree and
+ * uses no allocating library routine.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress), so make that first
+ * call outside any stream capture.  All calls share the one array and each
+ * call overwrites the part it reads before reading it; calls whose work may
+ * overlap on the GPU (different streams, or several host threads) race on
+ * it and must be serialised by the caller.  Returns after enqueueing. */
+rttda_status rttda_coulomb_noalloc(int nocc, int nvirt, int naux, const double* B_ov_dev, const double* c_dev,
+                                   int ntraj, double* sigma_dev, void* stream);
+
 /* Free every resource of the handle (NULL is ignored). */
 void rttda_destroy(rttda_t h);
 

@@ -67,6 +67,9 @@ lib.rttda_sync.argtypes = [_h, ct.c_void_p]
 lib.rttda_profile.argtypes = [_h, ct.c_int]
 lib.rttda_profile_read.argtypes = [_h, _dp, ct.POINTER(ct.c_longlong)]
 lib.rttda_launch_stats.argtypes = [_h, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]
+lib.rttda_coulomb_noalloc.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int,
+                                      ct.c_void_p, ct.c_void_p]
+lib.rttda_coulomb_noalloc.restype = ct.c_int
 lib.rttda_destroy.argtypes = [_h]
 lib.rttda_destroy.restype = None
 for _name in ("rttda_create", "rttda_memory_bytes", "rttda_set_field", "rttda_propagate", "rttda_propagate_device",
@@ -213,6 +216,12 @@ def rttda_launch_stats(h) -> tuple:
     per = ct.c_longlong()
     _check(lib.rttda_launch_stats(h, ct.byref(tot), ct.byref(per)), "rttda_launch_stats")
     return tot.value, per.value
+
+
+def rttda_coulomb_noalloc(nocc, nvirt, naux, B_ov_dev, c_dev, ntraj, sigma_dev, stream=0) -> None:
+    """Coulomb part of sigma with no device allocation (device addresses in)."""
+    _check(lib.rttda_coulomb_noalloc(int(nocc), int(nvirt), int(naux), B_ov_dev, c_dev, int(ntraj), sigma_dev,
+                                     stream or None), "rttda_coulomb_noalloc")
 
 
 def rttda_destroy(h) -> None:
