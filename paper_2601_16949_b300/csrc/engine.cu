@@ -126,7 +126,8 @@ struct rttda_ctx {
   void* Jpart = nullptr;
   void* Zt = nullptr;
   void* Kpart = nullptr;
-  int SJ = 1, pchunkJ = 1, SK = 1, zchunk = 1, obsG = 1;
+  int SJ = 1, pchunkJ = 1, SK = 1, zchunk = 1, obsG = 1, SW = 1, wslice = 1;
+  bool coul_vec = false;
   long long obs_rows = 1;
   size_t dev_bytes = 0;
 
@@ -240,24 +241,27 @@ namespace {
 
 // --- tensor-core exchange -------------------------------------------------
 constexpr int kZBN = 256, kZStages = 3;   // Z = B_oo c   (K = nocc, short)
-constexpr int kMStages = 4;               // main contraction over (P, b)
 
+// Persistent launch: one CTA per SM (or per tile if fewer tiles).
 template <int BN, int ST, int BM, int EP>
-void tc_launch(dim3 g, const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s) {
-  tc::k_tc_gemm<BN, ST, BM, EP><<<g, tc::kThreads, tc::smem_bytes<BN, ST>(), s>>>(a, b, prm);
+void tc_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s) {
+  const long long tiles = cdiv(prm.N, BN) * cdiv(prm.M, tc::kBM) * prm.nsplit;
+  const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(tiles, kNumSM));
+  tc::k_tc_gemm<BN, ST, BM, EP><<<grid, tc::kThreads, tc::smem_bytes<BN, ST, EP>(), s>>>(a, b, prm);
 }
 
 template <int BN, int ST, int BM, int EP>
 void tc_attr() {
+  static_assert(tc::smem_bytes<BN, ST, EP>() <= 232448, "shared memory per block exceeds 227 KB");
   cudaFuncSetAttribute(tc::k_tc_gemm<BN, ST, BM, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)tc::smem_bytes<BN, ST>());
+                       (int)tc::smem_bytes<BN, ST, EP>());
 }
 
 void set_tc_smem_limits() {
   tc_attr<kZBN, kZStages, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>();
-  tc_attr<128, kMStages + 2, tc::BMODE_VV, tc::EPI_PARTIAL>();
-  tc_attr<224, kMStages, tc::BMODE_VV, tc::EPI_PARTIAL>();
-  tc_attr<256, kMStages, tc::BMODE_VV, tc::EPI_PARTIAL>();
+  tc_attr<128, 7, tc::BMODE_VV, tc::EPI_PARTIAL>();
+  tc_attr<224, 5, tc::BMODE_VV, tc::EPI_PARTIAL>();
+  tc_attr<256, 4, tc::BMODE_VV, tc::EPI_PARTIAL>();
 }
 
 void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
@@ -279,15 +283,15 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.N = C * vp;
       prm.kt_total = (int)cdiv(op, tc::kBK);
       prm.kt_per_split = prm.kt_total;
+      prm.nsplit = 1;
       prm.nprod = h->nprod;
       prm.zhi = h->Zk;
       prm.zlo = h->nplanes > 1 ? h->Zk + h->zplane : nullptr;
       prm.o = o;
       prm.vp = vp;
-      prm.zld = (long long)pc * vp;
+      prm.zrows = C * o;
       prm.err = h->d_err;
-      dim3 g(blocks_for((long long)C * vp, kZBN), blocks_for((long long)pc * o, tc::kBM), 1);
-      tc_launch<kZBN, kZStages, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>(g, h->tmZA[c], h->tmZB, prm, s);
+      tc_launch<kZBN, kZStages, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>(h->tmZA[c], h->tmZB, prm, s);
     }
     {
       // K_(col,i),a (+)= sum_{P in chunk, b} Z^P_(col,i),b B^P_ab   (split-K)
@@ -298,6 +302,7 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.N = v;
       prm.kt_total = pc * (vp / tc::kBK);
       prm.kt_per_split = h->tc_kper[c];
+      prm.nsplit = h->SK;
       prm.nprod = h->nprod;
       prm.vtiles = vp / tc::kBK;
       prm.out = (float*)h->Kpart;
@@ -305,11 +310,10 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.split_stride = (long long)C * o * v;
       prm.accum = c > 0 ? 1 : 0;
       prm.err = h->d_err;
-      dim3 g(blocks_for(v, h->tc_bn), blocks_for((long long)C * o, tc::kBM), h->SK);
       switch (h->tc_bn) {
-        case 128: tc_launch<128, kMStages + 2, tc::BMODE_VV, tc::EPI_PARTIAL>(g, h->tmMA[c], h->tmMB[c], prm, s); break;
-        case 224: tc_launch<224, kMStages, tc::BMODE_VV, tc::EPI_PARTIAL>(g, h->tmMA[c], h->tmMB[c], prm, s); break;
-        default: tc_launch<256, kMStages, tc::BMODE_VV, tc::EPI_PARTIAL>(g, h->tmMA[c], h->tmMB[c], prm, s); break;
+        case 128: tc_launch<128, 7, tc::BMODE_VV, tc::EPI_PARTIAL>(h->tmMA[c], h->tmMB[c], prm, s); break;
+        case 224: tc_launch<224, 5, tc::BMODE_VV, tc::EPI_PARTIAL>(h->tmMA[c], h->tmMB[c], prm, s); break;
+        default: tc_launch<256, 4, tc::BMODE_VV, tc::EPI_PARTIAL>(h->tmMA[c], h->tmMB[c], prm, s); break;
       }
     }
   }
@@ -323,12 +327,24 @@ struct Ops {
     Prof pr(h, RTTDA_KC_COULOMB, s);
     h->launches += 2;
     const int C = 2 * h->T;
+    if (h->coul_vec) {
+      // 16-byte vector loads of B_ov rows (ov a multiple of the vector width)
+      constexpr int V = Vec16<TF>::V;
+      k_coul_w_vec<TF, TC, 6><<<dim3(blocks_for(h->P, 32), h->SW), 256, (size_t)h->wslice * C * sizeof(TC), s>>>(
+          (const TF*)h->Bov, X, h->P, h->ov, C, h->wslice, (TC*)h->w);
+      dim3 g(blocks_for(cdiv(h->ov, V), 256), h->SJ);
+      const size_t smem = (size_t)h->pchunkJ * C * sizeof(TC);
+      k_coul_J_vec<TF, TC, 6><<<g, 256, smem, s>>>((const TF*)h->Bov, (const TC*)h->w, h->SW, h->P, h->ov, C,
+                                                  h->pchunkJ, (TC*)h->Jpart);
+      return;
+    }
     constexpr int PB = 8;
-    k_coul_w<TF, TC, 8, PB><<<blocks_for(h->P, PB), 256, 0, s>>>((const TF*)h->Bov, X, h->P, h->ov, C, (TC*)h->w);
+    k_coul_w<TF, TC, 8, PB><<<dim3(blocks_for(h->P, PB), h->SW), 256, 0, s>>>((const TF*)h->Bov, X, h->P, h->ov, C,
+                                                                             (TC*)h->w);
     dim3 g(blocks_for(h->ov, 256), h->SJ);
     const size_t smem = (size_t)h->pchunkJ * C * sizeof(TC);
-    k_coul_J<TF, TC, 8><<<g, 256, smem, s>>>((const TF*)h->Bov, (const TC*)h->w, h->P, h->ov, C, h->pchunkJ,
-                                            (TC*)h->Jpart);
+    k_coul_J<TF, TC, 8><<<g, 256, smem, s>>>((const TF*)h->Bov, (const TC*)h->w, h->SW, h->P, h->ov, C,
+                                            h->pchunkJ, (TC*)h->Jpart);
   }
 
   static void exchange(rttda_ctx* h, const double* X, cudaStream_t s) {
@@ -384,7 +400,7 @@ struct Ops {
     Prof pr(h, RTTDA_KC_COMBINE, s);
     h->launches += 1;
     const int C = 2 * h->T;
-    k_combine<TC><<<blocks_for(h->N, 256), 256, 0, s>>>(
+    k_combine<TC><<<blocks_for(h->N * h->T, 256), 256, 0, s>>>(
         mode, stage, h->N, h->o, h->v, h->T, h->eps_o, h->eps_v, h->cx, (const TC*)h->Jpart, h->SJ,
         (const TC*)h->Kpart, h->SK, (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn,
         const_cast<double*>(Xin), h->acc, sig_out);
@@ -392,6 +408,8 @@ struct Ops {
 
   static void set_smem_limits() {
     cudaFuncSetAttribute(k_coul_J<TF, TC, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_coul_J_vec<TF, TC, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_coul_w_vec<TF, TC, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (XTC) set_tc_smem_limits();
   }
 };
@@ -580,10 +598,11 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
       CKS(bf16_map(&za, h->Boo_tc + (size_t)p0 * o * op, 3, dims, str, box));
     }
     {
-      const uint64_t dims[3] = {(uint64_t)pc * vp, (uint64_t)C * o, (uint64_t)h->nplanes};
-      const uint64_t str[2] = {(uint64_t)pc * vp * 2, (uint64_t)h->zplane * 2};
-      const uint32_t box[3] = {64, 128, 1};
-      CKS(bf16_map(&ma, h->Zk, 3, dims, str, box));
+      // Z as [plane][(P, b/64)][(col, i)][64]: one box per (K tile, 128 rows)
+      const uint64_t dims[4] = {64, (uint64_t)C * o, (uint64_t)pc * (vp / 64), (uint64_t)h->nplanes};
+      const uint64_t str[3] = {128, (uint64_t)C * o * 128, (uint64_t)h->zplane * 2};
+      const uint32_t box[4] = {64, 128, 1, 1};
+      CKS(bf16_map(&ma, h->Zk, 4, dims, str, box));
     }
     {
       const uint64_t dims[4] = {(uint64_t)vp, (uint64_t)vp, (uint64_t)pc, (uint64_t)h->nplanes};
@@ -615,14 +634,27 @@ rttda_status rttda_ctx::alloc_batch() {
   CKS(dalloc(&d_step, 1));
   // Coulomb scratch
   {
-    const long long xblocks = cdiv(ov, 256);
-    SJ = (int)std::max(1LL, std::min<long long>(P, cdiv(4 * kNumSM, xblocks)));
+    const int V = (int)(16 / fbytes);
+    coul_vec = (ov % V) == 0 && C <= 12;
     const size_t max_smem = 96 * 1024;
+    if (coul_vec) {
+      // pass 1: amplitude slices of wslice rows staged in shared memory
+      wslice = (int)std::min<long long>(ov, std::max<long long>(V * 32, (long long)(max_smem / (C * cbytes)) / (V * 32) * (V * 32)));
+      wslice = (int)std::min<long long>(wslice, std::max<long long>(V * 32, cdiv(cdiv(ov, cdiv(4 * kNumSM, cdiv(P, 32))), V * 32) * V * 32));
+      SW = (int)cdiv(ov, wslice);
+      // pass 2: each thread owns V rows; split P so that ~4 blocks per SM run
+      const long long xblocks = cdiv(cdiv(ov, V), 256);
+      SJ = (int)std::max(1LL, std::min<long long>(std::min(P, 16), cdiv(4 * kNumSM, xblocks)));
+    } else {
+      SW = (int)std::max(1LL, std::min(cdiv(4 * kNumSM, cdiv(P, 8)), cdiv(ov, 2048)));
+      const long long xblocks = cdiv(ov, 256);
+      SJ = (int)std::max(1LL, std::min<long long>(P, cdiv(4 * kNumSM, xblocks)));
+    }
     pchunkJ = (int)cdiv(P, SJ);
     while ((size_t)pchunkJ * C * cbytes > max_smem && pchunkJ > 1) pchunkJ = (pchunkJ + 1) / 2;
     SJ = (int)cdiv(P, pchunkJ);
     char* p = nullptr;
-    CK(cudaMalloc((void**)&p, (size_t)P * C * cbytes));
+    CK(cudaMalloc((void**)&p, (size_t)SW * P * C * cbytes));
     w = p;
     CK(cudaMalloc((void**)&p, (size_t)SJ * ov * C * cbytes));
     Jpart = p;

@@ -84,10 +84,16 @@ __device__ __forceinline__ T block_sum(T x, T* scratch) {
 // ---------------------------------------------------------------------------
 template <typename TF, typename TC, int CG, int PB>
 __global__ void __launch_bounds__(256) k_coul_w(const TF* __restrict__ Bov, const double* __restrict__ X, int P,
-                                                long long ov, int C, TC* __restrict__ w) {
+                                                long long ov, int C, TC* __restrict__ wpart) {
+  // grid (ceil(P/PB), nsplit_ia): block (pb, s) reduces rows p0..p0+PB over
+  // the s-th slice of ia and writes wpart[s][p][col] (summed in pass 2).
   __shared__ TC red[32];
   const int p0 = blockIdx.x * PB;
   const int pb = min(PB, P - p0);
+  const long long slice = (ov + gridDim.y - 1) / gridDim.y;
+  const long long ia0 = (long long)blockIdx.y * slice;
+  const long long ia1 = min(ov, ia0 + slice);
+  TC* w = wpart + (size_t)blockIdx.y * P * C;
   const double* Xs = X + C;
   for (int c0 = 0; c0 < C; c0 += CG) {
     const int cg = min(CG, C - c0);
@@ -96,24 +102,23 @@ __global__ void __launch_bounds__(256) k_coul_w(const TF* __restrict__ Bov, cons
     for (int r = 0; r < PB; ++r)
 #pragma unroll
       for (int c = 0; c < CG; ++c) acc[r][c] = TC(0);
-    for (long long ia = threadIdx.x; ia < ov; ia += blockDim.x) {
+    for (long long ia = ia0 + threadIdx.x; ia < ia1; ia += blockDim.x) {
       TC x[CG];
       const double* xr = Xs + ia * C + c0;
 #pragma unroll
       for (int c = 0; c < CG; ++c) x[c] = c < cg ? (TC)xr[c] : TC(0);
+      TC b[PB];
 #pragma unroll
-      for (int r = 0; r < PB; ++r) {
-        if (r < pb) {
-          const TC b = cvt<TC>(Bov[(size_t)(p0 + r) * ov + ia]);
+      for (int r = 0; r < PB; ++r) b[r] = r < pb ? cvt<TC>(Bov[(size_t)(p0 + r) * ov + ia]) : TC(0);
 #pragma unroll
-          for (int c = 0; c < CG; ++c) acc[r][c] = fma(b, x[c], acc[r][c]);
-        }
-      }
+      for (int r = 0; r < PB; ++r)
+#pragma unroll
+        for (int c = 0; c < CG; ++c) acc[r][c] = fma(b[r], x[c], acc[r][c]);
     }
     for (int r = 0; r < pb; ++r) {
       for (int c = 0; c < cg; ++c) {
-        const TC s = block_sum(acc[r][c], red);
-        if (threadIdx.x == 0) w[(size_t)(p0 + r) * C + c0 + c] = s;
+        const TC sum = block_sum(acc[r][c], red);
+        if (threadIdx.x == 0) w[(size_t)(p0 + r) * C + c0 + c] = sum;
       }
     }
   }
@@ -124,13 +129,18 @@ __global__ void __launch_bounds__(256) k_coul_w(const TF* __restrict__ Bov, cons
 // grid (ceil(ov/256), nsplit); the chunk of w is staged in shared memory.
 // ---------------------------------------------------------------------------
 template <typename TF, typename TC, int CG>
-__global__ void __launch_bounds__(256) k_coul_J(const TF* __restrict__ Bov, const TC* __restrict__ w, int P,
-                                                long long ov, int C, int pchunk, TC* __restrict__ Jpart) {
+__global__ void __launch_bounds__(256) k_coul_J(const TF* __restrict__ Bov, const TC* __restrict__ w, int nw,
+                                                int P, long long ov, int C, int pchunk, TC* __restrict__ Jpart) {
   extern __shared__ unsigned char smem_raw[];
   TC* ws = reinterpret_cast<TC*>(smem_raw);
   const int s = blockIdx.y;
   const int p0 = s * pchunk, p1 = min(P, p0 + pchunk);
-  for (int e = threadIdx.x; e < (p1 - p0) * C; e += blockDim.x) ws[e] = w[(size_t)p0 * C + e];
+  // w = sum of the nw pass-1 slices, added in a fixed order
+  for (int e = threadIdx.x; e < (p1 - p0) * C; e += blockDim.x) {
+    TC acc = w[(size_t)p0 * C + e];
+    for (int k = 1; k < nw; ++k) acc += w[(size_t)k * P * C + (size_t)p0 * C + e];
+    ws[e] = acc;
+  }
   __syncthreads();
   const long long ia = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (ia >= ov) return;
@@ -138,6 +148,7 @@ __global__ void __launch_bounds__(256) k_coul_J(const TF* __restrict__ Bov, cons
     TC acc[CG];
 #pragma unroll
     for (int c = 0; c < CG; ++c) acc[c] = TC(0);
+#pragma unroll 4
     for (int p = p0; p < p1; ++p) {
       const TC b = cvt<TC>(Bov[(size_t)p * ov + ia]);
       const TC* wr = ws + (p - p0) * C + c0;
@@ -148,6 +159,168 @@ __global__ void __launch_bounds__(256) k_coul_J(const TF* __restrict__ Bov, cons
 #pragma unroll
     for (int c = 0; c < CG; ++c)
       if (c0 + c < C) Jpart[((size_t)s * ov + ia) * C + c0 + c] = TC(2) * acc[c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Vector loads of factor rows: 16 bytes at a time (V = 16 / sizeof(TF)).
+// ---------------------------------------------------------------------------
+template <typename TF>
+struct Vec16 {
+  static constexpr int V = 16 / sizeof(TF);
+};
+
+template <typename TF, typename TC>
+__device__ __forceinline__ void load16(const TF* p, TC (&out)[Vec16<TF>::V]) {
+  const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+  const TF* e = reinterpret_cast<const TF*>(&u);
+#pragma unroll
+  for (int k = 0; k < Vec16<TF>::V; ++k) out[k] = cvt<TC>(e[k]);
+}
+
+// ---------------------------------------------------------------------------
+// Coulomb, pass 1 (vectorised): grid (ceil(P/32), nslice); block 256 = 8 warps
+// x 4 factor rows each.  The block stages its slice of amplitudes (converted
+// to TC) in shared memory once and streams 32 rows of B_ov against it with
+// 16-byte loads; each warp reduces its rows by shuffles and writes
+// wpart[slice][p][col].  Requires ov % V == 0 (16-byte aligned rows).
+// ---------------------------------------------------------------------------
+template <typename TC, int V>
+__device__ __forceinline__ void smem_vload(const TC* p, TC (&x)[V]) {
+  // V consecutive TC values from a 16-byte aligned shared-memory address
+  if constexpr (sizeof(TC) * V % 16 == 0) {
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(TC) * V / 16); ++k) {
+      const uint4 u = reinterpret_cast<const uint4*>(p)[k];
+      const TC* e = reinterpret_cast<const TC*>(&u);
+#pragma unroll
+      for (int j = 0; j < (int)(16 / sizeof(TC)); ++j) x[k * (16 / sizeof(TC)) + j] = e[j];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) x[k] = p[k];
+  }
+}
+
+template <typename TF, typename TC, int CG>
+__global__ void __launch_bounds__(256, 3) k_coul_w_vec(const TF* __restrict__ Bov, const double* __restrict__ X,
+                                                       int P, long long ov, int C, int slice,
+                                                       TC* __restrict__ wpart) {
+  constexpr int V = Vec16<TF>::V;
+  constexpr int RPW = 4;
+  extern __shared__ unsigned char smem_raw[];
+  TC* xs = reinterpret_cast<TC*>(smem_raw);  // [C][slice], column-major
+  const long long ia0 = (long long)blockIdx.y * slice;
+  const int len = (int)min((long long)slice, ov - ia0);
+  {
+    // stage the slice with 8 independent loads in flight per thread
+    const int total = len * C;
+    const double* src = X + (size_t)(1 + ia0) * C;
+    for (int e0 = threadIdx.x; e0 < total; e0 += blockDim.x * 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = e < total ? src[e] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < total) xs[(e % C) * slice + e / C] = (TC)v[u];
+      }
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pw = blockIdx.x * 32 + warp * RPW;
+  TC* w = wpart + (size_t)blockIdx.y * P * C;
+  for (int c0 = 0; c0 < C; c0 += CG) {
+    const int cg = min(CG, C - c0);
+    TC acc[RPW][CG];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+      for (int c = 0; c < CG; ++c) acc[r][c] = TC(0);
+    for (int k = lane * V; k < len; k += 32 * V) {
+      TC b[RPW][V];
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) {
+        if (pw + r < P) {
+          load16<TF, TC>(Bov + (size_t)(pw + r) * ov + ia0 + k, b[r]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < V; ++u) b[r][u] = TC(0);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CG; ++c) {
+        if (c < cg) {
+          TC x[V];
+          smem_vload<TC, V>(xs + (size_t)(c0 + c) * slice + k, x);
+#pragma unroll
+          for (int u = 0; u < V; ++u)
+#pragma unroll
+            for (int r = 0; r < RPW; ++r) acc[r][c] = fma(b[r][u], x[u], acc[r][c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+#pragma unroll
+      for (int c = 0; c < CG; ++c) {
+        const TC sum = warp_sum(acc[r][c]);
+        if (lane == 0 && c < cg && pw + r < P) w[(size_t)(pw + r) * C + c0 + c] = sum;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coulomb, pass 2 (vectorised): Jpart[s][ia][col] = 2 sum_{P in chunk s}
+// B^P_ia w[P][col]; each thread owns V consecutive ia (one 16-byte load per
+// P).  grid (ceil(ov / (256 V)), nsplit).  Requires ov % V == 0.
+// ---------------------------------------------------------------------------
+template <typename TF, typename TC, int CG>
+__global__ void __launch_bounds__(256) k_coul_J_vec(const TF* __restrict__ Bov, const TC* __restrict__ w, int nw,
+                                                    int P, long long ov, int C, int pchunk,
+                                                    TC* __restrict__ Jpart) {
+  constexpr int V = Vec16<TF>::V;
+  extern __shared__ unsigned char smem_raw[];
+  TC* ws = reinterpret_cast<TC*>(smem_raw);
+  const int s = blockIdx.y;
+  const int p0 = s * pchunk, p1 = min(P, p0 + pchunk);
+  for (int e = threadIdx.x; e < (p1 - p0) * C; e += blockDim.x) {
+    TC acc = w[(size_t)p0 * C + e];
+    for (int k = 1; k < nw; ++k) acc += w[(size_t)k * P * C + (size_t)p0 * C + e];
+    ws[e] = acc;
+  }
+  __syncthreads();
+  const long long ia = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * V;
+  if (ia >= ov) return;
+  for (int c0 = 0; c0 < C; c0 += CG) {
+    TC acc[V][CG];
+#pragma unroll
+    for (int u = 0; u < V; ++u)
+#pragma unroll
+      for (int c = 0; c < CG; ++c) acc[u][c] = TC(0);
+#pragma unroll 2
+    for (int p = p0; p < p1; ++p) {
+      TC b[V];
+      load16<TF, TC>(Bov + (size_t)p * ov + ia, b);
+      const TC* wr = ws + (p - p0) * C + c0;
+      TC wv[CG];
+#pragma unroll
+      for (int c = 0; c < CG; ++c) wv[c] = (c0 + c < C) ? wr[c] : TC(0);
+#pragma unroll
+      for (int u = 0; u < V; ++u)
+#pragma unroll
+        for (int c = 0; c < CG; ++c) acc[u][c] = fma(b[u], wv[c], acc[u][c]);
+    }
+#pragma unroll
+    for (int u = 0; u < V; ++u)
+#pragma unroll
+      for (int c = 0; c < CG; ++c)
+        if (c0 + c < C) Jpart[((size_t)s * ov + ia + u) * C + c0 + c] = TC(2) * acc[u][c];
   }
 }
 
@@ -398,70 +571,69 @@ __global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long 
                                                  int use_field, double dt, double* __restrict__ Xn,
                                                  double* __restrict__ Xs, double* __restrict__ acc,
                                                  double* __restrict__ sig_out) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
+  // one thread per (trajectory t, row n), n fastest
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * T) return;
+  const long long n = e % N;
+  const int t = (int)(e / N);
   const int C = 2 * T;
   const long long ov = N - 1;
-  int i = 0, a = 0;
-  double d = 0.0;
+  double sg[2];
   if (n > 0) {
-    i = (int)((n - 1) / v);
-    a = (int)((n - 1) % v);
-    d = eps_v[a] - eps_o[i];
-  }
-  for (int t = 0; t < T; ++t) {
-    double sg[2];
+    const int i = (int)((n - 1) / v), a = (int)((n - 1) % v);
+    const double d = eps_v[a] - eps_o[i];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int col = 2 * t + q;
-      const size_t idx = (size_t)n * C + col;
-      double s = 0.0;
-      if (n > 0) {
-        s = d * Xs[idx];
-        double j = 0.0;
-        for (int p = 0; p < SJ; ++p) j += (double)Jpart[((size_t)p * ov + (n - 1)) * C + col];
-        double kx = 0.0;
-        for (int p = 0; p < SK; ++p)
-          kx += (double)Kpart[(size_t)p * Kstride + ((size_t)col * o + i) * v + a];
-        s += j - cx * kx;
-      }
-      if (use_field) s -= E[stage * T + t] * F[idx];
-      sg[q] = s;
+      double j = 0.0;
+      for (int p = 0; p < SJ; ++p) j += (double)Jpart[((size_t)p * ov + (n - 1)) * C + col];
+      double kx = 0.0;
+      const TC* kp = Kpart + ((size_t)col * o + i) * v + a;
+#pragma unroll 4
+      for (int p = 0; p < SK; ++p) kx += (double)kp[(size_t)p * Kstride];
+      sg[q] = d * Xs[(size_t)n * C + col] + j - cx * kx;
     }
-    const size_t ir = (size_t)n * C + 2 * t, ii = ir + 1;
-    if (mode == 1) {
-      sig_out[ir] = sg[0];
-      sig_out[ii] = sg[1];
-      continue;
-    }
-    const double kr = sg[1], ki = -sg[0];  // k = -i sigma
-    switch (stage) {
-      case 0:
-        acc[ir] = kr;
-        acc[ii] = ki;
-        Xs[ir] = Xn[ir] + 0.5 * dt * kr;
-        Xs[ii] = Xn[ii] + 0.5 * dt * ki;
-        break;
-      case 1:
-        acc[ir] += 2.0 * kr;
-        acc[ii] += 2.0 * ki;
-        Xs[ir] = Xn[ir] + 0.5 * dt * kr;
-        Xs[ii] = Xn[ii] + 0.5 * dt * ki;
-        break;
-      case 2:
-        acc[ir] += 2.0 * kr;
-        acc[ii] += 2.0 * ki;
-        Xs[ir] = Xn[ir] + dt * kr;
-        Xs[ii] = Xn[ii] + dt * ki;
-        break;
-      default: {
-        const double xr = Xn[ir] + (dt / 6.0) * (acc[ir] + kr);
-        const double xi = Xn[ii] + (dt / 6.0) * (acc[ii] + ki);
-        Xn[ir] = xr;
-        Xn[ii] = xi;
-        Xs[ir] = xr;
-        Xs[ii] = xi;
-      }
+  } else {
+    sg[0] = sg[1] = 0.0;
+  }
+  const size_t ir = (size_t)n * C + 2 * t, ii = ir + 1;
+  if (use_field) {
+    const double Et = E[stage * T + t];
+    sg[0] -= Et * F[ir];
+    sg[1] -= Et * F[ii];
+  }
+  if (mode == 1) {
+    sig_out[ir] = sg[0];
+    sig_out[ii] = sg[1];
+    return;
+  }
+  const double kr = sg[1], ki = -sg[0];  // k = -i sigma
+  switch (stage) {
+    case 0:
+      acc[ir] = kr;
+      acc[ii] = ki;
+      Xs[ir] = Xn[ir] + 0.5 * dt * kr;
+      Xs[ii] = Xn[ii] + 0.5 * dt * ki;
+      break;
+    case 1:
+      acc[ir] += 2.0 * kr;
+      acc[ii] += 2.0 * ki;
+      Xs[ir] = Xn[ir] + 0.5 * dt * kr;
+      Xs[ii] = Xn[ii] + 0.5 * dt * ki;
+      break;
+    case 2:
+      acc[ir] += 2.0 * kr;
+      acc[ii] += 2.0 * ki;
+      Xs[ir] = Xn[ir] + dt * kr;
+      Xs[ii] = Xn[ii] + dt * ki;
+      break;
+    default: {
+      const double xr = Xn[ir] + (dt / 6.0) * (acc[ir] + kr);
+      const double xi = Xn[ii] + (dt / 6.0) * (acc[ii] + ki);
+      Xn[ir] = xr;
+      Xn[ii] = xi;
+      Xs[ir] = xr;
+      Xs[ii] = xi;
     }
   }
 }

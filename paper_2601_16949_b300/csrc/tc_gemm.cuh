@@ -2,11 +2,12 @@
 //
 //   D[m][n] = sum_k A[m][k] * B[n][k]   (A, B K-major BF16, D FP32 in TMEM)
 //
-// One CTA computes a 128 x BN tile over a K range (split-K).  Warp roles:
+// Persistent: each CTA walks a strided list of 128 x BN output tiles (each
+// over one K range of a split-K decomposition).  Warp roles:
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM allocator + MMA issuer (one elected lane)
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator, one TMEM lane
-//               (tile row) per thread.
+//   warps 2..9  epilogue: tcgen05.ld of the accumulator, one TMEM lane
+//               (tile row) per thread, two warps per lane quarter.
 // Shared-memory tiles are 128-byte rows (64 BF16 along K) in the 128-byte
 // swizzled K-major layout that TMA writes with CU_TENSOR_MAP_SWIZZLE_128B.
 //
@@ -26,7 +27,8 @@
 namespace rttda {
 namespace tc {
 
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                    // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer + MMA warp + epilogue
 constexpr int kBM = 128;
 constexpr int kBK = 64;                  // BF16 elements per 128-byte row
 constexpr int kABytes = kBM * 128;       // one A stage
@@ -47,17 +49,19 @@ struct Params {
   int M, N;              // logical output extents
   int kt_total;          // real K tiles
   int kt_per_split;      // real K tiles per split
+  int nsplit;            // number of K splits
   int nprod;             // 1 (single BF16) or 3 (hi/lo split)
   int vtiles;            // vp / 64 (BMODE_VV)
   // EPI_PARTIAL
   float* out;
   long long ldo, split_stride;
   int accum;             // 1: out += tile (later P chunks), 0: out = tile
-  // EPI_ZSPLIT
+  // EPI_ZSPLIT: Z stored as [plane][(P, b/64)][(col, i)][64] (the main
+  // contraction's TMA box order)
   __nv_bfloat16* zhi;
   __nv_bfloat16* zlo;
   int o, vp;
-  long long zld;         // row length of Z (= P * vp)
+  int zrows;             // C * o rows per K tile
   int* err;
 };
 
@@ -79,6 +83,10 @@ __device__ __forceinline__ void mbar_fence_init() {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -189,22 +197,72 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+        "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+        "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Z epilogue staging: per epilogue warp, hi and lo blocks of 32 rows x 64 B,
+// rows padded to 80 B so that both the row writes and the transposed reads
+// stay (nearly) free of bank conflicts.
+constexpr int kStageRowWords = 20;
+constexpr int kZStageBytesPerWarp = 2 * 32 * kStageRowWords * 4;
+
+// BF16 hi/lo of two floats: hi = rn(x), lo = rn(x - hi), each packed (x0 in
+// the low half).
+__device__ __forceinline__ void split_pack(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  hi = pack_bf16x2(x0, x1);
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+  lo = pack_bf16x2(x0 - h0, x1 - h1);
+}
+
 template <int BN>
 struct Cfg {
   static constexpr int kBBytes = BN * 128;
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kTmemCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : BN <= 256 ? 256 : 512;
+  static constexpr uint32_t kAccCols = 256;   // column offset of accumulator buffer 1
+  static constexpr uint32_t kTmemCols = 512;  // two accumulator buffers
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M=128 must be a multiple of 16 in [16, 256]");
   static_assert(kStageBytes % 1024 == 0, "stage must keep 1024-byte alignment");
 };
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int EPI = 0>
 constexpr size_t smem_bytes() {
-  return (size_t)STAGES * Cfg<BN>::kStageBytes + 1024 /*alignment slack*/ + 256 /*barriers*/;
+  return (size_t)STAGES * Cfg<BN>::kStageBytes + 1024 /*alignment slack*/ + 256 /*barriers*/ +
+         (EPI == 1 ? kEpiWarps * kZStageBytesPerWarp : 0);
+}
+
+// Tile t -> (split, m tile, n tile), n fastest so that consecutive tiles of a
+// CTA reuse the same A rows from L2.
+struct TileCoord {
+  int n0, m0, split;
+};
+__device__ __forceinline__ TileCoord tile_coord(int t, int tiles_n, int tiles_m, int BN) {
+  TileCoord c;
+  c.n0 = (t % tiles_n) * BN;
+  c.m0 = ((t / tiles_n) % tiles_m) * kBM;
+  c.split = t / (tiles_n * tiles_m);
+  return c;
 }
 
 // ---------------------------------------------------------------------------
-// The kernel
+// The kernel: persistent, one CTA per SM; CTA b handles tiles b, b + grid, ...
+// Two TMEM accumulators (columns [0, BN) and [256, 256 + BN)) let the
+// epilogue of one tile overlap the loads and MMAs of the next.
 // ---------------------------------------------------------------------------
 template <int BN, int STAGES, int BMODE, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -214,21 +272,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * CF::kStageBytes);
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  uint64_t* accf = empty + STAGES;  // [2] accumulator ready (MMA -> epilogue)
+  uint64_t* acce = accf + 2;        // [2] accumulator drained (epilogue -> MMA)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * kBM, split = blockIdx.z;
-  const int kr0 = split * p.kt_per_split;
-  const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
-  const int niter = max(0, kr1 - kr0) * p.nprod;
+  const int tiles_n = (p.N + BN - 1) / BN;
+  const int tiles_m = (p.M + kBM - 1) / kBM;
+  const int ntiles = tiles_n * tiles_m * p.nsplit;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], kEpiWarps);  // one arrive per epilogue warp
+    }
     mbar_fence_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, CF::kTmemCols);
@@ -240,21 +301,35 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      for (int it = 0; it < niter; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, p.err, ERR_WAIT_EMPTY)) break;
-        const int kr = kr0 + it / p.nprod, pr = it % p.nprod;
-        const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
-        uint8_t* sA = smem + s * CF::kStageBytes;
-        uint8_t* sB = sA + kABytes;
-        mbar_expect_tx(&full[s], CF::kStageBytes);
-        tma_load_3d(sA, &tmA, &full[s], kr * kBK, m0, pa);
-        if (BMODE == BMODE_PLAIN) {
-          tma_load_3d(sB, &tmB, &full[s], kr * kBK, n0, pb);
-        } else {
-          const int P = kr / p.vtiles, b0 = (kr % p.vtiles) * kBK;
-          tma_load_4d(sB, &tmB, &full[s], b0, n0, P, pb);
+      int it = 0;
+      bool alive = true;
+      for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+        const TileCoord tc = tile_coord(t, tiles_n, tiles_m, BN);
+        const int kr0 = tc.split * p.kt_per_split;
+        const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
+        const int niter = max(0, kr1 - kr0) * p.nprod;
+        for (int j = 0; j < niter; ++j, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, p.err, ERR_WAIT_EMPTY)) {
+            alive = false;
+            break;
+          }
+          const int kr = kr0 + j / p.nprod, pr = j % p.nprod;
+          const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
+          uint8_t* sA = smem + s * CF::kStageBytes;
+          uint8_t* sB = sA + kABytes;
+          mbar_expect_tx(&full[s], CF::kStageBytes);
+          if (BMODE == BMODE_PLAIN)
+            tma_load_3d(sA, &tmA, &full[s], kr * kBK, tc.m0, pa);
+          else  // A pre-tiled: (k in tile, row, K tile, plane)
+            tma_load_4d(sA, &tmA, &full[s], 0, tc.m0, kr, pa);
+          if (BMODE == BMODE_PLAIN) {
+            tma_load_3d(sB, &tmB, &full[s], kr * kBK, tc.n0, pb);
+          } else {
+            const int P = kr / p.vtiles, b0 = (kr % p.vtiles) * kBK;
+            tma_load_4d(sB, &tmB, &full[s], b0, tc.n0, P, pb);
+          }
         }
       }
     }
@@ -262,74 +337,130 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
       constexpr uint32_t idesc = idesc_bf16(kBM, BN);
-      for (int it = 0; it < niter; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(&full[s], ph, p.err, ERR_WAIT_FULL)) break;
+      int it = 0, tcount = 0;
+      bool alive = true;
+      for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x, ++tcount) {
+        const TileCoord tc = tile_coord(t, tiles_n, tiles_m, BN);
+        const int kr0 = tc.split * p.kt_per_split;
+        const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
+        const int niter = max(0, kr1 - kr0) * p.nprod;
+        const int buf = tcount & 1;
+        const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
+        if (!mbar_wait(&acce[buf], aph ^ 1u, p.err, ERR_WAIT_ACC)) break;
         tc_fence_after();
-        const uint32_t aaddr = smem_u32(smem + s * CF::kStageBytes);
-        const uint64_t adesc = sdesc_sw128(aaddr);
-        const uint64_t bdesc = sdesc_sw128(aaddr + kABytes);
+        const uint32_t dcol = tmem + (buf ? CF::kAccCols : 0u);
+        for (int j = 0; j < niter; ++j, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph, p.err, ERR_WAIT_FULL)) {
+            alive = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aaddr = smem_u32(smem + s * CF::kStageBytes);
+          const uint64_t adesc = sdesc_sw128(aaddr);
+          const uint64_t bdesc = sdesc_sw128(aaddr + kABytes);
 #pragma unroll
-        for (int k = 0; k < kBK / 16; ++k)  // 16 BF16 = 32 bytes per MMA along K
-          mma_bf16(tmem, adesc + 2 * k, bdesc + 2 * k, idesc, (it > 0 || k > 0) ? 1u : 0u);
-        mma_commit(&empty[s]);
+          for (int k = 0; k < kBK / 16; ++k)  // 16 BF16 = 32 bytes per MMA along K
+            mma_bf16(dcol, adesc + 2 * k, bdesc + 2 * k, idesc, (j > 0 || k > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&accf[buf]);
       }
-      mma_commit(accf);
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const int q = warp & 3;                 // TMEM lane quarter this warp may access
+    // ---------------- epilogue (warps 2..9) ----------------
+    // warp w may read TMEM lanes 32*(w % 4) .. +31; the two warps of a lane
+    // quarter take alternate 32-column chunks.
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int nchunks = (BN + 31) / 32;
     const int row = q * 32 + lane;
-    const int m = m0 + row;
-    const bool ok = mbar_wait(accf, 0, p.err, ERR_WAIT_ACC);
-    tc_fence_after();
-    if (EPI == EPI_PARTIAL) {
-      float* dst = p.out + (size_t)split * p.split_stride + (size_t)m * p.ldo;
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c, r);
-        if (m < p.M && ok) {
+    int tcount = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tcount) {
+      const TileCoord tc = tile_coord(t, tiles_n, tiles_m, BN);
+      const int kr0 = tc.split * p.kt_per_split;
+      const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
+      const bool has_k = kr1 > kr0;
+      const int buf = tcount & 1;
+      const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
+      const bool ok = mbar_wait(&accf[buf], aph, p.err, ERR_WAIT_ACC);
+      tc_fence_after();
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (buf ? CF::kAccCols : 0u);
+      const int m = tc.m0 + row;
+      if (EPI == EPI_PARTIAL) {
+        float* dst = p.out + (size_t)tc.split * p.split_stride + (size_t)m * p.ldo;
+        for (int ci = half; ci < nchunks; ci += 2) {
+          const int c = ci * 32;
+          uint32_t r[32];
+          tmem_ld32(tbase + c, r);
+          if (m < p.M && ok) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c + j;
-            if (n < p.N) {
-              const float x = niter > 0 ? __uint_as_float(r[j]) : 0.0f;
-              dst[n] = p.accum ? dst[n] + x : x;
+            for (int j = 0; j < 32; ++j) {
+              const int n = tc.n0 + c + j;
+              if (n < p.N) {
+                const float x = has_k ? __uint_as_float(r[j]) : 0.0f;
+                dst[n] = p.accum ? dst[n] + x : x;
+              }
             }
           }
         }
-      }
-    } else {
-      // rows m = (P, i); columns n = (col, b) with b inside one 32-aligned chunk
-      const int P = m / p.o, i = m - P * p.o;
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c, r);
-        const int n = n0 + c;
-        if (m < p.M && n < p.N && ok) {
-          const int col = n / p.vp, b = n - col * p.vp;
-          const size_t off = (size_t)(col * p.o + i) * p.zld + (size_t)P * p.vp + b;
-          uint4 hi4[4], lo4[4];
-          __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(hi4);
-          __nv_bfloat16* lo = reinterpret_cast<__nv_bfloat16*>(lo4);
+      } else {
+        // rows m = (P, i); columns n = (col, b) with b inside one 32-aligned
+        // chunk.  Each warp converts its 32 x 32 block to BF16 hi/lo, stages
+        // it in shared memory and writes it back transposed: four threads per
+        // row, so every store instruction covers eight full 64-byte segments.
+        uint32_t* stg = reinterpret_cast<uint32_t*>(smem + STAGES * CF::kStageBytes + 256) +
+                        (size_t)(warp - 2) * (kZStageBytesPerWarp / 4);
+        uint32_t* stg_lo = stg + 32 * kStageRowWords;
+        for (int ci = half; ci < nchunks; ci += 2) {
+          const int c = ci * 32;
+          uint32_t r[32];
+          tmem_ld32(tbase + c, r);
+          if (!has_k) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float x = niter > 0 ? __uint_as_float(r[j]) : 0.0f;
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            hi[j] = h;
-            lo[j] = __float2bfloat16_rn(x - __bfloat162float(h));
+            for (int j = 0; j < 32; ++j) r[j] = 0u;
           }
-          uint4* dh = reinterpret_cast<uint4*>(p.zhi + off);
+          uint32_t hw[16], lw[16];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) dh[j] = hi4[j];
-          if (p.zlo) {
-            uint4* dl = reinterpret_cast<uint4*>(p.zlo + off);
+          for (int j = 0; j < 16; ++j)
+            split_pack(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]), hw[j], lw[j]);
+          uint4* sh = reinterpret_cast<uint4*>(stg + lane * kStageRowWords);
+          uint4* sl = reinterpret_cast<uint4*>(stg_lo + lane * kStageRowWords);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) dl[j] = lo4[j];
+          for (int j = 0; j < 4; ++j) {
+            sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
+            sl[j] = make_uint4(lw[4 * j], lw[4 * j + 1], lw[4 * j + 2], lw[4 * j + 3]);
           }
+          __syncwarp();
+          const int n = tc.n0 + c;
+          if (n < p.N && ok) {
+            const int col = n / p.vp, b = n - col * p.vp;
+            const int vt = p.vp >> 6;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int rr = (lane >> 2) + 8 * k, cc = lane & 3;
+              const int mr = tc.m0 + q * 32 + rr;
+              if (mr < p.M) {
+                const int Pr = mr / p.o, ir = mr - Pr * p.o;
+                const size_t kt = (size_t)Pr * vt + (b >> 6);
+                const size_t off = (kt * p.zrows + (size_t)(col * p.o + ir)) * 64 + (b & 63) + 8 * cc;
+                *reinterpret_cast<uint4*>(p.zhi + off) =
+                    *reinterpret_cast<const uint4*>(stg + rr * kStageRowWords + 4 * cc);
+                if (p.zlo)
+                  *reinterpret_cast<uint4*>(p.zlo + off) =
+                      *reinterpret_cast<const uint4*>(stg_lo + rr * kStageRowWords + 4 * cc);
+              }
+            }
+          }
+          __syncwarp();
         }
       }
+      // hand the accumulator buffer back to the MMA warp
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
+      if (!ok) break;
     }
   }
   tc_fence_before();
