@@ -186,6 +186,7 @@ PREC_INFO = {  # factor bytes, exchange planes, tensor products per K tile
     "fp32": dict(fb=4, planes=1, nprod=1, tensor=False),
     "bf16": dict(fb=2, planes=1, nprod=1, tensor=True),
     "bf16x3": dict(fb=4, planes=2, nprod=3, tensor=True),
+    "bf16x2": dict(fb=4, planes=2, nprod=2, tensor=True, zplanes=1),
 }
 
 
@@ -201,12 +202,15 @@ def algorithmic_work(prec: str, cls: str, T: int):
     if cls == "exchange_main":
         M, N, K = C * o, v, P * v
         eb = 2 if pi["tensor"] else pi["fb"]
-        return pi["nprod"] * 2.0 * M * N * K, pi["planes"] * eb * (M * K + P * v * v)
+        zp = pi.get("zplanes", pi["planes"])
+        return pi["nprod"] * 2.0 * M * N * K, eb * (zp * M * K + pi["planes"] * P * v * v)
     if cls == "coulomb":
         return 2 * 2.0 * P * o * v * C, 2.0 * P * o * v * (pi["fb"] if prec != "bf16x3" else 4)
     if cls == "exchange_z":
         eb = 2 if pi["tensor"] else pi["fb"]
-        return pi["nprod"] * 2.0 * P * o * o * v * C, pi["planes"] * eb * (P * o * v * C + P * o * o)
+        zp = pi.get("zplanes", pi["planes"])
+        nz = 3 if prec in ("bf16x3", "bf16x2") else pi["nprod"]
+        return nz * 2.0 * P * o * o * v * C, eb * (zp * P * o * v * C + pi["planes"] * P * o * o)
     return None, None
 
 
@@ -381,7 +385,7 @@ def run_gpu(args):
         cb = time_oracle(mol, 8, args.cpu_steps, warmup=1)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
-    dtype = {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.prec]
+    dtype = {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "bf16x2": "bf16x2"}[args.prec]
     cfg = base_config(args.prec, world)
     cfg.update({"fp64_path_traj_steps_per_s": fp64_rate, "speedup_vs_fp64_path": value / world / fp64_rate,
                 "fp64_path": f"plain FP64, one trajectory (z kick), {k64} timed steps",
@@ -409,30 +413,32 @@ def run_accuracy(args):
     mol = synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
     pulse = [dict(kind=rb.KICK, E0=KAPPA, direction=(0.0, 0.0, 1.0))]
     n = args.accuracy
+    ref_prec = args.accuracy_ref
     res = {}
-    for prec in ["fp64"] + [p for p in args.accuracy_precs.split(",") if p]:
+    for prec in [ref_prec] + [p for p in args.accuracy_precs.split(",") if p and p != ref_prec]:
         pr = rb.Propagator(mol, CX, prec)
         pr.set_field(pulse)
         t0 = time.perf_counter()
         _, dip, nrm = pr.propagate(DT, n, want_state=False)
         res[prec] = (dip[0], nrm[0], time.perf_counter() - t0)
         pr.close()
-    d64, n64, _ = res["fp64"]
+    d64, n64, _ = res[ref_prec]
     ref = d64 - d64[0]
-    out = {"mode": "accuracy", "workload": WORKLOAD, "steps": n, "horizon_au": n * DT,
-           "fp64_norm_drift": float(np.max(np.abs(n64 - n64[0]))), "results": {}}
+    out = {"mode": "accuracy", "reference": ref_prec, "workload": WORKLOAD, "steps": n, "horizon_au": n * DT,
+           "trajectory": "z kick", "reference_norm_drift": float(np.max(np.abs(n64 - n64[0]))), "results": {}}
     for prec, (d, nr, sec) in res.items():
-        if prec == "fp64":
+        if prec == ref_prec:
             continue
         err = np.abs(d - d64) / np.max(np.abs(ref))
         k = np.arange(len(err))
         out["results"][prec] = {
             "dipole_rel_err": float(np.max(err)),
-            "dipole_rel_err_at": {str(int(m)): float(np.max(err[: m + 1])) for m in (n // 8, n // 4, n // 2, n)},
-            "norm_diff_vs_fp64": float(np.max(np.abs(nr - n64))),
+            "dipole_rel_err_at": {str(int(m)): float(np.max(err[: m + 1]))
+                                  for m in (n // 16, n // 8, n // 4, n // 2, n)},
+            "norm_diff_vs_reference": float(np.max(np.abs(nr - n64))),
             "seconds": sec}
         del k
-    out["fp64_seconds"] = res["fp64"][2]
+    out["reference_seconds"] = res[ref_prec][2]
     print(json.dumps(out), flush=True)
     return 0
 
@@ -443,11 +449,12 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x2", choices=["fp64", "fp32", "bf16", "bf16x3", "bf16x2"])
     ap.add_argument("--accuracy", type=int, default=0,
                     help="instead of timing: propagate N steps with FP64 and the chosen precisions "
                          "(z kick) and print their dipole/norm errors against FP64")
-    ap.add_argument("--accuracy-precs", default="fp32,bf16x3,bf16")
+    ap.add_argument("--accuracy-precs", default="fp32,bf16x3,bf16x2,bf16")
+    ap.add_argument("--accuracy-ref", default="fp64")
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-steps", type=int, default=3)

@@ -74,9 +74,11 @@ typedef enum {
  *   BF16X3: exchange on tcgen05 tensor cores with every operand split into
  *           BF16 hi + lo parts (x = hi + lo) and the products hi*hi + hi*lo +
  *           lo*hi accumulated in FP32 (about 16 significant bits per
- *           operand); Coulomb and field in FP32 on CUDA cores. */
+ *           operand); Coulomb and field in FP32 on CUDA cores.
+ *   BF16X2: as BF16X3 for the factors and for Z = B_oo c, but Z enters the
+ *           main contraction as one BF16 plane: products Z*B_hi + Z*B_lo. */
 typedef enum {
-  RTTDA_FP64 = 0, RTTDA_FP32 = 1, RTTDA_TF32 = 2, RTTDA_BF16 = 3, RTTDA_BF16X3 = 4
+  RTTDA_FP64 = 0, RTTDA_FP32 = 1, RTTDA_TF32 = 2, RTTDA_BF16 = 3, RTTDA_BF16X3 = 4, RTTDA_BF16X2 = 5
 } rttda_prec;
 
 /* Pulse shapes E(t) (Sec. 2.2, Eqs. delta_pulse, continuous wave,

@@ -137,6 +137,7 @@ struct rttda_ctx {
   // tensor-core exchange (BF16 / BF16X3): padded BF16 planes and TMA maps
   bool tc = false;
   int nplanes = 1, nprod = 1, vp = 0, op = 0, tc_bn = 256;
+  int zplanes = 1, nprod_main = 1;  // Z planes kept; products in the main contraction
   __nv_bfloat16* Bvv_tc = nullptr;  // [plane][P][vp][vp]
   __nv_bfloat16* Boo_tc = nullptr;  // [plane][P*o][op]
   __nv_bfloat16* Xt = nullptr;      // [plane][C*vp][op]
@@ -286,7 +287,7 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.nsplit = 1;
       prm.nprod = h->nprod;
       prm.zhi = h->Zk;
-      prm.zlo = h->nplanes > 1 ? h->Zk + h->zplane : nullptr;
+      prm.zlo = h->zplanes > 1 ? h->Zk + h->zplane : nullptr;
       prm.o = o;
       prm.vp = vp;
       prm.zrows = C * o;
@@ -303,7 +304,7 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.kt_total = pc * (vp / tc::kBK);
       prm.kt_per_split = h->tc_kper[c];
       prm.nsplit = h->SK;
-      prm.nprod = h->nprod;
+      prm.nprod = h->nprod_main;
       prm.vtiles = vp / tc::kBK;
       prm.out = (float*)h->Kpart;
       prm.ldo = v;
@@ -420,7 +421,7 @@ void dispatch(int prec, F&& f) {
     case RTTDA_FP64: f(Ops<double, double, false>{}); break;
     case RTTDA_FP32: f(Ops<float, float, false>{}); break;
     case RTTDA_BF16: f(Ops<__nv_bfloat16, float, true>{}); break;
-    default: f(Ops<float, float, true>{}); break;  // RTTDA_BF16X3
+    default: f(Ops<float, float, true>{}); break;  // RTTDA_BF16X3, RTTDA_BF16X2
   }
 }
 
@@ -560,10 +561,10 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   const size_t xt = (size_t)C * vp * op;
   CKS(dalloc(&h->Xt, xt * h->nplanes));
   // Z chunk: C*o rows of zchunk*vp BF16 per plane, at most ~2 GiB in total
-  const size_t zper = (size_t)C * o * vp * 2 * h->nplanes;
+  const size_t zper = (size_t)C * o * vp * 2 * h->zplanes;
   h->zchunk = (int)std::max<size_t>(1, std::min<size_t>(P, ((size_t)2 << 30) / std::max<size_t>(zper, 1)));
   h->zplane = (size_t)C * o * h->zchunk * vp;
-  CKS(dalloc(&h->Zk, h->zplane * h->nplanes));
+  CKS(dalloc(&h->Zk, h->zplane * h->zplanes));
   // main contraction tile width along a (N = nvirt)
   int best = 256;
   long long bestw = -1;
@@ -599,7 +600,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
     }
     {
       // Z as [plane][(P, b/64)][(col, i)][64]: one box per (K tile, 128 rows)
-      const uint64_t dims[4] = {64, (uint64_t)C * o, (uint64_t)pc * (vp / 64), (uint64_t)h->nplanes};
+      const uint64_t dims[4] = {64, (uint64_t)C * o, (uint64_t)pc * (vp / 64), (uint64_t)h->zplanes};
       const uint64_t str[3] = {128, (uint64_t)C * o * 128, (uint64_t)h->zplane * 2};
       const uint32_t box[4] = {64, 128, 1, 1};
       CKS(bf16_map(&ma, h->Zk, 4, dims, str, box));
@@ -786,7 +787,8 @@ rttda_status rttda_create(int nocc, int nvirt, int naux, const double* eps_occ, 
   if (nocc < 1 || nvirt < 1 || naux < 1) return set_error(RTTDA_E_ARG, "rttda_create: nocc, nvirt, naux must be >= 1");
   if (!eps_occ || !eps_virt || !B_ov || !B_oo || !B_vv || !mu_oo || !mu_vv || !mu_0ov)
     return set_error(RTTDA_E_ARG, "rttda_create: NULL input array");
-  if (prec != RTTDA_FP64 && prec != RTTDA_FP32 && prec != RTTDA_BF16 && prec != RTTDA_BF16X3)
+  if (prec != RTTDA_FP64 && prec != RTTDA_FP32 && prec != RTTDA_BF16 && prec != RTTDA_BF16X3 &&
+      prec != RTTDA_BF16X2)
     return set_error(RTTDA_E_ARG, "rttda_create: unsupported precision");
   if (!std::isfinite(c_x)) return set_error(RTTDA_E_ARG, "rttda_create: c_x not finite");
 
@@ -800,9 +802,11 @@ rttda_status rttda_create(int nocc, int nvirt, int naux, const double* eps_occ, 
   h->prec = prec;
   h->fbytes = prec == RTTDA_FP64 ? 8 : prec == RTTDA_BF16 ? 2 : 4;
   h->cbytes = prec == RTTDA_FP64 ? 8 : 4;
-  h->tc = prec == RTTDA_BF16 || prec == RTTDA_BF16X3;
-  h->nplanes = prec == RTTDA_BF16X3 ? 2 : 1;
-  h->nprod = prec == RTTDA_BF16X3 ? 3 : 1;
+  h->tc = prec == RTTDA_BF16 || prec == RTTDA_BF16X3 || prec == RTTDA_BF16X2;
+  h->nplanes = prec == RTTDA_BF16 ? 1 : 2;          // factor / amplitude planes
+  h->nprod = prec == RTTDA_BF16 ? 1 : 3;            // Z = B_oo c products
+  h->zplanes = prec == RTTDA_BF16X3 ? 2 : 1;        // Z planes kept
+  h->nprod_main = prec == RTTDA_BF16X3 ? 3 : prec == RTTDA_BF16X2 ? 2 : 1;
   h->vp = (int)cdiv(nvirt, 64) * 64;
   h->op = (int)cdiv(nocc, 8) * 8;
 
