@@ -443,6 +443,63 @@ def run_accuracy(args):
     return 0
 
 
+def run_serving(args):
+    """Continuous-batching trace (scaled-down serving workload): Poisson
+    arrivals, a random molecule, pulse and length per request, admitted by
+    footprint; reports p50/p99 time-to-spectrum and trajectory-steps/s."""
+    import torch
+    from paper_2601_16949_b300 import binding as rb
+    from paper_2601_16949_b300 import synth
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(args.serving_seed)
+    n = args.serving_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serving_rate, n))
+    spec = dict(gamma=1e-3, wmin=0.1, wmax=3.0, nfreq=512)
+    reqs = []
+    for k in range(n):
+        while True:
+            o = int(rng.integers(16, 49))
+            v = int(rng.integers(64, 193))
+            if v >= 4 * o:
+                break
+        P = 4 * v
+        steps = int(rng.integers(200, 2001))
+        if rng.random() < 0.5:
+            pulse = dict(kind=rb.KICK, E0=1e-3, direction=(0.0, 0.0, 1.0))
+        else:
+            pulse = dict(kind=rb.SIN2, E0=float(np.exp(rng.uniform(np.log(1e-3), np.log(5e-2)))),
+                         omega=float(rng.uniform(0.4, 2.5)), duration=0.8 * steps * DT, direction=(0.0, 0.0, 1.0))
+        mol = synth.molecule(o, v, P, seed=1000 + k)
+        reqs.append((mol, rb.make_request(mol, CX, args.prec, pulse, DT, steps, **spec), steps))
+    srv = rb.rttda_server_create(int(args.serving_budget_gb * (1 << 30)), args.serving_slots, args.serving_chunk)
+    ids = []
+    t0 = time.perf_counter()
+    for k, (mol, q, steps) in enumerate(reqs):
+        delay = arrivals[k] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(rb.rttda_server_submit(srv, q))
+    for rid in ids:
+        rb.rttda_server_wait(srv, rid, 3600.0)
+    wall = time.perf_counter() - t0
+    st = rb.rttda_server_stats_get(srv)
+    states = [rb.rttda_server_poll(srv, rid)[0] for rid in ids]
+    rb.rttda_server_destroy(srv)
+    line = {"mode": "serving", "metric": "time-to-spectrum p50/p99 and trajectory-steps/s (continuous batching)",
+            "requests": n, "arrival_rate_per_s": args.serving_rate, "precision": args.prec,
+            "workload": ("scaled serving trace: nocc U[16,48], nvirt U[64,192] with nvirt >= 4 nocc, naux = 4 nvirt, "
+                         "kick or sin^2 pulse (E0 log-uniform 1e-3..5e-2), 200-2000 RK4 steps, dt 0.05"),
+            "completed": st["completed"], "failed": st["failed"], "all_done": all(x == rb.REQ_DONE for x in states),
+            "p50_time_to_spectrum_s": st["p50_latency_s"], "p99_time_to_spectrum_s": st["p99_latency_s"],
+            "mean_time_to_spectrum_s": st["mean_latency_s"],
+            "trajectory_steps_per_s": st["trajectory_steps"] / max(st["busy_seconds"], 1e-9),
+            "trajectory_steps": st["trajectory_steps"], "busy_seconds": st["busy_seconds"], "wall_seconds": wall,
+            "max_concurrent": st["max_concurrent"], "slots": args.serving_slots,
+            "budget_gb": args.serving_budget_gb, "chunk_steps": args.serving_chunk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -455,6 +512,13 @@ def main():
                          "(z kick) and print their dipole/norm errors against FP64")
     ap.add_argument("--accuracy-precs", default="fp32,bf16x3,bf16x2,bf16")
     ap.add_argument("--accuracy-ref", default="fp64")
+    ap.add_argument("--serving", action="store_true", help="run the continuous-batching serving trace instead")
+    ap.add_argument("--serving-requests", type=int, default=60)
+    ap.add_argument("--serving-rate", type=float, default=5.0)
+    ap.add_argument("--serving-slots", type=int, default=16)
+    ap.add_argument("--serving-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serving-chunk", type=int, default=200)
+    ap.add_argument("--serving-seed", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-steps", type=int, default=3)
@@ -468,6 +532,8 @@ def main():
         return run_reference(args)
     if args.accuracy:
         return run_accuracy(args)
+    if args.serving:
+        return run_serving(args)
     return run_gpu(args)
 
 

@@ -1,0 +1,105 @@
+/*
+ * rttda_server.h - continuous-batching RT-TDA propagation server.
+ *
+ * Serving pattern for the RT-TDA hot path (real-time TDA propagation,
+ * arXiv 2601.16949, Sec. 2.2 "Propagation Algorithm", followed by the
+ * spectrum of Eq. fourier_transform on the dipole trace): many independent
+ * propagation requests, each with its own molecule (nocc, nvirt, naux), pulse
+ * and length, arrive over time.  A scheduler thread admits a request when
+ * its device-memory footprint fits the budget and an active slot is free,
+ * keeps its factors and amplitudes resident on the GPU, and advances every
+ * active request in chunks of RK4 steps on its own CUDA stream, so the work
+ * of different requests overlaps on the device.  A finished request's dipole
+ * trace is turned into a spectrum on the GPU; its memory is then released
+ * and the next request is admitted.
+ *
+ * Conventions are those of rttda.h.  All functions are thread-safe.
+ */
+#ifndef RTTDA_SERVER_H
+#define RTTDA_SERVER_H
+
+#include <stddef.h>
+
+#include "rttda.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One propagation request: molecule (as in rttda_create), one pulse, the
+ * time grid and the spectrum wanted.  Host arrays are copied by
+ * rttda_server_submit and may be freed when it returns.  The spectrum is
+ *   S(w_j) = (w_j / E0) sum_k wt_k (mu_k - mu_0) exp(-gamma t_k) sin(w_j t_k) dt
+ * over the request's dipole trace (rttda_spectrum with kappa = pulse.E0). */
+typedef struct {
+  int nocc, nvirt, naux;
+  const double *eps_occ, *eps_virt, *B_ov, *B_oo, *B_vv, *mu_oo, *mu_vv, *mu_0ov;
+  double c_x;
+  int prec;            /* rttda_prec */
+  rttda_pulse pulse;
+  double dt;           /* > 0 */
+  long nsteps;         /* >= 1 */
+  double gamma, wmin, wmax;
+  long nfreq;          /* >= 1 */
+} rttda_request;
+
+typedef enum {
+  RTTDA_REQ_PENDING = 0,
+  RTTDA_REQ_ACTIVE = 1,
+  RTTDA_REQ_DONE = 2,
+  RTTDA_REQ_FAILED = 3,
+  RTTDA_REQ_CANCELLED = 4
+} rttda_request_state;
+
+typedef struct {
+  long submitted, completed, failed, cancelled, pending, active;
+  int max_concurrent;          /* largest number of requests active at once */
+  double trajectory_steps;     /* RK4 steps completed, summed over requests  */
+  double p50_latency_s;        /* time to spectrum: submit -> spectrum ready */
+  double p99_latency_s;
+  double mean_latency_s;
+  double busy_seconds;         /* first submit -> last completion            */
+  size_t bytes_in_use, bytes_budget;
+} rttda_server_stats;
+
+/* Start a server on the current CUDA device.
+ *   hbm_budget   device bytes the server may hold for admitted requests
+ *                (their estimated footprints, rttda_estimate_bytes);
+ *   max_active   most requests on the GPU at once (>= 1);
+ *   chunk_steps  RK4 steps per scheduling chunk (>= 1).
+ * Errors: RTTDA_E_ARG, RTTDA_E_CUDA (no usable device). */
+rttda_status rttda_server_create(size_t hbm_budget, int max_active, long chunk_steps, rttda_server_t* out);
+
+/* Queue a request; *id receives its identifier.  RTTDA_E_ARG for invalid
+ * fields (sizes, NULL arrays, pulse as in rttda_set_field, nsteps, nfreq). */
+rttda_status rttda_server_submit(rttda_server_t s, const rttda_request* req, long* id);
+
+/* Non-blocking status.  *state gets an rttda_request_state.  When the
+ * request is DONE and the pointers are not NULL: spectrum[nfreq],
+ * omega[nfreq], dipole[nsteps+1] receive its results and *latency_s its
+ * time to spectrum.  A FAILED request's reason is in rttda_last_error(). */
+rttda_status rttda_server_poll(rttda_server_t s, long id, int* state, double* spectrum, double* omega,
+                               double* dipole, double* latency_s);
+
+/* Block until the request leaves PENDING/ACTIVE or timeout_s elapses
+ * (RTTDA_E_TIMEOUT; the request keeps running). */
+rttda_status rttda_server_wait(rttda_server_t s, long id, double timeout_s);
+
+/* Cancel a pending or active request (an active one stops after its chunk
+ * in flight and releases its memory). */
+rttda_status rttda_server_cancel(rttda_server_t s, long id);
+
+rttda_status rttda_server_stats_get(rttda_server_t s, rttda_server_stats* st);
+
+/* Device bytes a handle with this shape and precision needs for ntraj
+ * trajectories and nsteps-long host traces (upper estimate). */
+rttda_status rttda_estimate_bytes(int nocc, int nvirt, int naux, int ntraj, int prec, long nsteps, size_t* bytes);
+
+/* Stop the scheduler (active requests are cancelled) and free everything. */
+void rttda_server_destroy(rttda_server_t s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTTDA_SERVER_H */

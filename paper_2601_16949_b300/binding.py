@@ -38,6 +38,25 @@ class rttda_pulse(ct.Structure):
                 ("dir", ct.c_double * 3)]
 
 
+class rttda_request(ct.Structure):
+    _fields_ = [("nocc", ct.c_int), ("nvirt", ct.c_int), ("naux", ct.c_int)] + \
+               [(n, ct.POINTER(ct.c_double)) for n in ("eps_occ", "eps_virt", "B_ov", "B_oo", "B_vv", "mu_oo",
+                                                        "mu_vv", "mu_0ov")] + \
+               [("c_x", ct.c_double), ("prec", ct.c_int), ("pulse", rttda_pulse), ("dt", ct.c_double),
+                ("nsteps", ct.c_long), ("gamma", ct.c_double), ("wmin", ct.c_double), ("wmax", ct.c_double),
+                ("nfreq", ct.c_long)]
+
+
+class rttda_server_stats(ct.Structure):
+    _fields_ = [(n, ct.c_long) for n in ("submitted", "completed", "failed", "cancelled", "pending", "active")] + \
+               [("max_concurrent", ct.c_int), ("trajectory_steps", ct.c_double), ("p50_latency_s", ct.c_double),
+                ("p99_latency_s", ct.c_double), ("mean_latency_s", ct.c_double), ("busy_seconds", ct.c_double),
+                ("bytes_in_use", ct.c_size_t), ("bytes_budget", ct.c_size_t)]
+
+
+REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
+
+
 class RTTDAError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -70,6 +89,19 @@ lib.rttda_launch_stats.argtypes = [_h, ct.POINTER(ct.c_longlong), ct.POINTER(ct.
 lib.rttda_coulomb_noalloc.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int,
                                       ct.c_void_p, ct.c_void_p]
 lib.rttda_coulomb_noalloc.restype = ct.c_int
+lib.rttda_server_create.argtypes = [ct.c_size_t, ct.c_int, ct.c_long, ct.POINTER(_h)]
+lib.rttda_server_submit.argtypes = [_h, ct.POINTER(rttda_request), ct.POINTER(ct.c_long)]
+lib.rttda_server_poll.argtypes = [_h, ct.c_long, ct.POINTER(ct.c_int), _dp, _dp, _dp, _dp]
+lib.rttda_server_wait.argtypes = [_h, ct.c_long, ct.c_double]
+lib.rttda_server_cancel.argtypes = [_h, ct.c_long]
+lib.rttda_server_stats_get.argtypes = [_h, ct.POINTER(rttda_server_stats)]
+lib.rttda_estimate_bytes.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_long,
+                                     ct.POINTER(ct.c_size_t)]
+lib.rttda_server_destroy.argtypes = [_h]
+lib.rttda_server_destroy.restype = None
+for _name in ("rttda_server_create", "rttda_server_submit", "rttda_server_poll", "rttda_server_wait",
+              "rttda_server_cancel", "rttda_server_stats_get", "rttda_estimate_bytes"):
+    getattr(lib, _name).restype = ct.c_int
 lib.rttda_destroy.argtypes = [_h]
 lib.rttda_destroy.restype = None
 for _name in ("rttda_create", "rttda_memory_bytes", "rttda_set_field", "rttda_propagate", "rttda_propagate_device",
@@ -226,6 +258,73 @@ def rttda_coulomb_noalloc(nocc, nvirt, naux, B_ov_dev, c_dev, ntraj, sigma_dev, 
 
 def rttda_destroy(h) -> None:
     lib.rttda_destroy(h)
+
+
+def rttda_estimate_bytes(nocc, nvirt, naux, ntraj, prec, nsteps) -> int:
+    n = ct.c_size_t()
+    prec = PRECISIONS.get(prec, prec) if isinstance(prec, str) else prec
+    _check(lib.rttda_estimate_bytes(nocc, nvirt, naux, ntraj, int(prec), int(nsteps), ct.byref(n)),
+           "rttda_estimate_bytes")
+    return n.value
+
+
+def rttda_server_create(hbm_budget, max_active, chunk_steps):
+    h = _h()
+    _check(lib.rttda_server_create(int(hbm_budget), int(max_active), int(chunk_steps), ct.byref(h)),
+           "rttda_server_create")
+    return h
+
+
+def make_request(mol, c_x, prec, pulse, dt, nsteps, gamma, wmin, wmax, nfreq):
+    """Build an rttda_request; the returned tuple keeps the arrays alive."""
+    arrs = [_f64(mol[k]) for k in ("eps_occ", "eps_virt", "B_ov", "B_oo", "B_vv", "mu_oo", "mu_vv", "mu_0ov")]
+    q = rttda_request()
+    q.nocc, q.nvirt, q.naux = mol["nocc"], mol["nvirt"], mol["naux"]
+    for name, a in zip(("eps_occ", "eps_virt", "B_ov", "B_oo", "B_vv", "mu_oo", "mu_vv", "mu_0ov"), arrs):
+        setattr(q, name, _ptr(a))
+    q.c_x = float(c_x)
+    q.prec = PRECISIONS.get(prec, prec) if isinstance(prec, str) else int(prec)
+    q.pulse = make_pulses([pulse])[0]
+    q.dt, q.nsteps = float(dt), int(nsteps)
+    q.gamma, q.wmin, q.wmax, q.nfreq = float(gamma), float(wmin), float(wmax), int(nfreq)
+    return q, arrs
+
+
+def rttda_server_submit(srv, request) -> int:
+    q = request[0] if isinstance(request, tuple) else request
+    rid = ct.c_long()
+    _check(lib.rttda_server_submit(srv, ct.byref(q), ct.byref(rid)), "rttda_server_submit")
+    return rid.value
+
+
+def rttda_server_poll(srv, rid, nfreq=0, nsteps=-1):
+    st = ct.c_int()
+    S = np.zeros(max(nfreq, 1))
+    om = np.zeros(max(nfreq, 1))
+    dip = np.zeros(max(nsteps + 1, 1))
+    lat = ct.c_double()
+    _check(lib.rttda_server_poll(srv, int(rid), ct.byref(st), _ptr(S) if nfreq else None,
+                                 _ptr(om) if nfreq else None, _ptr(dip) if nsteps >= 0 else None,
+                                 ct.byref(lat)), "rttda_server_poll")
+    return st.value, (S if nfreq else None), (om if nfreq else None), (dip if nsteps >= 0 else None), lat.value
+
+
+def rttda_server_wait(srv, rid, timeout_s) -> None:
+    _check(lib.rttda_server_wait(srv, int(rid), float(timeout_s)), "rttda_server_wait")
+
+
+def rttda_server_cancel(srv, rid) -> None:
+    _check(lib.rttda_server_cancel(srv, int(rid)), "rttda_server_cancel")
+
+
+def rttda_server_stats_get(srv) -> dict:
+    st = rttda_server_stats()
+    _check(lib.rttda_server_stats_get(srv, ct.byref(st)), "rttda_server_stats_get")
+    return {name: getattr(st, name) for name, _ in rttda_server_stats._fields_}
+
+
+def rttda_server_destroy(srv) -> None:
+    lib.rttda_server_destroy(srv)
 
 
 # ---------------------------------------------------------------------------

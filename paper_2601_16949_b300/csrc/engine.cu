@@ -451,13 +451,13 @@ void enqueue_observe(rttda_ctx* h, const double* X, double* dip, double* nrm, lo
 // One RK4 step (four sigma builds) plus the observables of the step's start.
 template <typename O>
 void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, double* dip, double* nrm, long long ld,
-                  cudaStream_t s) {
+                  long long offset, cudaStream_t s) {
   h->launches += 2;  // efield + step counter
   k_efield<<<1, 128, 0, s>>>(h->T, h->d_pulses, h->d_step, base, t_off, dt, h->E);
   for (int st = 0; st < 4; ++st) {
     const bool fld = h->any_field;
     if (st == 0 || fld) O::field(h, h->Xs, s);
-    if (st == 0 && dip) enqueue_observe(h, h->Xn, dip, nrm, ld, 0, s);
+    if (st == 0 && dip) enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
     O::coulomb(h, h->Xs, s);
     O::exchange(h, h->Xs, s);
     O::combine(h, 0, st, fld, dt, h->Xs, nullptr, s);
@@ -466,7 +466,7 @@ void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, doub
 }
 
 rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, double* dip, double* nrm,
-                       cudaStream_t s) {
+                       long long ld, long long offset, cudaStream_t s) {
   // stage times are t_off + (base + k + c_s) dt with an integer base when the
   // start time is a whole number of steps
   long long base = 0;
@@ -476,21 +476,20 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
     base = (long long)nb;
     t_off = 0.0;
   }
-  const long long ld = nsteps + 1;
   CK(cudaMemsetAsync(h->d_step, 0, sizeof(long long), s));
   CK(cudaMemcpyAsync(h->Xs, h->Xn, sizeof(double) * h->N * 2 * h->T, cudaMemcpyDeviceToDevice, s));
   if (nsteps > 0 && h->prof_on) {
     // profiling: direct launches so that every kernel class gets its events
     const long long l0 = h->launches;
     for (long k = 0; k < nsteps; ++k)
-      dispatch(h->prec, [&](auto ops) { enqueue_step(h, ops, base, t_off, dt, dip, nrm, ld, s); });
+      dispatch(h->prec, [&](auto ops) { enqueue_step(h, ops, base, t_off, dt, dip, nrm, ld, offset, s); });
     h->launches_per_step = (h->launches - l0) / nsteps;
   } else if (nsteps > 0) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const long long l0 = h->launches;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    dispatch(h->prec, [&](auto ops) { enqueue_step(h, ops, base, t_off, dt, dip, nrm, ld, s); });
+    dispatch(h->prec, [&](auto ops) { enqueue_step(h, ops, base, t_off, dt, dip, nrm, ld, offset, s); });
     h->launches_per_step = h->launches - l0;
     h->launches = l0 + h->launches_per_step * nsteps;
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
@@ -510,7 +509,7 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
   }
   if (dip) {
     dispatch(h->prec, [&](auto ops) { decltype(ops)::field(h, h->Xn, s); });
-    enqueue_observe(h, h->Xn, dip, nrm, ld, 0, s);
+    enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
   }
   CK(cudaGetLastError());
   h->t_now = t_off + (double)(base + nsteps) * dt;
@@ -924,7 +923,8 @@ rttda_status rttda_set_field(rttda_t h, const rttda_pulse* pulses, int ntraj) {
 }
 
 static rttda_status propagate_impl(rttda_t h, bool fresh, const double* c0_dev, double dt, long nsteps,
-                                   double* c_out_dev, double* dip_dev, double* nrm_dev, cudaStream_t s) {
+                                   double* c_out_dev, double* dip_dev, double* nrm_dev, cudaStream_t s,
+                                   long long ld = -1, long long offset = 0) {
   if (h->T < 1) return set_error(RTTDA_E_STATE, "rttda_propagate: call rttda_set_field first");
   if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(RTTDA_E_ARG, "rttda_propagate: dt must be > 0");
   if (nsteps < 0) return set_error(RTTDA_E_ARG, "rttda_propagate: nsteps must be >= 0");
@@ -950,7 +950,8 @@ static rttda_status propagate_impl(rttda_t h, bool fresh, const double* c0_dev, 
     if (!dip) dip = tmp;
     if (!nrm) nrm = tmp;
   }
-  rttda_status st = run_steps(h, t_call, dt, nsteps, dip, nrm, s);
+  if (ld < 0) ld = nsteps + 1;
+  rttda_status st = run_steps(h, t_call, dt, nsteps, dip, nrm, ld, offset, s);
   if (st == RTTDA_OK && c_out_dev) k_dev_to_abi<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->Xn, c_out_dev);
   if (tmp) {
     cudaStreamSynchronize(s);
@@ -961,6 +962,16 @@ static rttda_status propagate_impl(rttda_t h, bool fresh, const double* c0_dev, 
   return RTTDA_OK;
 }
 
+}  // extern "C"
+namespace rttda {
+rttda_status advance(rttda_t h, bool fresh, double dt, long nsteps, double* dip, double* nrm, long long ld,
+                     long long offset, cudaStream_t s) {
+  return propagate_impl(h, fresh, nullptr, dt, nsteps, nullptr, dip, nrm, s ? s : h->stream, ld, offset);
+}
+cudaStream_t handle_stream(rttda_t h) { return h->stream; }
+}  // namespace rttda
+extern "C" {
+
 rttda_status rttda_propagate_device(rttda_t h, const double* c0_dev, double dt, long nsteps, double* c_out_dev,
                                     double* dipole_dev, double* norm_dev, void* stream) {
   g_last_error.clear();
@@ -970,6 +981,12 @@ rttda_status rttda_propagate_device(rttda_t h, const double* c0_dev, double dt, 
 }
 
 // A bounded device wait that ran out leaves a code in d_err.
+static rttda_status check_device_error(rttda_t h);
+}  // extern "C"
+namespace rttda {
+rttda_status device_error(rttda_t h) { return check_device_error(h); }
+}  // namespace rttda
+extern "C" {
 static rttda_status check_device_error(rttda_t h) {
   int e = 0;
   CK(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1072,6 +1089,49 @@ rttda_status rttda_sigma(rttda_t h, const double* c_dev, double t, double* sigma
   });
   k_dev_to_abi<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->term, sigma_dev);
   CK(cudaGetLastError());
+  return RTTDA_OK;
+}
+
+}  // extern "C"
+namespace rttda {
+rttda_status spectrum_device(const double* trace_dev, long long ntr, long long npts, double dt, double kappa,
+                             double gamma, double wmin, double wmax, long long nfreq, double* om_dev, double* S_dev,
+                             cudaStream_t s) {
+  if (ntr < 1 || npts < 2 || nfreq < 1 || !(dt > 0.0) || kappa == 0.0 || !(gamma >= 0.0))
+    return set_error(RTTDA_E_ARG, "spectrum: bad arguments");
+  const double dw = nfreq > 1 ? (wmax - wmin) / (double)(nfreq - 1) : 0.0;
+  k_spectrum<<<(unsigned)nfreq, 256, 0, s>>>(trace_dev, ntr, npts, dt, kappa, gamma, wmin, dw, om_dev, S_dev);
+  CK(cudaGetLastError());
+  return RTTDA_OK;
+}
+
+// Device bytes a handle needs for a batch (upper estimate, used for admission).
+size_t estimate_bytes(int nocc, int nvirt, int naux, int ntraj, int prec, long nsteps) {
+  const size_t o = nocc, v = nvirt, P = naux, T = ntraj, C = 2 * T, ov = o * v, N = 1 + ov;
+  const bool tc = prec == RTTDA_BF16 || prec == RTTDA_BF16X3 || prec == RTTDA_BF16X2;
+  const size_t fb = prec == RTTDA_FP64 ? 8 : prec == RTTDA_BF16 ? 2 : 4, cb = prec == RTTDA_FP64 ? 8 : 4;
+  const size_t vp = (v + 63) / 64 * 64, op = (o + 7) / 8 * 8;
+  const size_t planes = prec == RTTDA_BF16 ? 1 : 2, zplanes = prec == RTTDA_BF16X3 ? 2 : 1;
+  size_t b = P * ov * fb + (o + v + 3 * (o * o + v * v + ov)) * 8;
+  b += tc ? (P * o * op + P * vp * vp) * 2 * planes : (P * o * o + P * v * v) * fb;
+  b += N * C * 8 * 6 + T * (o * o + v * v + ov) * (8 + cb);               // state, dipole blocks
+  b += (size_t)32 * P * C * cb + (size_t)16 * ov * C * cb;                 // Coulomb partials
+  const size_t zcap = (size_t)2 << 30;
+  if (tc)
+    b += std::min(zcap, C * o * vp * 2 * zplanes * P) + C * vp * op * 2 * planes + (size_t)kNumSM * C * o * v * 4;
+  else
+    b += std::min((size_t)1 << 30, v * C * o * cb * P) + (size_t)4 * kNumSM * C * o * v * cb;
+  b += (2 * N * T * 2 + 2 * T * (size_t)(nsteps + 1)) * 8;                 // host-call staging
+  return b + b / 10 + ((size_t)64 << 20);
+}
+}  // namespace rttda
+extern "C" {
+
+rttda_status rttda_estimate_bytes(int nocc, int nvirt, int naux, int ntraj, int prec, long nsteps, size_t* bytes) {
+  g_last_error.clear();
+  if (!bytes || nocc < 1 || nvirt < 1 || naux < 1 || ntraj < 1 || nsteps < 0)
+    return set_error(RTTDA_E_ARG, "rttda_estimate_bytes: bad arguments");
+  *bytes = estimate_bytes(nocc, nvirt, naux, ntraj, prec, nsteps);
   return RTTDA_OK;
 }
 
