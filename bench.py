@@ -27,11 +27,78 @@ if ROOT not in sys.path:
 
 METRIC = "RT-TDA trajectory-steps/s vs plain FP64 path at stated dipole err; p50/p99 latency"
 UNIT = "trajectory-steps/s"
-NOCC, NVIRT, NAUX, CX, DT, KAPPA, SEED = 64, 448, 1536, 0.2, 0.05, 1e-3, 0
+CX, KAPPA, SEED = 0.2, 1e-3, 0
 DIRS = [(1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)]
+# workloads: the linear-absorption one is the default bench line; the others
+# are the batched field scan and the large system
+WORKLOADS = {
+    "absorption": dict(nocc=64, nvirt=448, naux=1536, dt=0.05,
+                       desc="linear absorption: 3 trajectories (x/y/z kicks, kappa=1e-3) per GPU"),
+    "fieldscan": dict(nocc=128, nvirt=768, naux=3072, dt=0.04,
+                      desc=("batched field scan: 32 sin^2 pulses (400 au) per GPU at omega = lambda_min(A) and "
+                            "lambda_min/2, amplitudes log-spaced 1e-3..5e-2, z-polarised")),
+    "large": dict(nocc=256, nvirt=1536, naux=4096, dt=0.05, desc="large system: one z kick kappa=1e-3"),
+}
+NOCC, NVIRT, NAUX, DT = 64, 448, 1536, 0.05
 NDIM = 1 + NOCC * NVIRT
-WORKLOAD = (f"linear absorption: nocc={NOCC} nvirt={NVIRT} naux={NAUX} (dim {NDIM}), "
-            f"3 trajectories (x/y/z kicks, kappa={KAPPA}) per GPU, RK4 dt={DT} au, c_x={CX}")
+WORKLOAD = ""
+
+
+def set_workload(name: str) -> None:
+    global NOCC, NVIRT, NAUX, DT, NDIM, WORKLOAD
+    w = WORKLOADS[name]
+    NOCC, NVIRT, NAUX, DT = w["nocc"], w["nvirt"], w["naux"], w["dt"]
+    NDIM = 1 + NOCC * NVIRT
+    WORKLOAD = (f"{w['desc']}: nocc={NOCC} nvirt={NVIRT} naux={NAUX} (dim {NDIM}), RK4 dt={DT} au, c_x={CX}")
+
+
+set_workload("absorption")
+
+
+def lowest_eigenvalue(rb, mol, iters=60):
+    """lambda_min of A by Lanczos with full reorthogonalisation, using the
+    library's sigma (a kicked trajectory has E = 0 for t > 0, so sigma = A c)."""
+    import torch
+    prop = rb.Propagator(mol, CX, "bf16x3")
+    prop.set_field([dict(kind=rb.KICK, E0=KAPPA, direction=(0.0, 0.0, 1.0))])
+    n = prop.n
+    rng = np.random.default_rng(7)
+    q = rng.standard_normal(n)
+    q[0] = 0.0
+    q /= np.linalg.norm(q)
+    Q, alpha, beta = [q], [], []
+    cd = torch.zeros((1, n, 2), dtype=torch.float64, device="cuda")
+    sd = torch.zeros_like(cd)
+    for k in range(iters):
+        cd[0, :, 0] = torch.from_numpy(Q[-1])
+        cd[0, :, 1] = 0.0
+        rb.rttda_sigma(prop.h, cd.data_ptr(), 1.0, sd.data_ptr(), 0)
+        rb.rttda_sync(prop.h)
+        w = sd[0, :, 0].cpu().numpy()
+        a = float(w @ Q[-1])
+        w = w - a * Q[-1] - (beta[-1] * Q[-2] if beta else 0.0)
+        for qq in Q:
+            w -= (w @ qq) * qq
+        alpha.append(a)
+        b = float(np.linalg.norm(w))
+        if b < 1e-12 or k == iters - 1:
+            break
+        beta.append(b)
+        Q.append(w / b)
+    prop.close()
+    Tm = np.diag(alpha) + np.diag(beta[:len(alpha) - 1], 1) + np.diag(beta[:len(alpha) - 1], -1)
+    return float(np.linalg.eigvalsh(Tm)[0])
+
+
+def workload_pulses(rb, name, mol):
+    if name == "fieldscan":
+        lam = lowest_eigenvalue(rb, mol)
+        amps = np.exp(np.linspace(np.log(1e-3), np.log(5e-2), 16))
+        return [dict(kind=rb.SIN2, E0=float(a), omega=w, duration=400.0, direction=(0.0, 0.0, 1.0))
+                for w in (lam, 0.5 * lam) for a in amps], {"lambda_min": lam}
+    if name == "large":
+        return [dict(kind=rb.KICK, E0=KAPPA, direction=(0.0, 0.0, 1.0))], {}
+    return [dict(kind=rb.KICK, E0=KAPPA, direction=d) for d in DIRS], {}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 CUDA-core peak from unit counts: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz.
 FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
@@ -44,10 +111,10 @@ def dist_info():
     return rank, world, local
 
 
-def base_config(prec: str, world: int) -> dict:
-    return {"workload": WORKLOAD, "precision": prec, "trajectories_per_gpu": 3,
-            "global_trajectories": 3 * world, "parallelism": f"trajectory replicas x{world}",
-            "l2": "inputs larger than L2: every stage streams B_vv (1.23 GB fp32) and B_ov",
+def base_config(prec: str, world: int, T: int = 3) -> dict:
+    return {"workload": WORKLOAD, "precision": prec, "trajectories_per_gpu": T,
+            "global_trajectories": T * world, "parallelism": f"trajectory replicas x{world}",
+            "l2": "inputs larger than L2: every stage streams the B_vv planes (>1 GB) and B_ov",
             "seed": SEED}
 
 
@@ -272,8 +339,8 @@ def run_gpu(args):
         return float(t.item())
 
     mol = synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
-    pulses = [dict(kind=rb.KICK, E0=KAPPA, direction=d) for d in DIRS]
-    T, K, W = 3, args.steps, args.warmup
+    pulses, wl_info = workload_pulses(rb, args.workload, mol)
+    T, K, W = len(pulses), args.steps, args.warmup
     prop = rb.Propagator(mol, CX, args.prec)
     prop.set_field(pulses)
     h = prop.h
@@ -332,9 +399,10 @@ def run_gpu(args):
     prof = rb.rttda_profile_read(h)
     rb.rttda_profile(h, False)
 
-    # plain FP64 single-trajectory path on the same molecule (z kick)
+    # plain FP64 single-trajectory path on the same molecule (the batch's
+    # last trajectory)
     p64 = rb.Propagator(mol, CX, "fp64")
-    p64.set_field([pulses[2]])
+    p64.set_field([pulses[-1]])
     k64 = max(2, min(args.fp64_steps, K))
     d64 = torch.zeros((1, k64 + 1), dtype=torch.float64, device=dev)
     n64 = torch.zeros_like(d64)
@@ -349,7 +417,7 @@ def run_gpu(args):
     fp64_rate = k64 / (e0.elapsed_time(e1) / 1e3)
     d64h = d64.cpu().numpy()[0]
     ref = d64h - d64h[0]
-    dip_err = float(np.max(np.abs(dip32[2, :k64 + 1] - d64h)) / max(np.max(np.abs(ref)), 1e-300))
+    dip_err = float(np.max(np.abs(dip32[T - 1, :k64 + 1] - d64h)) / max(np.max(np.abs(ref)), 1e-300))
     p64.close()
 
     # end to end through the host-buffer ABI: per step, H2D of the state from
@@ -382,13 +450,16 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cb = time_oracle(mol, 8, args.cpu_steps, warmup=1)
+        # row block of the explicit A of at most ~1 GB
+        rows_occ = int(max(1, min(8, (1 << 27) // (NVIRT * NDIM))))
+        cb = time_oracle(mol, rows_occ, args.cpu_steps, warmup=1)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     dtype = {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "bf16x2": "bf16x2"}[args.prec]
-    cfg = base_config(args.prec, world)
+    cfg = base_config(args.prec, world, T)
+    cfg.update(wl_info)
     cfg.update({"fp64_path_traj_steps_per_s": fp64_rate, "speedup_vs_fp64_path": value / world / fp64_rate,
-                "fp64_path": f"plain FP64, one trajectory (z kick), {k64} timed steps",
+                "fp64_path": f"plain FP64, one trajectory (the batch's last), {k64} timed steps",
                 "dipole_rel_err_vs_fp64": dip_err, "dipole_err_horizon_steps": k64,
                 "launches_per_step": per_step})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -506,6 +577,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="absorption", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="bf16x2", choices=["fp64", "fp32", "bf16", "bf16x3", "bf16x2"])
     ap.add_argument("--accuracy", type=int, default=0,
                     help="instead of timing: propagate N steps with FP64 and the chosen precisions "
@@ -528,6 +600,7 @@ def main():
                          "no FP64 comparison, no end-to-end or CPU legs")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
+    set_workload(args.workload)
     if args.impl == "reference":
         return run_reference(args)
     if args.accuracy:

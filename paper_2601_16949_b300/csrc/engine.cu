@@ -147,6 +147,15 @@ struct rttda_ctx {
   CUtensorMap tmZB;
   std::vector<int> tc_kper;
   int* d_err = nullptr;
+  // tensor-core Coulomb (batches with 2T >= 16 columns)
+  __nv_bfloat16* Bov_tc = nullptr;   // [plane][P][ov]
+  __nv_bfloat16* BovT_tc = nullptr;  // [plane][ov][P]
+  __nv_bfloat16* Xc = nullptr;       // [plane][C][ov]
+  __nv_bfloat16* Wt = nullptr;       // [plane][C][P]
+  float* wpart_tc = nullptr;         // [SKc1][P][C]
+  bool coul_tc = false;
+  int SKc1 = 1, SKc2 = 1;
+  CUtensorMap tmC1A, tmC1B, tmC2A, tmC2B;
 
   // host staging for the host-buffer entry points
   double* h_io = nullptr;  // device staging [T][N][2] + traces
@@ -180,13 +189,15 @@ rttda_ctx::~rttda_ctx() {
   dfree(mu_0);
   dfree(Bvv_tc);
   dfree(Boo_tc);
+  dfree(Bov_tc);
+  dfree(BovT_tc);
   dfree(d_err);
   if (stream) cudaStreamDestroy(stream);
 }
 
 void rttda_ctx::free_batch() {
   void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xn, Xs, acc, F, E, term,
-                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk};
+                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk, Xc, Wt, wpart_tc};
   for (void* p : ps) dfree(p);
   d_pulses = nullptr;
   d_kappa = d_dirs = moo64 = mvv64 = m064 = nullptr;
@@ -195,6 +206,9 @@ void rttda_ctx::free_batch() {
   d_step = nullptr;
   w = Jpart = Zt = Kpart = nullptr;
   Xt = Zk = nullptr;
+  Xc = Wt = nullptr;
+  wpart_tc = nullptr;
+  coul_tc = false;
   tmZA.clear();
   tmMA.clear();
   tmMB.clear();
@@ -263,6 +277,49 @@ void set_tc_smem_limits() {
   tc_attr<128, 7, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<224, 5, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<256, 4, tc::BMODE_VV, tc::EPI_PARTIAL>();
+  tc_attr<64, 8, tc::BMODE_PLAIN, tc::EPI_PARTIAL>();
+}
+
+// Batched Coulomb on tensor cores: w = B_ov c (split-K over ia), then
+// J = B_ov^T (2w) with B_ov^T stored transposed; BF16 planes as in the
+// exchange, J as FP32 split-K partials for the combine.
+void coulomb_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
+  Prof pr(h, RTTDA_KC_COULOMB, s);
+  h->launches += 4;
+  const int C = 2 * h->T, P = h->P;
+  const long long ov = h->ov;
+  k_prep_xc<<<blocks_for(ov, 32), 256, (size_t)32 * (C + 1) * sizeof(double), s>>>(
+      ov, C, X, h->Xc, h->nplanes > 1 ? h->Xc + (size_t)C * ov : nullptr);
+  {
+    tc::Params prm{};
+    prm.M = P;
+    prm.N = C;
+    prm.kt_total = (int)cdiv(ov, tc::kBK);
+    prm.nsplit = h->SKc1;
+    prm.kt_per_split = (int)cdiv(prm.kt_total, h->SKc1);
+    prm.nprod = h->nprod;
+    prm.out = h->wpart_tc;
+    prm.ldo = C;
+    prm.split_stride = (long long)P * C;
+    prm.err = h->d_err;
+    tc_launch<64, 8, tc::BMODE_PLAIN, tc::EPI_PARTIAL>(h->tmC1A, h->tmC1B, prm, s);
+  }
+  k_prep_wt<<<blocks_for((long long)P * C, 256), 256, 0, s>>>(P, C, h->SKc1, h->wpart_tc, h->Wt,
+                                                               h->nplanes > 1 ? h->Wt + (size_t)C * P : nullptr);
+  {
+    tc::Params prm{};
+    prm.M = (int)ov;
+    prm.N = C;
+    prm.kt_total = (int)cdiv(P, tc::kBK);
+    prm.nsplit = h->SKc2;
+    prm.kt_per_split = (int)cdiv(prm.kt_total, h->SKc2);
+    prm.nprod = h->nprod;
+    prm.out = (float*)h->Jpart;
+    prm.ldo = C;
+    prm.split_stride = ov * C;
+    prm.err = h->d_err;
+    tc_launch<64, 8, tc::BMODE_PLAIN, tc::EPI_PARTIAL>(h->tmC2A, h->tmC2B, prm, s);
+  }
 }
 
 void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
@@ -325,6 +382,10 @@ struct Ops {
   using TL = Tile<TC>;
 
   static void coulomb(rttda_ctx* h, const double* X, cudaStream_t s) {
+    if (XTC && h->coul_tc) {
+      coulomb_tc(h, X, s);
+      return;
+    }
     Prof pr(h, RTTDA_KC_COULOMB, s);
     h->launches += 2;
     const int C = 2 * h->T;
@@ -554,6 +615,76 @@ static rttda_status bf16_map(CUtensorMap* m, const void* base, int rank, const u
   return RTTDA_OK;
 }
 
+// Bytes allowed for one chunk of Z (all of P when it fits): at most 40 GiB
+// and at most a third of the device memory free now.
+static size_t zbudget_bytes() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)6 << 30;
+  return std::max<size_t>((size_t)256 << 20, std::min<size_t>((size_t)40 << 30, fr / 3));
+}
+
+// Split-K count for a persistent launch over `tiles` output tiles: the split
+// whose tile count best fills whole waves of the SMs (ties and near-ties go
+// to fewer splits), keeping at least 16 K tiles per split.
+static int choose_splits(long long tiles, long long kt) {
+  int best = 1;
+  double best_score = -1.0;
+  for (int sk = 1; sk <= 64; ++sk) {
+    if (sk > 1 && kt / sk < 16) break;
+    const double x = (double)(tiles * sk) / kNumSM;
+    const double score = x / std::ceil(x) - 0.002 * sk;
+    if (score > best_score) {
+      best = sk;
+      best_score = score;
+    }
+  }
+  return best;
+}
+
+// Buffers, split-K plans and TMA maps of the tensor-core Coulomb.
+static rttda_status alloc_coul_tc(rttda_ctx* h, int C) {
+  const int P = h->P;
+  const long long ov = h->ov;
+  const size_t np = (size_t)h->nplanes;
+  CKS(dalloc(&h->Xc, (size_t)C * ov * np));
+  CKS(dalloc(&h->Wt, (size_t)C * P * np));
+  h->SKc1 = choose_splits(cdiv(P, tc::kBM) * cdiv(C, 64), cdiv(ov, tc::kBK));
+  h->SKc2 = choose_splits(cdiv(ov, tc::kBM) * cdiv(C, 64), cdiv(P, tc::kBK));
+  CKS(dalloc(&h->wpart_tc, (size_t)h->SKc1 * P * C));
+  char* p = nullptr;
+  CK(cudaMalloc((void**)&p, (size_t)h->SKc2 * ov * C * sizeof(float)));
+  h->Jpart = p;
+  h->SJ = h->SKc2;
+  h->SW = 1;
+  CK(cudaMalloc((void**)&p, sizeof(float)));  // pass-1 SIMT scratch is unused here
+  h->w = p;
+  {
+    const uint64_t dims[3] = {(uint64_t)ov, (uint64_t)P, np};
+    const uint64_t str[2] = {(uint64_t)ov * 2, (uint64_t)P * ov * 2};
+    const uint32_t box[3] = {64, 128, 1};
+    CKS(bf16_map(&h->tmC1A, h->Bov_tc, 3, dims, str, box));
+  }
+  {
+    const uint64_t dims[3] = {(uint64_t)ov, (uint64_t)C, np};
+    const uint64_t str[2] = {(uint64_t)ov * 2, (uint64_t)C * ov * 2};
+    const uint32_t box[3] = {64, 64, 1};
+    CKS(bf16_map(&h->tmC1B, h->Xc, 3, dims, str, box));
+  }
+  {
+    const uint64_t dims[3] = {(uint64_t)P, (uint64_t)ov, np};
+    const uint64_t str[2] = {(uint64_t)P * 2, (uint64_t)ov * P * 2};
+    const uint32_t box[3] = {64, 128, 1};
+    CKS(bf16_map(&h->tmC2A, h->BovT_tc, 3, dims, str, box));
+  }
+  {
+    const uint64_t dims[3] = {(uint64_t)P, (uint64_t)C, np};
+    const uint64_t str[2] = {(uint64_t)P * 2, (uint64_t)C * P * 2};
+    const uint32_t box[3] = {64, 64, 1};
+    CKS(bf16_map(&h->tmC2B, h->Wt, 3, dims, str, box));
+  }
+  return RTTDA_OK;
+}
+
 // Buffers, split-K plan and TMA maps of the tensor-core exchange for C columns.
 static rttda_status alloc_tc(rttda_ctx* h, int C) {
   const int o = h->o, v = h->v, P = h->P, vp = h->vp, op = h->op;
@@ -561,7 +692,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   CKS(dalloc(&h->Xt, xt * h->nplanes));
   // Z chunk: C*o rows of zchunk*vp BF16 per plane, at most ~2 GiB in total
   const size_t zper = (size_t)C * o * vp * 2 * h->zplanes;
-  h->zchunk = (int)std::max<size_t>(1, std::min<size_t>(P, ((size_t)2 << 30) / std::max<size_t>(zper, 1)));
+  h->zchunk = (int)std::max<size_t>(1, std::min<size_t>(P, zbudget_bytes() / std::max<size_t>(zper, 1)));
   h->zplane = (size_t)C * o * h->zchunk * vp;
   CKS(dalloc(&h->Zk, h->zplane * h->zplanes));
   // main contraction tile width along a (N = nvirt)
@@ -577,7 +708,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   h->tc_bn = best;
   const long long tiles = cdiv((long long)C * o, tc::kBM) * cdiv(v, best);
   const long long kt_full = (long long)h->zchunk * (vp / tc::kBK);
-  h->SK = (int)std::max(1LL, std::min(kt_full, kNumSM / std::max(1LL, tiles)));
+  h->SK = choose_splits(tiles, kt_full);
   char* p = nullptr;
   CK(cudaMalloc((void**)&p, (size_t)h->SK * C * o * v * sizeof(float)));
   h->Kpart = p;
@@ -633,7 +764,10 @@ rttda_status rttda_ctx::alloc_batch() {
   CKS(dalloc(&E, 4 * (size_t)T));
   CKS(dalloc(&d_step, 1));
   // Coulomb scratch
-  {
+  coul_tc = tc && Bov_tc != nullptr && C >= 16;
+  if (coul_tc) {
+    CKS(alloc_coul_tc(this, C));
+  } else {
     const int V = (int)(16 / fbytes);
     coul_vec = (ov % V) == 0 && C <= 12;
     const size_t max_smem = 96 * 1024;
@@ -752,6 +886,23 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
   if (h->tc) {
     CKS(pack(B_oo, o * o, o * (size_t)h->op, false, &h->Boo_tc));
     CKS(pack(B_vv, v * v, (size_t)h->vp * h->vp, true, &h->Bvv_tc));
+    if ((o * v) % 8 == 0 && P % 8 == 0) {
+      // B_ov and its transpose as BF16 planes for batched Coulomb passes
+      const size_t ov = o * v, plane = P * ov;
+      CK(cudaMalloc((void**)&h->Bov_tc, plane * h->nplanes * 2));
+      CK(cudaMalloc((void**)&h->BovT_tc, plane * h->nplanes * 2));
+      const size_t per = std::max<size_t>(1, chunk / ov);
+      for (size_t p0 = 0; p0 < P; p0 += per) {
+        const size_t pc = std::min(per, P - p0);
+        CK(cudaMemcpyAsync(stage, B_ov + p0 * ov, pc * ov * 8, cudaMemcpyHostToDevice, h->stream));
+        dim3 g((unsigned)cdiv(ov, 32), (unsigned)cdiv(pc, 32));
+        k_pack_ov<<<g, dim3(32, 8), 0, h->stream>>>((int)pc, (int)p0, (int)P, (long long)ov, stage, h->Bov_tc,
+                                                   h->nplanes > 1 ? h->Bov_tc + plane : nullptr, h->BovT_tc,
+                                                   h->nplanes > 1 ? h->BovT_tc + plane : nullptr, (long long)plane);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->stream));
+      }
+    }
   } else {
     CKS(upload(B_oo, P * o * o, &h->Boo));
     CKS(upload(B_vv, P * v * v, &h->Bvv));
@@ -1113,10 +1264,10 @@ size_t estimate_bytes(int nocc, int nvirt, int naux, int ntraj, int prec, long n
   const size_t vp = (v + 63) / 64 * 64, op = (o + 7) / 8 * 8;
   const size_t planes = prec == RTTDA_BF16 ? 1 : 2, zplanes = prec == RTTDA_BF16X3 ? 2 : 1;
   size_t b = P * ov * fb + (o + v + 3 * (o * o + v * v + ov)) * 8;
-  b += tc ? (P * o * op + P * vp * vp) * 2 * planes : (P * o * o + P * v * v) * fb;
+  b += tc ? (P * o * op + P * vp * vp + 2 * P * ov) * 2 * planes : (P * o * o + P * v * v) * fb;
   b += N * C * 8 * 6 + T * (o * o + v * v + ov) * (8 + cb);               // state, dipole blocks
   b += (size_t)32 * P * C * cb + (size_t)16 * ov * C * cb;                 // Coulomb partials
-  const size_t zcap = (size_t)2 << 30;
+  const size_t zcap = (size_t)40 << 30;
   if (tc)
     b += std::min(zcap, C * o * vp * 2 * zplanes * P) + C * vp * op * 2 * planes + (size_t)kNumSM * C * o * v * 4;
   else

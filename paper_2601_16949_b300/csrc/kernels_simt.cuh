@@ -849,3 +849,85 @@ __global__ void k_prep_xt(int o, int v, int vp, int op, int C, const double* __r
 }
 
 }  // namespace rttda
+
+namespace rttda {
+
+// B_ov rows p0..p0+pc (FP64 [pc][ov]) -> BF16 planes [plane][P][ov] (rows as
+// is) and [plane][ov][P] (transposed), through a 32 x 32 shared-memory tile.
+// grid (ceil(ov/32), ceil(pc/32)), block (32, 8).
+__global__ void k_pack_ov(int pc, int p0, int P, long long ov, const double* __restrict__ src,
+                          __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                          __nv_bfloat16* __restrict__ thi, __nv_bfloat16* __restrict__ tlo, long long plane) {
+  __shared__ double tile[32][33];
+  const long long ia0 = (long long)blockIdx.x * 32;
+  const int pb = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int p = pb + r;
+    const long long ia = ia0 + threadIdx.x;
+    double x = 0.0;
+    if (p < pc && ia < ov) {
+      x = src[(size_t)p * ov + ia];
+      __nv_bfloat16 h, l;
+      split_bf16(x, h, l);
+      const size_t e = (size_t)(p0 + p) * ov + ia;
+      hi[e] = h;
+      if (lo) lo[e] = l;
+    }
+    tile[r][threadIdx.x] = x;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const long long ia = ia0 + r;
+    const int p = pb + threadIdx.x;
+    if (p < pc && ia < ov) {
+      __nv_bfloat16 h, l;
+      split_bf16(tile[threadIdx.x][r], h, l);
+      const size_t e = (size_t)ia * P + p0 + p;
+      thi[e] = h;
+      if (tlo) tlo[e] = l;
+    }
+  }
+  (void)plane;
+}
+
+// Amplitudes -> Xc[plane][col][ia] = X[1 + ia][col] (K-major B operand of
+// w = B_ov X), via a 32 (ia) x C tile.  grid ceil(ov/32), block 256.
+__global__ void k_prep_xc(long long ov, int C, const double* __restrict__ X, __nv_bfloat16* __restrict__ hi,
+                          __nv_bfloat16* __restrict__ lo) {
+  extern __shared__ double xt[];  // [32][C + 1]
+  const long long ia0 = (long long)blockIdx.x * 32;
+  for (int e = threadIdx.x; e < 32 * C; e += blockDim.x) {
+    const int r = e / C, c = e % C;
+    const long long ia = ia0 + r;
+    xt[r * (C + 1) + c] = ia < ov ? X[(size_t)(1 + ia) * C + c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * C; e += blockDim.x) {
+    const int c = e / 32, r = e % 32;
+    const long long ia = ia0 + r;
+    if (ia < ov) {
+      __nv_bfloat16 h, l;
+      split_bf16(xt[r * (C + 1) + c], h, l);
+      const size_t o = (size_t)c * ov + ia;
+      hi[o] = h;
+      if (lo) lo[o] = l;
+    }
+  }
+}
+
+// Wt[plane][col][p] = 2 sum_s wpart[s][p][col] (the Coulomb factor 2 folded
+// in), split into BF16 hi/lo.
+__global__ void k_prep_wt(int P, int C, int nsplit, const float* __restrict__ wpart, __nv_bfloat16* __restrict__ hi,
+                          __nv_bfloat16* __restrict__ lo) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)P * C) return;
+  const int c = (int)(e / P), p = (int)(e % P);
+  double acc = 0.0;
+  for (int s = 0; s < nsplit; ++s) acc += (double)wpart[((size_t)s * P + p) * C + c];
+  __nv_bfloat16 h, l;
+  split_bf16(2.0 * acc, h, l);
+  hi[e] = h;
+  if (lo) lo[e] = l;
+}
+
+}  // namespace rttda

@@ -118,3 +118,23 @@ def test_bf16x3_config2_sampled_rows(rb):
         sall = np.abs(Arows) @ np.abs(c[k]) + abs(E) * (np.abs(Mrows) @ np.abs(c[k]))
         err = np.abs(got[k, rows] - ref)
         assert np.all(err <= 2e-4 * s2e + 2e-6 * sall + 1e-300), (k, np.max(err / np.maximum(s2e, 1e-300)))
+
+
+@pytest.mark.parametrize("prec,tol2e", [("bf16x3", 2e-4), ("bf16x2", 1e-2), ("bf16", 3e-2)])
+@pytest.mark.parametrize("shape", [(4, 70, 40), (8, 64, 48)])
+def test_batched_sigma_with_tensorcore_coulomb(rb, prec, tol2e, shape):
+    """Eight or more trajectories (16+ real columns) route the Coulomb passes
+    through the tensor-core GEMM as well."""
+    mol = synth.molecule(*shape, seed=31)
+    pulses = [dict(kind=1, E0=0.01 * (k + 1), omega=0.3 + 0.1 * k, direction=(k % 3 == 0, k % 3 == 1, k % 3 == 2))
+              for k in range(9)]
+    prop = rb.Propagator(mol, 0.2, prec)
+    prop.set_field(pulses)
+    c = synth.random_state(prop.n, len(pulses), seed=6)
+    got = _sigma_gpu(rb, prop, c, 0.8)
+    ref = oracle_sigma(mol, 0.2, pulses, c, 0.8)
+    s2e = np.max(np.abs(_two_electron_part(mol, 0.2, c)), axis=1)
+    sall = np.max(np.abs(ref), axis=1)
+    err = np.max(np.abs(got - ref), axis=1)
+    assert np.all(err <= tol2e * s2e + 2e-6 * sall), (err, s2e, sall)
+    prop.close()
