@@ -338,7 +338,12 @@ def run_gpu(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
-    mol = synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
+    if args.workload == "large":
+        # FP64 factors of this size do not fit in host memory: draw them on the GPU
+        mol = synth.molecule_device(NOCC, NVIRT, NAUX, seed=SEED)
+        args.no_cpu_baseline = True
+    else:
+        mol = synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
     pulses, wl_info = workload_pulses(rb, args.workload, mol)
     T, K, W = len(pulses), args.steps, args.warmup
     prop = rb.Propagator(mol, CX, args.prec)

@@ -135,6 +135,16 @@ rttda_status rttda_create(int nocc, int nvirt, int naux,
                           const double* mu_oo, const double* mu_vv, const double* mu_0ov,
                           double c_x, int prec, rttda_t* out);
 
+/* As rttda_create, but every array argument is device memory of the current
+ * device (FP64, same layouts), e.g. factors produced on the GPU; they are
+ * read during the call and may be freed when it returns.  Needed for
+ * molecules whose FP64 factors do not fit in host memory. */
+rttda_status rttda_create_device(int nocc, int nvirt, int naux,
+                                 const double* eps_occ, const double* eps_virt,
+                                 const double* B_ov, const double* B_oo, const double* B_vv,
+                                 const double* mu_oo, const double* mu_vv, const double* mu_0ov,
+                                 double c_x, int prec, rttda_t* out);
+
 /* Device memory the handle holds right now, in bytes. */
 rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes);
 

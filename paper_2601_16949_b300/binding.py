@@ -72,6 +72,9 @@ lib.rttda_last_error.restype = ct.c_char_p
 lib.rttda_create.argtypes = [ct.c_int, ct.c_int, ct.c_int] + [_dp] * 8 + [ct.c_double, ct.c_int, ct.POINTER(_h)]
 lib.rttda_create.restype = ct.c_int
 lib.rttda_memory_bytes.argtypes = [_h, ct.POINTER(ct.c_size_t)]
+lib.rttda_create_device.argtypes = [ct.c_int, ct.c_int, ct.c_int] + [ct.c_void_p] * 8 + [ct.c_double, ct.c_int,
+                                                                                          ct.POINTER(_h)]
+lib.rttda_create_device.restype = ct.c_int
 lib.rttda_set_field.argtypes = [_h, ct.POINTER(rttda_pulse), ct.c_int]
 lib.rttda_propagate.argtypes = [_h, _dp, ct.c_double, ct.c_long, _dp, _dp, _dp]
 lib.rttda_propagate_device.argtypes = [_h, ct.c_void_p, ct.c_double, ct.c_long, ct.c_void_p, ct.c_void_p,
@@ -145,6 +148,15 @@ def rttda_create(nocc, nvirt, naux, eps_occ, eps_virt, B_ov, B_oo, B_vv, mu_oo, 
     prec = PRECISIONS.get(prec, prec) if isinstance(prec, str) else prec
     _check(lib.rttda_create(nocc, nvirt, naux, *[_ptr(a) for a in arrs], float(c_x), int(prec), ct.byref(h)),
            "rttda_create")
+    return h
+
+
+def rttda_create_device(nocc, nvirt, naux, ptrs, c_x, prec):
+    """ptrs: device addresses of eps_occ, eps_virt, B_ov, B_oo, B_vv, mu_oo, mu_vv, mu_0ov (FP64)."""
+    h = _h()
+    prec = PRECISIONS.get(prec, prec) if isinstance(prec, str) else prec
+    _check(lib.rttda_create_device(nocc, nvirt, naux, *[ct.c_void_p(int(p)) for p in ptrs], float(c_x), int(prec),
+                                   ct.byref(h)), "rttda_create_device")
     return h
 
 
@@ -333,11 +345,18 @@ def rttda_server_destroy(srv) -> None:
 class Propagator:
     """Owns one handle; numpy in, numpy out."""
 
+    KEYS = ("eps_occ", "eps_virt", "B_ov", "B_oo", "B_vv", "mu_oo", "mu_vv", "mu_0ov")
+
     def __init__(self, mol: dict, c_x: float, prec="fp64"):
         self.nocc, self.nvirt, self.naux = mol["nocc"], mol["nvirt"], mol["naux"]
         self.n = 1 + self.nocc * self.nvirt
-        self.h = rttda_create(self.nocc, self.nvirt, self.naux, mol["eps_occ"], mol["eps_virt"], mol["B_ov"],
-                              mol["B_oo"], mol["B_vv"], mol["mu_oo"], mol["mu_vv"], mol["mu_0ov"], c_x, prec)
+        first = mol["B_vv"]
+        if hasattr(first, "data_ptr") and getattr(first, "is_cuda", False):
+            # torch CUDA tensors (float64, contiguous): factors made on the GPU
+            self.h = rttda_create_device(self.nocc, self.nvirt, self.naux,
+                                         [mol[k].data_ptr() for k in self.KEYS], c_x, prec)
+        else:
+            self.h = rttda_create(self.nocc, self.nvirt, self.naux, *[mol[k] for k in self.KEYS], c_x, prec)
         self.ntraj = 0
 
     def set_field(self, pulses):

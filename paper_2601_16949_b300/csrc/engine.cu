@@ -843,9 +843,9 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
     for (size_t off = 0; off < n; off += chunk) {
       const size_t m = std::min(chunk, n - off);
       if (h->fbytes == 8) {
-        CK(cudaMemcpyAsync((double*)*dst + off, src + off, m * 8, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync((double*)*dst + off, src + off, m * 8, cudaMemcpyDefault, h->stream));
       } else {
-        CK(cudaMemcpyAsync(stage, src + off, m * 8, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(stage, src + off, m * 8, cudaMemcpyDefault, h->stream));
         if (h->fbytes == 4)
           k_cast<float><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, stage, (float*)*dst + off);
         else
@@ -864,7 +864,7 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
     const size_t per = std::max<size_t>(1, chunk / std::max<size_t>(slab, 1));
     for (size_t p0 = 0; p0 < P; p0 += per) {
       const size_t pc = std::min(per, P - p0);
-      CK(cudaMemcpyAsync(stage, src + p0 * slab, pc * slab * 8, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(stage, src + p0 * slab, pc * slab * 8, cudaMemcpyDefault, h->stream));
       __nv_bfloat16* hi = *dst + p0 * out_slab;
       __nv_bfloat16* lo = h->nplanes > 1 ? hi + plane : nullptr;
       const long long tot = (long long)(pc * out_slab);
@@ -879,7 +879,7 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
   };
   auto upload64 = [&](const double* src, size_t n, double** dst) -> rttda_status {
     CK(cudaMalloc((void**)dst, std::max<size_t>(n, 1) * 8));
-    CK(cudaMemcpyAsync(*dst, src, n * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(*dst, src, n * 8, cudaMemcpyDefault, h->stream));
     return RTTDA_OK;
   };
   CKS(upload(B_ov, P * o * v, &h->Bov));
@@ -894,7 +894,7 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
       const size_t per = std::max<size_t>(1, chunk / ov);
       for (size_t p0 = 0; p0 < P; p0 += per) {
         const size_t pc = std::min(per, P - p0);
-        CK(cudaMemcpyAsync(stage, B_ov + p0 * ov, pc * ov * 8, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(stage, B_ov + p0 * ov, pc * ov * 8, cudaMemcpyDefault, h->stream));
         dim3 g((unsigned)cdiv(ov, 32), (unsigned)cdiv(pc, 32));
         k_pack_ov<<<g, dim3(32, 8), 0, h->stream>>>((int)pc, (int)p0, (int)P, (long long)ov, stage, h->Bov_tc,
                                                    h->nplanes > 1 ? h->Bov_tc + plane : nullptr, h->BovT_tc,
@@ -913,9 +913,15 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
   CKS(upload64(mu_vv, 3 * v * v, &h->mu_vv));
   CKS(upload64(mu_0ov, 3 * o * v, &h->mu_0));
   CK(cudaStreamSynchronize(h->stream));
-  // spectral-norm bound of M_x: |m_x| + |mu_vv,x|_F + |mu_oo,x|_F
+  // spectral-norm bound of M_x: |m_x| + |mu_vv,x|_F + |mu_oo,x|_F (from host
+  // copies, so the inputs may live in host or device memory)
+  std::vector<double> hm0(3 * o * v), hmv(3 * v * v), hmo(3 * o * o);
+  CK(cudaMemcpy(hm0.data(), mu_0ov, hm0.size() * 8, cudaMemcpyDefault));
+  CK(cudaMemcpy(hmv.data(), mu_vv, hmv.size() * 8, cudaMemcpyDefault));
+  CK(cudaMemcpy(hmo.data(), mu_oo, hmo.size() * 8, cudaMemcpyDefault));
   for (int x = 0; x < 3; ++x)
-    h->mu_bound[x] = fro(mu_0ov + x * o * v, o * v) + fro(mu_vv + x * v * v, v * v) + fro(mu_oo + x * o * o, o * o);
+    h->mu_bound[x] = fro(hm0.data() + x * o * v, o * v) + fro(hmv.data() + x * v * v, v * v) +
+                     fro(hmo.data() + x * o * o, o * o);
   return RTTDA_OK;
 }
 
@@ -967,6 +973,13 @@ rttda_status rttda_create(int nocc, int nvirt, int naux, const double* eps_occ, 
   }
   *out = h;
   return RTTDA_OK;
+}
+
+rttda_status rttda_create_device(int nocc, int nvirt, int naux, const double* eps_occ, const double* eps_virt,
+                                 const double* B_ov, const double* B_oo, const double* B_vv, const double* mu_oo,
+                                 const double* mu_vv, const double* mu_0ov, double c_x, int prec, rttda_t* out) {
+  // the upload path copies with cudaMemcpyDefault, so device sources work as is
+  return rttda_create(nocc, nvirt, naux, eps_occ, eps_virt, B_ov, B_oo, B_vv, mu_oo, mu_vv, mu_0ov, c_x, prec, out);
 }
 
 rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes) {

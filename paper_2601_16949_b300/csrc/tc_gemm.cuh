@@ -413,6 +413,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t* stg = reinterpret_cast<uint32_t*>(smem + STAGES * CF::kStageBytes + 256) +
                         (size_t)(warp - 2) * (kZStageBytesPerWarp / 4);
         uint32_t* stg_lo = stg + 32 * kStageRowWords;
+        const bool two = p.zlo != nullptr;
+        // (P, i) of this warp's first row; later rows step i and wrap into P
+        const int mb = tc.m0 + q * 32;
+        const int Pb = mb / p.o, ib = mb - Pb * p.o;
+        const int vt = p.vp >> 6;
         for (int ci = half; ci < nchunks; ci += 2) {
           const int c = ci * 32;
           uint32_t r[32];
@@ -421,33 +426,43 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) r[j] = 0u;
           }
-          uint32_t hw[16], lw[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            split_pack(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]), hw[j], lw[j]);
           uint4* sh = reinterpret_cast<uint4*>(stg + lane * kStageRowWords);
-          uint4* sl = reinterpret_cast<uint4*>(stg_lo + lane * kStageRowWords);
+          if (two) {
+            uint32_t hw[16], lw[16];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
-            sl[j] = make_uint4(lw[4 * j], lw[4 * j + 1], lw[4 * j + 2], lw[4 * j + 3]);
+            for (int j = 0; j < 16; ++j)
+              split_pack(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]), hw[j], lw[j]);
+            uint4* sl = reinterpret_cast<uint4*>(stg_lo + lane * kStageRowWords);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
+              sl[j] = make_uint4(lw[4 * j], lw[4 * j + 1], lw[4 * j + 2], lw[4 * j + 3]);
+            }
+          } else {
+            uint32_t hw[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) hw[j] = pack_bf16x2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
           }
           __syncwarp();
           const int n = tc.n0 + c;
           if (n < p.N && ok) {
             const int col = n / p.vp, b = n - col * p.vp;
-            const int vt = p.vp >> 6;
+            const size_t cbase = (size_t)(b >> 6) * p.zrows + (size_t)col * p.o;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               const int rr = (lane >> 2) + 8 * k, cc = lane & 3;
-              const int mr = tc.m0 + q * 32 + rr;
-              if (mr < p.M) {
-                const int Pr = mr / p.o, ir = mr - Pr * p.o;
-                const size_t kt = (size_t)Pr * vt + (b >> 6);
-                const size_t off = (kt * p.zrows + (size_t)(col * p.o + ir)) * 64 + (b & 63) + 8 * cc;
+              if (mb + rr < p.M) {
+                int ir = ib + rr, Pr = Pb;
+                while (ir >= p.o) {
+                  ir -= p.o;
+                  ++Pr;
+                }
+                const size_t off = ((size_t)Pr * vt * p.zrows + cbase + (size_t)ir) * 64 + (b & 63) + 8 * cc;
                 *reinterpret_cast<uint4*>(p.zhi + off) =
                     *reinterpret_cast<const uint4*>(stg + rr * kStageRowWords + 4 * cc);
-                if (p.zlo)
+                if (two)
                   *reinterpret_cast<uint4*>(p.zlo + off) =
                       *reinterpret_cast<const uint4*>(stg_lo + rr * kStageRowWords + 4 * cc);
               }

@@ -22,7 +22,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["molecule", "random_state", "FACTOR_SIGMA", "MU_SIGMA", "MU0_SIGMA"]
+__all__ = ["molecule", "molecule_device", "random_state", "FACTOR_SIGMA", "MU_SIGMA", "MU0_SIGMA"]
 
 FACTOR_SIGMA = 0.05
 MU_SIGMA = 0.5
@@ -75,3 +75,41 @@ def random_state(n: int, ntraj: int = 1, seed: int = 1, normalise: bool = True) 
     if normalise:
         c /= np.linalg.norm(c, axis=1, keepdims=True)
     return c
+
+
+def molecule_device(nocc: int, nvirt: int, naux: int, seed: int = 0, device="cuda",
+                    eps_occ_range=(-1.0, -0.3), eps_virt_range=(0.05, 2.0), slab: int = 128) -> dict:
+    """Same distributions as molecule(), drawn on the GPU with torch's seeded
+    Philox generator (a different stream than numpy's, so the values differ
+    from molecule() for the same seed).  For molecules whose FP64 factors do
+    not fit in host memory.  Returns contiguous float64 CUDA tensors with the
+    same keys and layouts; symmetric blocks are drawn in slabs of P."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f64 = dict(dtype=torch.float64, device=device)
+
+    def uni(n, lo, hi):
+        return torch.sort(lo + (hi - lo) * torch.rand(n, generator=g, **f64)).values
+
+    def sym(lead, n, scale):
+        out = torch.empty((lead, n, n), **f64)
+        for p0 in range(0, lead, slab):
+            p1 = min(lead, p0 + slab)
+            gm = torch.randn((p1 - p0, n, n), generator=g, **f64) * scale
+            out[p0:p1] = torch.triu(gm) + torch.triu(gm, 1).transpose(1, 2)
+            del gm
+        return out
+
+    fs = FACTOR_SIGMA / np.sqrt(naux)
+    eps_occ = uni(nocc, *eps_occ_range)
+    eps_virt = uni(nvirt, *eps_virt_range)
+    B_ov = torch.randn((naux, nocc, nvirt), generator=g, **f64) * fs
+    B_oo = sym(naux, nocc, fs)
+    B_vv = sym(naux, nvirt, fs)
+    mu_oo = sym(3, nocc, MU_SIGMA)
+    mu_vv = sym(3, nvirt, MU_SIGMA)
+    mu_0ov = torch.randn((3, nocc, nvirt), generator=g, **f64) * MU0_SIGMA
+    return dict(nocc=nocc, nvirt=nvirt, naux=naux, eps_occ=eps_occ, eps_virt=eps_virt,
+                B_ov=B_ov, B_oo=B_oo, B_vv=B_vv, mu_oo=mu_oo, mu_vv=mu_vv, mu_0ov=mu_0ov)
