@@ -115,6 +115,7 @@ struct rttda_ctx {
   // state and scratch
   double* Xn = nullptr;
   double* Xs = nullptr;
+  double* Xs2 = nullptr;  // second stage-input buffer
   double* acc = nullptr;
   double* F = nullptr;
   double* E = nullptr;
@@ -143,7 +144,7 @@ struct rttda_ctx {
   __nv_bfloat16* Xt = nullptr;      // [plane][C*vp][op]
   __nv_bfloat16* Zk = nullptr;      // [plane][C*o][zchunk*vp]
   size_t zplane = 0;
-  std::vector<CUtensorMap> tmZA, tmMA, tmMB;
+  std::vector<CUtensorMap> tmZA, tmMA, tmMB, tmZS;
   CUtensorMap tmZB;
   std::vector<int> tc_kper;
   int* d_err = nullptr;
@@ -196,13 +197,13 @@ rttda_ctx::~rttda_ctx() {
 }
 
 void rttda_ctx::free_batch() {
-  void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xn, Xs, acc, F, E, term,
+  void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xn, Xs, Xs2, acc, F, E, term,
                 obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk, Xc, Wt, wpart_tc};
   for (void* p : ps) dfree(p);
   d_pulses = nullptr;
   d_kappa = d_dirs = moo64 = mvv64 = m064 = nullptr;
   mooC = mvvC = m0C = nullptr;
-  Xn = Xs = acc = F = E = term = obs_part = Xq = nullptr;
+  Xn = Xs = Xs2 = acc = F = E = term = obs_part = Xq = nullptr;
   d_step = nullptr;
   w = Jpart = Zt = Kpart = nullptr;
   Xt = Zk = nullptr;
@@ -210,6 +211,7 @@ void rttda_ctx::free_batch() {
   wpart_tc = nullptr;
   coul_tc = false;
   tmZA.clear();
+  tmZS.clear();
   tmMA.clear();
   tmMB.clear();
   tc_kper.clear();
@@ -259,10 +261,11 @@ constexpr int kZBN = 256, kZStages = 3;   // Z = B_oo c   (K = nocc, short)
 
 // Persistent launch: one CTA per SM (or per tile if fewer tiles).
 template <int BN, int ST, int BM, int EP>
-void tc_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s) {
+void tc_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s,
+               const CUtensorMap* z = nullptr) {
   const long long tiles = cdiv(prm.N, BN) * cdiv(prm.M, tc::kBM) * prm.nsplit;
   const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(tiles, kNumSM));
-  tc::k_tc_gemm<BN, ST, BM, EP><<<grid, tc::kThreads, tc::smem_bytes<BN, ST, EP>(), s>>>(a, b, prm);
+  tc::k_tc_gemm<BN, ST, BM, EP><<<grid, tc::kThreads, tc::smem_bytes<BN, ST, EP>(), s>>>(a, b, z ? *z : a, prm);
 }
 
 template <int BN, int ST, int BM, int EP>
@@ -342,14 +345,18 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.kt_total = (int)cdiv(op, tc::kBK);
       prm.kt_per_split = prm.kt_total;
       prm.nsplit = 1;
-      prm.nprod = h->nprod;
+      // Z enters the main contraction as one BF16 plane in BF16X2: its
+      // activation part needs no lo plane, B_oo keeps hi + lo
+      prm.nprod = h->zplanes == 1 && h->nplanes > 1 ? 2 : h->nprod;
+      prm.alo = prm.nprod == 2 ? 1 : 0;
       prm.zhi = h->Zk;
       prm.zlo = h->zplanes > 1 ? h->Zk + h->zplane : nullptr;
       prm.o = o;
       prm.vp = vp;
       prm.zrows = C * o;
+      prm.ztma = (o % 32 == 0) ? 1 : 0;
       prm.err = h->d_err;
-      tc_launch<kZBN, kZStages, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>(h->tmZA[c], h->tmZB, prm, s);
+      tc_launch<kZBN, kZStages, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
     }
     {
       // K_(col,i),a (+)= sum_{P in chunk, b} Z^P_(col,i),b B^P_ab   (split-K)
@@ -458,14 +465,14 @@ struct Ops {
   }
 
   static void combine(rttda_ctx* h, int mode, int stage, bool use_field, double dt, const double* Xin,
-                      double* sig_out, cudaStream_t s) {
+                      double* Xnext, double* sig_out, cudaStream_t s) {
     Prof pr(h, RTTDA_KC_COMBINE, s);
     h->launches += 1;
     const int C = 2 * h->T;
-    k_combine<TC><<<blocks_for(h->N * h->T, 256), 256, 0, s>>>(
+    k_combine<TC><<<blocks_for(h->N * 2 * h->T, 256), 256, 0, s>>>(
         mode, stage, h->N, h->o, h->v, h->T, h->eps_o, h->eps_v, h->cx, (const TC*)h->Jpart, h->SJ,
-        (const TC*)h->Kpart, h->SK, (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn,
-        const_cast<double*>(Xin), h->acc, sig_out);
+        (const TC*)h->Kpart, h->SK, (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn, Xin,
+        Xnext, h->acc, sig_out);
   }
 
   static void set_smem_limits() {
@@ -516,12 +523,16 @@ void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, doub
   h->launches += 2;  // efield + step counter
   k_efield<<<1, 128, 0, s>>>(h->T, h->d_pulses, h->d_step, base, t_off, dt, h->E);
   for (int st = 0; st < 4; ++st) {
+    // stage inputs alternate between two buffers (the combine reads one and
+    // writes the other); stage 3 writes back into Xs, so every step starts there
+    double* xin = (st % 2 == 0) ? h->Xs : h->Xs2;
+    double* xnext = (st % 2 == 0) ? h->Xs2 : h->Xs;
     const bool fld = h->any_field;
-    if (st == 0 || fld) O::field(h, h->Xs, s);
+    if (st == 0 || fld) O::field(h, xin, s);
     if (st == 0 && dip) enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
-    O::coulomb(h, h->Xs, s);
-    O::exchange(h, h->Xs, s);
-    O::combine(h, 0, st, fld, dt, h->Xs, nullptr, s);
+    O::coulomb(h, xin, s);
+    O::exchange(h, xin, s);
+    O::combine(h, 0, st, fld, dt, xin, xnext, nullptr, s);
   }
   k_step_inc<<<1, 1, 0, s>>>(h->d_step);
 }
@@ -602,14 +613,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 // BF16 tile map with 128-byte swizzle; dims/box innermost first, strides in
 // bytes for dims 1..rank-1.
 static rttda_status bf16_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
-                             const uint64_t* strides, const uint32_t* box) {
+                             const uint64_t* strides, const uint32_t* box,
+                             CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   auto enc = tmap_encoder();
   if (!enc) return set_error(RTTDA_E_CUDA, "cuTensorMapEncodeTiled unavailable");
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base),
                    reinterpret_cast<const cuuint64_t*>(dims), reinterpret_cast<const cuuint64_t*>(strides),
                    reinterpret_cast<const cuuint32_t*>(box), es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(RTTDA_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return RTTDA_OK;
@@ -721,7 +733,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   }
   for (int p0 = 0; p0 < P; p0 += h->zchunk) {
     const int pc = std::min(h->zchunk, P - p0);
-    CUtensorMap za, ma, mb;
+    CUtensorMap za, ma, mb, zs;
     {
       const uint64_t dims[3] = {(uint64_t)op, (uint64_t)pc * o, (uint64_t)h->nplanes};
       const uint64_t str[2] = {(uint64_t)op * 2, (uint64_t)P * o * op * 2};
@@ -734,6 +746,9 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
       const uint64_t str[3] = {128, (uint64_t)C * o * 128, (uint64_t)h->zplane * 2};
       const uint32_t box[4] = {64, 128, 1, 1};
       CKS(bf16_map(&ma, h->Zk, 4, dims, str, box));
+      // the Z build's TMA stores: 32 x 32 boxes, dense (no swizzle)
+      const uint32_t sbox[4] = {32, 32, 1, 1};
+      CKS(bf16_map(&zs, h->Zk, 4, dims, str, sbox, CU_TENSOR_MAP_SWIZZLE_NONE));
     }
     {
       const uint64_t dims[4] = {(uint64_t)vp, (uint64_t)vp, (uint64_t)pc, (uint64_t)h->nplanes};
@@ -743,6 +758,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
     }
     h->tmZA.push_back(za);
     h->tmMA.push_back(ma);
+    h->tmZS.push_back(zs);
     h->tmMB.push_back(mb);
     const long long kt = (long long)pc * (vp / tc::kBK);
     h->tc_kper.push_back((int)cdiv(kt, h->SK));
@@ -757,6 +773,7 @@ rttda_status rttda_ctx::alloc_batch() {
   const long long NC = N * C;
   CKS(dalloc(&Xn, NC));
   CKS(dalloc(&Xs, NC));
+  CKS(dalloc(&Xs2, NC));
   CKS(dalloc(&acc, NC));
   CKS(dalloc(&F, NC));
   CKS(dalloc(&term, NC));
@@ -1249,7 +1266,7 @@ rttda_status rttda_sigma(rttda_t h, const double* c_dev, double t, double* sigma
     if (h->any_field) O::field(h, h->Xq, s);
     O::coulomb(h, h->Xq, s);
     O::exchange(h, h->Xq, s);
-    O::combine(h, 1, 0, h->any_field, 0.0, h->Xq, h->term, s);
+    O::combine(h, 1, 0, h->any_field, 0.0, h->Xq, nullptr, h->term, s);
   });
   k_dev_to_abi<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->term, sigma_dev);
   CK(cudaGetLastError());

@@ -569,71 +569,65 @@ __global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long 
                                                  const TC* __restrict__ Kpart, int SK, long long Kstride,
                                                  const double* __restrict__ F, const double* __restrict__ E,
                                                  int use_field, double dt, double* __restrict__ Xn,
-                                                 double* __restrict__ Xs, double* __restrict__ acc,
-                                                 double* __restrict__ sig_out) {
-  // one thread per (trajectory t, row n), n fastest
+                                                 const double* __restrict__ Xs, double* __restrict__ Xs_next,
+                                                 double* __restrict__ acc, double* __restrict__ sig_out) {
+  // one thread per (trajectory t, part q, row n), n fastest.  Xs is this
+  // stage's input and is only read; the next stage's input goes to Xs_next.  sigma_q is the
+  // real (q = 0) or imaginary (q = 1) part; k = -i sigma swaps them, so the
+  // thread updates the other part of k: k_re = sigma_im, k_im = -sigma_re.
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * T) return;
+  if (e >= N * 2 * T) return;
   const long long n = e % N;
-  const int t = (int)(e / N);
-  const int C = 2 * T;
+  const int tq = (int)(e / N), t = tq >> 1, q = tq & 1;
+  const int C = 2 * T, col = 2 * t + q;
   const long long ov = N - 1;
-  double sg[2];
+  const size_t idx = (size_t)n * C + col;
+  double sg = 0.0;
   if (n > 0) {
     const int i = (int)((n - 1) / v), a = (int)((n - 1) % v);
-    const double d = eps_v[a] - eps_o[i];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int col = 2 * t + q;
-      double j = 0.0;
-      for (int p = 0; p < SJ; ++p) j += (double)Jpart[((size_t)p * ov + (n - 1)) * C + col];
-      double kx = 0.0;
-      const TC* kp = Kpart + ((size_t)col * o + i) * v + a;
-#pragma unroll 4
-      for (int p = 0; p < SK; ++p) kx += (double)kp[(size_t)p * Kstride];
-      sg[q] = d * Xs[(size_t)n * C + col] + j - cx * kx;
+    double j0 = 0.0, j1 = 0.0, k0 = 0.0, k1 = 0.0;
+    const TC* jp = Jpart + (size_t)(n - 1) * C + col;
+    const size_t js = (size_t)ov * C;
+    int p = 0;
+    for (; p + 1 < SJ; p += 2) {
+      j0 += (double)jp[(size_t)p * js];
+      j1 += (double)jp[(size_t)(p + 1) * js];
     }
-  } else {
-    sg[0] = sg[1] = 0.0;
+    if (p < SJ) j0 += (double)jp[(size_t)p * js];
+    const TC* kp = Kpart + ((size_t)col * o + i) * v + a;
+    p = 0;
+    for (; p + 1 < SK; p += 2) {
+      k0 += (double)kp[(size_t)p * Kstride];
+      k1 += (double)kp[(size_t)(p + 1) * Kstride];
+    }
+    if (p < SK) k0 += (double)kp[(size_t)p * Kstride];
+    sg = (eps_v[a] - eps_o[i]) * Xs[idx] + (j0 + j1) - cx * (k0 + k1);
   }
-  const size_t ir = (size_t)n * C + 2 * t, ii = ir + 1;
-  if (use_field) {
-    const double Et = E[stage * T + t];
-    sg[0] -= Et * F[ir];
-    sg[1] -= Et * F[ii];
-  }
+  if (use_field) sg -= E[stage * T + t] * F[idx];
   if (mode == 1) {
-    sig_out[ir] = sg[0];
-    sig_out[ii] = sg[1];
+    sig_out[idx] = sg;
     return;
   }
-  const double kr = sg[1], ki = -sg[0];  // k = -i sigma
+  // this thread's sigma part feeds the other component of k
+  const size_t kidx = (size_t)n * C + 2 * t + (1 - q);
+  const double kv = q == 0 ? -sg : sg;  // k_im = -sigma_re ; k_re = sigma_im
   switch (stage) {
     case 0:
-      acc[ir] = kr;
-      acc[ii] = ki;
-      Xs[ir] = Xn[ir] + 0.5 * dt * kr;
-      Xs[ii] = Xn[ii] + 0.5 * dt * ki;
+      acc[kidx] = kv;
+      Xs_next[kidx] = Xn[kidx] + 0.5 * dt * kv;
       break;
     case 1:
-      acc[ir] += 2.0 * kr;
-      acc[ii] += 2.0 * ki;
-      Xs[ir] = Xn[ir] + 0.5 * dt * kr;
-      Xs[ii] = Xn[ii] + 0.5 * dt * ki;
+      acc[kidx] += 2.0 * kv;
+      Xs_next[kidx] = Xn[kidx] + 0.5 * dt * kv;
       break;
     case 2:
-      acc[ir] += 2.0 * kr;
-      acc[ii] += 2.0 * ki;
-      Xs[ir] = Xn[ir] + dt * kr;
-      Xs[ii] = Xn[ii] + dt * ki;
+      acc[kidx] += 2.0 * kv;
+      Xs_next[kidx] = Xn[kidx] + dt * kv;
       break;
     default: {
-      const double xr = Xn[ir] + (dt / 6.0) * (acc[ir] + kr);
-      const double xi = Xn[ii] + (dt / 6.0) * (acc[ii] + ki);
-      Xn[ir] = xr;
-      Xn[ii] = xi;
-      Xs[ir] = xr;
-      Xs[ii] = xi;
+      const double x = Xn[kidx] + (dt / 6.0) * (acc[kidx] + kv);
+      Xn[kidx] = x;
+      Xs_next[kidx] = x;
     }
   }
 }

@@ -50,7 +50,8 @@ struct Params {
   int kt_total;          // real K tiles
   int kt_per_split;      // real K tiles per split
   int nsplit;            // number of K splits
-  int nprod;             // 1 (single BF16) or 3 (hi/lo split)
+  int nprod;             // 1 (single BF16), 2 or 3 (hi/lo split)
+  int alo;               // with nprod 2: products (hi,hi), (lo,hi) instead of (hi,hi), (hi,lo)
   int vtiles;            // vp / 64 (BMODE_VV)
   // EPI_PARTIAL
   float* out;
@@ -62,6 +63,7 @@ struct Params {
   __nv_bfloat16* zlo;
   int o, vp;
   int zrows;             // C * o rows per K tile
+  int ztma;              // 1: store Z chunks with TMA (nocc % 32 == 0)
   int* err;
 };
 
@@ -136,6 +138,22 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
+}
+
+// TMA tensor store from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2,
+                                             int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -220,7 +238,11 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // rows padded to 80 B so that both the row writes and the transposed reads
 // stay (nearly) free of bank conflicts.
 constexpr int kStageRowWords = 20;
-constexpr int kZStageBytesPerWarp = 2 * 32 * kStageRowWords * 4;
+constexpr int kZChunkBytes = 32 * 64;  // TMA path: one 32 x 32 BF16 block
+// per warp: manual path hi + lo with 80-byte rows (5 KB), or TMA path two
+// buffers x two planes of dense blocks (8 KB)
+constexpr int kZStageBytesPerWarp = 4 * kZChunkBytes;
+static_assert(2 * 32 * kStageRowWords * 4 <= kZStageBytesPerWarp, "manual staging must fit");
 
 // BF16 hi/lo of two floats: hi = rn(x), lo = rn(x - hi), each packed (x0 in
 // the low half).
@@ -266,7 +288,8 @@ __device__ __forceinline__ TileCoord tile_coord(int t, int tiles_n, int tiles_m,
 // ---------------------------------------------------------------------------
 template <int BN, int STAGES, int BMODE, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p) {
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmZ, const Params p) {
   using CF = Cfg<BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -316,7 +339,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           const int kr = kr0 + j / p.nprod, pr = j % p.nprod;
-          const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
+          // operand planes of product pr: (hi,hi), (hi,lo), (lo,hi); with
+          // alo the second product is (lo,hi)
+          const int pa = (pr == 2 || (pr == 1 && p.alo)) ? 1 : 0;
+          const int pb = (pr == 1 && !p.alo) ? 1 : 0;
           uint8_t* sA = smem + s * CF::kStageBytes;
           uint8_t* sB = sA + kABytes;
           mbar_expect_tx(&full[s], CF::kStageBytes);
@@ -377,6 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int nchunks = (BN + 31) / 32;
     const int row = q * 32 + lane;
     int tcount = 0;
+    int zcount = 0;  // TMA-stored Z chunks of this warp (staging double buffer)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tcount) {
       const TileCoord tc = tile_coord(t, tiles_n, tiles_m, BN);
       const int kr0 = tc.split * p.kt_per_split;
@@ -418,6 +445,56 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int mb = tc.m0 + q * 32;
         const int Pb = mb / p.o, ib = mb - Pb * p.o;
         const int vt = p.vp >> 6;
+        if (p.ztma) {
+          // 32 rows of one P and one col per warp: stage the BF16 block densely
+          // (double-buffered) and store it with one TMA box per plane.
+          uint8_t* tb = reinterpret_cast<uint8_t*>(stg);  // [buf][plane][32][64 B]
+          for (int ci = half; ci < nchunks; ci += 2, ++zcount) {
+            const int c = ci * 32;
+            uint32_t r[32];
+            tmem_ld32(tbase + c, r);
+            if (!has_k) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) r[j] = 0u;
+            }
+            const int buf = zcount & 1;
+            if (zcount >= 2) {
+              if (lane == 0) bulk_wait_read1();
+              __syncwarp();
+            }
+            uint4* sh = reinterpret_cast<uint4*>(tb + (buf * 2) * kZChunkBytes + lane * 64);
+            if (two) {
+              uint32_t hw[16], lw[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                split_pack(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]), hw[j], lw[j]);
+              uint4* sl = reinterpret_cast<uint4*>(tb + (buf * 2 + 1) * kZChunkBytes + lane * 64);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
+                sl[j] = make_uint4(lw[4 * j], lw[4 * j + 1], lw[4 * j + 2], lw[4 * j + 3]);
+              }
+            } else {
+              uint32_t hw[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                hw[j] = pack_bf16x2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            const int n = tc.n0 + c;
+            if (lane == 0 && n < p.N && mb < p.M && ok) {
+              const int col = n / p.vp, b = n - col * p.vp;
+              const int kt = Pb * vt + (b >> 6);
+              tma_store_4d(&tmZ, tb + (buf * 2) * kZChunkBytes, b & 63, col * p.o + ib, kt, 0);
+              if (two) tma_store_4d(&tmZ, tb + (buf * 2 + 1) * kZChunkBytes, b & 63, col * p.o + ib, kt, 1);
+            }
+            if (lane == 0) bulk_commit();
+          }
+        } else
         for (int ci = half; ci < nchunks; ci += 2) {
           const int c = ci * 32;
           uint32_t r[32];
@@ -477,6 +554,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) mbar_arrive(&acce[buf]);
       if (!ok) break;
     }
+    // every TMA store of this warp must have completed before the CTA exits
+    if (EPI == EPI_ZSPLIT && lane == 0) bulk_wait_all();
   }
   tc_fence_before();
   __syncthreads();
