@@ -139,6 +139,7 @@ struct rttda_ctx {
   bool tc = false;
   int nplanes = 1, nprod = 1, vp = 0, op = 0, tc_bn = 256;
   int zplanes = 1, nprod_main = 1;  // Z planes kept; products in the main contraction
+  int wide_mb = 0;                   // >0: main contraction on the wide-M kernel with this many 128-row blocks
   __nv_bfloat16* Bvv_tc = nullptr;  // [plane][P][vp][vp]
   __nv_bfloat16* Boo_tc = nullptr;  // [plane][P*o][op]
   __nv_bfloat16* Xt = nullptr;      // [plane][C*vp][op]
@@ -268,6 +269,20 @@ void tc_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm
   tc::k_tc_gemm<BN, ST, BM, EP><<<grid, tc::kThreads, tc::smem_bytes<BN, ST, EP>(), s>>>(a, b, z ? *z : a, prm);
 }
 
+template <int BN, int MB, int NBP, int ST>
+void wide_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s) {
+  const long long tiles = cdiv(prm.N, BN) * cdiv(prm.M, (long long)tc::kBM * MB) * prm.nsplit;
+  const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(tiles, kNumSM));
+  tc::k_tc_wide<BN, MB, NBP, ST><<<grid, tc::kThreads, tc::wide_smem_bytes<BN, MB, NBP, ST>(), s>>>(a, b, prm);
+}
+
+template <int BN, int MB, int NBP, int ST>
+void wide_attr() {
+  static_assert(tc::wide_smem_bytes<BN, MB, NBP, ST>() <= 232448, "shared memory per block exceeds 227 KB");
+  cudaFuncSetAttribute(tc::k_tc_wide<BN, MB, NBP, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::wide_smem_bytes<BN, MB, NBP, ST>());
+}
+
 template <int BN, int ST, int BM, int EP>
 void tc_attr() {
   static_assert(tc::smem_bytes<BN, ST, EP>() <= 232448, "shared memory per block exceeds 227 KB");
@@ -281,6 +296,10 @@ void set_tc_smem_limits() {
   tc_attr<224, 5, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<256, 4, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<64, 8, tc::BMODE_PLAIN, tc::EPI_PARTIAL>();
+  wide_attr<160, 3, 2, 2>();
+  wide_attr<192, 2, 2, 2>();
+  wide_attr<160, 3, 1, 3>();
+  wide_attr<192, 2, 1, 4>();
 }
 
 // Batched Coulomb on tensor cores: w = B_ov c (split-K over ia), then
@@ -375,7 +394,17 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.split_stride = (long long)C * o * v;
       prm.accum = c > 0 ? 1 : 0;
       prm.err = h->d_err;
-      switch (h->tc_bn) {
+      if (h->wide_mb) {
+        // wide-M tiles: MB accumulators share each B tile; both B planes per stage
+        const int key = h->tc_bn * 10 + h->wide_mb;
+        if (h->nprod_main == 2) {
+          if (key == 1603) wide_launch<160, 3, 2, 2>(h->tmMA[c], h->tmMB[c], prm, s);
+          else wide_launch<192, 2, 2, 2>(h->tmMA[c], h->tmMB[c], prm, s);
+        } else {
+          if (key == 1603) wide_launch<160, 3, 1, 3>(h->tmMA[c], h->tmMB[c], prm, s);
+          else wide_launch<192, 2, 1, 4>(h->tmMA[c], h->tmMB[c], prm, s);
+        }
+      } else switch (h->tc_bn) {
         case 128: tc_launch<128, 7, tc::BMODE_VV, tc::EPI_PARTIAL>(h->tmMA[c], h->tmMB[c], prm, s); break;
         case 224: tc_launch<224, 5, tc::BMODE_VV, tc::EPI_PARTIAL>(h->tmMA[c], h->tmMB[c], prm, s); break;
         default: tc_launch<256, 4, tc::BMODE_VV, tc::EPI_PARTIAL>(h->tmMA[c], h->tmMB[c], prm, s); break;
@@ -707,19 +736,39 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   h->zchunk = (int)std::max<size_t>(1, std::min<size_t>(P, zbudget_bytes() / std::max<size_t>(zper, 1)));
   h->zplane = (size_t)C * o * h->zchunk * vp;
   CKS(dalloc(&h->Zk, h->zplane * h->zplanes));
-  // main contraction tile width along a (N = nvirt)
+  // main contraction tiles.  BF16 and BF16X2 (Z is one plane): wide-M tiles
+  // (MB 128-row accumulators per CTA) chosen for the least padded work;
+  // BF16X3: 128-row tiles with the N width that wastes least.
+  const long long M = (long long)C * o;
+  const long long kt_full = (long long)h->zchunk * (vp / tc::kBK);
   int best = 256;
-  long long bestw = -1;
-  for (int bn : {128, 224, 256}) {
-    const long long wasted = cdiv(v, bn) * bn;
-    if (bestw < 0 || wasted < bestw || (wasted == bestw && bn > best)) {
-      best = bn;
-      bestw = wasted;
+  long long tiles = 0;
+  h->wide_mb = 0;
+  if (h->nprod_main <= 2) {
+    long long bestw = -1;
+    const int cand[2][2] = {{160, 3}, {192, 2}};
+    for (const auto& cb : cand) {
+      const long long tm = (long long)tc::kBM * cb[1];
+      const long long work = cdiv(M, tm) * tm * cdiv(v, cb[0]) * cb[0];
+      if (bestw < 0 || work < bestw) {
+        bestw = work;
+        best = cb[0];
+        h->wide_mb = cb[1];
+      }
     }
+    tiles = cdiv(M, (long long)tc::kBM * h->wide_mb) * cdiv(v, best);
+  } else {
+    long long bestw = -1;
+    for (int bn : {128, 224, 256}) {
+      const long long wasted = cdiv(v, bn) * bn;
+      if (bestw < 0 || wasted < bestw || (wasted == bestw && bn > best)) {
+        best = bn;
+        bestw = wasted;
+      }
+    }
+    tiles = cdiv(M, tc::kBM) * cdiv(v, best);
   }
   h->tc_bn = best;
-  const long long tiles = cdiv((long long)C * o, tc::kBM) * cdiv(v, best);
-  const long long kt_full = (long long)h->zchunk * (vp / tc::kBK);
   h->SK = choose_splits(tiles, kt_full);
   char* p = nullptr;
   CK(cudaMalloc((void**)&p, (size_t)h->SK * C * o * v * sizeof(float)));

@@ -565,5 +565,182 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Wide-M variant for the main exchange contraction (A = Z, one BF16 plane):
+// a CTA tile is MB x 128 rows by BN columns, i.e. MB TMEM accumulators that
+// share every B tile, and one pipeline stage holds the MB A tiles together
+// with all NBP planes of the B tile (B_hi, B_lo).  Per K tile the MMA warp
+// issues NBP x MB x 4 MMAs.  Fewer bytes move from L2 per multiply-add than
+// with 128-row tiles.  Persistent over (split, m tile, n tile); the
+// accumulators are drained by the epilogue before the next tile starts.
+// ---------------------------------------------------------------------------
+template <int BN, int MB, int NBP>
+struct WideCfg {
+  static constexpr int kABlock = kBM * 128;       // one 128-row A tile
+  static constexpr int kBBytes = BN * 128;        // one B plane
+  static constexpr int kStageBytes = MB * kABlock + NBP * kBBytes;
+  static constexpr int kCols = MB * BN;
+  static constexpr uint32_t kTmemCols = kCols <= 32 ? 32 : kCols <= 64 ? 64 : kCols <= 128 ? 128
+                                        : kCols <= 256 ? 256 : 512;
+  static_assert(kCols <= 512, "accumulators exceed TMEM");
+  static_assert(kStageBytes % 1024 == 0, "stage must keep 1024-byte alignment");
+  static_assert(BN % 32 == 0 && BN <= 256, "BN must be a multiple of 32 and <= 256");
+};
+
+template <int BN, int MB, int NBP, int STAGES>
+constexpr size_t wide_smem_bytes() {
+  return (size_t)STAGES * WideCfg<BN, MB, NBP>::kStageBytes + 1024 + 256;
+}
+
+template <int BN, int MB, int NBP, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_wide(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p) {
+  using CF = WideCfg<BN, MB, NBP>;
+  constexpr int TM = kBM * MB;  // rows per tile
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * CF::kStageBytes);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint64_t* acce = accf + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_n = (p.N + BN - 1) / BN;
+  const int tiles_m = (p.M + TM - 1) / TM;
+  const int ntiles = tiles_n * tiles_m * p.nsplit;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, kEpiWarps);
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, CF::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto coords = [&](int t, int& n0, int& m0, int& split) {
+    n0 = (t % tiles_n) * BN;
+    m0 = ((t / tiles_n) % tiles_m) * TM;
+    split = t / (tiles_n * tiles_m);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool alive = true;
+      for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+        int n0, m0, split;
+        coords(t, n0, m0, split);
+        const int kr0 = split * p.kt_per_split;
+        const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
+        for (int kr = kr0; kr < kr1; ++kr, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, p.err, ERR_WAIT_EMPTY)) {
+            alive = false;
+            break;
+          }
+          uint8_t* st = smem + s * CF::kStageBytes;
+          mbar_expect_tx(&full[s], CF::kStageBytes);
+#pragma unroll
+          for (int b = 0; b < MB; ++b) tma_load_4d(st + b * CF::kABlock, &tmA, &full[s], 0, m0 + b * kBM, kr, 0);
+          const int P = kr / p.vtiles, b0 = (kr % p.vtiles) * kBK;
+#pragma unroll
+          for (int q = 0; q < NBP; ++q)
+            tma_load_4d(st + MB * CF::kABlock + q * CF::kBBytes, &tmB, &full[s], b0, n0, P, q);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+      int it = 0, tcount = 0;
+      bool alive = true;
+      for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x, ++tcount) {
+        int n0, m0, split;
+        coords(t, n0, m0, split);
+        const int kr0 = split * p.kt_per_split;
+        const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
+        if (!mbar_wait(acce, ((uint32_t)tcount & 1u) ^ 1u, p.err, ERR_WAIT_ACC)) break;
+        tc_fence_after();
+        for (int kr = kr0; kr < kr1; ++kr, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph, p.err, ERR_WAIT_FULL)) {
+            alive = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t base = smem_u32(smem + s * CF::kStageBytes);
+#pragma unroll
+          for (int q = 0; q < NBP; ++q) {
+            const uint64_t bdesc = sdesc_sw128(base + MB * CF::kABlock + q * CF::kBBytes);
+#pragma unroll
+            for (int b = 0; b < MB; ++b) {
+              const uint64_t adesc = sdesc_sw128(base + b * CF::kABlock);
+#pragma unroll
+              for (int k = 0; k < kBK / 16; ++k)
+                mma_bf16(tmem + b * BN, adesc + 2 * k, bdesc + 2 * k, idesc,
+                         (kr > kr0 || q > 0 || k > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(accf);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    int tcount = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tcount) {
+      int n0, m0, split;
+      coords(t, n0, m0, split);
+      const int kr0 = split * p.kt_per_split;
+      const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
+      const bool has_k = kr1 > kr0;
+      const bool ok = mbar_wait(accf, (uint32_t)tcount & 1u, p.err, ERR_WAIT_ACC);
+      tc_fence_after();
+      for (int b = 0; b < MB; ++b) {
+        const int m = m0 + b * kBM + row;
+        float* dst = p.out + (size_t)split * p.split_stride + (size_t)m * p.ldo;
+        for (int ci = half; ci < BN / 32; ci += 2) {
+          const int c = ci * 32;
+          uint32_t r[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * BN + c, r);
+          if (m < p.M && ok) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int n = n0 + c + j;
+              if (n < p.N) {
+                const float x = has_k ? __uint_as_float(r[j]) : 0.0f;
+                dst[n] = p.accum ? dst[n] + x : x;
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce);
+      if (!ok) break;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, CF::kTmemCols);
+  }
+}
+
 }  // namespace tc
 }  // namespace rttda
