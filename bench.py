@@ -111,6 +111,41 @@ def dist_info():
     return rank, world, local
 
 
+class Ranks:
+    """Process-group plumbing of a multi-GPU run.  Every rank propagates its
+    own batch (weak scaling); the only cross-rank operations are a barrier
+    around the timed region and the maximum of the timed seconds."""
+
+    def __init__(self, backend: str = "nccl", device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.rank, self.world, self.local = dist_info()
+        self.device = device
+        if self.world > 1:
+            import torch.distributed as dist
+            kw = {"device_id": torch.device("cuda", self.local)} if backend == "nccl" else {}
+            dist.init_process_group(backend, **kw)
+
+    def barrier(self) -> None:
+        if self.world > 1:
+            self.torch.distributed.barrier()
+
+    def max(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        t = self.torch.tensor([x], dtype=self.torch.float64, device=self.device)
+        self.torch.distributed.all_reduce(t, op=self.torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def aggregate_rate(self, units_per_rank: float, seconds: float) -> float:
+        """Whole-job throughput: all ranks' units over the slowest rank's time."""
+        return self.world * units_per_rank / self.max(seconds)
+
+    def close(self) -> None:
+        if self.world > 1:
+            self.torch.distributed.destroy_process_group()
+
+
 def base_config(prec: str, world: int, T: int = 3) -> dict:
     return {"workload": WORKLOAD, "precision": prec, "trajectories_per_gpu": T,
             "global_trajectories": T * world, "parallelism": f"trajectory replicas x{world}",
@@ -321,22 +356,10 @@ def run_gpu(args):
     import torch
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ranks = Ranks("nccl", "cuda")
     from paper_2601_16949_b300 import binding as rb
     from paper_2601_16949_b300 import synth
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     if args.workload == "large":
         # FP64 factors of this size do not fit in host memory: draw them on the GPU
@@ -393,6 +416,7 @@ def run_gpu(args):
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                               "warmup": W, "ms_per_step": ms / K, "mode": "only-timed", "prec": args.prec}))
         prop.close()
+        ranks.close()
         return 0
 
     # per-kernel timing pass (events around every kernel class, same workload)
@@ -474,8 +498,7 @@ def run_gpu(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     prop.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    ranks.close()
     return 0
 
 
@@ -606,6 +629,15 @@ def main():
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     set_workload(args.workload)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and args.impl == "ours":
+        # one process per GPU: relaunch under torch.distributed.run
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+        return subprocess.call(cmd)
     if args.impl == "reference":
         return run_reference(args)
     if args.accuracy:

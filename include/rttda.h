@@ -267,6 +267,14 @@ rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step
 rttda_status rttda_coulomb_noalloc(int nocc, int nvirt, int naux, const double* B_ov_dev, const double* c_dev,
                                    int ntraj, double* sigma_dev, void* stream);
 
+/* Failure-detection self-test.  Launches one kernel whose single thread
+ * waits, with a wall-clock limit of limit_s seconds (1e-3 .. 2), for a device
+ * flag that nothing sets; the kernel then records the expiry and returns, as
+ * the tensor-core kernels do when one of their pipeline waits runs out.
+ * Returns RTTDA_E_TIMEOUT when the wait ran out (the expected outcome); the
+ * CUDA context stays usable.  The paper has no counterpart. */
+rttda_status rttda_selftest_wait(double limit_s);
+
 /* Free every resource of the handle (NULL is ignored). */
 void rttda_destroy(rttda_t h);
 

@@ -105,6 +105,8 @@ lib.rttda_server_destroy.restype = None
 for _name in ("rttda_server_create", "rttda_server_submit", "rttda_server_poll", "rttda_server_wait",
               "rttda_server_cancel", "rttda_server_stats_get", "rttda_estimate_bytes"):
     getattr(lib, _name).restype = ct.c_int
+lib.rttda_selftest_wait.argtypes = [ct.c_double]
+lib.rttda_selftest_wait.restype = ct.c_int
 lib.rttda_destroy.argtypes = [_h]
 lib.rttda_destroy.restype = None
 for _name in ("rttda_create", "rttda_memory_bytes", "rttda_set_field", "rttda_propagate", "rttda_propagate_device",
@@ -266,6 +268,11 @@ def rttda_coulomb_noalloc(nocc, nvirt, naux, B_ov_dev, c_dev, ntraj, sigma_dev, 
     """Coulomb part of sigma with no device allocation (device addresses in)."""
     _check(lib.rttda_coulomb_noalloc(int(nocc), int(nvirt), int(naux), B_ov_dev, c_dev, int(ntraj), sigma_dev,
                                      stream or None), "rttda_coulomb_noalloc")
+
+
+def rttda_selftest_wait(limit_s) -> int:
+    """Status of the bounded-device-wait self-test (RTTDA_E_TIMEOUT expected)."""
+    return lib.rttda_selftest_wait(float(limit_s))
 
 
 def rttda_destroy(h) -> None:

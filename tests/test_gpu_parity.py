@@ -186,3 +186,20 @@ def test_config2_sampled_rows_fp64_and_fp32(rb):
             scale = np.abs(Arows) @ np.abs(c[k]) + abs(E) * (np.abs(Mrows) @ np.abs(c[k]))
             err = np.abs(got[k, rows] - ref) / np.maximum(scale, 1e-300)
             assert np.max(err) < tol, (prec, k, np.max(err))
+
+
+def test_bounded_device_wait_reports_timeout_and_context_survives(rb):
+    """A device wait on a flag nothing sets runs out after its limit, the
+    library returns RTTDA_E_TIMEOUT, and the same context keeps working."""
+    import time
+    t0 = time.perf_counter()
+    st = rb.rttda_selftest_wait(0.02)
+    assert st == rb.E_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    mol = synth.molecule(3, 5, 7, seed=1)
+    prop = rb.Propagator(mol, 0.2, "bf16x3")
+    prop.set_field([dict(kind=0, E0=1e-3)])
+    c, dip, nrm = prop.propagate(0.05, 10)
+    rb.rttda_sync(prop.h)
+    assert np.all(np.isfinite(dip)) and abs(nrm[0, -1] - 1.0) < 1e-6
+    prop.close()
