@@ -292,6 +292,15 @@ PREC_INFO = {  # factor bytes, exchange planes, tensor products per K tile
 }
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant kernel, from one ncu --set full capture of that kernel on this
+# workload.  Keyed by (workload, precision, kernel class, BN, MB, K tile):
+# the number holds only for that kernel and plan.
+PROFILED_TRAFFIC = {
+    ("absorption", "bf16x2", "exchange_main", 160, 3, 32): 1.780069e9 + 4.38272e6,
+}
+
+
 def algorithmic_work(prec: str, cls: str, T: int):
     """(flop, bytes) of one launch of a kernel class on this workload.
 
@@ -316,20 +325,32 @@ def algorithmic_work(prec: str, cls: str, T: int):
     return None, None
 
 
-def roofline(prec: str, cls: str, prof_entry, T: int, peaks: dict) -> dict:
+def roofline(prec: str, cls: str, prof_entry, T: int, peaks: dict, nsigma: int) -> dict:
+    """Roofline of one kernel class.  The unit is one sigma build (one RK4
+    stage): when the exchange is chunked over P, a stage is several launches
+    of the class, so work and time are both taken per stage (the sum over
+    its launches), which keeps achieved = work / duration for any chunking.
+
+    The class is timed inside a long run of steps, so the tensor peak is the
+    sustained (power-capped) measured bf16 rate; the burst rate is reported
+    beside it."""
     ms, n = prof_entry
     flop, byts = algorithmic_work(prec, cls, T)
     hbm = peaks.get("hbm_gbs", 6400.0)
-    bf16 = peaks.get("bf16_tflops", 1800.0)
-    out = {"kernel": cls, "avg_launch_ms": ms / max(n, 1), "launches_timed": n, "traffic": None,
-           "flop_per_launch": flop, "bytes_per_launch": byts}
+    bf16_burst = peaks.get("bf16_tflops", 1800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", 1400.0)
+    out = {"kernel": cls, "unit_of_work": "one sigma build (all launches of the class in one RK4 stage)",
+           "avg_launch_ms": ms / max(n, 1), "launches_timed": n, "sigma_builds_timed": nsigma,
+           "launches_per_sigma": n / max(nsigma, 1), "ms_per_sigma": ms / max(nsigma, 1), "traffic": None,
+           "flop_per_sigma": flop, "bytes_per_sigma": byts}
     if flop is None or n == 0:
         out.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None})
         return out
-    sec = ms / n / 1e3
+    sec = ms / nsigma / 1e3
     pi = PREC_INFO[prec]
     if pi["tensor"]:
-        cpeak, cunit, csrc = bf16, "TFLOP/s", "measured bf16 burst (MEASURED_PEAKS.json)"
+        cpeak, cunit = bf16, "TFLOP/s"
+        csrc = "of measured: bf16 sustained (MEASURED_PEAKS.json bf16_tflops_sustained)"
         cbound = "tensor"
     else:
         lanes = 128 if prec == "fp32" else 64
@@ -340,12 +361,14 @@ def roofline(prec: str, cls: str, prof_entry, T: int, peaks: dict) -> dict:
     t_mem = byts / (hbm * 1e9)
     if t_mem >= t_comp:
         out.update({"bound": "hbm", "achieved": byts / sec / 1e9, "peak": hbm, "unit": "GB/s",
-                    "peak_source": "measured HBM copy (MEASURED_PEAKS.json)"})
+                    "peak_source": "of measured: HBM copy (MEASURED_PEAKS.json hbm_gbs)"})
     else:
         out.update({"bound": cbound, "achieved": flop / sec / 1e12, "peak": cpeak, "unit": cunit,
                     "peak_source": csrc})
     out["frac"] = out["achieved"] / out["peak"]
     out["other_bound_frac"] = (flop / sec / 1e12 / cpeak) if out["bound"] == "hbm" else (byts / sec / 1e9 / hbm)
+    if pi["tensor"]:
+        out["tensor_frac_of_burst"] = flop / sec / 1e12 / bf16_burst
     return out
 
 
@@ -396,6 +419,7 @@ def run_gpu(args):
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
         pass
+    plan = rb.rttda_plan(h)
     launches0, _ = rb.rttda_launch_stats(h)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(uuid) as clk:
@@ -473,7 +497,11 @@ def run_gpu(args):
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     ms_cls = {k: v[0] for k, v in prof.items()}
     dom = max(ms_cls, key=ms_cls.get)
-    roof = roofline(args.prec, dom, prof[dom], T, peaks)
+    roof = roofline(args.prec, dom, prof[dom], T, peaks, 4 * kp)
+    tkey = (args.workload, args.prec, dom, plan["main_bn"], plan["main_mb"], plan["main_kb"])
+    if tkey in PROFILED_TRAFFIC and plan["z_chunk"] >= NAUX:
+        roof["traffic"] = PROFILED_TRAFFIC[tkey]
+        roof["traffic_source"] = "ncu capture of this kernel and plan (one launch = one sigma build)"
     roof["class_ms_share"] = {k: round(v / max(sum(ms_cls.values()), 1e-30), 4) for k, v in ms_cls.items()}
     roof["class_ms_per_step"] = {k: round(v / kp, 4) for k, v in ms_cls.items()}
 
@@ -490,7 +518,7 @@ def run_gpu(args):
     cfg.update({"fp64_path_traj_steps_per_s": fp64_rate, "speedup_vs_fp64_path": value / world / fp64_rate,
                 "fp64_path": f"plain FP64, one trajectory (the batch's last), {k64} timed steps",
                 "dipole_rel_err_vs_fp64": dip_err, "dipole_err_horizon_steps": k64,
-                "launches_per_step": per_step})
+                "launches_per_step": per_step, "plan": plan})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype, "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu,

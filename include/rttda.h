@@ -151,8 +151,9 @@ rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes);
 /* Set the batch: one pulse per trajectory (Eq. e_field, Eqs. e_fields).
  * ntraj >= 1; pulses[ntraj] (host).  Builds mu_d = sum_x d_x mu_x per
  * trajectory on the device.  Discards any propagated state.
- * Errors: RTTDA_E_ARG (ntraj < 1, unknown kind, zero polarisation,
- * non-positive fwhm/duration where used), RTTDA_E_OOM, RTTDA_E_CUDA. */
+ * Errors: RTTDA_E_ARG (ntraj < 1, (1 + nocc*nvirt) * 2 * ntraj >= 2^31,
+ * unknown kind, zero polarisation, non-positive fwhm/duration where used),
+ * RTTDA_E_OOM, RTTDA_E_CUDA. */
 rttda_status rttda_set_field(rttda_t h, const rttda_pulse* pulses, int ntraj);
 
 /* Propagate every trajectory of the batch from t = 0.
@@ -241,6 +242,32 @@ rttda_status rttda_profile_read(rttda_t h, double* ms, long long* launches);
 /* Kernels this handle has enqueued so far (*total) and in one RK4 step of
  * the last propagation (*per_step).  Either pointer may be NULL. */
 rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step);
+
+/* Execution plan of the sigma build chosen for the current batch (after
+ * rttda_set_field).  The exchange main contraction sum_{P,b} Z^P_ib B^P_ab
+ * (Sec. 2.2, exchange part of the A matrix elements) runs on
+ *   main_kernel 0: SIMT (FP64 / FP32),
+ *               1: tcgen05, 128-row tiles (BF16X3),
+ *               2: tcgen05, wide-M tiles of main_mb x 128 rows (BF16, BF16X2),
+ * with main_bn output columns per tile, K tiles of main_kb BF16 and
+ * main_splits split-K partials; Z^P = B^P_oo c is built for z_chunk values
+ * of P at a time.  coulomb_kernel 0: SIMT, 1: tcgen05.
+ * tuned 0: heuristic plan (or RTTDA_TUNE=0), 1: timed now (tune_ms[k] is the
+ * fastest of five launches of candidate k in milliseconds, ncand
+ * candidates), 2: taken
+ * from the tuning cache of this process or of the RTTDA_TUNE_CACHE file,
+ * 3: named by the environment variable RTTDA_WIDE_PLAN="BN,MB,KB" (an
+ * unknown candidate there makes rttda_set_field fail with RTTDA_E_ARG).
+ * Errors: RTTDA_E_ARG (NULL), RTTDA_E_STATE (no batch yet). */
+typedef struct {
+  int prec, ntraj;
+  int main_kernel, main_bn, main_mb, main_kb, main_splits;
+  int z_chunk;
+  int coulomb_kernel;
+  int tuned, ncand;
+  double tune_ms[8];
+} rttda_plan_info;
+rttda_status rttda_plan(rttda_t h, rttda_plan_info* out);
 
 /* Coulomb term of sigma without allocating any device memory.
  * The paper has no counterpart; this entry point exists for callers that

@@ -54,6 +54,12 @@ class rttda_server_stats(ct.Structure):
                 ("bytes_in_use", ct.c_size_t), ("bytes_budget", ct.c_size_t)]
 
 
+class rttda_plan_info(ct.Structure):
+    _fields_ = [(n, ct.c_int) for n in ("prec", "ntraj", "main_kernel", "main_bn", "main_mb", "main_kb",
+                                        "main_splits", "z_chunk", "coulomb_kernel", "tuned", "ncand")] + \
+               [("tune_ms", ct.c_double * 8)]
+
+
 REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
 
 
@@ -89,6 +95,7 @@ lib.rttda_sync.argtypes = [_h, ct.c_void_p]
 lib.rttda_profile.argtypes = [_h, ct.c_int]
 lib.rttda_profile_read.argtypes = [_h, _dp, ct.POINTER(ct.c_longlong)]
 lib.rttda_launch_stats.argtypes = [_h, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]
+lib.rttda_plan.argtypes = [_h, ct.POINTER(rttda_plan_info)]
 lib.rttda_coulomb_noalloc.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int,
                                       ct.c_void_p, ct.c_void_p]
 lib.rttda_coulomb_noalloc.restype = ct.c_int
@@ -111,7 +118,7 @@ lib.rttda_destroy.argtypes = [_h]
 lib.rttda_destroy.restype = None
 for _name in ("rttda_create", "rttda_memory_bytes", "rttda_set_field", "rttda_propagate", "rttda_propagate_device",
               "rttda_resume", "rttda_get_state", "rttda_set_state", "rttda_sigma", "rttda_spectrum",
-              "rttda_profile", "rttda_profile_read", "rttda_launch_stats", "rttda_sync"):
+              "rttda_profile", "rttda_profile_read", "rttda_launch_stats", "rttda_sync", "rttda_plan"):
     getattr(lib, _name).restype = ct.c_int
 
 
@@ -262,6 +269,15 @@ def rttda_launch_stats(h) -> tuple:
     per = ct.c_longlong()
     _check(lib.rttda_launch_stats(h, ct.byref(tot), ct.byref(per)), "rttda_launch_stats")
     return tot.value, per.value
+
+
+def rttda_plan(h) -> dict:
+    """The sigma build's execution plan for the current batch (see rttda.h)."""
+    pi = rttda_plan_info()
+    _check(lib.rttda_plan(h, ct.byref(pi)), "rttda_plan")
+    d = {name: getattr(pi, name) for name, _ in rttda_plan_info._fields_ if name != "tune_ms"}
+    d["tune_ms"] = [pi.tune_ms[k] for k in range(min(pi.ncand, 8))]
+    return d
 
 
 def rttda_coulomb_noalloc(nocc, nvirt, naux, B_ov_dev, c_dev, ntraj, sigma_dev, stream=0) -> None:

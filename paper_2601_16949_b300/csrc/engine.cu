@@ -7,7 +7,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -16,6 +21,7 @@
 #include "engine_internal.h"
 #include "kernels_simt.cuh"
 #include "tc_gemm.cuh"
+#include "coul_stream.cuh"
 
 using namespace rttda;
 
@@ -129,6 +135,8 @@ struct rttda_ctx {
   void* Kpart = nullptr;
   int SJ = 1, pchunkJ = 1, SK = 1, zchunk = 1, obsG = 1, SW = 1, wslice = 1;
   bool coul_vec = false;
+  bool coul_stream = false;  // Coulomb on the FP32 streaming kernels (FP32 / BF16 factors, 2T <= 12)
+  float* Xf = nullptr;       // [ov][C] FP32 amplitudes of the stage (streaming Coulomb)
   long long obs_rows = 1;
   size_t dev_bytes = 0;
 
@@ -140,6 +148,8 @@ struct rttda_ctx {
   int nplanes = 1, nprod = 1, vp = 0, op = 0, tc_bn = 256;
   int zplanes = 1, nprod_main = 1;  // Z planes kept; products in the main contraction
   int wide_mb = 0;                   // >0: main contraction on the wide-M kernel with this many 128-row blocks
+  int wide_kb = 32;                  // K tile width of the wide-M kernel (32 or 64 BF16)
+  rttda_plan_info plan{};            // the exchange plan in use (rttda_plan)
   __nv_bfloat16* Bvv_tc = nullptr;  // [plane][P][vp][vp]
   __nv_bfloat16* Boo_tc = nullptr;  // [plane][P*o][op]
   __nv_bfloat16* Xt = nullptr;      // [plane][C*vp][op]
@@ -199,7 +209,7 @@ rttda_ctx::~rttda_ctx() {
 
 void rttda_ctx::free_batch() {
   void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xn, Xs, Xs2, acc, F, E, term,
-                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk, Xc, Wt, wpart_tc};
+                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk, Xc, Wt, wpart_tc, Xf};
   for (void* p : ps) dfree(p);
   d_pulses = nullptr;
   d_kappa = d_dirs = moo64 = mvv64 = m064 = nullptr;
@@ -210,7 +220,9 @@ void rttda_ctx::free_batch() {
   Xt = Zk = nullptr;
   Xc = Wt = nullptr;
   wpart_tc = nullptr;
+  Xf = nullptr;
   coul_tc = false;
+  coul_stream = false;
   tmZA.clear();
   tmZS.clear();
   tmMA.clear();
@@ -258,7 +270,9 @@ struct Prof {
 namespace {
 
 // --- tensor-core exchange -------------------------------------------------
-constexpr int kZBN = 256, kZStages = 3;   // Z = B_oo c   (K = nocc, short)
+// Z = B_oo c (K = nocc, short): pipeline stages with hi/lo Z staging (two
+// planes) or one-plane staging
+constexpr int kZBN = 256, kZStages2 = 2, kZStages1 = 3;
 
 // Persistent launch: one CTA per SM (or per tile if fewer tiles).
 template <int BN, int ST, int BM, int EP>
@@ -269,18 +283,43 @@ void tc_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm
   tc::k_tc_gemm<BN, ST, BM, EP><<<grid, tc::kThreads, tc::smem_bytes<BN, ST, EP>(), s>>>(a, b, z ? *z : a, prm);
 }
 
-template <int BN, int MB, int NBP, int ST>
+template <int BN, int MB, int NBP, int ST, int KB>
 void wide_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s) {
   const long long tiles = cdiv(prm.N, BN) * cdiv(prm.M, (long long)tc::kBM * MB) * prm.nsplit;
   const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(tiles, kNumSM));
-  tc::k_tc_wide<BN, MB, NBP, ST><<<grid, tc::kThreads, tc::wide_smem_bytes<BN, MB, NBP, ST>(), s>>>(a, b, prm);
+  tc::k_tc_wide<BN, MB, NBP, ST, KB><<<grid, tc::kThreads, tc::wide_smem_bytes<BN, MB, NBP, ST, KB>(), s>>>(a, b, prm);
 }
 
-template <int BN, int MB, int NBP, int ST>
+template <int BN, int MB, int NBP, int ST, int KB>
 void wide_attr() {
-  static_assert(tc::wide_smem_bytes<BN, MB, NBP, ST>() <= 232448, "shared memory per block exceeds 227 KB");
-  cudaFuncSetAttribute(tc::k_tc_wide<BN, MB, NBP, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)tc::wide_smem_bytes<BN, MB, NBP, ST>());
+  static_assert(tc::wide_smem_bytes<BN, MB, NBP, ST, KB>() <= 232448, "shared memory per block exceeds 227 KB");
+  cudaFuncSetAttribute(tc::k_tc_wide<BN, MB, NBP, ST, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::wide_smem_bytes<BN, MB, NBP, ST, KB>());
+}
+
+// The wide-M configurations: (BN, MB) in {(160, 3), (192, 2)}, one or two B
+// planes, K tiles of 64 (128-byte rows) or 32 (64-byte rows, twice the
+// stages).  Stage counts fill the 227 KB of shared memory.
+void wide_dispatch(int bn, int mb, int nbp, int kb, const CUtensorMap& a, const CUtensorMap& b,
+                   const tc::Params& prm, cudaStream_t s) {
+  const bool w3 = bn == 160 && mb == 3;
+  if (kb == 32) {
+    if (nbp == 2) {
+      if (w3) wide_launch<160, 3, 2, 5, 32>(a, b, prm, s);
+      else wide_launch<192, 2, 2, 5, 32>(a, b, prm, s);
+    } else {
+      if (w3) wide_launch<160, 3, 1, 6, 32>(a, b, prm, s);
+      else wide_launch<192, 2, 1, 8, 32>(a, b, prm, s);
+    }
+  } else {
+    if (nbp == 2) {
+      if (w3) wide_launch<160, 3, 2, 2, 64>(a, b, prm, s);
+      else wide_launch<192, 2, 2, 2, 64>(a, b, prm, s);
+    } else {
+      if (w3) wide_launch<160, 3, 1, 3, 64>(a, b, prm, s);
+      else wide_launch<192, 2, 1, 4, 64>(a, b, prm, s);
+    }
+  }
 }
 
 template <int BN, int ST, int BM, int EP>
@@ -291,15 +330,20 @@ void tc_attr() {
 }
 
 void set_tc_smem_limits() {
-  tc_attr<kZBN, kZStages, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>();
+  tc_attr<kZBN, kZStages2, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>();
+  tc_attr<kZBN, kZStages1, tc::BMODE_PLAIN, tc::EPI_ZONE>();
   tc_attr<128, 7, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<224, 5, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<256, 4, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<64, 8, tc::BMODE_PLAIN, tc::EPI_PARTIAL>();
-  wide_attr<160, 3, 2, 2>();
-  wide_attr<192, 2, 2, 2>();
-  wide_attr<160, 3, 1, 3>();
-  wide_attr<192, 2, 1, 4>();
+  wide_attr<160, 3, 2, 5, 32>();
+  wide_attr<192, 2, 2, 5, 32>();
+  wide_attr<160, 3, 1, 6, 32>();
+  wide_attr<192, 2, 1, 8, 32>();
+  wide_attr<160, 3, 2, 2, 64>();
+  wide_attr<192, 2, 2, 2, 64>();
+  wide_attr<160, 3, 1, 3, 64>();
+  wide_attr<192, 2, 1, 4, 64>();
 }
 
 // Batched Coulomb on tensor cores: w = B_ov c (split-K over ia), then
@@ -375,20 +419,24 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.zrows = C * o;
       prm.ztma = (o % 32 == 0) ? 1 : 0;
       prm.err = h->d_err;
-      tc_launch<kZBN, kZStages, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
+      if (h->zplanes > 1)
+        tc_launch<kZBN, kZStages2, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
+      else
+        tc_launch<kZBN, kZStages1, tc::BMODE_PLAIN, tc::EPI_ZONE>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
     }
     {
       // K_(col,i),a (+)= sum_{P in chunk, b} Z^P_(col,i),b B^P_ab   (split-K)
       Prof pr(h, RTTDA_KC_EXCHANGE_MAIN, s);
       h->launches += 1;
       tc::Params prm{};
+      const int kb = h->wide_mb ? h->wide_kb : tc::kBK;
       prm.M = C * o;
       prm.N = v;
-      prm.kt_total = pc * (vp / tc::kBK);
+      prm.kt_total = pc * (vp / kb);
       prm.kt_per_split = h->tc_kper[c];
       prm.nsplit = h->SK;
       prm.nprod = h->nprod_main;
-      prm.vtiles = vp / tc::kBK;
+      prm.vtiles = vp / kb;
       prm.out = (float*)h->Kpart;
       prm.ldo = v;
       prm.split_stride = (long long)C * o * v;
@@ -396,14 +444,7 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.err = h->d_err;
       if (h->wide_mb) {
         // wide-M tiles: MB accumulators share each B tile; both B planes per stage
-        const int key = h->tc_bn * 10 + h->wide_mb;
-        if (h->nprod_main == 2) {
-          if (key == 1603) wide_launch<160, 3, 2, 2>(h->tmMA[c], h->tmMB[c], prm, s);
-          else wide_launch<192, 2, 2, 2>(h->tmMA[c], h->tmMB[c], prm, s);
-        } else {
-          if (key == 1603) wide_launch<160, 3, 1, 3>(h->tmMA[c], h->tmMB[c], prm, s);
-          else wide_launch<192, 2, 1, 4>(h->tmMA[c], h->tmMB[c], prm, s);
-        }
+        wide_dispatch(h->tc_bn, h->wide_mb, h->nprod_main, h->wide_kb, h->tmMA[c], h->tmMB[c], prm, s);
       } else switch (h->tc_bn) {
         case 128: tc_launch<128, 7, tc::BMODE_VV, tc::EPI_PARTIAL>(h->tmMA[c], h->tmMB[c], prm, s); break;
         case 224: tc_launch<224, 5, tc::BMODE_VV, tc::EPI_PARTIAL>(h->tmMA[c], h->tmMB[c], prm, s); break;
@@ -411,6 +452,72 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       }
     }
   }
+}
+
+// Coulomb on the FP32 streaming kernels: FP32 copy of the stage's amplitudes,
+// then both passes; column count as a template argument (2T in {2, ..., 12}).
+template <typename TF, int C>
+void coul_stream_launch_c(rttda_ctx* h, const double* X, cudaStream_t s) {
+  const long long nx = h->ov * C;
+  stream::k_prep_xf<<<(unsigned)std::min<long long>(cdiv(nx, 256), 8 * kNumSM), 256, 0, s>>>(nx, C, X, h->Xf);
+  stream::k_coul_w_stream<TF, C><<<dim3((unsigned)cdiv(h->P, stream::kW1Rows), h->SW), stream::kThreads,
+                                   (size_t)h->wslice * C * sizeof(float), s>>>((const TF*)h->Bov, h->Xf, h->P, h->ov,
+                                                                               h->wslice, (float*)h->w);
+  constexpr int V = 16 / sizeof(TF);
+  stream::k_coul_J_stream<TF, C><<<dim3((unsigned)cdiv(h->ov, 256 * V), h->SJ), stream::kThreads,
+                                   (size_t)h->pchunkJ * C * sizeof(float), s>>>(
+      (const TF*)h->Bov, (const float*)h->w, h->SW, h->P, h->ov, h->pchunkJ, (float*)h->Jpart);
+}
+
+template <typename TF>
+void coul_stream_launch(rttda_ctx* h, int C, const double* X, cudaStream_t s) {
+  switch (C) {
+    case 2: coul_stream_launch_c<TF, 2>(h, X, s); break;
+    case 4: coul_stream_launch_c<TF, 4>(h, X, s); break;
+    case 6: coul_stream_launch_c<TF, 6>(h, X, s); break;
+    case 8: coul_stream_launch_c<TF, 8>(h, X, s); break;
+    case 10: coul_stream_launch_c<TF, 10>(h, X, s); break;
+    default: coul_stream_launch_c<TF, 12>(h, X, s); break;
+  }
+}
+
+template <typename TF, int C>
+void coul_stream_attr_c() {
+  cudaFuncSetAttribute(stream::k_coul_w_stream<TF, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       stream::kW1SmemBytes);
+  cudaFuncSetAttribute(stream::k_coul_J_stream<TF, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+}
+
+// CTAs per SM of the two passes for C columns (register and shared-memory
+// limits as compiled).
+template <typename TF, int C>
+void coul_stream_occ_c(size_t smem_w, size_t smem_j, int* ow, int* oj) {
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(ow, stream::k_coul_w_stream<TF, C>, stream::kThreads, smem_w);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(oj, stream::k_coul_J_stream<TF, C>, stream::kThreads, smem_j);
+}
+
+template <typename TF>
+void coul_stream_occ(int C, size_t smem_w, size_t smem_j, int* ow, int* oj) {
+  switch (C) {
+    case 2: coul_stream_occ_c<TF, 2>(smem_w, smem_j, ow, oj); break;
+    case 4: coul_stream_occ_c<TF, 4>(smem_w, smem_j, ow, oj); break;
+    case 6: coul_stream_occ_c<TF, 6>(smem_w, smem_j, ow, oj); break;
+    case 8: coul_stream_occ_c<TF, 8>(smem_w, smem_j, ow, oj); break;
+    case 10: coul_stream_occ_c<TF, 10>(smem_w, smem_j, ow, oj); break;
+    default: coul_stream_occ_c<TF, 12>(smem_w, smem_j, ow, oj); break;
+  }
+  *ow = std::max(1, *ow);
+  *oj = std::max(1, *oj);
+}
+
+template <typename TF>
+void coul_stream_attr() {
+  coul_stream_attr_c<TF, 2>();
+  coul_stream_attr_c<TF, 4>();
+  coul_stream_attr_c<TF, 6>();
+  coul_stream_attr_c<TF, 8>();
+  coul_stream_attr_c<TF, 10>();
+  coul_stream_attr_c<TF, 12>();
 }
 
 template <typename TF, typename TC, bool XTC>
@@ -425,6 +532,13 @@ struct Ops {
     Prof pr(h, RTTDA_KC_COULOMB, s);
     h->launches += 2;
     const int C = 2 * h->T;
+    if constexpr (!std::is_same<TF, double>::value) {
+      if (h->coul_stream) {
+        h->launches += 1;  // the FP32 amplitude copy
+        coul_stream_launch<TF>(h, C, X, s);
+        return;
+      }
+    }
     if (h->coul_vec) {
       // 16-byte vector loads of B_ov rows (ov a multiple of the vector width)
       constexpr int V = Vec16<TF>::V;
@@ -508,6 +622,7 @@ struct Ops {
     cudaFuncSetAttribute(k_coul_J<TF, TC, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_coul_J_vec<TF, TC, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_coul_w_vec<TF, TC, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if constexpr (!std::is_same<TF, double>::value) coul_stream_attr<TF>();
     if (XTC) set_tc_smem_limits();
   }
 };
@@ -726,6 +841,209 @@ static rttda_status alloc_coul_tc(rttda_ctx* h, int C) {
   return RTTDA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the main exchange contraction (wide-M kernel).  Candidates:
+// (BN, MB) in {(160, 3), (192, 2)} x K tile {32, 64}, each with the split-K
+// count of choose_splits.  Each candidate runs the contraction over the
+// first Z chunk (filled with hashed values, so that the tensor cores see
+// data-like operands and power) once to warm up and then five times,
+// interleaved with the others, timed with CUDA events on the handle's
+// stream; the candidate with the fastest launch wins.  Results are cached per shape for the process
+// and, when RTTDA_TUNE_CACHE names a file, in that file (one JSON object per
+// line).  RTTDA_TUNE=0 skips the timing and takes the first candidate with
+// the least padded work and K tile 32; RTTDA_WIDE_PLAN="BN,MB,KB" names the
+// candidate to use (for tests and experiments).
+// ---------------------------------------------------------------------------
+struct WidePlan {
+  int bn = 160, mb = 3, kb = 32, sk = 1;
+};
+
+static std::mutex g_tune_mu;
+static std::map<std::string, WidePlan> g_tune_cache;
+static bool g_tune_file_loaded = false;
+
+static std::string tune_key(int o, int v, int vp, int pc, int C, int nprod, int zplanes) {
+  std::ostringstream k;
+  k << "wide:o=" << o << ",v=" << v << ",vp=" << vp << ",pc=" << pc << ",C=" << C << ",nprod=" << nprod
+    << ",zplanes=" << zplanes;
+  return k.str();
+}
+
+// {"key": "...", "bn": B, "mb": M, "kb": K, "sk": S}
+static void tune_file_load() {
+  const char* f = std::getenv("RTTDA_TUNE_CACHE");
+  if (g_tune_file_loaded || !f || !*f) return;
+  g_tune_file_loaded = true;
+  std::ifstream in(f);
+  std::string line;
+  while (std::getline(in, line)) {
+    const size_t k0 = line.find("\"key\": \"");
+    if (k0 == std::string::npos) continue;
+    const size_t ks = k0 + 8, ke = line.find('"', ks);
+    if (ke == std::string::npos) continue;
+    WidePlan w;
+    auto num = [&](const char* name, int& dst) {
+      const size_t q = line.find(std::string("\"") + name + "\": ");
+      if (q != std::string::npos) dst = std::atoi(line.c_str() + q + std::strlen(name) + 4);
+    };
+    num("bn", w.bn);
+    num("mb", w.mb);
+    num("kb", w.kb);
+    num("sk", w.sk);
+    const bool valid = ((w.bn == 160 && w.mb == 3) || (w.bn == 192 && w.mb == 2)) && (w.kb == 32 || w.kb == 64) &&
+                       w.sk >= 1 && w.sk <= 64;
+    if (valid) g_tune_cache[line.substr(ks, ke - ks)] = w;
+  }
+}
+
+static void tune_file_append(const std::string& key, const WidePlan& w) {
+  const char* f = std::getenv("RTTDA_TUNE_CACHE");
+  if (!f || !*f) return;
+  std::ofstream out(f, std::ios::app);
+  out << "{\"key\": \"" << key << "\", \"bn\": " << w.bn << ", \"mb\": " << w.mb << ", \"kb\": " << w.kb
+      << ", \"sk\": " << w.sk << "}\n";
+}
+
+static rttda_status wide_maps(rttda_ctx* h, int C, int pc, int p0, int bn, int kb, CUtensorMap* ma, CUtensorMap* mb) {
+  const int o = h->o, vp = h->vp, P = h->P;
+  const CUtensorMapSwizzle sw = kb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+  {
+    const uint64_t dims[4] = {64, (uint64_t)C * o, (uint64_t)pc * (vp / 64), (uint64_t)h->zplanes};
+    const uint64_t str[3] = {128, (uint64_t)C * o * 128, (uint64_t)h->zplane * 2};
+    const uint32_t box[4] = {(uint32_t)kb, 128, 1, 1};
+    CKS(bf16_map(ma, h->Zk, 4, dims, str, box, sw));
+  }
+  {
+    const uint64_t dims[4] = {(uint64_t)vp, (uint64_t)vp, (uint64_t)pc, (uint64_t)h->nplanes};
+    const uint64_t str[3] = {(uint64_t)vp * 2, (uint64_t)vp * vp * 2, (uint64_t)P * vp * vp * 2};
+    const uint32_t box[4] = {(uint32_t)kb, (uint32_t)bn, 1, 1};
+    CKS(bf16_map(mb, h->Bvv_tc + (size_t)p0 * vp * vp, 4, dims, str, box, sw));
+  }
+  return RTTDA_OK;
+}
+
+static rttda_status tune_wide(rttda_ctx* h, int C, WidePlan& out) {
+  const int o = h->o, v = h->v, vp = h->vp;
+  const long long M = (long long)C * o;
+  const int pc = std::min(h->zchunk, h->P);
+  struct Cand {
+    WidePlan w;
+    float ms = 0.0f;
+  };
+  std::vector<Cand> cands;
+  const int shapes[2][2] = {{160, 3}, {192, 2}};
+  long long bestw = -1;
+  int first = 0;
+  for (int si = 0; si < 2; ++si) {
+    const long long tm = (long long)tc::kBM * shapes[si][1];
+    const long long work = cdiv(M, tm) * tm * cdiv(v, shapes[si][0]) * shapes[si][0];
+    if (bestw < 0 || work < bestw) {
+      bestw = work;
+      first = si;
+    }
+  }
+  for (int si = 0; si < 2; ++si)
+    for (int kb : {32, 64}) {
+      Cand c;
+      c.w.bn = shapes[si][0];
+      c.w.mb = shapes[si][1];
+      c.w.kb = kb;
+      const long long tiles = cdiv(M, (long long)tc::kBM * c.w.mb) * cdiv(v, c.w.bn);
+      c.w.sk = choose_splits(tiles, (long long)h->zchunk * (vp / kb));
+      cands.push_back(c);
+    }
+  const char* force = std::getenv("RTTDA_WIDE_PLAN");
+  if (force && *force) {
+    int fb = 0, fm = 0, fk = 0;
+    if (std::sscanf(force, "%d,%d,%d", &fb, &fm, &fk) == 3)
+      for (const Cand& c : cands)
+        if (c.w.bn == fb && c.w.mb == fm && c.w.kb == fk) {
+          out = c.w;
+          h->plan.tuned = 3;
+          return RTTDA_OK;
+        }
+    return set_error(RTTDA_E_ARG, std::string("RTTDA_WIDE_PLAN names no candidate: ") + force);
+  }
+  // default: least padded work, K tile 32 (index 2*first)
+  const char* env = std::getenv("RTTDA_TUNE");
+  const bool timed = !(env && env[0] == '0');
+  const std::string key = tune_key(o, v, vp, pc, C, h->nprod_main, h->zplanes);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_file_load();
+    auto it = g_tune_cache.find(key);
+    if (timed && it != g_tune_cache.end()) {
+      out = it->second;
+      h->plan.tuned = 2;
+      return RTTDA_OK;
+    }
+  }
+  out = cands[2 * first].w;
+  h->plan.ncand = (int)cands.size();
+  if (!timed) return RTTDA_OK;
+
+  int maxsk = 1;
+  for (auto& c : cands) maxsk = std::max(maxsk, c.w.sk);
+  float* part = nullptr;
+  CK(cudaMalloc((void**)&part, (size_t)maxsk * M * v * sizeof(float)));
+  struct Free {
+    float* p;
+    ~Free() { cudaFree(p); }
+  } fr{part};
+  k_fill_hash_bf16<<<4 * kNumSM, 256, 0, h->stream>>>((long long)(h->zplane * h->zplanes), 0.05f, h->Zk);
+  std::vector<CUtensorMap> ma(cands.size()), mb(cands.size());
+  for (size_t i = 0; i < cands.size(); ++i)
+    CKS(wide_maps(h, C, pc, 0, cands[i].w.bn, cands[i].w.kb, &ma[i], &mb[i]));
+  auto launch = [&](size_t i) {
+    const WidePlan& w = cands[i].w;
+    tc::Params prm{};
+    prm.M = (int)M;
+    prm.N = v;
+    prm.kt_total = pc * (vp / w.kb);
+    prm.kt_per_split = (int)cdiv(prm.kt_total, w.sk);
+    prm.nsplit = w.sk;
+    prm.nprod = h->nprod_main;
+    prm.vtiles = vp / w.kb;
+    prm.out = part;
+    prm.ldo = v;
+    prm.split_stride = M * v;
+    prm.accum = 0;
+    prm.err = h->d_err;
+    wide_dispatch(w.bn, w.mb, h->nprod_main, w.kb, ma[i], mb[i], prm, h->stream);
+  };
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (size_t i = 0; i < cands.size(); ++i) launch(i);
+  for (auto& c : cands) c.ms = 1e30f;
+  for (int r = 0; r < 5; ++r)
+    for (size_t i = 0; i < cands.size(); ++i) {
+      cudaEventRecord(e0, h->stream);
+      launch(i);
+      cudaEventRecord(e1, h->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cands[i].ms = std::min(cands[i].ms, ms);
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  int herr = 0;
+  CK(cudaMemcpy(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) return set_error(RTTDA_E_TIMEOUT, "exchange autotuner: a device wait ran out (code " + std::to_string(herr) + ")");
+  size_t bi = 0;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    if (i < 8) h->plan.tune_ms[i] = cands[i].ms;
+    if (cands[i].ms < cands[bi].ms) bi = i;
+  }
+  out = cands[bi].w;
+  h->plan.tuned = 1;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  if (g_tune_cache.emplace(key, out).second) tune_file_append(key, out);
+  return RTTDA_OK;
+}
+
 // Buffers, split-K plan and TMA maps of the tensor-core exchange for C columns.
 static rttda_status alloc_tc(rttda_ctx* h, int C) {
   const int o = h->o, v = h->v, P = h->P, vp = h->vp, op = h->op;
@@ -737,27 +1055,21 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   h->zplane = (size_t)C * o * h->zchunk * vp;
   CKS(dalloc(&h->Zk, h->zplane * h->zplanes));
   // main contraction tiles.  BF16 and BF16X2 (Z is one plane): wide-M tiles
-  // (MB 128-row accumulators per CTA) chosen for the least padded work;
-  // BF16X3: 128-row tiles with the N width that wastes least.
+  // (MB 128-row accumulators per CTA), plan chosen by timing the candidates
+  // (tune_wide); BF16X3: 128-row tiles with the N width that wastes least.
   const long long M = (long long)C * o;
-  const long long kt_full = (long long)h->zchunk * (vp / tc::kBK);
-  int best = 256;
-  long long tiles = 0;
+  int kb = tc::kBK;  // main K tile width
   h->wide_mb = 0;
+  h->plan = rttda_plan_info{};
   if (h->nprod_main <= 2) {
-    long long bestw = -1;
-    const int cand[2][2] = {{160, 3}, {192, 2}};
-    for (const auto& cb : cand) {
-      const long long tm = (long long)tc::kBM * cb[1];
-      const long long work = cdiv(M, tm) * tm * cdiv(v, cb[0]) * cb[0];
-      if (bestw < 0 || work < bestw) {
-        bestw = work;
-        best = cb[0];
-        h->wide_mb = cb[1];
-      }
-    }
-    tiles = cdiv(M, (long long)tc::kBM * h->wide_mb) * cdiv(v, best);
+    WidePlan wp;
+    CKS(tune_wide(h, C, wp));
+    h->tc_bn = wp.bn;
+    h->wide_mb = wp.mb;
+    h->wide_kb = kb = wp.kb;
+    h->SK = wp.sk;
   } else {
+    int best = 256;
     long long bestw = -1;
     for (int bn : {128, 224, 256}) {
       const long long wasted = cdiv(v, bn) * bn;
@@ -766,10 +1078,16 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
         bestw = wasted;
       }
     }
-    tiles = cdiv(M, tc::kBM) * cdiv(v, best);
+    h->tc_bn = best;
+    h->SK = choose_splits(cdiv(M, tc::kBM) * cdiv(v, best), (long long)h->zchunk * (vp / kb));
   }
-  h->tc_bn = best;
-  h->SK = choose_splits(tiles, kt_full);
+  const int best = h->tc_bn;
+  h->plan.main_kernel = h->wide_mb ? 2 : 1;
+  h->plan.main_bn = best;
+  h->plan.main_mb = h->wide_mb ? h->wide_mb : 1;
+  h->plan.main_kb = kb;
+  h->plan.main_splits = h->SK;
+  h->plan.z_chunk = h->zchunk;
   char* p = nullptr;
   CK(cudaMalloc((void**)&p, (size_t)h->SK * C * o * v * sizeof(float)));
   h->Kpart = p;
@@ -790,26 +1108,20 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
       CKS(bf16_map(&za, h->Boo_tc + (size_t)p0 * o * op, 3, dims, str, box));
     }
     {
-      // Z as [plane][(P, b/64)][(col, i)][64]: one box per (K tile, 128 rows)
+      // Z as [plane][(P, b/64)][(col, i)][64]; the Z build stores 32-row x
+      // 64-column boxes from 128-byte swizzled staging
       const uint64_t dims[4] = {64, (uint64_t)C * o, (uint64_t)pc * (vp / 64), (uint64_t)h->zplanes};
       const uint64_t str[3] = {128, (uint64_t)C * o * 128, (uint64_t)h->zplane * 2};
-      const uint32_t box[4] = {64, 128, 1, 1};
-      CKS(bf16_map(&ma, h->Zk, 4, dims, str, box));
-      // the Z build's TMA stores: 32 x 32 boxes, dense (no swizzle)
-      const uint32_t sbox[4] = {32, 32, 1, 1};
-      CKS(bf16_map(&zs, h->Zk, 4, dims, str, sbox, CU_TENSOR_MAP_SWIZZLE_NONE));
+      const uint32_t sbox[4] = {64, 32, 1, 1};
+      CKS(bf16_map(&zs, h->Zk, 4, dims, str, sbox, CU_TENSOR_MAP_SWIZZLE_128B));
     }
-    {
-      const uint64_t dims[4] = {(uint64_t)vp, (uint64_t)vp, (uint64_t)pc, (uint64_t)h->nplanes};
-      const uint64_t str[3] = {(uint64_t)vp * 2, (uint64_t)vp * vp * 2, (uint64_t)P * vp * vp * 2};
-      const uint32_t box[4] = {64, (uint32_t)best, 1, 1};
-      CKS(bf16_map(&mb, h->Bvv_tc + (size_t)p0 * vp * vp, 4, dims, str, box));
-    }
+    // main contraction operands: Z tiles and B^P_vv tiles of K-tile width kb
+    CKS(wide_maps(h, C, pc, p0, best, kb, &ma, &mb));
     h->tmZA.push_back(za);
     h->tmMA.push_back(ma);
     h->tmZS.push_back(zs);
     h->tmMB.push_back(mb);
-    const long long kt = (long long)pc * (vp / tc::kBK);
+    const long long kt = (long long)pc * (vp / kb);
     h->tc_kper.push_back((int)cdiv(kt, h->SK));
   }
   return RTTDA_OK;
@@ -836,8 +1148,48 @@ rttda_status rttda_ctx::alloc_batch() {
   } else {
     const int V = (int)(16 / fbytes);
     coul_vec = (ov % V) == 0 && C <= 12;
+    coul_stream = coul_vec && prec != RTTDA_FP64;
     const size_t max_smem = 96 * 1024;
-    if (coul_vec) {
+    if (coul_stream) {
+      // pass 1 over (32-row blocks) x SW slices (a slice's FP32 amplitudes
+      // fit the 48 KB of shared memory), pass 2 over (256 V-wide ia blocks) x
+      // SJ chunks of P; each count chosen for whole waves of the CTAs that
+      // fit on the SMs (ties to fewer partials)
+      const long long smax = std::max<long long>(V, (stream::kW1SmemBytes / (C * 4)) / V * V);
+      int occ_w = 1, occ_j = 1;
+      if (prec == RTTDA_BF16)
+        coul_stream_occ<__nv_bfloat16>(C, (size_t)smax * C * 4, (size_t)cdiv(P, 8) * C * 4, &occ_w, &occ_j);
+      else
+        coul_stream_occ<float>(C, (size_t)smax * C * 4, (size_t)cdiv(P, 8) * C * 4, &occ_w, &occ_j);
+      auto waves = [](long long blocks, int occ) {
+        const double x = (double)blocks / ((double)kNumSM * occ);
+        return x / std::ceil(x);
+      };
+      const long long nrb = cdiv(P, stream::kW1Rows);
+      double best = -1.0;
+      for (int sw = (int)cdiv(ov, smax); sw <= std::max<long long>(64, cdiv(ov, smax)); ++sw) {
+        const long long sl = cdiv(cdiv(ov, sw), V) * V;
+        if (cdiv(ov, sl) != sw || sl > smax) continue;
+        const double sc = waves(nrb * sw, occ_w) - 0.002 * sw;
+        if (sc > best) {
+          best = sc;
+          SW = sw;
+          wslice = (int)sl;
+        }
+      }
+      const long long nib = cdiv(ov, 256LL * V);
+      best = -1.0;
+      for (int sj = 1; sj <= 64; ++sj) {
+        const long long pc = cdiv(P, sj);
+        if (cdiv(P, pc) != sj || (sj > 1 && pc < 8) || pc * C * 4 > 48 * 1024) continue;
+        const double sc = waves(nib * sj, occ_j) - 0.002 * sj;
+        if (sc > best) {
+          best = sc;
+          SJ = sj;
+          pchunkJ = (int)pc;
+        }
+      }
+    } else if (coul_vec) {
       // pass 1: amplitude slices of wslice rows staged in shared memory
       wslice = (int)std::min<long long>(ov, std::max<long long>(V * 32, (long long)(max_smem / (C * cbytes)) / (V * 32) * (V * 32)));
       wslice = (int)std::min<long long>(wslice, std::max<long long>(V * 32, cdiv(cdiv(ov, cdiv(4 * kNumSM, cdiv(P, 32))), V * 32) * V * 32));
@@ -850,9 +1202,12 @@ rttda_status rttda_ctx::alloc_batch() {
       const long long xblocks = cdiv(ov, 256);
       SJ = (int)std::max(1LL, std::min<long long>(P, cdiv(4 * kNumSM, xblocks)));
     }
-    pchunkJ = (int)cdiv(P, SJ);
-    while ((size_t)pchunkJ * C * cbytes > max_smem && pchunkJ > 1) pchunkJ = (pchunkJ + 1) / 2;
-    SJ = (int)cdiv(P, pchunkJ);
+    if (!coul_stream) {
+      pchunkJ = (int)cdiv(P, SJ);
+      while ((size_t)pchunkJ * C * cbytes > max_smem && pchunkJ > 1) pchunkJ = (pchunkJ + 1) / 2;
+      SJ = (int)cdiv(P, pchunkJ);
+    }
+    if (coul_stream) CKS(dalloc(&Xf, (size_t)ov * C));
     char* p = nullptr;
     CK(cudaMalloc((void**)&p, (size_t)SW * P * C * cbytes));
     w = p;
@@ -1070,6 +1425,8 @@ rttda_status rttda_set_field(rttda_t h, const rttda_pulse* pulses, int ntraj) {
   g_last_error.clear();
   if (!h || !pulses) return set_error(RTTDA_E_ARG, "rttda_set_field: NULL argument");
   if (ntraj < 1) return set_error(RTTDA_E_ARG, "rttda_set_field: ntraj must be >= 1");
+  if ((long long)h->N * 2 * ntraj >= (1LL << 31))
+    return set_error(RTTDA_E_ARG, "rttda_set_field: (1 + nocc*nvirt) * 2 * ntraj must be below 2^31");
   std::vector<PulseDev> pd(ntraj);
   std::vector<double> kappa(ntraj, 0.0), dirs(3 * ntraj);
   bool any_field = false, any_kick = false;
@@ -1438,6 +1795,25 @@ rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step
   if (!h) return set_error(RTTDA_E_ARG, "rttda_launch_stats: NULL handle");
   if (total) *total = h->launches;
   if (per_step) *per_step = h->launches_per_step;
+  return RTTDA_OK;
+}
+
+rttda_status rttda_plan(rttda_t h, rttda_plan_info* out) {
+  g_last_error.clear();
+  if (!h || !out) return set_error(RTTDA_E_ARG, "rttda_plan: NULL argument");
+  if (h->T == 0) return set_error(RTTDA_E_STATE, "rttda_plan: no batch (call rttda_set_field first)");
+  rttda_plan_info p = h->tc ? h->plan : rttda_plan_info{};
+  if (!h->tc) {
+    p.main_bn = h->prec == RTTDA_FP64 ? Tile<double>::BN : Tile<float>::BN;
+    p.main_mb = 1;
+    p.main_kb = h->prec == RTTDA_FP64 ? Tile<double>::BK : Tile<float>::BK;
+    p.main_splits = h->SK;
+    p.z_chunk = h->zchunk;
+  }
+  p.prec = (int)h->prec;
+  p.ntraj = h->T;
+  p.coulomb_kernel = h->coul_tc ? 1 : 0;
+  *out = p;
   return RTTDA_OK;
 }
 

@@ -561,6 +561,25 @@ __global__ void k_step_inc(long long* step) { *step += 1; }
 // mode 1: write sigma to sig_out (same layout as X).
 // Kpart is the exchange partial sum laid out [s][(col*o + i)][a].
 // ---------------------------------------------------------------------------
+// sum_{p < np} x[p * stride] in the partials' own type, fixed order:
+// partial p is added to accumulator p % 4, the accumulators are added last
+// as (a0 + a1) + (a2 + a3).  FP32 partials are summed in FP32 (the FP64 pipe
+// of this GPU is a small fraction of its FP32 rate).
+template <typename TC>
+__device__ __forceinline__ double sum_partials(const TC* __restrict__ x, size_t stride, int np) {
+  TC a[4] = {TC(0), TC(0), TC(0), TC(0)};
+  int p = 0;
+  for (; p + 8 <= np; p += 8) {
+    TC r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) r[u] = x[(size_t)(p + u) * stride];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u & 3] += r[u];
+  }
+  for (; p < np; ++p) a[p & 3] += x[(size_t)p * stride];
+  return (double)((a[0] + a[1]) + (a[2] + a[3]));
+}
+
 template <typename TC>
 __global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long N, int o, int v, int T,
                                                  const double* __restrict__ eps_o,
@@ -575,33 +594,25 @@ __global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long 
   // stage's input and is only read; the next stage's input goes to Xs_next.  sigma_q is the
   // real (q = 0) or imaginary (q = 1) part; k = -i sigma swaps them, so the
   // thread updates the other part of k: k_re = sigma_im, k_im = -sigma_re.
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * 2 * T) return;
-  const long long n = e % N;
-  const int tq = (int)(e / N), t = tq >> 1, q = tq & 1;
+  // N * 2T < 2^31 (checked by the host): 32-bit index arithmetic
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n32 = (int)N;
+  if (e >= n32 * 2 * T) return;
+  const int n = e % n32;
+  const int tq = e / n32, t = tq >> 1, q = tq & 1;
   const int C = 2 * T, col = 2 * t + q;
   const long long ov = N - 1;
   const size_t idx = (size_t)n * C + col;
   double sg = 0.0;
   if (n > 0) {
-    const int i = (int)((n - 1) / v), a = (int)((n - 1) % v);
-    double j0 = 0.0, j1 = 0.0, k0 = 0.0, k1 = 0.0;
+    const int i = (n - 1) / v, a = (n - 1) - i * v;
+    // split-K partial sums in a fixed order: eight loads in flight, four
+    // accumulators (partial p goes to accumulator p % 4)
     const TC* jp = Jpart + (size_t)(n - 1) * C + col;
-    const size_t js = (size_t)ov * C;
-    int p = 0;
-    for (; p + 1 < SJ; p += 2) {
-      j0 += (double)jp[(size_t)p * js];
-      j1 += (double)jp[(size_t)(p + 1) * js];
-    }
-    if (p < SJ) j0 += (double)jp[(size_t)p * js];
+    const double jsum = sum_partials(jp, (size_t)ov * C, SJ);
     const TC* kp = Kpart + ((size_t)col * o + i) * v + a;
-    p = 0;
-    for (; p + 1 < SK; p += 2) {
-      k0 += (double)kp[(size_t)p * Kstride];
-      k1 += (double)kp[(size_t)(p + 1) * Kstride];
-    }
-    if (p < SK) k0 += (double)kp[(size_t)p * Kstride];
-    sg = (eps_v[a] - eps_o[i]) * Xs[idx] + (j0 + j1) - cx * (k0 + k1);
+    const double ksum = sum_partials(kp, (size_t)Kstride, SK);
+    sg = (eps_v[a] - eps_o[i]) * Xs[idx] + jsum - cx * ksum;
   }
   if (use_field) sg -= E[stage * T + t] * F[idx];
   if (mode == 1) {
@@ -739,6 +750,18 @@ template <>
 __global__ void k_cast<__nv_bfloat16>(long long n, const double* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) dst[e] = __double2bfloat16(src[e]);
+}
+
+// Timing filler for the autotuner: BF16 values in [-scale, scale) from an
+// integer hash of the index (operands that toggle like real data).
+__global__ void k_fill_hash_bf16(long long n, float scale, __nv_bfloat16* __restrict__ dst) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    uint32_t x = (uint32_t)e * 0x9E3779B1u ^ (uint32_t)(e >> 32);
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    dst[e] = __float2bfloat16(scale * ((float)(x & 0xFFFFu) * (1.0f / 32768.0f) - 1.0f));
+  }
 }
 
 // out[t][e] = sum_x d[t][x] src[x][e]  (mu_d = mu . d, Eq. e_field)

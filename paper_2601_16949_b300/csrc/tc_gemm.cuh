@@ -43,7 +43,8 @@ enum : int { BMODE_PLAIN = 0,  // B[plane][n][k], 3-D map (k, n, plane)
 
 // epilogue kinds
 enum : int { EPI_PARTIAL = 0,  // out[split][m][n] FP32
-             EPI_ZSPLIT = 1 }; // Z[plane][(col*o + i)][P*vp + b] BF16 hi/lo
+             EPI_ZSPLIT = 1,   // Z as BF16 hi/lo planes (see Params)
+             EPI_ZONE = 2 };   // Z as one BF16 plane
 
 struct Params {
   int M, N;              // logical output extents
@@ -52,13 +53,13 @@ struct Params {
   int nsplit;            // number of K splits
   int nprod;             // 1 (single BF16), 2 or 3 (hi/lo split)
   int alo;               // with nprod 2: products (hi,hi), (lo,hi) instead of (hi,hi), (hi,lo)
-  int vtiles;            // vp / 64 (BMODE_VV)
+  int vtiles;            // vp / (K tile width) (BMODE_VV)
   // EPI_PARTIAL
   float* out;
   long long ldo, split_stride;
   int accum;             // 1: out += tile (later P chunks), 0: out = tile
-  // EPI_ZSPLIT: Z stored as [plane][(P, b/64)][(col, i)][64] (the main
-  // contraction's TMA box order)
+  // EPI_ZSPLIT / EPI_ZONE: Z stored as [plane][(P, b/64)][(col, i)][64]
+  // (the main contraction's TMA box order)
   __nv_bfloat16* zhi;
   __nv_bfloat16* zlo;
   int o, vp;
@@ -171,6 +172,24 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Same with 64-byte swizzle (rows of 32 BF16 along K): 8-row groups 512
+// bytes apart, layout type 4.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;                       // SWIZZLE_64B
+  return d;
+}
+
+template <int KB>
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr) {
+  static_assert(KB == 64 || KB == 32, "K tile of 64 (128-byte rows) or 32 (64-byte rows) BF16");
+  return KB == 64 ? sdesc_sw128(saddr) : sdesc_sw64(saddr);
+}
+
 // Instruction descriptor, kind::f16: D F32, A/B BF16, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -234,15 +253,18 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// Z epilogue staging: per epilogue warp, hi and lo blocks of 32 rows x 64 B,
-// rows padded to 80 B so that both the row writes and the transposed reads
-// stay (nearly) free of bank conflicts.
+// Z epilogue staging, per epilogue warp.  TMA path: two buffers x ZPL
+// planes of one 32-row x 64-column BF16 group (128-byte rows in the
+// 128-byte swizzled layout that the store map reads, so the row writes are
+// free of bank conflicts).  Manual path: hi and lo blocks of 32 rows x 64 B,
+// rows padded to 80 B.
 constexpr int kStageRowWords = 20;
-constexpr int kZChunkBytes = 32 * 64;  // TMA path: one 32 x 32 BF16 block
-// per warp: manual path hi + lo with 80-byte rows (5 KB), or TMA path two
-// buffers x two planes of dense blocks (8 KB)
-constexpr int kZStageBytesPerWarp = 4 * kZChunkBytes;
-static_assert(2 * 32 * kStageRowWords * 4 <= kZStageBytesPerWarp, "manual staging must fit");
+constexpr int kZGroupBytes = 32 * 128;
+template <int EPI>
+constexpr int zstage_bytes_per_warp() {
+  return EPI == 1 ? 4 * kZGroupBytes : EPI == 2 ? 2 * kZGroupBytes : 0;
+}
+static_assert(2 * 32 * kStageRowWords * 4 <= 2 * kZGroupBytes, "manual staging must fit");
 
 // BF16 hi/lo of two floats: hi = rn(x), lo = rn(x - hi), each packed (x0 in
 // the low half).
@@ -265,7 +287,7 @@ struct Cfg {
 template <int BN, int STAGES, int EPI = 0>
 constexpr size_t smem_bytes() {
   return (size_t)STAGES * Cfg<BN>::kStageBytes + 1024 /*alignment slack*/ + 256 /*barriers*/ +
-         (EPI == 1 ? kEpiWarps * kZStageBytesPerWarp : 0);
+         (size_t)kEpiWarps * zstage_bytes_per_warp<EPI>();
 }
 
 // Tile t -> (split, m tile, n tile), n fastest so that consecutive tiles of a
@@ -291,9 +313,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmZ, const Params p) {
   using CF = Cfg<BN>;
+  constexpr int kStgWarp = zstage_bytes_per_warp<EPI>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * CF::kStageBytes);
+  // [stages][Z staging (1024-aligned)][barriers]
+  uint8_t* zstage = smem + STAGES * CF::kStageBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(zstage + kEpiWarps * kStgWarp);
   uint64_t* empty = full + STAGES;
   uint64_t* accf = empty + STAGES;  // [2] accumulator ready (MMA -> epilogue)
   uint64_t* acce = accf + 2;        // [2] accumulator drained (epilogue -> MMA)
@@ -433,23 +458,70 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       } else {
-        // rows m = (P, i); columns n = (col, b) with b inside one 32-aligned
-        // chunk.  Each warp converts its 32 x 32 block to BF16 hi/lo, stages
-        // it in shared memory and writes it back transposed: four threads per
-        // row, so every store instruction covers eight full 64-byte segments.
-        uint32_t* stg = reinterpret_cast<uint32_t*>(smem + STAGES * CF::kStageBytes + 256) +
-                        (size_t)(warp - 2) * (kZStageBytesPerWarp / 4);
-        uint32_t* stg_lo = stg + 32 * kStageRowWords;
-        const bool two = p.zlo != nullptr;
+        // rows m = (P, i); columns n = (col, b).  Each warp converts its 32
+        // rows of the tile to BF16 (hi, and lo with EPI_ZSPLIT), stages them
+        // in shared memory and writes them out in the Z tile order.
+        constexpr int ZPL = EPI == EPI_ZSPLIT ? 2 : 1;
+        uint8_t* wst = zstage + (size_t)(warp - 2) * kStgWarp;
+        const bool two = ZPL == 2 && p.zlo != nullptr;
         // (P, i) of this warp's first row; later rows step i and wrap into P
         const int mb = tc.m0 + q * 32;
         const int Pb = mb / p.o, ib = mb - Pb * p.o;
         const int vt = p.vp >> 6;
         if (p.ztma) {
-          // 32 rows of one P and one col per warp: stage the BF16 block densely
-          // (double-buffered) and store it with one TMA box per plane.
-          uint8_t* tb = reinterpret_cast<uint8_t*>(stg);  // [buf][plane][32][64 B]
-          for (int ci = half; ci < nchunks; ci += 2, ++zcount) {
+          // 32 rows of one P (nocc % 32 == 0) by 64 columns of one col (vp and
+          // the tile start are multiples of 64): one TMA box per plane.  The
+          // two warps of a lane quarter take alternate 64-column groups;
+          // staging is double-buffered per warp.
+          for (int gi = half; gi < BN / 64; gi += 2, ++zcount) {
+            const int c = gi * 64;
+            uint32_t r0[32], r1[32];
+            tmem_ld32_nowait(tbase + c, r0);
+            tmem_ld32_nowait(tbase + c + 32, r1);
+            tmem_wait_ld();
+            if (!has_k) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) r0[j] = r1[j] = 0u;
+            }
+            const int zb = zcount & 1;
+            if (zcount >= 2) {
+              if (lane == 0) bulk_wait_read1();
+              __syncwarp();
+            }
+            uint8_t* gh = wst + (zb * ZPL) * kZGroupBytes + lane * 128;
+            uint8_t* gl = gh + kZGroupBytes;
+            // 16-byte chunk j of row `lane` lives at chunk j ^ (lane & 7)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const uint32_t* r = j < 4 ? r0 : r1;
+              const int o8 = (j & 3) * 8;
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                if (two)
+                  split_pack(__uint_as_float(r[o8 + 2 * e]), __uint_as_float(r[o8 + 2 * e + 1]), hw[e], lw[e]);
+                else
+                  hw[e] = pack_bf16x2(__uint_as_float(r[o8 + 2 * e]), __uint_as_float(r[o8 + 2 * e + 1]));
+              }
+              const int sw = (j ^ (lane & 7)) * 16;
+              *reinterpret_cast<uint4*>(gh + sw) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              if (two) *reinterpret_cast<uint4*>(gl + sw) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            const int n = tc.n0 + c;
+            if (lane == 0 && n < p.N && mb < p.M && ok) {
+              const int col = n / p.vp, b = n - col * p.vp;
+              const int kt = Pb * vt + (b >> 6);
+              tma_store_4d(&tmZ, wst + (zb * ZPL) * kZGroupBytes, 0, col * p.o + ib, kt, 0);
+              if (two) tma_store_4d(&tmZ, wst + (zb * ZPL + 1) * kZGroupBytes, 0, col * p.o + ib, kt, 1);
+            }
+            if (lane == 0) bulk_commit();
+          }
+        } else {
+          uint32_t* stg = reinterpret_cast<uint32_t*>(wst);
+          uint32_t* stg_lo = stg + 32 * kStageRowWords;
+          for (int ci = half; ci < nchunks; ci += 2) {
             const int c = ci * 32;
             uint32_t r[32];
             tmem_ld32(tbase + c, r);
@@ -457,18 +529,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int j = 0; j < 32; ++j) r[j] = 0u;
             }
-            const int buf = zcount & 1;
-            if (zcount >= 2) {
-              if (lane == 0) bulk_wait_read1();
-              __syncwarp();
-            }
-            uint4* sh = reinterpret_cast<uint4*>(tb + (buf * 2) * kZChunkBytes + lane * 64);
+            uint4* sh = reinterpret_cast<uint4*>(stg + lane * kStageRowWords);
             if (two) {
               uint32_t hw[16], lw[16];
 #pragma unroll
               for (int j = 0; j < 16; ++j)
                 split_pack(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]), hw[j], lw[j]);
-              uint4* sl = reinterpret_cast<uint4*>(tb + (buf * 2 + 1) * kZChunkBytes + lane * 64);
+              uint4* sl = reinterpret_cast<uint4*>(stg_lo + lane * kStageRowWords);
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
                 sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
@@ -477,75 +544,35 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else {
               uint32_t hw[16];
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                hw[j] = pack_bf16x2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+              for (int j = 0; j < 16; ++j) hw[j] = pack_bf16x2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
 #pragma unroll
-              for (int j = 0; j < 4; ++j)
-                sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
+              for (int j = 0; j < 4; ++j) sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
             }
-            fence_proxy_async_smem();
             __syncwarp();
             const int n = tc.n0 + c;
-            if (lane == 0 && n < p.N && mb < p.M && ok) {
+            if (n < p.N && ok) {
               const int col = n / p.vp, b = n - col * p.vp;
-              const int kt = Pb * vt + (b >> 6);
-              tma_store_4d(&tmZ, tb + (buf * 2) * kZChunkBytes, b & 63, col * p.o + ib, kt, 0);
-              if (two) tma_store_4d(&tmZ, tb + (buf * 2 + 1) * kZChunkBytes, b & 63, col * p.o + ib, kt, 1);
-            }
-            if (lane == 0) bulk_commit();
-          }
-        } else
-        for (int ci = half; ci < nchunks; ci += 2) {
-          const int c = ci * 32;
-          uint32_t r[32];
-          tmem_ld32(tbase + c, r);
-          if (!has_k) {
+              const size_t cbase = (size_t)(b >> 6) * p.zrows + (size_t)col * p.o;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) r[j] = 0u;
-          }
-          uint4* sh = reinterpret_cast<uint4*>(stg + lane * kStageRowWords);
-          if (two) {
-            uint32_t hw[16], lw[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              split_pack(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]), hw[j], lw[j]);
-            uint4* sl = reinterpret_cast<uint4*>(stg_lo + lane * kStageRowWords);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
-              sl[j] = make_uint4(lw[4 * j], lw[4 * j + 1], lw[4 * j + 2], lw[4 * j + 3]);
-            }
-          } else {
-            uint32_t hw[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) hw[j] = pack_bf16x2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-#pragma unroll
-            for (int j = 0; j < 4; ++j) sh[j] = make_uint4(hw[4 * j], hw[4 * j + 1], hw[4 * j + 2], hw[4 * j + 3]);
-          }
-          __syncwarp();
-          const int n = tc.n0 + c;
-          if (n < p.N && ok) {
-            const int col = n / p.vp, b = n - col * p.vp;
-            const size_t cbase = (size_t)(b >> 6) * p.zrows + (size_t)col * p.o;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const int rr = (lane >> 2) + 8 * k, cc = lane & 3;
-              if (mb + rr < p.M) {
-                int ir = ib + rr, Pr = Pb;
-                while (ir >= p.o) {
-                  ir -= p.o;
-                  ++Pr;
+              for (int k = 0; k < 4; ++k) {
+                const int rr = (lane >> 2) + 8 * k, cc = lane & 3;
+                if (mb + rr < p.M) {
+                  int ir = ib + rr, Pr = Pb;
+                  while (ir >= p.o) {
+                    ir -= p.o;
+                    ++Pr;
+                  }
+                  const size_t off = ((size_t)Pr * vt * p.zrows + cbase + (size_t)ir) * 64 + (b & 63) + 8 * cc;
+                  *reinterpret_cast<uint4*>(p.zhi + off) =
+                      *reinterpret_cast<const uint4*>(stg + rr * kStageRowWords + 4 * cc);
+                  if (two)
+                    *reinterpret_cast<uint4*>(p.zlo + off) =
+                        *reinterpret_cast<const uint4*>(stg_lo + rr * kStageRowWords + 4 * cc);
                 }
-                const size_t off = ((size_t)Pr * vt * p.zrows + cbase + (size_t)ir) * 64 + (b & 63) + 8 * cc;
-                *reinterpret_cast<uint4*>(p.zhi + off) =
-                    *reinterpret_cast<const uint4*>(stg + rr * kStageRowWords + 4 * cc);
-                if (two)
-                  *reinterpret_cast<uint4*>(p.zlo + off) =
-                      *reinterpret_cast<const uint4*>(stg_lo + rr * kStageRowWords + 4 * cc);
               }
             }
+            __syncwarp();
           }
-          __syncwarp();
         }
       }
       // hand the accumulator buffer back to the MMA warp
@@ -555,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
     }
     // every TMA store of this warp must have completed before the CTA exits
-    if (EPI == EPI_ZSPLIT && lane == 0) bulk_wait_all();
+    if (EPI != EPI_PARTIAL && lane == 0) bulk_wait_all();
   }
   tc_fence_before();
   __syncthreads();
@@ -570,14 +597,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 // a CTA tile is MB x 128 rows by BN columns, i.e. MB TMEM accumulators that
 // share every B tile, and one pipeline stage holds the MB A tiles together
 // with all NBP planes of the B tile (B_hi, B_lo).  Per K tile the MMA warp
-// issues NBP x MB x 4 MMAs.  Fewer bytes move from L2 per multiply-add than
-// with 128-row tiles.  Persistent over (split, m tile, n tile); the
-// accumulators are drained by the epilogue before the next tile starts.
+// issues NBP x MB x KB/16 MMAs.  Fewer bytes move from L2 per multiply-add
+// than with 128-row tiles.  KB = 32 halves the stage (64-byte swizzled rows)
+// so that twice as many stages, and twice the bytes in flight, fit in
+// shared memory.  Persistent over (split, m tile, n tile); the accumulators
+// are drained by the epilogue before the next tile starts.
+//
+// K tiles are numbered in units of KB along (P, b): tile kr covers
+// b = (kr % (vp/KB)) * KB .. +KB of P = kr / (vp/KB).  Z is stored in
+// 64-wide b tiles, so a 32-wide K tile is the half (kr & 1) of Z tile kr/2.
 // ---------------------------------------------------------------------------
-template <int BN, int MB, int NBP>
+template <int BN, int MB, int NBP, int KB>
 struct WideCfg {
-  static constexpr int kABlock = kBM * 128;       // one 128-row A tile
-  static constexpr int kBBytes = BN * 128;        // one B plane
+  static constexpr int kRowBytes = KB * 2;
+  static constexpr int kABlock = kBM * kRowBytes;   // one 128-row A tile
+  static constexpr int kBBytes = BN * kRowBytes;    // one B plane
   static constexpr int kStageBytes = MB * kABlock + NBP * kBBytes;
   static constexpr int kCols = MB * BN;
   static constexpr uint32_t kTmemCols = kCols <= 32 ? 32 : kCols <= 64 ? 64 : kCols <= 128 ? 128
@@ -585,17 +619,18 @@ struct WideCfg {
   static_assert(kCols <= 512, "accumulators exceed TMEM");
   static_assert(kStageBytes % 1024 == 0, "stage must keep 1024-byte alignment");
   static_assert(BN % 32 == 0 && BN <= 256, "BN must be a multiple of 32 and <= 256");
+  static_assert(KB == 64 || KB == 32, "K tile of 64 or 32 BF16");
 };
 
-template <int BN, int MB, int NBP, int STAGES>
+template <int BN, int MB, int NBP, int STAGES, int KB>
 constexpr size_t wide_smem_bytes() {
-  return (size_t)STAGES * WideCfg<BN, MB, NBP>::kStageBytes + 1024 + 256;
+  return (size_t)STAGES * WideCfg<BN, MB, NBP, KB>::kStageBytes + 1024 + 256;
 }
 
-template <int BN, int MB, int NBP, int STAGES>
+template <int BN, int MB, int NBP, int STAGES, int KB>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_wide(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p) {
-  using CF = WideCfg<BN, MB, NBP>;
+  using CF = WideCfg<BN, MB, NBP, KB>;
   constexpr int TM = kBM * MB;  // rows per tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -649,9 +684,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           uint8_t* st = smem + s * CF::kStageBytes;
           mbar_expect_tx(&full[s], CF::kStageBytes);
+          const int zt = KB == 64 ? kr : kr >> 1, zx = KB == 64 ? 0 : (kr & 1) * KB;
 #pragma unroll
-          for (int b = 0; b < MB; ++b) tma_load_4d(st + b * CF::kABlock, &tmA, &full[s], 0, m0 + b * kBM, kr, 0);
-          const int P = kr / p.vtiles, b0 = (kr % p.vtiles) * kBK;
+          for (int b = 0; b < MB; ++b) tma_load_4d(st + b * CF::kABlock, &tmA, &full[s], zx, m0 + b * kBM, zt, 0);
+          const int P = kr / p.vtiles, b0 = (kr % p.vtiles) * KB;
 #pragma unroll
           for (int q = 0; q < NBP; ++q)
             tma_load_4d(st + MB * CF::kABlock + q * CF::kBBytes, &tmB, &full[s], b0, n0, P, q);
@@ -681,12 +717,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t base = smem_u32(smem + s * CF::kStageBytes);
 #pragma unroll
           for (int q = 0; q < NBP; ++q) {
-            const uint64_t bdesc = sdesc_sw128(base + MB * CF::kABlock + q * CF::kBBytes);
+            const uint64_t bdesc = sdesc_k<KB>(base + MB * CF::kABlock + q * CF::kBBytes);
 #pragma unroll
             for (int b = 0; b < MB; ++b) {
-              const uint64_t adesc = sdesc_sw128(base + b * CF::kABlock);
+              const uint64_t adesc = sdesc_k<KB>(base + b * CF::kABlock);
 #pragma unroll
-              for (int k = 0; k < kBK / 16; ++k)
+              for (int k = 0; k < KB / 16; ++k)
                 mma_bf16(tmem + b * BN, adesc + 2 * k, bdesc + 2 * k, idesc,
                          (kr > kr0 || q > 0 || k > 0) ? 1u : 0u);
             }

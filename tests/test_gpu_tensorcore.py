@@ -138,3 +138,65 @@ def test_batched_sigma_with_tensorcore_coulomb(rb, prec, tol2e, shape):
     err = np.max(np.abs(got - ref), axis=1)
     assert np.all(err <= tol2e * s2e + 2e-6 * sall), (err, s2e, sall)
     prop.close()
+
+
+WIDE_PLANS = ["160,3,32", "160,3,64", "192,2,32", "192,2,64"]
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x2", 1e-2), ("bf16", 3e-2)])
+def test_every_wide_plan_gives_the_same_exchange(rb, prec, tol, monkeypatch):
+    """Exchange only (no Coulomb factors, orbital energies or field): each
+    wide-M plan of the main contraction (tile width x row blocks x K tile)
+    computes the same sum up to FP32 summation order, and matches the FP64
+    exchange within the BF16 rounding of Z.  o=64 with 3 trajectories gives
+    3 row blocks; v=128 is ragged for both tile widths."""
+    mol = synth.molecule(64, 128, 40, seed=31)
+    mol["B_ov"][:] = 0.0
+    mol["eps_occ"][:] = 0.0
+    mol["eps_virt"][:] = 0.0
+    c = synth.random_state(1 + 64 * 128, 3, seed=6)
+    outs = []
+    for plan in WIDE_PLANS:
+        monkeypatch.setenv("RTTDA_WIDE_PLAN", plan)
+        prop = rb.Propagator(mol, 1.0, prec)
+        prop.set_field([dict(kind=0, E0=0.0)] * 3)
+        info = rb.rttda_plan(prop.h)
+        assert info["tuned"] == 3 and info["main_kernel"] == 2
+        assert (info["main_bn"], info["main_mb"], info["main_kb"]) == tuple(int(x) for x in plan.split(","))
+        outs.append(_sigma_gpu(rb, prop, c, 0.5))
+        prop.close()
+    A = orc.build_A(mol, 1.0)
+    ref = np.array([A @ ck for ck in c])
+    scale = np.max(np.abs(ref))
+    for plan, got in zip(WIDE_PLANS, outs):
+        assert np.max(np.abs(got - outs[0])) <= 2e-5 * scale, plan
+        assert np.max(np.abs(got - ref)) <= tol * scale, plan
+
+
+def test_wide_plan_tuner_times_every_candidate(rb, monkeypatch):
+    monkeypatch.delenv("RTTDA_WIDE_PLAN", raising=False)
+    monkeypatch.delenv("RTTDA_TUNE", raising=False)
+    mol = synth.molecule(48, 96, 24, seed=8)
+    prop = rb.Propagator(mol, 0.2, "bf16x2")
+    prop.set_field(PULSES)
+    info = rb.rttda_plan(prop.h)
+    assert info["main_kernel"] == 2 and info["tuned"] in (1, 2) and info["ntraj"] == 3
+    if info["tuned"] == 1:
+        assert info["ncand"] == 4 and all(t > 0 for t in info["tune_ms"])
+    # the tuned plan is cached for the shape: a second handle reuses it
+    p2 = rb.Propagator(mol, 0.2, "bf16x2")
+    p2.set_field(PULSES)
+    i2 = rb.rttda_plan(p2.h)
+    assert i2["tuned"] == 2
+    assert (i2["main_bn"], i2["main_mb"], i2["main_kb"], i2["main_splits"]) == \
+        (info["main_bn"], info["main_mb"], info["main_kb"], info["main_splits"])
+    c = synth.random_state(prop.n, 3, seed=2)
+    assert np.array_equal(_sigma_gpu(rb, prop, c, 0.7), _sigma_gpu(rb, p2, c, 0.7))
+    prop.close()
+    p2.close()
+    monkeypatch.setenv("RTTDA_WIDE_PLAN", "128,4,32")
+    p3 = rb.Propagator(mol, 0.2, "bf16x2")
+    with pytest.raises(rb.RTTDAError) as e:
+        p3.set_field(PULSES)
+    assert e.value.status == rb.E_ARG
+    p3.close()
