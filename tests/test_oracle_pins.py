@@ -274,6 +274,105 @@ def test_rk4_is_fourth_order_with_time_dependent_field():
 
 
 # ---------------------------------------------------------------------------
+# Symplectic split-operator integrator
+# ---------------------------------------------------------------------------
+
+def leapfrog_power(x, n):
+    """n steps of Stormer-Verlet on one harmonic mode q' = w p, p' = -w q
+    with x = w dt, as the 2x2 map (q, p) -> T^n (q, p).  Textbook facts used:
+    T has unit determinant and trace 2 - x^2, so its eigenvalues are
+    exp(+-i theta) with cos(theta) = 1 - x^2/2, and for such a matrix
+    T^n = sin(n theta)/sin(theta) T - sin((n-1) theta)/sin(theta) I
+    (Chebyshev recursion).  T itself is the product of the three shears
+    p -= (x/2) q, q += x p, p -= (x/2) q."""
+    x = np.asarray(x, dtype=np.float64)
+    kick = lambda a: np.array([[np.ones_like(a), np.zeros_like(a)], [-a / 2, np.ones_like(a)]])
+    drift = lambda a: np.array([[np.ones_like(a), a], [np.zeros_like(a), np.ones_like(a)]])
+    T = np.einsum("ij...,jk...,kl...->il...", kick(x), drift(x), kick(x))
+    th = np.arccos(1 - x ** 2 / 2)
+    I = np.array([[np.ones_like(x), np.zeros_like(x)], [np.zeros_like(x), np.ones_like(x)]])
+    small = np.abs(th) < 1e-12          # x = 0 (the ground row): sin(k th)/sin(th) -> k
+    st = np.where(small, 1.0, np.sin(th))
+    un = np.where(small, n, np.sin(n * th) / st)
+    un1 = np.where(small, n - 1, np.sin((n - 1) * th) / st)
+    return un * T - un1 * I
+
+
+@pytest.mark.parametrize("shape", [(2, 3, 4), (3, 5, 7)])
+def test_sso_field_free_equals_per_mode_leapfrog(shape):
+    """Field-free SSO in the eigenbasis of A is Stormer-Verlet on each mode."""
+    mol = synth.molecule(*shape, seed=1)
+    A = orc.build_A(mol, 0.2)
+    M = orc.build_M(*orc.dipole_along(mol, (0, 0, 1)))
+    lam, V = np.linalg.eigh(A)
+    c0 = synth.random_state(A.shape[0], 1, seed=2)[0]
+    dt, n = 0.05, 300
+    tr = orc.propagate_sso(A, M, orc.Pulse(kind=orc.CW, E0=0.0, omega=1.0), c0, dt, n)
+    bq, bp = V.T @ c0.real, V.T @ c0.imag
+    Tn = leapfrog_power(lam * dt, n)
+    q = Tn[0, 0] * bq + Tn[0, 1] * bp
+    p = Tn[1, 0] * bq + Tn[1, 1] * bp
+    ref = V @ q + 1j * (V @ p)
+    assert np.max(np.abs(tr.c - ref)) < 1e-12
+
+
+def test_sso_is_time_reversible():
+    mol = small_mol(3, 4, 5, seed=6)
+    A = orc.build_A(mol, 0.2)
+    M = orc.build_M(*orc.dipole_along(mol, (1, 0, 0)))
+    p0 = orc.Pulse(kind=orc.CW, E0=0.0, omega=1.0)
+    c0 = synth.random_state(A.shape[0], 1, seed=3)[0]
+    c = c0.copy()
+    for k in range(100):
+        c = orc.sso_step(A, M, p0, k * 0.05, 0.05, c)
+    for k in range(100):
+        c = orc.sso_step(A, M, p0, (100 - k) * 0.05, -0.05, c)
+    assert np.max(np.abs(c - c0)) < 1e-12
+
+
+def test_sso_mean_norm_error_is_second_order_as_in_paper():
+    """Sec. 3.4: start from a stationary state in the real part, run a fixed
+    50 au, and the norm error averaged over the run falls with slope 2 in
+    dt.  For one mode of frequency w the leapfrog norm is
+    1 - (w dt / 2)^2 sin^2(n theta), so the mean error is (w dt)^2 / 8 to
+    leading order."""
+    mol = small_mol(3, 4, 6, seed=9)
+    A = orc.build_A(mol, 0.2)
+    M = orc.build_M(*orc.dipole_along(mol, (0, 1, 0)))
+    lam, V = np.linalg.eigh(A)
+    k = int(np.argsort(lam)[1])          # first excited state (lam[0] is the ground row)
+    c0 = V[:, k].astype(np.complex128)
+    p0 = orc.Pulse(kind=orc.CW, E0=0.0, omega=1.0)
+    errs = []
+    dts = [0.2, 0.1, 0.05, 0.025]
+    for dt in dts:
+        tr = orc.propagate_sso(A, M, p0, c0, dt, int(round(50.0 / dt)))
+        errs.append(np.mean(np.abs(tr.norm - 1.0)))
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(dts) - 1)]
+    assert all(abs(s - 2.0) < 0.1 for s in slopes), slopes
+    w = lam[k]
+    assert abs(errs[-1] / ((w * dts[-1]) ** 2 / 8) - 1.0) < 0.05
+    # RK4 on the same problem loses norm monotonically instead
+    tr4 = orc.propagate(A, M, p0, c0, 0.2, 250)
+    assert np.all(np.diff(tr4.norm) <= 1e-15)
+
+
+def test_sso_is_second_order_with_time_dependent_field():
+    """The field enters each sub-step at the middle of the interval it
+    advances; a first-order placement would show slope 1 here."""
+    mol = small_mol(2, 3, 4, seed=4)
+    A = orc.build_A(mol, 0.2)
+    M = orc.build_M(*orc.dipole_along(mol, (1, 0, 0)))
+    p = orc.Pulse(kind=orc.GAUSS_TL, E0=0.05, omega=0.9, t0=4.0, fwhm=3.0)
+    T = 8.0
+    ref = orc.propagate(A, M, p, None, 0.2 / 64, int(round(T / (0.2 / 64)))).c
+    errs = [np.linalg.norm(orc.propagate_sso(A, M, p, None, dt, int(round(T / dt))).c - ref)
+            for dt in (0.1, 0.05, 0.025)]
+    slopes = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(abs(s - 2.0) < 0.1 for s in slopes), slopes
+
+
+# ---------------------------------------------------------------------------
 # Kick
 # ---------------------------------------------------------------------------
 
