@@ -392,7 +392,7 @@ def run_gpu(args):
         mol = synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
     pulses, wl_info = workload_pulses(rb, args.workload, mol)
     T, K, W = len(pulses), args.steps, args.warmup
-    prop = rb.Propagator(mol, CX, args.prec)
+    prop = rb.Propagator(mol, CX, args.prec, integrator=args.integrator)
     prop.set_field(pulses)
     h = prop.h
     dev = torch.device("cuda", local)
@@ -454,7 +454,7 @@ def run_gpu(args):
 
     # plain FP64 single-trajectory path on the same molecule (the batch's
     # last trajectory)
-    p64 = rb.Propagator(mol, CX, "fp64")
+    p64 = rb.Propagator(mol, CX, "fp64", integrator=args.integrator)
     p64.set_field([pulses[-1]])
     k64 = max(2, min(args.fp64_steps, K))
     d64 = torch.zeros((1, k64 + 1), dtype=torch.float64, device=dev)
@@ -497,7 +497,10 @@ def run_gpu(args):
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     ms_cls = {k: v[0] for k, v in prof.items()}
     dom = max(ms_cls, key=ms_cls.get)
-    roof = roofline(args.prec, dom, prof[dom], T, peaks, 4 * kp)
+    # sigma builds in the profiled call: 4 per RK4 step; 2 per split-operator
+    # step plus the call's first half step
+    nsig = 4 * kp if args.integrator == "rk4" else 2 * kp + 1
+    roof = roofline(args.prec, dom, prof[dom], T, peaks, nsig)
     tkey = (args.workload, args.prec, dom, plan["main_bn"], plan["main_mb"], plan["main_kb"])
     if tkey in PROFILED_TRAFFIC and plan["z_chunk"] >= NAUX:
         roof["traffic"] = PROFILED_TRAFFIC[tkey]
@@ -514,6 +517,8 @@ def run_gpu(args):
 
     dtype = {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "bf16x2": "bf16x2"}[args.prec]
     cfg = base_config(args.prec, world, T)
+    cfg["integrator"] = {"rk4": "classical RK4 (4 sigma builds per step)",
+                         "sso": "symplectic split operator (2 sigma builds per step)"}[args.integrator]
     cfg.update(wl_info)
     cfg.update({"fp64_path_traj_steps_per_s": fp64_rate, "speedup_vs_fp64_path": value / world / fp64_rate,
                 "fp64_path": f"plain FP64, one trajectory (the batch's last), {k64} timed steps",
@@ -635,6 +640,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="absorption", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="bf16x2", choices=["fp64", "fp32", "bf16", "bf16x3", "bf16x2"])
+    ap.add_argument("--integrator", default="rk4", choices=["rk4", "sso"],
+                    help="time integrator of the timed propagation (the plain FP64 comparison path uses the same)")
     ap.add_argument("--accuracy", type=int, default=0,
                     help="instead of timing: propagate N steps with FP64 and the chosen precisions "
                          "(z kick) and print their dipole/norm errors against FP64")

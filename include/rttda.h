@@ -243,6 +243,23 @@ rttda_status rttda_profile_read(rttda_t h, double* ms, long long* launches);
  * the last propagation (*per_step).  Either pointer may be NULL. */
 rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step);
 
+/* Time integrator of later propagations (the state and time are kept).
+ *   RTTDA_INT_RK4  classical 4-stage Runge-Kutta on dc/dt = -i H(t) c,
+ *                  stages at t, t+dt/2, t+dt/2, t+dt (default; 4 sigma
+ *                  builds per step);
+ *   RTTDA_INT_SSO  second-order symplectic split operator on
+ *                  dq/dt = H p, dp/dt = -H q with c = q + i p (Sec. 2.2,
+ *                  Eq. x_real_imagiary; convergence Sec. 3.4):
+ *                    p_{n+1/2} = p_n - dt/2 H(t_n) q_n,
+ *                    q_{n+1} = q_n + dt H(t_n + dt/2) p_{n+1/2},
+ *                    p_{n+1} = p_{n+1/2} - dt/2 H(t_n + dt) q_{n+1};
+ *                  two sigma builds per step plus one per propagation call.
+ * A kick is applied exactly before either integrator.  Stopping after n
+ * steps and resuming reproduces an uninterrupted run bit for bit with both.
+ * Errors: RTTDA_E_ARG (NULL handle, unknown integrator). */
+typedef enum { RTTDA_INT_RK4 = 0, RTTDA_INT_SSO = 1 } rttda_integrator;
+rttda_status rttda_set_integrator(rttda_t h, int integrator);
+
 /* Execution plan of the sigma build chosen for the current batch (after
  * rttda_set_field).  The exchange main contraction sum_{P,b} Z^P_ib B^P_ab
  * (Sec. 2.2, exchange part of the A matrix elements) runs on

@@ -96,6 +96,7 @@ lib.rttda_profile.argtypes = [_h, ct.c_int]
 lib.rttda_profile_read.argtypes = [_h, _dp, ct.POINTER(ct.c_longlong)]
 lib.rttda_launch_stats.argtypes = [_h, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]
 lib.rttda_plan.argtypes = [_h, ct.POINTER(rttda_plan_info)]
+lib.rttda_set_integrator.argtypes = [_h, ct.c_int]
 lib.rttda_coulomb_noalloc.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int,
                                       ct.c_void_p, ct.c_void_p]
 lib.rttda_coulomb_noalloc.restype = ct.c_int
@@ -118,7 +119,8 @@ lib.rttda_destroy.argtypes = [_h]
 lib.rttda_destroy.restype = None
 for _name in ("rttda_create", "rttda_memory_bytes", "rttda_set_field", "rttda_propagate", "rttda_propagate_device",
               "rttda_resume", "rttda_get_state", "rttda_set_state", "rttda_sigma", "rttda_spectrum",
-              "rttda_profile", "rttda_profile_read", "rttda_launch_stats", "rttda_sync", "rttda_plan"):
+              "rttda_profile", "rttda_profile_read", "rttda_launch_stats", "rttda_sync", "rttda_plan",
+              "rttda_set_integrator"):
     getattr(lib, _name).restype = ct.c_int
 
 
@@ -271,6 +273,15 @@ def rttda_launch_stats(h) -> tuple:
     return tot.value, per.value
 
 
+INTEGRATORS = {"rk4": 0, "sso": 1}
+
+
+def rttda_set_integrator(h, integrator) -> None:
+    """'rk4' (default) or 'sso' (symplectic split operator), or the enum value."""
+    code = INTEGRATORS[integrator] if isinstance(integrator, str) else int(integrator)
+    _check(lib.rttda_set_integrator(h, code), "rttda_set_integrator")
+
+
 def rttda_plan(h) -> dict:
     """The sigma build's execution plan for the current batch (see rttda.h)."""
     pi = rttda_plan_info()
@@ -370,7 +381,7 @@ class Propagator:
 
     KEYS = ("eps_occ", "eps_virt", "B_ov", "B_oo", "B_vv", "mu_oo", "mu_vv", "mu_0ov")
 
-    def __init__(self, mol: dict, c_x: float, prec="fp64"):
+    def __init__(self, mol: dict, c_x: float, prec="fp64", integrator="rk4"):
         self.nocc, self.nvirt, self.naux = mol["nocc"], mol["nvirt"], mol["naux"]
         self.n = 1 + self.nocc * self.nvirt
         first = mol["B_vv"]
@@ -381,6 +392,8 @@ class Propagator:
         else:
             self.h = rttda_create(self.nocc, self.nvirt, self.naux, *[mol[k] for k in self.KEYS], c_x, prec)
         self.ntraj = 0
+        if integrator != "rk4":
+            rttda_set_integrator(self.h, integrator)
 
     def set_field(self, pulses):
         rttda_set_field(self.h, pulses)

@@ -149,6 +149,7 @@ struct rttda_ctx {
   int zplanes = 1, nprod_main = 1;  // Z planes kept; products in the main contraction
   int wide_mb = 0;                   // >0: main contraction on the wide-M kernel with this many 128-row blocks
   int wide_kb = 32;                  // K tile width of the wide-M kernel (32 or 64 BF16)
+  int integrator = RTTDA_INT_RK4;    // rttda_integrator
   rttda_plan_info plan{};            // the exchange plan in use (rttda_plan)
   __nv_bfloat16* Bvv_tc = nullptr;  // [plane][P][vp][vp]
   __nv_bfloat16* Boo_tc = nullptr;  // [plane][P*o][op]
@@ -618,6 +619,16 @@ struct Ops {
         Xnext, h->acc, sig_out);
   }
 
+  // split-operator sub-step on the stage input X (in place); see k_sso_update
+  static void sso_update(rttda_ctx* h, int mode, int stage, bool use_field, double dt, double* X, cudaStream_t s) {
+    Prof pr(h, RTTDA_KC_COMBINE, s);
+    h->launches += 1;
+    const int C = 2 * h->T;
+    k_sso_update<TC><<<blocks_for(h->N * h->T, 256), 256, 0, s>>>(
+        mode, stage, h->N, h->o, h->v, h->T, h->eps_o, h->eps_v, h->cx, (const TC*)h->Jpart, h->SJ,
+        (const TC*)h->Kpart, h->SK, (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn, X);
+  }
+
   static void set_smem_limits() {
     cudaFuncSetAttribute(k_coul_J<TF, TC, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_coul_J_vec<TF, TC, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -681,6 +692,43 @@ void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, doub
   k_step_inc<<<1, 1, 0, s>>>(h->d_step);
 }
 
+// One symplectic split-operator step (Sec. 2.2): two sigma builds, each on one
+// component of the stage input Xs, which holds (q_n, p_{n+1/2}) at the start
+// of a step; Xn holds (q_n, p_n) for the observables and the state.
+//   sigma build at t_n + dt/2 (stage 1) -> drift  q_{n+1} = q_n + dt H p_{n+1/2}
+//   sigma build at t_n + dt   (stage 3) -> p_{n+1}, then p_{n+3/2}
+template <typename O>
+void enqueue_step_sso(rttda_ctx* h, O, long long base, double t_off, double dt, double* dip, double* nrm,
+                      long long ld, long long offset, cudaStream_t s) {
+  h->launches += 2;  // efield + step counter
+  k_efield<<<1, 128, 0, s>>>(h->T, h->d_pulses, h->d_step, base, t_off, dt, h->E);
+  const bool fld = h->any_field;
+  if (dip) {
+    O::field(h, h->Xn, s);
+    enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
+  }
+  for (int half = 0; half < 2; ++half) {
+    if (fld) O::field(h, h->Xs, s);
+    O::coulomb(h, h->Xs, s);
+    O::exchange(h, h->Xs, s);
+    O::sso_update(h, half == 0 ? 1 : 2, half == 0 ? 1 : 3, fld, dt, h->Xs, s);
+  }
+  k_step_inc<<<1, 1, 0, s>>>(h->d_step);
+}
+
+// First half step of the split operator at the start of a propagation:
+// Xs = (q_0, p_0) -> (q_0, p_0 - dt/2 H(t_0) q_0).
+template <typename O>
+void enqueue_sso_prologue(rttda_ctx* h, O, long long base, double t_off, double dt, cudaStream_t s) {
+  h->launches += 1;
+  k_efield<<<1, 128, 0, s>>>(h->T, h->d_pulses, h->d_step, base, t_off, dt, h->E);
+  const bool fld = h->any_field;
+  if (fld) O::field(h, h->Xs, s);
+  O::coulomb(h, h->Xs, s);
+  O::exchange(h, h->Xs, s);
+  O::sso_update(h, 0, 0, fld, dt, h->Xs, s);
+}
+
 rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, double* dip, double* nrm,
                        long long ld, long long offset, cudaStream_t s) {
   // stage times are t_off + (base + k + c_s) dt with an integer base when the
@@ -694,18 +742,25 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
   }
   CK(cudaMemsetAsync(h->d_step, 0, sizeof(long long), s));
   CK(cudaMemcpyAsync(h->Xs, h->Xn, sizeof(double) * h->N * 2 * h->T, cudaMemcpyDeviceToDevice, s));
+  const bool sso = h->integrator == RTTDA_INT_SSO;
+  auto step = [&](auto ops) {
+    if (sso)
+      enqueue_step_sso(h, ops, base, t_off, dt, dip, nrm, ld, offset, s);
+    else
+      enqueue_step(h, ops, base, t_off, dt, dip, nrm, ld, offset, s);
+  };
+  if (nsteps > 0 && sso) dispatch(h->prec, [&](auto ops) { enqueue_sso_prologue(h, ops, base, t_off, dt, s); });
   if (nsteps > 0 && h->prof_on) {
     // profiling: direct launches so that every kernel class gets its events
     const long long l0 = h->launches;
-    for (long k = 0; k < nsteps; ++k)
-      dispatch(h->prec, [&](auto ops) { enqueue_step(h, ops, base, t_off, dt, dip, nrm, ld, offset, s); });
+    for (long k = 0; k < nsteps; ++k) dispatch(h->prec, step);
     h->launches_per_step = (h->launches - l0) / nsteps;
   } else if (nsteps > 0) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const long long l0 = h->launches;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    dispatch(h->prec, [&](auto ops) { enqueue_step(h, ops, base, t_off, dt, dip, nrm, ld, offset, s); });
+    dispatch(h->prec, step);
     h->launches_per_step = h->launches - l0;
     h->launches = l0 + h->launches_per_step * nsteps;
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
@@ -1795,6 +1850,15 @@ rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step
   if (!h) return set_error(RTTDA_E_ARG, "rttda_launch_stats: NULL handle");
   if (total) *total = h->launches;
   if (per_step) *per_step = h->launches_per_step;
+  return RTTDA_OK;
+}
+
+rttda_status rttda_set_integrator(rttda_t h, int integrator) {
+  g_last_error.clear();
+  if (!h) return set_error(RTTDA_E_ARG, "rttda_set_integrator: NULL handle");
+  if (integrator != RTTDA_INT_RK4 && integrator != RTTDA_INT_SSO)
+    return set_error(RTTDA_E_ARG, "rttda_set_integrator: unknown integrator");
+  h->integrator = integrator;
   return RTTDA_OK;
 }
 

@@ -644,6 +644,58 @@ __global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long 
 }
 
 // ---------------------------------------------------------------------------
+// Symplectic split-operator update (Sec. 2.2: dq/dt = H p, dp/dt = -H q with
+// c = q + i p).  sigma of one component of the stage input X is assembled
+// as in k_combine -- the real part q (modes 0 and 2) or the imaginary part p
+// (mode 1) -- and the sub-step is applied in place (one thread owns both
+// components of its row, so reading and writing X is race free):
+//   mode 0, first half step:   p <- p - dt/2 H q
+//   mode 1, drift:             q <- q + dt H p;            Xn.q <- q
+//   mode 2, closing half step: p_{n+1} = p - dt/2 H q;     Xn.p <- p_{n+1};
+//                              p <- p_{n+1} - dt/2 H q     (next step's first half)
+// The two half steps of mode 2 are separate roundings, so a propagation
+// that stops at step n and resumes from Xn with mode 0 reproduces it bit for
+// bit.  One thread per (trajectory t, row n), n fastest; N * T < 2^31.
+// ---------------------------------------------------------------------------
+template <typename TC>
+__global__ void __launch_bounds__(256) k_sso_update(int mode, int stage, long long N, int o, int v, int T,
+                                                    const double* __restrict__ eps_o,
+                                                    const double* __restrict__ eps_v, double cx,
+                                                    const TC* __restrict__ Jpart, int SJ,
+                                                    const TC* __restrict__ Kpart, int SK, long long Kstride,
+                                                    const double* __restrict__ F, const double* __restrict__ E,
+                                                    int use_field, double dt, double* __restrict__ Xn,
+                                                    double* __restrict__ X) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n32 = (int)N;
+  if (e >= n32 * T) return;
+  const int n = e % n32, t = e / n32;
+  const int C = 2 * T, qc = mode == 1 ? 1 : 0, col = 2 * t + qc;
+  const long long ov = N - 1;
+  const size_t iq = (size_t)n * C + 2 * t, ip = iq + 1, idx = iq + qc;
+  double sg = 0.0;
+  if (n > 0) {
+    const int i = (n - 1) / v, a = (n - 1) - i * v;
+    const double jsum = sum_partials(Jpart + (size_t)(n - 1) * C + col, (size_t)ov * C, SJ);
+    const double ksum = sum_partials(Kpart + ((size_t)col * o + i) * v + a, (size_t)Kstride, SK);
+    sg = (eps_v[a] - eps_o[i]) * X[idx] + jsum - cx * ksum;
+  }
+  if (use_field) sg -= E[stage * T + t] * F[idx];
+  const double h = 0.5 * dt;
+  if (mode == 0) {
+    X[ip] = X[ip] - h * sg;
+  } else if (mode == 1) {
+    const double q1 = X[iq] + dt * sg;
+    X[iq] = q1;
+    Xn[iq] = q1;
+  } else {
+    const double p1 = X[ip] - h * sg;
+    Xn[ip] = p1;
+    X[ip] = p1 - h * sg;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Observables: mu_d = Re c^dagger F (F = M_d c) and |c|^2 per trajectory.
 // Two-phase fixed-order reduction in FP64.
 // ---------------------------------------------------------------------------

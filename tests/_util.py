@@ -15,13 +15,14 @@ def unit(d):
     return d / np.linalg.norm(d)
 
 
-def oracle_runs(mol, c_x, pulses, dt, nsteps, c0=None):
+def oracle_runs(mol, c_x, pulses, dt, nsteps, c0=None, integrator="rk4"):
     """Dense-oracle trajectories, one per pulse (each with its own M_d)."""
     A = orc.build_A(mol, c_x)
+    run = orc.propagate if integrator == "rk4" else orc.propagate_sso
     out = []
     for t, p in enumerate(pulses):
         M = orc.build_M(*orc.dipole_along(mol, unit(p.get("direction", (0, 0, 1)))))
-        out.append(orc.propagate(A, M, oracle_pulse(p), None if c0 is None else c0[t], dt, nsteps))
+        out.append(run(A, M, oracle_pulse(p), None if c0 is None else c0[t], dt, nsteps))
     return out
 
 
