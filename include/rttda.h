@@ -243,6 +243,37 @@ rttda_status rttda_profile_read(rttda_t h, double* ms, long long* launches);
  * the last propagation (*per_step).  Either pointer may be NULL. */
 rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step);
 
+/* Lowest excited states of the TI-TDA problem A X_i = w_i X_i (Sec. 2.1,
+ * Eq. casida_tda; A without the field, in the handle's precision), for the
+ * population projections of Eq. populations.  Davidson iteration on the
+ * library's sigma build (up to 2*ntraj vectors per build, so a batch must be
+ * set with rttda_set_field first), diagonal preconditioner e_a - e_i, stop
+ * when every residual norm |A X_i - w_i X_i| < tol.
+ *   k        number of states, 1 <= k <= nocc*nvirt;
+ *   evals    host [k], ascending;
+ *   evecs    host or device [k][1 + nocc*nvirt] FP64, unit norm, component 0
+ *            (the ground state) = 0; may be NULL;
+ *   iters    iterations used (may be NULL).
+ * Errors: RTTDA_E_ARG, RTTDA_E_STATE (no batch; or not converged within
+ * max_iter -- evals/evecs then hold the last estimates), RTTDA_E_OOM,
+ * RTTDA_E_CUDA. */
+rttda_status rttda_eigenstates(rttda_t h, int k, double tol, int max_iter, double* evals, double* evecs, int* iters);
+
+/* Projectors for overlap and population recording (Eq. populations,
+ * P_i(t) = |X_i^T c(t)|^2 with real state vectors X_i).  X: host or device
+ * [k][1 + nocc*nvirt] FP64, copied.  Later propagations record, for every
+ * trajectory t, step n = 0..nsteps and projector i, the complex overlap
+ * o[t][n][i] = sum_m X_i[m] c_t[m](t_n).  k = 0 removes the projectors.
+ * Errors: RTTDA_E_ARG (k < 0, k > 4096, NULL X), RTTDA_E_OOM. */
+rttda_status rttda_set_projectors(rttda_t h, int k, const double* X);
+
+/* Overlaps of the last rttda_propagate / rttda_resume call:
+ * out[ntraj][npts][k][2] (host or device; re, im), npts = nsteps + 1 of
+ * that call.  Synchronises the handle.
+ * Errors: RTTDA_E_ARG (NULL, npts mismatch), RTTDA_E_STATE (no projectors,
+ * or no propagation since they were set). */
+rttda_status rttda_get_overlaps(rttda_t h, double* out, long npts);
+
 /* Time integrator of later propagations (the state and time are kept).
  *   RTTDA_INT_RK4  classical 4-stage Runge-Kutta on dc/dt = -i H(t) c,
  *                  stages at t, t+dt/2, t+dt/2, t+dt (default; 4 sigma

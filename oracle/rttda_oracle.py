@@ -34,7 +34,9 @@ GPU-Accelerated Real-Time Tamm-Dancoff Approximation", arXiv 2601.16949):
   at t, t + dt/2, t + dt/2, t + dt (the integrator this project specifies),
   and the paper's own second-order symplectic split operator (Sec. 2.2,
   Sec. 3.4) on dq/dt = H p, dp/dt = -H q (sso_step).
-* Observables after every step: mu_d(t_n) = Re c^dagger M_d c and |c|^2.
+* Observables after every step: mu_d(t_n) = Re c^dagger M_d c and |c|^2;
+  populations P_i(t) = |X_i^T c(t)|^2 of the TI-TDA states X_i (eigenvectors
+  of A's singles block, Eq. populations).
 * Spectrum: S(w) = (w / kappa) Im sum_n w_n (mu_n - mu_0) exp((i w - g) t_n) dt
   with trapezoid weights, the dipole-trace analogue of Eq. fourier_transform;
   several polarisations are averaged as in Eq. spectrum_average.
@@ -352,6 +354,31 @@ def propagate_sso(A, M, p: Pulse, c0, dt: float, nsteps: int) -> Trajectory:
         c = sso_step(A, M, p, s * dt, dt, c)
         dip[s + 1], nrm[s + 1] = observables(M, c)
     return Trajectory(c=c, dipole=dip, norm=nrm)
+
+
+# ---------------------------------------------------------------------------
+# Stationary states and populations (Sec. 2.2, Eq. populations)
+# ---------------------------------------------------------------------------
+
+def ti_states(A: np.ndarray, k: int) -> tuple:
+    """The k lowest excited TI-TDA states (Sec. 2.1, Eq. casida_tda): the
+    eigenpairs of A's singles block, as full-length vectors with a zero
+    ground component.  (The ground row and column of A are zero, so |0> is
+    an eigenvector with eigenvalue 0 that is left out.)"""
+    w, U = np.linalg.eigh(A[1:, 1:])
+    X = np.zeros((k, A.shape[0]))
+    X[:, 1:] = U[:, :k].T
+    return w[:k], X
+
+
+def overlaps(X: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """o_i = X_i^T c for real states X_i (rows of X)."""
+    return np.asarray(X, dtype=np.float64) @ np.asarray(c)
+
+
+def populations(X: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """P_i = |X_i^T c|^2 (Eq. populations)."""
+    return np.abs(overlaps(X, c)) ** 2
 
 
 # ---------------------------------------------------------------------------

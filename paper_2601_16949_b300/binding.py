@@ -97,6 +97,9 @@ lib.rttda_profile_read.argtypes = [_h, _dp, ct.POINTER(ct.c_longlong)]
 lib.rttda_launch_stats.argtypes = [_h, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]
 lib.rttda_plan.argtypes = [_h, ct.POINTER(rttda_plan_info)]
 lib.rttda_set_integrator.argtypes = [_h, ct.c_int]
+lib.rttda_eigenstates.argtypes = [_h, ct.c_int, ct.c_double, ct.c_int, _dp, _dp, ct.POINTER(ct.c_int)]
+lib.rttda_set_projectors.argtypes = [_h, ct.c_int, _dp]
+lib.rttda_get_overlaps.argtypes = [_h, _dp, ct.c_long]
 lib.rttda_coulomb_noalloc.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int,
                                       ct.c_void_p, ct.c_void_p]
 lib.rttda_coulomb_noalloc.restype = ct.c_int
@@ -120,7 +123,7 @@ lib.rttda_destroy.restype = None
 for _name in ("rttda_create", "rttda_memory_bytes", "rttda_set_field", "rttda_propagate", "rttda_propagate_device",
               "rttda_resume", "rttda_get_state", "rttda_set_state", "rttda_sigma", "rttda_spectrum",
               "rttda_profile", "rttda_profile_read", "rttda_launch_stats", "rttda_sync", "rttda_plan",
-              "rttda_set_integrator"):
+              "rttda_set_integrator", "rttda_eigenstates", "rttda_set_projectors", "rttda_get_overlaps"):
     getattr(lib, _name).restype = ct.c_int
 
 
@@ -282,6 +285,33 @@ def rttda_set_integrator(h, integrator) -> None:
     _check(lib.rttda_set_integrator(h, code), "rttda_set_integrator")
 
 
+def rttda_eigenstates(h, k: int, dim: int = 0, tol: float = 1e-8, max_iter: int = 200):
+    """(evals[k], evecs[k][dim] or None when dim = 0, iterations): the k
+    lowest TI-TDA states of A (dim = 1 + nocc * nvirt)."""
+    n = ct.c_int()
+    ev = np.zeros(k)
+    vecs = np.zeros((k, dim)) if dim else None
+    _check(lib.rttda_eigenstates(h, int(k), float(tol), int(max_iter), _ptr(ev),
+                                 _ptr(vecs) if vecs is not None else None, ct.byref(n)), "rttda_eigenstates")
+    return ev, vecs, n.value
+
+
+def rttda_set_projectors(h, X) -> None:
+    """Real projector vectors X[k][N] (numpy); None or an empty array removes them."""
+    if X is None or len(X) == 0:
+        _check(lib.rttda_set_projectors(h, 0, None), "rttda_set_projectors")
+        return
+    X = _f64(np.atleast_2d(X))
+    _check(lib.rttda_set_projectors(h, X.shape[0], _ptr(X)), "rttda_set_projectors")
+
+
+def rttda_get_overlaps(h, ntraj: int, npts: int, k: int) -> np.ndarray:
+    """Complex overlaps [ntraj][npts][k] of the last propagation."""
+    out = np.zeros((ntraj, npts, k, 2))
+    _check(lib.rttda_get_overlaps(h, _ptr(out), int(npts)), "rttda_get_overlaps")
+    return out[..., 0] + 1j * out[..., 1]
+
+
 def rttda_plan(h) -> dict:
     """The sigma build's execution plan for the current batch (see rttda.h)."""
     pi = rttda_plan_info()
@@ -412,6 +442,16 @@ class Propagator:
         rttda_propagate(self.h, c0a, dt, nsteps, c_out, dip, nrm)
         c = None if c_out is None else c_out[..., 0] + 1j * c_out[..., 1]
         return c, dip, nrm
+
+    def eigenstates(self, k, tol=1e-8, max_iter=200):
+        return rttda_eigenstates(self.h, k, self.n, tol, max_iter)
+
+    def set_projectors(self, X):
+        rttda_set_projectors(self.h, X)
+        self.nproj = 0 if X is None else len(X)
+
+    def overlaps(self, nsteps):
+        return rttda_get_overlaps(self.h, self.ntraj, nsteps + 1, self.nproj)
 
     def resume(self, dt, nsteps):
         c_out = np.zeros((self.ntraj, self.n, 2))

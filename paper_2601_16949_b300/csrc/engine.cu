@@ -150,6 +150,13 @@ struct rttda_ctx {
   int wide_mb = 0;                   // >0: main contraction on the wide-M kernel with this many 128-row blocks
   int wide_kb = 32;                  // K tile width of the wide-M kernel (32 or 64 BF16)
   int integrator = RTTDA_INT_RK4;    // rttda_integrator
+  // projectors (Eq. populations) and the overlaps of the last propagation
+  int nproj = 0;
+  double* d_proj = nullptr;   // [nproj][N]
+  double* d_ovl = nullptr;    // [T][ovl_ld][nproj][2]
+  double* d_proj_part = nullptr;
+  long long ovl_ld = 0, ovl_cap = 0, proj_rows = 1, part_cap = 0;
+  int proj_G = 1;
   rttda_plan_info plan{};            // the exchange plan in use (rttda_plan)
   __nv_bfloat16* Bvv_tc = nullptr;  // [plane][P][vp][vp]
   __nv_bfloat16* Boo_tc = nullptr;  // [plane][P*o][op]
@@ -205,6 +212,9 @@ rttda_ctx::~rttda_ctx() {
   dfree(Bov_tc);
   dfree(BovT_tc);
   dfree(d_err);
+  dfree(d_proj);
+  dfree(d_ovl);
+  dfree(d_proj_part);
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -671,6 +681,17 @@ void enqueue_observe(rttda_ctx* h, const double* X, double* dip, double* nrm, lo
   k_obs_final<<<1, 128, 0, s>>>(h->obsG, h->T, h->obs_part, h->d_step, step_offset, ld, dip, nrm);
 }
 
+// Overlaps of the state X with the projectors, recorded at the step index.
+void enqueue_project(rttda_ctx* h, const double* X, long long ld, long long step_offset, cudaStream_t s) {
+  if (h->nproj < 1 || !h->d_ovl) return;
+  Prof pr(h, RTTDA_KC_OBSERVE, s);
+  h->launches += 2;
+  const int C = 2 * h->T;
+  k_proj_partial<<<dim3(h->proj_G, h->nproj), 256, 0, s>>>(h->N, C, h->nproj, h->proj_rows, h->d_proj, X,
+                                                          h->d_proj_part);
+  k_proj_final<<<1, 256, 0, s>>>(h->proj_G, C, h->nproj, h->d_proj_part, h->d_step, step_offset, ld, h->d_ovl);
+}
+
 // One RK4 step (four sigma builds) plus the observables of the step's start.
 template <typename O>
 void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, double* dip, double* nrm, long long ld,
@@ -685,6 +706,7 @@ void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, doub
     const bool fld = h->any_field;
     if (st == 0 || fld) O::field(h, xin, s);
     if (st == 0 && dip) enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
+    if (st == 0) enqueue_project(h, h->Xn, ld, offset, s);
     O::coulomb(h, xin, s);
     O::exchange(h, xin, s);
     O::combine(h, 0, st, fld, dt, xin, xnext, nullptr, s);
@@ -707,6 +729,7 @@ void enqueue_step_sso(rttda_ctx* h, O, long long base, double t_off, double dt, 
     O::field(h, h->Xn, s);
     enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
   }
+  enqueue_project(h, h->Xn, ld, offset, s);
   for (int half = 0; half < 2; ++half) {
     if (fld) O::field(h, h->Xs, s);
     O::coulomb(h, h->Xs, s);
@@ -782,6 +805,7 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
     dispatch(h->prec, [&](auto ops) { decltype(ops)::field(h, h->Xn, s); });
     enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
   }
+  enqueue_project(h, h->Xn, ld, offset, s);
   CK(cudaGetLastError());
   h->t_now = t_off + (double)(base + nsteps) * dt;
   h->have_state = true;
@@ -1593,6 +1617,25 @@ static rttda_status propagate_impl(rttda_t h, bool fresh, const double* c0_dev, 
     if (!nrm) nrm = tmp;
   }
   if (ld < 0) ld = nsteps + 1;
+  if (h->nproj > 0) {
+    const long long need = (long long)h->T * ld * h->nproj * 2;
+    if (need > h->ovl_cap) {
+      dfree(h->d_ovl);
+      h->d_ovl = nullptr;
+      h->ovl_cap = 0;
+      CKS(dalloc(&h->d_ovl, (size_t)need));
+      h->ovl_cap = need;
+    }
+    const long long pneed = (long long)h->proj_G * h->nproj * 2 * h->T;
+    if (pneed > h->part_cap) {
+      dfree(h->d_proj_part);
+      h->d_proj_part = nullptr;
+      h->part_cap = 0;
+      CKS(dalloc(&h->d_proj_part, (size_t)pneed));
+      h->part_cap = pneed;
+    }
+    h->ovl_ld = ld;
+  }
   rttda_status st = run_steps(h, t_call, dt, nsteps, dip, nrm, ld, offset, s);
   if (st == RTTDA_OK && c_out_dev) k_dev_to_abi<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->Xn, c_out_dev);
   if (tmp) {
@@ -1611,6 +1654,31 @@ rttda_status advance(rttda_t h, bool fresh, double dt, long nsteps, double* dip,
   return propagate_impl(h, fresh, nullptr, dt, nsteps, nullptr, dip, nrm, s ? s : h->stream, ld, offset);
 }
 cudaStream_t handle_stream(rttda_t h) { return h->stream; }
+
+rttda_status batch_view(rttda_t h, BatchView* bv) {
+  if (h->T < 1) return set_error(RTTDA_E_STATE, "no batch: call rttda_set_field first");
+  bv->N = h->N;
+  bv->T = h->T;
+  bv->nocc = h->o;
+  bv->nvirt = h->v;
+  bv->eps_o = h->eps_o;
+  bv->eps_v = h->eps_v;
+  bv->X = h->Xq;
+  bv->out = h->term;
+  bv->stream = h->stream;
+  return RTTDA_OK;
+}
+
+rttda_status sigma_A(rttda_t h, cudaStream_t s) {
+  dispatch(h->prec, [&](auto ops) {
+    using O = decltype(ops);
+    O::coulomb(h, h->Xq, s);
+    O::exchange(h, h->Xq, s);
+    O::combine(h, 1, 0, false, 0.0, h->Xq, nullptr, h->term, s);
+  });
+  CK(cudaGetLastError());
+  return RTTDA_OK;
+}
 }  // namespace rttda
 extern "C" {
 
@@ -1850,6 +1918,37 @@ rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step
   if (!h) return set_error(RTTDA_E_ARG, "rttda_launch_stats: NULL handle");
   if (total) *total = h->launches;
   if (per_step) *per_step = h->launches_per_step;
+  return RTTDA_OK;
+}
+
+rttda_status rttda_set_projectors(rttda_t h, int k, const double* X) {
+  g_last_error.clear();
+  if (!h) return set_error(RTTDA_E_ARG, "rttda_set_projectors: NULL handle");
+  if (k < 0 || k > 4096 || (k > 0 && !X)) return set_error(RTTDA_E_ARG, "rttda_set_projectors: need 0 <= k <= 4096 and X");
+  dfree(h->d_proj);
+  dfree(h->d_proj_part);
+  dfree(h->d_ovl);
+  h->d_proj = h->d_proj_part = h->d_ovl = nullptr;
+  h->nproj = 0;
+  h->ovl_cap = h->ovl_ld = h->part_cap = 0;
+  if (k == 0) return RTTDA_OK;
+  CKS(dalloc(&h->d_proj, (size_t)k * h->N));
+  CK(cudaMemcpy(h->d_proj, X, sizeof(double) * (size_t)k * h->N, cudaMemcpyDefault));
+  h->proj_rows = std::max<long long>(2048, cdiv(h->N, 2 * kNumSM));
+  h->proj_G = (int)cdiv(h->N, h->proj_rows);
+  h->nproj = k;
+  return RTTDA_OK;
+}
+
+rttda_status rttda_get_overlaps(rttda_t h, double* out, long npts) {
+  g_last_error.clear();
+  if (!h || !out) return set_error(RTTDA_E_ARG, "rttda_get_overlaps: NULL argument");
+  if (h->nproj < 1 || !h->d_ovl || h->ovl_ld < 1)
+    return set_error(RTTDA_E_STATE, "rttda_get_overlaps: no projectors or no propagation since they were set");
+  if (npts != h->ovl_ld) return set_error(RTTDA_E_ARG, "rttda_get_overlaps: npts must be nsteps + 1 of the last call");
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(out, h->d_ovl, sizeof(double) * (size_t)h->T * npts * h->nproj * 2, cudaMemcpyDefault));
   return RTTDA_OK;
 }
 

@@ -27,4 +27,21 @@ rttda_status spectrum_device(const double* trace_dev, long long ntr, long long n
                              double gamma, double wmin, double wmax, long long nfreq, double* om_dev, double* S_dev,
                              cudaStream_t s);
 size_t estimate_bytes(int nocc, int nvirt, int naux, int ntraj, int prec, long nsteps);
+
+// The handle's batch as seen by the eigensolver: N rows, C = 2T real
+// columns, orbital energies (device), the sigma input X and output buffers
+// (device, [N][C] row-major).
+struct BatchView {
+  long long N = 0;
+  int T = 0, nocc = 0, nvirt = 0;
+  const double* eps_o = nullptr;
+  const double* eps_v = nullptr;
+  double* X = nullptr;
+  double* out = nullptr;
+  cudaStream_t stream = nullptr;
+};
+// RTTDA_E_STATE when no batch is set.
+rttda_status batch_view(rttda_t h, BatchView* bv);
+// out = A X for the batch buffers of batch_view (the field term excluded), on stream s.
+rttda_status sigma_A(rttda_t h, cudaStream_t s);
 }  // namespace rttda

@@ -742,6 +742,59 @@ __global__ void k_obs_final(int G, int T, const double* __restrict__ part, const
 }
 
 // ---------------------------------------------------------------------------
+// Overlaps with K real projectors (Eq. populations: P_i(t) = |X_i^T c(t)|^2):
+// o[t][i] = sum_n Pj_i[n] c_t[n], complex (column 2t real part, 2t+1
+// imaginary part).  Pass 1: block (g, i) sums the rows of chunk g for up to
+// eight columns at a time, warp shuffles then a fixed-order sum over warps
+// -> part[(g K + i) C + col].  Pass 2 adds the chunks in order and writes
+// ovl[((t ld + k) K + i) 2 + re/im] with k = *step + step_offset.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_proj_partial(long long N, int C, int K, long long rows,
+                                                      const double* __restrict__ Pj, const double* __restrict__ X,
+                                                      double* __restrict__ part) {
+  __shared__ double ws[8][8];
+  const int g = blockIdx.x, i = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long n0 = (long long)g * rows, n1 = min(N, n0 + rows);
+  const double* pr = Pj + (size_t)i * N;
+  for (int c0 = 0; c0 < C; c0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+    for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+      const double pv = pr[n];
+      const double* xr = X + (size_t)n * C + c0;
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c0 + c < C) acc[c] = fma(pv, xr[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const double v = warp_sum(acc[c]);
+      if (lane == 0) ws[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && c0 + threadIdx.x < C) {
+      double sum = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += ws[w][threadIdx.x];
+      part[((size_t)g * K + i) * C + c0 + threadIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_proj_final(int G, int C, int K, const double* __restrict__ part, const long long* __restrict__ step,
+                             long long step_offset, long long ld, double* __restrict__ ovl) {
+  const long long k = *step + step_offset;
+  for (int e = threadIdx.x; e < K * C; e += blockDim.x) {
+    const int i = e / C, col = e % C;
+    double sum = 0.0;
+    for (int g = 0; g < G; ++g) sum += part[((size_t)g * K + i) * C + col];
+    ovl[(((size_t)(col >> 1) * ld + k) * K + i) * 2 + (col & 1)] = sum;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Kick exp(+i kappa M_d) by its Taylor series: with F = M_d term,
 // term <- (i kappa / k) F, out += term.
 // ---------------------------------------------------------------------------

@@ -373,6 +373,72 @@ def test_sso_is_second_order_with_time_dependent_field():
 
 
 # ---------------------------------------------------------------------------
+# Stationary states and populations
+# ---------------------------------------------------------------------------
+
+def test_populations_over_all_states_sum_to_the_norm():
+    """Completeness: the TI states plus |0> are an orthonormal basis, so the
+    populations of all of them add up to |c|^2 at every step (a driven
+    trajectory, so the state is not stationary)."""
+    mol = small_mol(2, 3, 4, seed=5)
+    A = orc.build_A(mol, 0.2)
+    M = orc.build_M(*orc.dipole_along(mol, (0, 1, 0)))
+    n = A.shape[0]
+    w, X = orc.ti_states(A, n - 1)
+    e0 = np.zeros(n)
+    e0[0] = 1.0
+    allX = np.vstack([e0, X])
+    p = orc.Pulse(kind=orc.GAUSS_TL, E0=0.08, omega=0.8, t0=2.0, fwhm=2.0)
+    c = np.zeros(n, dtype=np.complex128)
+    c[0] = 1.0
+    for s in range(60):
+        c = orc.rk4_step(A, M, p, s * 0.05, 0.05, c)
+        assert abs(np.sum(orc.populations(allX, c)) - np.vdot(c, c).real) < 1e-13
+    # and the states really are eigenvectors of A
+    assert np.max(np.abs(A @ X.T - X.T * w)) < 1e-12
+
+
+def test_field_free_rk4_populations_follow_the_stability_polynomial():
+    mol = small_mol(3, 4, 5, seed=2)
+    A = orc.build_A(mol, 0.2)
+    M = orc.build_M(*orc.dipole_along(mol, (0, 0, 1)))
+    w, X = orc.ti_states(A, 5)
+    c0 = synth.random_state(A.shape[0], 1, seed=8)[0]
+    dt, n = 0.05, 120
+    tr = orc.propagate(A, M, orc.Pulse(kind=orc.CW, E0=0.0, omega=1.0), c0, dt, n)
+    b = X @ c0
+    pred = np.abs(rk4_R(-1j * w * dt)) ** (2 * n) * np.abs(b) ** 2
+    assert np.max(np.abs(orc.populations(X, tr.c) - pred)) < 1e-13
+
+
+def test_resonant_two_level_population_is_rabi_flopping():
+    """Two levels (nocc = nvirt = 1), resonant CW drive E0 sin(w0 t) with
+    coupling m: in the rotating-wave approximation the upper population is
+    sin^2(m E0 t / 2) (a textbook result); the neglected counter-rotating
+    terms are of relative size m E0 / w0."""
+    w0, m, E0 = 0.5, 1.0, 0.004
+    mol = zero_mol(1, 1)
+    mol["eps_virt"][:] = w0
+    mol["mu_0ov"][2, 0, 0] = m
+    A = orc.build_A(mol, 0.0)
+    M = orc.build_M(*orc.dipole_along(mol, (0, 0, 1)))
+    w, X = orc.ti_states(A, 1)
+    assert abs(w[0] - w0) < 1e-15
+    p = orc.Pulse(kind=orc.CW, E0=E0, omega=w0)
+    T = 2 * math.pi / (m * E0)
+    dt = 0.05
+    nsteps = int(round(T / dt))
+    c = np.array([1.0, 0.0], dtype=np.complex128)
+    worst = 0.0
+    for s in range(nsteps):
+        c = orc.rk4_step(A, M, p, s * dt, dt, c)
+        if (s + 1) % 200 == 0:
+            t = (s + 1) * dt
+            worst = max(worst, abs(orc.populations(X, c)[0] - math.sin(m * E0 * t / 2) ** 2))
+    assert worst < 3 * m * E0 / w0
+
+
+# ---------------------------------------------------------------------------
 # Kick
 # ---------------------------------------------------------------------------
 
