@@ -274,6 +274,34 @@ rttda_status rttda_set_projectors(rttda_t h, int k, const double* X);
  * or no propagation since they were set). */
 rttda_status rttda_get_overlaps(rttda_t h, double* out, long npts);
 
+/* Autocorrelation recording (Eq. time_correlation_function):
+ * R_t(t_n) = X_t^dagger(eps) X_t(eps + t_n), with eps right after the kick
+ * (the state a fresh propagation starts from, kick applied).  enable != 0:
+ * every fresh propagation stores its X(eps) and every propagation or resume
+ * records R for its steps n = 0..nsteps; 0 turns it off. */
+rttda_status rttda_set_autocorrelation(rttda_t h, int enable);
+
+/* R of the last call: out[ntraj][npts][2] (host or device; re, im),
+ * npts = nsteps + 1 of that call.  Synchronises the handle.
+ * Errors: RTTDA_E_ARG (NULL, npts mismatch), RTTDA_E_STATE (off, or no
+ * fresh propagation since it was enabled). */
+rttda_status rttda_get_autocorrelation(rttda_t h, double* out, long npts);
+
+/* The paper's spectrum from autocorrelation records (Sec. 3.1 with Eqs.
+ * time_correlation_function, fourier_transform, spectrum_average): each
+ * record R(t_j), t_j = j dt, j < npts, is mirrored (R(-t) = conj R(t), 2
+ * npts - 1 points), multiplied by a Hann window peaked at t = 0, padded with
+ * npad zeros, and transformed, F(w) = sum_m win_m R(t_m) e^{+i w t_m} dt; the
+ * spectrum w Re F(w) is averaged over the ntraces records and evaluated on
+ * the padded FFT grid w_k = 2 pi k / ((2 npts - 1 + npad) dt), k < nfreq
+ * (by a direct sum on the GPU, which equals the FFT there).  normalize != 0
+ * divides by the largest value of the nfreq outputs.
+ *   R host or device [ntraces][npts][2]; omega_out host [nfreq] (may be
+ *   NULL); S_out host [nfreq].  No handle needed.
+ * Errors: RTTDA_E_ARG, RTTDA_E_OOM, RTTDA_E_CUDA. */
+rttda_status rttda_spectrum_autocorr(const double* R, long ntraces, long npts, double dt, long npad, long nfreq,
+                                     int normalize, double* omega_out, double* S_out);
+
 /* Time integrator of later propagations (the state and time are kept).
  *   RTTDA_INT_RK4  classical 4-stage Runge-Kutta on dc/dt = -i H(t) c,
  *                  stages at t, t+dt/2, t+dt/2, t+dt (default; 4 sigma

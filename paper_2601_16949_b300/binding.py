@@ -100,6 +100,10 @@ lib.rttda_set_integrator.argtypes = [_h, ct.c_int]
 lib.rttda_eigenstates.argtypes = [_h, ct.c_int, ct.c_double, ct.c_int, _dp, _dp, ct.POINTER(ct.c_int)]
 lib.rttda_set_projectors.argtypes = [_h, ct.c_int, _dp]
 lib.rttda_get_overlaps.argtypes = [_h, _dp, ct.c_long]
+lib.rttda_set_autocorrelation.argtypes = [_h, ct.c_int]
+lib.rttda_get_autocorrelation.argtypes = [_h, _dp, ct.c_long]
+lib.rttda_spectrum_autocorr.argtypes = [_dp, ct.c_long, ct.c_long, ct.c_double, ct.c_long, ct.c_long, ct.c_int,
+                                        _dp, _dp]
 lib.rttda_coulomb_noalloc.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int,
                                       ct.c_void_p, ct.c_void_p]
 lib.rttda_coulomb_noalloc.restype = ct.c_int
@@ -123,7 +127,8 @@ lib.rttda_destroy.restype = None
 for _name in ("rttda_create", "rttda_memory_bytes", "rttda_set_field", "rttda_propagate", "rttda_propagate_device",
               "rttda_resume", "rttda_get_state", "rttda_set_state", "rttda_sigma", "rttda_spectrum",
               "rttda_profile", "rttda_profile_read", "rttda_launch_stats", "rttda_sync", "rttda_plan",
-              "rttda_set_integrator", "rttda_eigenstates", "rttda_set_projectors", "rttda_get_overlaps"):
+              "rttda_set_integrator", "rttda_eigenstates", "rttda_set_projectors", "rttda_get_overlaps",
+              "rttda_set_autocorrelation", "rttda_get_autocorrelation", "rttda_spectrum_autocorr"):
     getattr(lib, _name).restype = ct.c_int
 
 
@@ -312,6 +317,28 @@ def rttda_get_overlaps(h, ntraj: int, npts: int, k: int) -> np.ndarray:
     return out[..., 0] + 1j * out[..., 1]
 
 
+def rttda_set_autocorrelation(h, enable: bool = True) -> None:
+    _check(lib.rttda_set_autocorrelation(h, 1 if enable else 0), "rttda_set_autocorrelation")
+
+
+def rttda_get_autocorrelation(h, ntraj: int, npts: int) -> np.ndarray:
+    """Complex R[ntraj][npts] of the last propagation."""
+    out = np.zeros((ntraj, npts, 2))
+    _check(lib.rttda_get_autocorrelation(h, _ptr(out), int(npts)), "rttda_get_autocorrelation")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def rttda_spectrum_autocorr(R, dt: float, npad: int = 50000, nfreq: int = 1024, normalize: bool = True):
+    """(omega[nfreq], S[nfreq]) from complex autocorrelation records R[ntr][npts]."""
+    R = np.atleast_2d(np.asarray(R))
+    Rri = _f64(np.stack([R.real, R.imag], axis=-1))
+    om = np.zeros(nfreq)
+    S = np.zeros(nfreq)
+    _check(lib.rttda_spectrum_autocorr(_ptr(Rri), Rri.shape[0], Rri.shape[1], float(dt), int(npad), int(nfreq),
+                                       1 if normalize else 0, _ptr(om), _ptr(S)), "rttda_spectrum_autocorr")
+    return om, S
+
+
 def rttda_plan(h) -> dict:
     """The sigma build's execution plan for the current batch (see rttda.h)."""
     pi = rttda_plan_info()
@@ -452,6 +479,9 @@ class Propagator:
 
     def overlaps(self, nsteps):
         return rttda_get_overlaps(self.h, self.ntraj, nsteps + 1, self.nproj)
+
+    def autocorrelation(self, nsteps):
+        return rttda_get_autocorrelation(self.h, self.ntraj, nsteps + 1)
 
     def resume(self, dt, nsteps):
         c_out = np.zeros((self.ntraj, self.n, 2))

@@ -157,6 +157,13 @@ struct rttda_ctx {
   double* d_proj_part = nullptr;
   long long ovl_ld = 0, ovl_cap = 0, proj_rows = 1, part_cap = 0;
   int proj_G = 1;
+  // autocorrelation R(t) = X(eps)^dagger X(eps + t) (Eq. time_correlation_function)
+  bool acf_on = false;
+  double* d_xeps = nullptr;   // [N][2T] state right after the kick of the last fresh propagation
+  double* d_acf = nullptr;    // [T][acf_ld][2]
+  double* d_acf_part = nullptr;
+  long long acf_ld = 0, acf_cap = 0, acf_eps_cap = 0, acf_part_cap = 0;
+  bool have_eps = false;
   rttda_plan_info plan{};            // the exchange plan in use (rttda_plan)
   __nv_bfloat16* Bvv_tc = nullptr;  // [plane][P][vp][vp]
   __nv_bfloat16* Boo_tc = nullptr;  // [plane][P*o][op]
@@ -215,6 +222,9 @@ rttda_ctx::~rttda_ctx() {
   dfree(d_proj);
   dfree(d_ovl);
   dfree(d_proj_part);
+  dfree(d_xeps);
+  dfree(d_acf);
+  dfree(d_acf_part);
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -243,6 +253,8 @@ void rttda_ctx::free_batch() {
   h_io_count = 0;
   T = 0;
   have_state = false;
+  have_eps = false;
+  acf_ld = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -692,6 +704,15 @@ void enqueue_project(rttda_ctx* h, const double* X, long long ld, long long step
   k_proj_final<<<1, 256, 0, s>>>(h->proj_G, C, h->nproj, h->d_proj_part, h->d_step, step_offset, ld, h->d_ovl);
 }
 
+// Autocorrelation of the state X with the stored X(eps), recorded at the step index.
+void enqueue_acf(rttda_ctx* h, const double* X, long long ld, long long step_offset, cudaStream_t s) {
+  if (!h->acf_on || !h->have_eps || !h->d_acf) return;
+  Prof pr(h, RTTDA_KC_OBSERVE, s);
+  h->launches += 2;
+  k_acf_partial<<<dim3(h->proj_G, h->T), 256, 0, s>>>(h->N, h->T, h->proj_rows, h->d_xeps, X, h->d_acf_part);
+  k_acf_final<<<1, 128, 0, s>>>(h->proj_G, h->T, h->d_acf_part, h->d_step, step_offset, ld, h->d_acf);
+}
+
 // One RK4 step (four sigma builds) plus the observables of the step's start.
 template <typename O>
 void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, double* dip, double* nrm, long long ld,
@@ -706,7 +727,10 @@ void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, doub
     const bool fld = h->any_field;
     if (st == 0 || fld) O::field(h, xin, s);
     if (st == 0 && dip) enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
-    if (st == 0) enqueue_project(h, h->Xn, ld, offset, s);
+    if (st == 0) {
+      enqueue_project(h, h->Xn, ld, offset, s);
+      enqueue_acf(h, h->Xn, ld, offset, s);
+    }
     O::coulomb(h, xin, s);
     O::exchange(h, xin, s);
     O::combine(h, 0, st, fld, dt, xin, xnext, nullptr, s);
@@ -730,6 +754,7 @@ void enqueue_step_sso(rttda_ctx* h, O, long long base, double t_off, double dt, 
     enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
   }
   enqueue_project(h, h->Xn, ld, offset, s);
+  enqueue_acf(h, h->Xn, ld, offset, s);
   for (int half = 0; half < 2; ++half) {
     if (fld) O::field(h, h->Xs, s);
     O::coulomb(h, h->Xs, s);
@@ -806,6 +831,7 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
     enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
   }
   enqueue_project(h, h->Xn, ld, offset, s);
+  enqueue_acf(h, h->Xn, ld, offset, s);
   CK(cudaGetLastError());
   h->t_now = t_off + (double)(base + nsteps) * dt;
   h->have_state = true;
@@ -1603,6 +1629,18 @@ static rttda_status propagate_impl(rttda_t h, bool fresh, const double* c0_dev, 
     else
       k_ground<<<blocks_for(NT * 2, 256), 256, 0, s>>>(h->N, h->T, h->Xn);
     if (h->any_kick) enqueue_kick(h, s);
+    if (h->acf_on) {
+      const long long ne = h->N * 2 * h->T;
+      if (ne > h->acf_eps_cap) {
+        dfree(h->d_xeps);
+        h->d_xeps = nullptr;
+        h->acf_eps_cap = 0;
+        CKS(dalloc(&h->d_xeps, (size_t)ne));
+        h->acf_eps_cap = ne;
+      }
+      CK(cudaMemcpyAsync(h->d_xeps, h->Xn, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+      h->have_eps = true;
+    }
   } else {
     if (!h->have_state) return set_error(RTTDA_E_STATE, "rttda_resume: no state to resume from");
     t_call = h->t_now;
@@ -1635,6 +1673,24 @@ static rttda_status propagate_impl(rttda_t h, bool fresh, const double* c0_dev, 
       h->part_cap = pneed;
     }
     h->ovl_ld = ld;
+  }
+  if (h->acf_on && h->have_eps) {
+    const long long need = (long long)h->T * ld * 2, pneed = (long long)h->proj_G * h->T * 2;
+    if (need > h->acf_cap) {
+      dfree(h->d_acf);
+      h->d_acf = nullptr;
+      h->acf_cap = 0;
+      CKS(dalloc(&h->d_acf, (size_t)need));
+      h->acf_cap = need;
+    }
+    if (pneed > h->acf_part_cap) {
+      dfree(h->d_acf_part);
+      h->d_acf_part = nullptr;
+      h->acf_part_cap = 0;
+      CKS(dalloc(&h->d_acf_part, (size_t)pneed));
+      h->acf_part_cap = pneed;
+    }
+    h->acf_ld = ld;
   }
   rttda_status st = run_steps(h, t_call, dt, nsteps, dip, nrm, ld, offset, s);
   if (st == RTTDA_OK && c_out_dev) k_dev_to_abi<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->Xn, c_out_dev);
@@ -1949,6 +2005,62 @@ rttda_status rttda_get_overlaps(rttda_t h, double* out, long npts) {
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaDeviceSynchronize());
   CK(cudaMemcpy(out, h->d_ovl, sizeof(double) * (size_t)h->T * npts * h->nproj * 2, cudaMemcpyDefault));
+  return RTTDA_OK;
+}
+
+rttda_status rttda_set_autocorrelation(rttda_t h, int enable) {
+  g_last_error.clear();
+  if (!h) return set_error(RTTDA_E_ARG, "rttda_set_autocorrelation: NULL handle");
+  h->acf_on = enable != 0;
+  if (h->acf_on && h->nproj == 0) {
+    h->proj_rows = std::max<long long>(2048, cdiv(h->N, 2 * kNumSM));
+    h->proj_G = (int)cdiv(h->N, h->proj_rows);
+  }
+  h->acf_ld = 0;
+  return RTTDA_OK;
+}
+
+rttda_status rttda_get_autocorrelation(rttda_t h, double* out, long npts) {
+  g_last_error.clear();
+  if (!h || !out) return set_error(RTTDA_E_ARG, "rttda_get_autocorrelation: NULL argument");
+  if (!h->acf_on || !h->d_acf || h->acf_ld < 1)
+    return set_error(RTTDA_E_STATE, "rttda_get_autocorrelation: not enabled, or no fresh propagation since");
+  if (npts != h->acf_ld)
+    return set_error(RTTDA_E_ARG, "rttda_get_autocorrelation: npts must be nsteps + 1 of the last call");
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(out, h->d_acf, sizeof(double) * (size_t)h->T * npts * 2, cudaMemcpyDefault));
+  return RTTDA_OK;
+}
+
+rttda_status rttda_spectrum_autocorr(const double* R, long ntraces, long npts, double dt, long npad, long nfreq,
+                                     int normalize, double* omega_out, double* S_out) {
+  g_last_error.clear();
+  if (!R || !S_out || ntraces < 1 || npts < 2 || nfreq < 1 || npad < 0 || !(dt > 0.0))
+    return set_error(RTTDA_E_ARG, "rttda_spectrum_autocorr: bad arguments");
+  double *d_R = nullptr, *d_w = nullptr, *d_S = nullptr;
+  struct Free {
+    double** p[3];
+    ~Free() {
+      for (auto q : p)
+        if (*q) cudaFree(*q);
+    }
+  } fr{{&d_R, &d_w, &d_S}};
+  CKS(dalloc(&d_R, (size_t)ntraces * npts * 2));
+  CKS(dalloc(&d_w, (size_t)nfreq));
+  CKS(dalloc(&d_S, (size_t)nfreq));
+  CK(cudaMemcpy(d_R, R, sizeof(double) * (size_t)ntraces * npts * 2, cudaMemcpyDefault));
+  k_spectrum_acf<<<(unsigned)nfreq, 256>>>(d_R, ntraces, npts, dt, npad, d_w, d_S);
+  CK(cudaGetLastError());
+  std::vector<double> S(nfreq);
+  CK(cudaMemcpy(S.data(), d_S, sizeof(double) * nfreq, cudaMemcpyDeviceToHost));
+  if (omega_out) CK(cudaMemcpy(omega_out, d_w, sizeof(double) * nfreq, cudaMemcpyDeviceToHost));
+  if (normalize) {
+    const double mx = *std::max_element(S.begin(), S.end());
+    if (mx > 0.0)
+      for (double& x : S) x /= mx;
+  }
+  std::memcpy(S_out, S.data(), sizeof(double) * nfreq);
   return RTTDA_OK;
 }
 

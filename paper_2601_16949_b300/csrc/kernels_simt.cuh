@@ -909,6 +909,88 @@ __global__ void __launch_bounds__(256) k_spectrum(const double* __restrict__ tra
   }
 }
 
+// ---------------------------------------------------------------------------
+// Autocorrelation R_t = sum_n conj(E_t[n]) c_t[n] of each trajectory's state
+// with its own stored state E = X(eps) (Eq. time_correlation_function), same
+// [N][2T] layout.  Pass 1: block (g, t) over the rows of chunk g, warp
+// shuffles and a fixed-order sum over warps -> part[(g T + t) 2 + re/im].
+// Pass 2: acf[(t ld + k) 2 + re/im] with k = *step + step_offset.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_acf_partial(long long N, int T, long long rows, const double* __restrict__ E,
+                                                     const double* __restrict__ X, double* __restrict__ part) {
+  __shared__ double ws[8][2];
+  const int g = blockIdx.x, t = blockIdx.y, C = 2 * T;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long n0 = (long long)g * rows, n1 = min(N, n0 + rows);
+  double re = 0.0, im = 0.0;
+  for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+    const size_t i = (size_t)n * C + 2 * t;
+    const double er = E[i], ei = E[i + 1], xr = X[i], xi = X[i + 1];
+    re = fma(er, xr, fma(ei, xi, re));
+    im = fma(er, xi, fma(-ei, xr, im));
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if (lane == 0) {
+    ws[warp][0] = re;
+    ws[warp][1] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += ws[w][threadIdx.x];
+    part[((size_t)g * T + t) * 2 + threadIdx.x] = sum;
+  }
+}
+
+__global__ void k_acf_final(int G, int T, const double* __restrict__ part, const long long* __restrict__ step,
+                            long long step_offset, long long ld, double* __restrict__ acf) {
+  const long long k = *step + step_offset;
+  for (int e = threadIdx.x; e < 2 * T; e += blockDim.x) {
+    const int t = e >> 1, r = e & 1;
+    double sum = 0.0;
+    for (int g = 0; g < G; ++g) sum += part[((size_t)g * T + t) * 2 + r];
+    acf[((size_t)t * ld + k) * 2 + r] = sum;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Spectrum from autocorrelation records, evaluated directly at the grid of
+// a zero-padded FFT of the mirrored record (Sec. 3.1): with M = 2 npts - 1
+// points (R(-t) = conj R(t)), a Hann window peaked at t = 0,
+// w_j = 0.5 + 0.5 cos(pi j / (npts - 1)) for t_j = j dt, and
+// w_k = 2 pi k / ((M + npad) dt):
+//   S_k = w_k (1/ntr) sum_tr dt [Re R_0 + 2 sum_{j>=1} w_j Re(R_j e^{i w_k t_j})]
+// (the imaginary parts cancel between t and -t).  One block per frequency,
+// fixed-order reduction.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_spectrum_acf(const double* __restrict__ R, long long ntr, long long npts,
+                                                      double dt, long long npad, double* __restrict__ om_out,
+                                                      double* __restrict__ S) {
+  __shared__ double red[32];
+  const long long k = blockIdx.x;
+  const double two_pi = 6.283185307179586476925286766559;
+  const double pi = 3.1415926535897932384626433832795;
+  const long long ntot = 2 * npts - 1 + npad;
+  const double w = two_pi * (double)k / ((double)ntot * dt);
+  double acc = 0.0;
+  for (long long tr = 0; tr < ntr; ++tr) {
+    const double* r = R + (size_t)tr * npts * 2;
+    for (long long j = threadIdx.x; j < npts; j += blockDim.x) {
+      const double wj = npts > 1 ? 0.5 + 0.5 * cos(pi * (double)j / (double)(npts - 1)) : 1.0;
+      double sn, cs;
+      sincos(w * dt * (double)j, &sn, &cs);
+      const double val = r[2 * j] * cs - r[2 * j + 1] * sn;  // Re(R_j e^{i w t_j})
+      acc += (j == 0 ? 1.0 : 2.0) * wj * val;
+    }
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    S[k] = w * acc * dt / (double)ntr;
+    om_out[k] = w;
+  }
+}
+
 }  // namespace rttda
 
 namespace rttda {

@@ -439,6 +439,75 @@ def test_resonant_two_level_population_is_rabi_flopping():
 
 
 # ---------------------------------------------------------------------------
+# Autocorrelation spectrum (the paper's mode)
+# ---------------------------------------------------------------------------
+
+def _direct_acf_spectrum(R, dt, npad, nfreq):
+    """The same spectrum by a direct sum over the mirrored, windowed record
+    at the padded-grid frequencies (no FFT): written from the definition."""
+    R = np.atleast_2d(R)
+    n = R.shape[1]
+    M = 2 * n - 1
+    w = 2 * np.pi * np.arange(nfreq) / ((M + npad) * dt)
+    S = np.zeros(nfreq)
+    for r in R:
+        for k in range(nfreq):
+            F = 0.0
+            for m in range(M):
+                j = m - (n - 1)
+                val = r[j] if j >= 0 else np.conj(r[-j])
+                win = 0.5 - 0.5 * math.cos(2 * math.pi * m / (M - 1))
+                F += win * val * np.exp(1j * w[k] * j * dt) * dt
+            S[k] += w[k] * F.real
+    return S / R.shape[0]
+
+
+def test_autocorrelation_of_a_kicked_run_is_its_eigen_expansion():
+    """Field free after the kick: with b = V^T c(eps), RK4 gives
+    R(t_n) = sum_i |b_i|^2 R4(-i lambda_i dt)^n exactly."""
+    mol = small_mol(3, 4, 5, seed=12)
+    A = orc.build_A(mol, 0.2)
+    M = orc.build_M(*orc.dipole_along(mol, (0, 0, 1)))
+    tr = orc.propagate(A, M, orc.Pulse(kind=orc.KICK, E0=0.05), None, 0.05, 80, keep_every=1)
+    R = orc.autocorrelation(tr.c_history[0], tr.c_history)
+    lam, V = np.linalg.eigh(A)
+    b = V.T @ tr.c_history[0]
+    ref = np.array([np.sum(np.abs(b) ** 2 * rk4_R(-1j * lam * 0.05) ** n) for n in range(81)])
+    assert np.max(np.abs(R - ref)) < 1e-13
+
+
+def test_autocorr_spectrum_fft_equals_direct_sum():
+    rng = np.random.default_rng(4)
+    R = rng.standard_normal((2, 40)) + 1j * rng.standard_normal((2, 40))
+    R[:, 0] = 1.0
+    got = orc.spectrum_autocorr(R, 0.1, 25, 30, normalize=False)
+    ref = _direct_acf_spectrum(R, 0.1, 25, 30)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_autocorr_spectrum_peaks_at_state_energies_with_weights():
+    """R(t) = sum_i |b_i|^2 exp(-i E_i t) for a state b expanded in
+    eigenstates (exact for a stationary H): peaks at w = E_i on the grid,
+    heights proportional to E_i |b_i|^2 (the w prefactor of Eq.
+    fourier_transform), the Hann window's peak value being the same for
+    every line; the |0> line at w = 0 is removed by the w factor."""
+    dt, n, npad = 0.1, 3001, 50000
+    grid = orc.autocorr_grid(n, dt, npad, 4000)
+    E = np.array([grid[700], grid[1500]])
+    wts = np.array([0.3, 0.1])
+    t = dt * np.arange(n)
+    R = 0.6 + (wts[:, None] * np.exp(-1j * E[:, None] * t)).sum(axis=0)
+    S = orc.spectrum_autocorr(R, dt, npad, 4000, normalize=False)
+    peaks = [int(np.argmax(S[600:800])) + 600, int(np.argmax(S[1400:1600])) + 1400]
+    assert peaks == [700, 1500]
+    ratio = S[1500] / S[700]
+    assert abs(ratio / ((E[1] * wts[1]) / (E[0] * wts[0])) - 1.0) < 1e-3
+    assert abs(S[0]) < 1e-12
+    Sn = orc.spectrum_autocorr(R, dt, npad, 4000)
+    assert abs(np.max(Sn) - 1.0) < 1e-15
+
+
+# ---------------------------------------------------------------------------
 # Kick
 # ---------------------------------------------------------------------------
 
