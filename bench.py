@@ -395,6 +395,20 @@ def run_gpu(args):
     prop = rb.Propagator(mol, CX, args.prec, integrator=args.integrator)
     prop.set_field(pulses)
     h = prop.h
+    pop_info = None
+    if args.populations > 0:
+        # TI-TDA states by Davidson on the library's sigma (set-up, timed
+        # apart), then their overlaps recorded at every timed step
+        t0 = time.perf_counter()
+        w_st, X_st, it_st = prop.eigenstates(args.populations, tol=1e-5, max_iter=300)
+        pop_info = {"states": args.populations, "eigensolver_s": time.perf_counter() - t0,
+                    "davidson_iterations": it_st, "lowest_excitation_ha": float(w_st[0]),
+                    "recorded": "overlaps with every state at every step, inside the timed region"}
+        prop.set_projectors(X_st)
+        if args.autocorrelation:
+            pop_info["autocorrelation"] = "recorded at every step, inside the timed region"
+    if args.autocorrelation:
+        rb.rttda_set_autocorrelation(h, True)
     dev = torch.device("cuda", local)
     c_out = torch.zeros((T, NDIM, 2), dtype=torch.float64, device=dev)
     dip = torch.zeros((T, K + 1), dtype=torch.float64, device=dev)
@@ -517,6 +531,10 @@ def run_gpu(args):
 
     dtype = {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "bf16x2": "bf16x2"}[args.prec]
     cfg = base_config(args.prec, world, T)
+    if pop_info:
+        cfg["populations"] = pop_info
+    elif args.autocorrelation:
+        cfg["autocorrelation"] = "recorded at every step, inside the timed region"
     cfg["integrator"] = {"rk4": "classical RK4 (4 sigma builds per step)",
                          "sso": "symplectic split operator (2 sigma builds per step)"}[args.integrator]
     cfg.update(wl_info)
@@ -640,6 +658,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="absorption", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="bf16x2", choices=["fp64", "fp32", "bf16", "bf16x3", "bf16x2"])
+    ap.add_argument("--populations", type=int, default=0,
+                    help="record overlaps with this many TI-TDA states (Davidson) at every step")
+    ap.add_argument("--autocorrelation", action="store_true", help="record R(t) at every step")
     ap.add_argument("--integrator", default="rk4", choices=["rk4", "sso"],
                     help="time integrator of the timed propagation (the plain FP64 comparison path uses the same)")
     ap.add_argument("--accuracy", type=int, default=0,
