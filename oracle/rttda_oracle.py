@@ -323,8 +323,9 @@ def propagate(A, M, p: Pulse, c0, dt: float, nsteps: int, keep_every: int = 0) -
 # With c = q + i p (Eq. x_real_imagiary) and a real symmetric H(t), the
 # equation of motion i dc/dt = H(t) c is the pair dq/dt = H p, dp/dt = -H q
 # (Sec. 2.2).  The second-order symmetric splitting takes half a step of the
-# p-flow, a whole step of the q-flow and again half a step of the p-flow,
-# each with H at the middle of its own time interval's end points:
+# p-flow, a whole step of the q-flow and again half a step of the p-flow;
+# with t treated as a coordinate, the p half steps use H at the two ends of
+# the step and the q step uses H at its middle:
 #     p_{n+1/2} = p_n       - (dt/2) H(t_n)       q_n
 #     q_{n+1}   = q_n       +  dt    H(t_n + dt/2) p_{n+1/2}
 #     p_{n+1}   = p_{n+1/2} - (dt/2) H(t_n + dt)  q_{n+1}
