@@ -295,7 +295,7 @@ namespace {
 // --- tensor-core exchange -------------------------------------------------
 // Z = B_oo c (K = nocc, short): pipeline stages with hi/lo Z staging (two
 // planes) or one-plane staging
-constexpr int kZBN = 256, kZStages2 = 2, kZStages1 = 3;
+constexpr int kZBN = 256, kZStages2 = 2, kZStages1 = 2;
 
 // Persistent launch: one CTA per SM (or per tile if fewer tiles).
 template <int BN, int ST, int BM, int EP>

@@ -274,20 +274,27 @@ __device__ __forceinline__ void split_pack(float x0, float x1, uint32_t& hi, uin
   lo = pack_bf16x2(x0 - h0, x1 - h1);
 }
 
-template <int BN>
+template <int BN, int NA = 1>
 struct Cfg {
   static constexpr int kBBytes = BN * 128;
-  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kStageBytes = NA * kABytes + kBBytes;  // NA A planes + one B plane
   static constexpr uint32_t kAccCols = 256;   // column offset of accumulator buffer 1
   static constexpr uint32_t kTmemCols = 512;  // two accumulator buffers
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M=128 must be a multiple of 16 in [16, 256]");
   static_assert(kStageBytes % 1024 == 0, "stage must keep 1024-byte alignment");
 };
 
+// EPI_ZONE stages hold both A planes and the B plane of one K tile (all
+// products of the tile from one stage); the other kinds one plane each.
+template <int EPI>
+constexpr int stage_a_planes() {
+  return EPI == 2 ? 2 : 1;
+}
+
 template <int BN, int STAGES, int EPI = 0>
 constexpr size_t smem_bytes() {
-  return (size_t)STAGES * Cfg<BN>::kStageBytes + 1024 /*alignment slack*/ + 256 /*barriers*/ +
-         (size_t)kEpiWarps * zstage_bytes_per_warp<EPI>();
+  return (size_t)STAGES * Cfg<BN, stage_a_planes<EPI>()>::kStageBytes + 1024 /*alignment slack*/ +
+         256 /*barriers*/ + (size_t)kEpiWarps * zstage_bytes_per_warp<EPI>();
 }
 
 // Tile t -> (split, m tile, n tile), n fastest so that consecutive tiles of a
@@ -312,7 +319,11 @@ template <int BN, int STAGES, int BMODE, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmZ, const Params p) {
-  using CF = Cfg<BN>;
+  // MERGED: a stage holds A hi, A lo and B hi of one K tile and the MMA warp
+  // issues every product of the tile from it (products (hi,hi), (lo,hi),
+  // i.e. nprod <= 2 with alo); otherwise one stage per product
+  constexpr bool MERGED = EPI == EPI_ZONE;
+  using CF = Cfg<BN, stage_a_planes<EPI>()>;
   constexpr int kStgWarp = zstage_bytes_per_warp<EPI>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -355,13 +366,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         const TileCoord tc = tile_coord(t, tiles_n, tiles_m, BN);
         const int kr0 = tc.split * p.kt_per_split;
         const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
-        const int niter = max(0, kr1 - kr0) * p.nprod;
+        const int niter = max(0, kr1 - kr0) * (MERGED ? 1 : p.nprod);
         for (int j = 0; j < niter; ++j, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, p.err, ERR_WAIT_EMPTY)) {
             alive = false;
             break;
+          }
+          if (MERGED) {
+            const int kr = kr0 + j, na = p.nprod >= 2 ? 2 : 1;
+            uint8_t* st = smem + s * CF::kStageBytes;
+            mbar_expect_tx(&full[s], (uint32_t)(na * kABytes + CF::kBBytes));
+            for (int a = 0; a < na; ++a) tma_load_3d(st + a * kABytes, &tmA, &full[s], kr * kBK, tc.m0, a);
+            tma_load_3d(st + 2 * kABytes, &tmB, &full[s], kr * kBK, tc.n0, 0);
+            continue;
           }
           const int kr = kr0 + j / p.nprod, pr = j % p.nprod;
           // operand planes of product pr: (hi,hi), (hi,lo), (lo,hi); with
@@ -394,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const TileCoord tc = tile_coord(t, tiles_n, tiles_m, BN);
         const int kr0 = tc.split * p.kt_per_split;
         const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
-        const int niter = max(0, kr1 - kr0) * p.nprod;
+        const int niter = max(0, kr1 - kr0) * (MERGED ? 1 : p.nprod);
         const int buf = tcount & 1;
         const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
         if (!mbar_wait(&acce[buf], aph ^ 1u, p.err, ERR_WAIT_ACC)) break;
@@ -409,11 +428,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t aaddr = smem_u32(smem + s * CF::kStageBytes);
-          const uint64_t adesc = sdesc_sw128(aaddr);
-          const uint64_t bdesc = sdesc_sw128(aaddr + kABytes);
+          if (MERGED) {
+            const uint64_t bdesc = sdesc_sw128(aaddr + 2 * kABytes);
+            for (int pr = 0; pr < p.nprod; ++pr) {
+              const uint64_t adesc = sdesc_sw128(aaddr + pr * kABytes);
 #pragma unroll
-          for (int k = 0; k < kBK / 16; ++k)  // 16 BF16 = 32 bytes per MMA along K
-            mma_bf16(dcol, adesc + 2 * k, bdesc + 2 * k, idesc, (j > 0 || k > 0) ? 1u : 0u);
+              for (int k = 0; k < kBK / 16; ++k)
+                mma_bf16(dcol, adesc + 2 * k, bdesc + 2 * k, idesc, (j > 0 || pr > 0 || k > 0) ? 1u : 0u);
+            }
+          } else {
+            const uint64_t adesc = sdesc_sw128(aaddr);
+            const uint64_t bdesc = sdesc_sw128(aaddr + kABytes);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)  // 16 BF16 = 32 bytes per MMA along K
+              mma_bf16(dcol, adesc + 2 * k, bdesc + 2 * k, idesc, (j > 0 || k > 0) ? 1u : 0u);
+          }
           mma_commit(&empty[s]);
         }
         mma_commit(&accf[buf]);
