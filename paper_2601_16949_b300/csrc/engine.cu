@@ -543,6 +543,20 @@ void coul_stream_attr() {
   coul_stream_attr_c<TF, 12>();
 }
 
+// F = M_d X (singles rows): the register-tiled kernel when its 32 x 64
+// tiles give at least one block per SM, else one output per thread.
+template <typename TM_, typename TC>
+void launch_field(rttda_ctx* h, const double* X, const TM_* moo, const TM_* mvv, const TM_* m0, cudaStream_t s) {
+  const long long tiled = cdiv(h->v, 64) * cdiv(h->o, 32) * (long long)h->T;
+  if (tiled >= kNumSM) {
+    dim3 g((unsigned)cdiv(h->v, 64), (unsigned)cdiv(h->o, 32), h->T);
+    k_field<TM_, TC><<<g, dim3(16, 16), 0, s>>>(h->o, h->v, h->T, X, moo, mvv, m0, h->F);
+  } else {
+    dim3 g((unsigned)cdiv(h->v, 32), (unsigned)cdiv(h->o, 8), h->T);
+    k_field_small<TM_, TC><<<g, dim3(32, 8), 0, s>>>(h->o, h->v, h->T, X, moo, mvv, m0, h->F);
+  }
+}
+
 template <typename TF, typename TC, bool XTC>
 struct Ops {
   using TL = Tile<TC>;
@@ -619,13 +633,11 @@ struct Ops {
   static void field(rttda_ctx* h, const double* X, cudaStream_t s) {
     Prof pr(h, RTTDA_KC_FIELD, s);
     h->launches += 2;
-    dim3 g(blocks_for(h->v, 32), blocks_for(h->o, 8), h->T);
     if (std::is_same<TC, double>::value) {
-      k_field<double, double><<<g, dim3(32, 8), 0, s>>>(h->o, h->v, h->T, X, h->moo64, h->mvv64, h->m064, h->F);
+      launch_field<double, double>(h, X, h->moo64, h->mvv64, h->m064, s);
       k_field0<double, double><<<h->T, 256, 0, s>>>(h->ov, h->T, X, h->m064, h->F);
     } else {
-      k_field<TC, TC><<<g, dim3(32, 8), 0, s>>>(h->o, h->v, h->T, X, (const TC*)h->mooC, (const TC*)h->mvvC,
-                                                (const TC*)h->m0C, h->F);
+      launch_field<TC, TC>(h, X, (const TC*)h->mooC, (const TC*)h->mvvC, (const TC*)h->m0C, s);
       k_field0<TC, TC><<<h->T, 256, 0, s>>>(h->ov, h->T, X, (const TC*)h->m0C, h->F);
     }
   }
@@ -677,9 +689,7 @@ void enqueue_kick(rttda_ctx* h, cudaStream_t s) {
   const long long NT = h->N * h->T;
   cudaMemcpyAsync(h->term, h->Xn, sizeof(double) * NT * 2, cudaMemcpyDeviceToDevice, s);
   for (int k = 1; k <= h->kick_terms; ++k) {
-    dim3 g(blocks_for(h->v, 32), blocks_for(h->o, 8), h->T);
-    k_field<double, double><<<g, dim3(32, 8), 0, s>>>(h->o, h->v, h->T, h->term, h->moo64, h->mvv64, h->m064,
-                                                      h->F);
+    launch_field<double, double>(h, h->term, h->moo64, h->mvv64, h->m064, s);
     k_field0<double, double><<<h->T, 256, 0, s>>>(h->ov, h->T, h->term, h->m064, h->F);
     k_kick_term<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->d_kappa, 1.0 / k, h->F, h->term, h->Xn);
   }

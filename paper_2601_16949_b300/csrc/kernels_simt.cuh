@@ -436,10 +436,125 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 // Field product F = M_d X for every trajectory (Slater-Condon rules, Eqs.
 // sc2-sc5), singles rows:
 //   F_ia = m_ia X_0 + sum_b mu_ab X_ib - sum_j mu_ji X_ja
-// grid (ceil(v/32), ceil(o/8), T), block (32, 8): thread (a, i).
+// Two small GEMMs per trajectory (X mu_vv and mu_oo^T X, real and imaginary
+// parts together) with register tiles: a block computes 32 i x 64 a (both
+// parts), thread (tx, ty) of 16 x 16 the rows i0 + ty + 16 r (r < 2) and
+// columns a0 + tx + 16 c (c < 4), i.e. 16 accumulators, from operand tiles
+// of 16 along K staged in shared memory (amplitudes converted to TC once per
+// block and K tile).  grid (ceil(v/64), ceil(o/32), T), block (16, 16).
 // ---------------------------------------------------------------------------
 template <typename TM_, typename TC>
 __global__ void __launch_bounds__(256) k_field(int o, int v, int T, const double* __restrict__ X,
+                                               const TM_* __restrict__ moo, const TM_* __restrict__ mvv,
+                                               const TM_* __restrict__ m0, double* __restrict__ F) {
+  constexpr int BI = 32, BA = 64, BK = 16;
+  __shared__ TC xi[2][BK][BI + 1];   // X[i0+ii][k0+kk] (re, im): A operand of X mu_vv
+  __shared__ TC mv[BK][BA];          // mu_vv[k0+kk][a0+aa]
+  __shared__ TC mo[BK][BI + 1];      // mu_oo[k0+kk][i0+ii]: A operand of mu_oo^T X
+  __shared__ TC xa[2][BK][BA];       // X[k0+kk][a0+aa] (re, im)
+  const int C = 2 * T;
+  const int t = blockIdx.z;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
+  const int a0 = blockIdx.x * BA, i0 = blockIdx.y * BI;
+  const TM_* Mv = mvv + (size_t)t * v * v;
+  const TM_* Mo = moo + (size_t)t * o * o;
+  const TM_* Mz = m0 + (size_t)t * o * v;
+  const double* Xt = X + 2 * t;
+  TC fr[2][4], fi[2][4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) fr[r][c] = fi[r][c] = TC(0);
+  // sum_b X_ib mu_ba
+  for (int k0 = 0; k0 < v; k0 += BK) {
+    for (int e = tid; e < BI * BK; e += 256) {
+      const int ii = e / BK, kk = e % BK;
+      const bool ok = (i0 + ii < o) && (k0 + kk < v);
+      const size_t row = 1 + (size_t)(i0 + ii) * v + k0 + kk;
+      xi[0][kk][ii] = ok ? (TC)Xt[row * C] : TC(0);
+      xi[1][kk][ii] = ok ? (TC)Xt[row * C + 1] : TC(0);
+    }
+    for (int e = tid; e < BK * BA; e += 256) {
+      const int kk = e / BA, aa = e % BA;
+      mv[kk][aa] = (k0 + kk < v && a0 + aa < v) ? cvt<TC>(Mv[(size_t)(k0 + kk) * v + a0 + aa]) : TC(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TC ar[2], ai[2], b[4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        ar[r] = xi[0][kk][ty + 16 * r];
+        ai[r] = xi[1][kk][ty + 16 * r];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = mv[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          fr[r][c] = fma(ar[r], b[c], fr[r][c]);
+          fi[r][c] = fma(ai[r], b[c], fi[r][c]);
+        }
+    }
+    __syncthreads();
+  }
+  // - sum_j mu_ji X_ja
+  for (int k0 = 0; k0 < o; k0 += BK) {
+    for (int e = tid; e < BK * BI; e += 256) {
+      const int kk = e / BI, ii = e % BI;
+      mo[kk][ii] = (k0 + kk < o && i0 + ii < o) ? cvt<TC>(Mo[(size_t)(k0 + kk) * o + i0 + ii]) : TC(0);
+    }
+    for (int e = tid; e < BK * BA; e += 256) {
+      const int kk = e / BA, aa = e % BA;
+      const bool ok = (k0 + kk < o) && (a0 + aa < v);
+      const size_t row = 1 + (size_t)(k0 + kk) * v + a0 + aa;
+      xa[0][kk][aa] = ok ? (TC)Xt[row * C] : TC(0);
+      xa[1][kk][aa] = ok ? (TC)Xt[row * C + 1] : TC(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TC m[2], br[4], bi[4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) m[r] = mo[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        br[c] = xa[0][kk][tx + 16 * c];
+        bi[c] = xa[1][kk][tx + 16 * c];
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          fr[r][c] = fma(-m[r], br[c], fr[r][c]);
+          fi[r][c] = fma(-m[r], bi[c], fi[r][c]);
+        }
+    }
+    __syncthreads();
+  }
+  const TC x0r = (TC)Xt[0], x0i = (TC)Xt[1];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int i = i0 + ty + 16 * r;
+    if (i >= o) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int a = a0 + tx + 16 * c;
+      if (a >= v) continue;
+      const TC mz = cvt<TC>(Mz[(size_t)i * v + a]);
+      const size_t row = 1 + (size_t)i * v + a;
+      F[row * C + 2 * t] = (double)fma(mz, x0r, fr[r][c]);
+      F[row * C + 2 * t + 1] = (double)fma(mz, x0i, fi[r][c]);
+    }
+  }
+}
+
+// The same product with one output per thread, for batches too small to give
+// the register-tiled kernel enough blocks: grid (ceil(v/32), ceil(o/8), T),
+// block (32, 8): thread (a, i).
+template <typename TM_, typename TC>
+__global__ void __launch_bounds__(256) k_field_small(int o, int v, int T, const double* __restrict__ X,
                                                const TM_* __restrict__ moo, const TM_* __restrict__ mvv,
                                                const TM_* __restrict__ m0, double* __restrict__ F) {
   __shared__ TC sx[8][32][2];    // X[i0+ii][b0+bb]

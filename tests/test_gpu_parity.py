@@ -4,7 +4,7 @@ import pytest
 
 from oracle import rttda_oracle as orc
 from paper_2601_16949_b300 import synth
-from tests._util import oracle_runs, oracle_sigma, to_ri, unit
+from tests._util import oracle_pulse, oracle_runs, oracle_sigma, to_ri, unit
 
 pytestmark = pytest.mark.gpu
 
@@ -225,4 +225,25 @@ def test_coulomb_matches_oracle(rb, prec, tol, shape, T):
         ref = A @ c[k]
         scale = np.abs(A) @ np.abs(c[k])
         assert np.max(np.abs(got[k] - ref) / np.maximum(scale, 1e-300)) < tol, (prec, shape, T, k)
+    prop.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 3e-6)])
+def test_field_product_on_the_register_tiled_kernel(rb, prec, tol):
+    """150 trajectories of an o=32, v=64 molecule: enough 32 x 64 field tiles
+    for the register-tiled field kernel (the small batches above take the
+    one-output-per-thread kernel).  Four pulse shapes and directions in turn."""
+    mol = synth.molecule(32, 64, 8, seed=13)
+    pulses = [PULSES4[k % 4] for k in range(150)]
+    prop = rb.Propagator(mol, 0.2, prec)
+    prop.set_field(pulses)
+    c = synth.random_state(prop.n, len(pulses), seed=9)
+    got = _sigma_gpu(rb, prop, c, 1.7)
+    A = orc.build_A(mol, 0.2)
+    Ms = [orc.build_M(*orc.dipole_along(mol, unit(p["direction"]))) for p in PULSES4]
+    for k in range(len(pulses)):
+        E = orc.field(oracle_pulse(pulses[k]), 1.7)
+        ref = A @ c[k] - E * (Ms[k % 4] @ c[k])
+        scale = np.abs(A) @ np.abs(c[k]) + abs(E) * (np.abs(Ms[k % 4]) @ np.abs(c[k]))
+        assert np.max(np.abs(got[k] - ref) / np.maximum(scale, 1e-300)) < tol, (prec, k)
     prop.close()
