@@ -137,6 +137,7 @@ struct rttda_ctx {
   bool coul_vec = false;
   bool coul_stream = false;  // Coulomb on the FP32 streaming kernels (FP32 / BF16 factors, 2T <= 12)
   float* Xf = nullptr;       // [ov][C] FP32 amplitudes of the stage (streaming Coulomb)
+  double* f0_part = nullptr; // [T][chunks][2] ground-row field partial sums
   long long obs_rows = 1;
   size_t dev_bytes = 0;
 
@@ -230,7 +231,7 @@ rttda_ctx::~rttda_ctx() {
 
 void rttda_ctx::free_batch() {
   void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xn, Xs, Xs2, acc, F, E, term,
-                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk, Xc, Wt, wpart_tc, Xf};
+                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk, Xc, Wt, wpart_tc, Xf, f0_part};
   for (void* p : ps) dfree(p);
   d_pulses = nullptr;
   d_kappa = d_dirs = moo64 = mvv64 = m064 = nullptr;
@@ -242,6 +243,7 @@ void rttda_ctx::free_batch() {
   Xc = Wt = nullptr;
   wpart_tc = nullptr;
   Xf = nullptr;
+  f0_part = nullptr;
   coul_tc = false;
   coul_stream = false;
   tmZA.clear();
@@ -543,6 +545,8 @@ void coul_stream_attr() {
   coul_stream_attr_c<TF, 12>();
 }
 
+constexpr int kF0Chunks = 64;  // most chunks of the ground-row field sum
+
 // F = M_d X (singles rows): the register-tiled kernel when its 32 x 64
 // tiles give at least one block per SM, else one output per thread.
 template <typename TM_, typename TC>
@@ -555,6 +559,15 @@ void launch_field(rttda_ctx* h, const double* X, const TM_* moo, const TM_* mvv,
     dim3 g((unsigned)cdiv(h->v, 32), (unsigned)cdiv(h->o, 8), h->T);
     k_field_small<TM_, TC><<<g, dim3(32, 8), 0, s>>>(h->o, h->v, h->T, X, moo, mvv, m0, h->F);
   }
+}
+
+// F_0 = sum_ia m_ia X_ia per trajectory: chunk sums, then their ordered sum.
+template <typename TM_, typename TC>
+void launch_field0(rttda_ctx* h, const double* X, const TM_* m0, cudaStream_t s) {
+  const long long rows = std::max<long long>(2048, cdiv(h->ov, kF0Chunks));
+  const int G = (int)cdiv(h->ov, rows);
+  k_field0<TM_, TC><<<dim3(G, h->T), 256, 0, s>>>(h->ov, h->T, rows, X, m0, h->f0_part);
+  k_field0_final<<<1, 64, 0, s>>>(G, h->T, h->f0_part, h->F);
 }
 
 template <typename TF, typename TC, bool XTC>
@@ -632,13 +645,13 @@ struct Ops {
 
   static void field(rttda_ctx* h, const double* X, cudaStream_t s) {
     Prof pr(h, RTTDA_KC_FIELD, s);
-    h->launches += 2;
+    h->launches += 3;  // M_d X rows, ground-row chunks, their sum
     if (std::is_same<TC, double>::value) {
       launch_field<double, double>(h, X, h->moo64, h->mvv64, h->m064, s);
-      k_field0<double, double><<<h->T, 256, 0, s>>>(h->ov, h->T, X, h->m064, h->F);
+      launch_field0<double, double>(h, X, h->m064, s);
     } else {
       launch_field<TC, TC>(h, X, (const TC*)h->mooC, (const TC*)h->mvvC, (const TC*)h->m0C, s);
-      k_field0<TC, TC><<<h->T, 256, 0, s>>>(h->ov, h->T, X, (const TC*)h->m0C, h->F);
+      launch_field0<TC, TC>(h, X, (const TC*)h->m0C, s);
     }
   }
 
@@ -685,12 +698,12 @@ void dispatch(int prec, F&& f) {
 // Exact kick exp(+i kappa M_d) on h->Xn (FP64 field products).
 void enqueue_kick(rttda_ctx* h, cudaStream_t s) {
   Prof pr(h, RTTDA_KC_KICK, s);
-  h->launches += 3 * h->kick_terms;
+  h->launches += 4 * h->kick_terms;
   const long long NT = h->N * h->T;
   cudaMemcpyAsync(h->term, h->Xn, sizeof(double) * NT * 2, cudaMemcpyDeviceToDevice, s);
   for (int k = 1; k <= h->kick_terms; ++k) {
     launch_field<double, double>(h, h->term, h->moo64, h->mvv64, h->m064, s);
-    k_field0<double, double><<<h->T, 256, 0, s>>>(h->ov, h->T, h->term, h->m064, h->F);
+    launch_field0<double, double>(h, h->term, h->m064, s);
     k_kick_term<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->d_kappa, 1.0 / k, h->F, h->term, h->Xn);
   }
 }
@@ -1352,6 +1365,7 @@ rttda_status rttda_ctx::alloc_batch() {
   obs_rows = cdiv(N, obsG);
   obsG = (int)cdiv(N, obs_rows);
   CKS(dalloc(&obs_part, (size_t)obsG * T * 2));
+  CKS(dalloc(&f0_part, (size_t)kF0Chunks * T * 2));
   return RTTDA_OK;
 }
 

@@ -624,15 +624,18 @@ __global__ void __launch_bounds__(256) k_field_small(int o, int v, int T, const 
 }
 
 // Ground row of the field product: F_0 = sum_ia m_ia X_ia (Hermitian
-// partner of sc2).  One block per trajectory, fixed-order reduction.
+// partner of sc2).  Two passes with a fixed order: block (g, t) sums the
+// rows of chunk g (part[(t G + g) 2 + re/im], accumulated in TC), then one
+// block adds the G chunk sums of every trajectory in order.
 template <typename TM_, typename TC>
-__global__ void __launch_bounds__(256) k_field0(long long ov, int T, const double* __restrict__ X,
-                                                const TM_* __restrict__ m0, double* __restrict__ F) {
+__global__ void __launch_bounds__(256) k_field0(long long ov, int T, long long rows, const double* __restrict__ X,
+                                                const TM_* __restrict__ m0, double* __restrict__ part) {
   __shared__ TC red[32];
-  const int C = 2 * T, t = blockIdx.x;
+  const int C = 2 * T, g = blockIdx.x, t = blockIdx.y, G = gridDim.x;
   const TM_* Mz = m0 + (size_t)t * ov;
+  const long long i0 = (long long)g * rows, i1 = min(ov, i0 + rows);
   TC sr = 0, si = 0;
-  for (long long ia = threadIdx.x; ia < ov; ia += blockDim.x) {
+  for (long long ia = i0 + threadIdx.x; ia < i1; ia += blockDim.x) {
     const TC m = cvt<TC>(Mz[ia]);
     sr = fma(m, (TC)X[(1 + ia) * C + 2 * t], sr);
     si = fma(m, (TC)X[(1 + ia) * C + 2 * t + 1], si);
@@ -640,8 +643,17 @@ __global__ void __launch_bounds__(256) k_field0(long long ov, int T, const doubl
   sr = block_sum(sr, red);
   si = block_sum(si, red);
   if (threadIdx.x == 0) {
-    F[2 * t] = (double)sr;
-    F[2 * t + 1] = (double)si;
+    part[((size_t)t * G + g) * 2] = (double)sr;
+    part[((size_t)t * G + g) * 2 + 1] = (double)si;
+  }
+}
+
+__global__ void k_field0_final(int G, int T, const double* __restrict__ part, double* __restrict__ F) {
+  for (int e = threadIdx.x; e < 2 * T; e += blockDim.x) {
+    const int t = e >> 1, r = e & 1;
+    double sum = 0.0;
+    for (int g = 0; g < G; ++g) sum += part[((size_t)t * G + g) * 2 + r];
+    F[2 * t + r] = sum;
   }
 }
 
