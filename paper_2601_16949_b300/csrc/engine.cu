@@ -62,16 +62,39 @@ template <typename TC> struct Tile;
 template <> struct Tile<double> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
 template <> struct Tile<float> { static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8; };
 
-template <typename T>
-rttda_status dalloc(T** p, size_t count) {
+// A handle's device buffers are allocated and freed in stream order on the
+// handle's stream (CUDA's memory pool) while a function of that handle runs:
+// creating, re-batching or destroying one handle then never waits for the
+// work of other handles on the device, as cudaMalloc / cudaFree can.
+thread_local cudaStream_t g_alloc_stream = nullptr;
+
+struct AllocStream {
+  cudaStream_t prev;
+  explicit AllocStream(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+  ~AllocStream() { g_alloc_stream = prev; }
+};
+
+rttda_status dalloc_bytes(void** p, size_t bytes) {
   *p = nullptr;
-  if (count == 0) count = 1;
-  CK(cudaMalloc((void**)p, count * sizeof(T)));
+  if (bytes == 0) bytes = 1;
+  if (g_alloc_stream)
+    CK(cudaMallocAsync(p, bytes, g_alloc_stream));
+  else
+    CK(cudaMalloc(p, bytes));
   return RTTDA_OK;
 }
 
+template <typename T>
+rttda_status dalloc(T** p, size_t count) {
+  return dalloc_bytes((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
 void dfree(void* p) {
-  if (p) cudaFree(p);
+  if (!p) return;
+  if (g_alloc_stream)
+    cudaFreeAsync(p, g_alloc_stream);
+  else
+    cudaFree(p);
 }
 
 double fro(const double* a, size_t n) {
@@ -204,6 +227,7 @@ struct rttda_ctx {
 
 rttda_ctx::~rttda_ctx() {
   if (stream) cudaStreamSynchronize(stream);
+  AllocStream as(stream);
   for (auto& v : prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
   free_batch();
@@ -226,7 +250,10 @@ rttda_ctx::~rttda_ctx() {
   dfree(d_xeps);
   dfree(d_acf);
   dfree(d_acf_part);
-  if (stream) cudaStreamDestroy(stream);
+  if (stream) {
+    cudaStreamSynchronize(stream);
+    cudaStreamDestroy(stream);
+  }
 }
 
 void rttda_ctx::free_batch() {
@@ -936,11 +963,11 @@ static rttda_status alloc_coul_tc(rttda_ctx* h, int C) {
   h->SKc2 = choose_splits(cdiv(ov, tc::kBM) * cdiv(C, 64), cdiv(P, tc::kBK));
   CKS(dalloc(&h->wpart_tc, (size_t)h->SKc1 * P * C));
   char* p = nullptr;
-  CK(cudaMalloc((void**)&p, (size_t)h->SKc2 * ov * C * sizeof(float)));
+  CKS(dalloc_bytes((void**)&p, (size_t)h->SKc2 * ov * C * sizeof(float)));
   h->Jpart = p;
   h->SJ = h->SKc2;
   h->SW = 1;
-  CK(cudaMalloc((void**)&p, sizeof(float)));  // pass-1 SIMT scratch is unused here
+  CKS(dalloc_bytes((void**)&p, sizeof(float)));  // pass-1 SIMT scratch is unused here
   h->w = p;
   {
     const uint64_t dims[3] = {(uint64_t)ov, (uint64_t)P, np};
@@ -1113,10 +1140,10 @@ static rttda_status tune_wide(rttda_ctx* h, int C, WidePlan& out) {
   int maxsk = 1;
   for (auto& c : cands) maxsk = std::max(maxsk, c.w.sk);
   float* part = nullptr;
-  CK(cudaMalloc((void**)&part, (size_t)maxsk * M * v * sizeof(float)));
+  CKS(dalloc_bytes((void**)&part, (size_t)maxsk * M * v * sizeof(float)));
   struct Free {
     float* p;
-    ~Free() { cudaFree(p); }
+    ~Free() { dfree(p); }
   } fr{part};
   k_fill_hash_bf16<<<4 * kNumSM, 256, 0, h->stream>>>((long long)(h->zplane * h->zplanes), 0.05f, h->Zk);
   std::vector<CUtensorMap> ma(cands.size()), mb(cands.size());
@@ -1217,7 +1244,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   h->plan.main_splits = h->SK;
   h->plan.z_chunk = h->zchunk;
   char* p = nullptr;
-  CK(cudaMalloc((void**)&p, (size_t)h->SK * C * o * v * sizeof(float)));
+  CKS(dalloc_bytes((void**)&p, (size_t)h->SK * C * o * v * sizeof(float)));
   h->Kpart = p;
   // maps
   {
@@ -1337,9 +1364,9 @@ rttda_status rttda_ctx::alloc_batch() {
     }
     if (coul_stream) CKS(dalloc(&Xf, (size_t)ov * C));
     char* p = nullptr;
-    CK(cudaMalloc((void**)&p, (size_t)SW * P * C * cbytes));
+    CKS(dalloc_bytes((void**)&p, (size_t)SW * P * C * cbytes));
     w = p;
-    CK(cudaMalloc((void**)&p, (size_t)SJ * ov * C * cbytes));
+    CKS(dalloc_bytes((void**)&p, (size_t)SJ * ov * C * cbytes));
     Jpart = p;
   }
   // exchange scratch: Z for a chunk of P (bounded size), split-K partials
@@ -1348,7 +1375,7 @@ rttda_status rttda_ctx::alloc_batch() {
     const size_t zbudget = (size_t)1 << 30;
     zchunk = (int)std::max<size_t>(1, std::min<size_t>(P, zbudget / std::max<size_t>(zper, 1)));
     char* p = nullptr;
-    CK(cudaMalloc((void**)&p, (size_t)zchunk * zper));
+    CKS(dalloc_bytes((void**)&p, (size_t)zchunk * zper));
     Zt = p;
     const int BM = prec == RTTDA_FP64 ? Tile<double>::BM : Tile<float>::BM;
     const int BN = prec == RTTDA_FP64 ? Tile<double>::BN : Tile<float>::BN;
@@ -1356,7 +1383,7 @@ rttda_status rttda_ctx::alloc_batch() {
     const long long tiles = cdiv((long long)C * o, BM) * cdiv(v, BN);
     const long long kchunks = cdiv((long long)zchunk * v, BK);
     SK = (int)std::max(1LL, std::min(kchunks, cdiv(4 * kNumSM, tiles)));
-    CK(cudaMalloc((void**)&p, (size_t)SK * C * o * v * cbytes));
+    CKS(dalloc_bytes((void**)&p, (size_t)SK * C * o * v * cbytes));
     Kpart = p;
   } else {
     CKS(alloc_tc(C));
@@ -1374,6 +1401,7 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
                                 const double* B_oo, const double* B_vv, const double* mu_oo, const double* mu_vv,
                                 const double* mu_0ov) {
   CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  AllocStream as(h->stream);
   dispatch(h->prec, [&](auto ops) { decltype(ops)::set_smem_limits(); });
   const size_t o = h->o, v = h->v, P = h->P;
   const size_t chunk = (size_t)1 << 26;  // elements per staging pass
@@ -1381,15 +1409,13 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
   double* stage = nullptr;
   struct Guard {
     double*& p;
-    ~Guard() {
-      if (p) cudaFree(p);
-    }
+    ~Guard() { dfree(p); }
   } guard{stage};
   if (h->prec != RTTDA_FP64) CKS(dalloc(&stage, std::max(stage_n, h->tc ? std::max(v * v, o * o) : (size_t)1)));
   CKS(dalloc(&h->d_err, 1));
-  CK(cudaMemset(h->d_err, 0, sizeof(int)));
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   auto upload = [&](const double* src, size_t n, void** dst) -> rttda_status {
-    CK(cudaMalloc(dst, std::max<size_t>(n, 1) * h->fbytes));
+    CKS(dalloc_bytes((void**)dst, std::max<size_t>(n, 1) * h->fbytes));
     for (size_t off = 0; off < n; off += chunk) {
       const size_t m = std::min(chunk, n - off);
       if (h->fbytes == 8) {
@@ -1410,7 +1436,7 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
   // slab by slab of whole P
   auto pack = [&](const double* src, size_t slab, size_t out_slab, bool vv, __nv_bfloat16** dst) -> rttda_status {
     const size_t plane = P * out_slab;
-    CK(cudaMalloc((void**)dst, plane * h->nplanes * 2));
+    CKS(dalloc_bytes((void**)dst, plane * h->nplanes * 2));
     const size_t per = std::max<size_t>(1, chunk / std::max<size_t>(slab, 1));
     for (size_t p0 = 0; p0 < P; p0 += per) {
       const size_t pc = std::min(per, P - p0);
@@ -1428,7 +1454,7 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
     return RTTDA_OK;
   };
   auto upload64 = [&](const double* src, size_t n, double** dst) -> rttda_status {
-    CK(cudaMalloc((void**)dst, std::max<size_t>(n, 1) * 8));
+    CKS(dalloc_bytes((void**)dst, std::max<size_t>(n, 1) * 8));
     CK(cudaMemcpyAsync(*dst, src, n * 8, cudaMemcpyDefault, h->stream));
     return RTTDA_OK;
   };
@@ -1439,8 +1465,8 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
     if ((o * v) % 8 == 0 && P % 8 == 0) {
       // B_ov and its transpose as BF16 planes for batched Coulomb passes
       const size_t ov = o * v, plane = P * ov;
-      CK(cudaMalloc((void**)&h->Bov_tc, plane * h->nplanes * 2));
-      CK(cudaMalloc((void**)&h->BovT_tc, plane * h->nplanes * 2));
+      CKS(dalloc_bytes((void**)&h->Bov_tc, plane * h->nplanes * 2));
+      CKS(dalloc_bytes((void**)&h->BovT_tc, plane * h->nplanes * 2));
       const size_t per = std::max<size_t>(1, chunk / ov);
       for (size_t p0 = 0; p0 < P; p0 += per) {
         const size_t pc = std::min(per, P - p0);
@@ -1600,6 +1626,7 @@ rttda_status rttda_set_field(rttda_t h, const rttda_pulse* pulses, int ntraj) {
     if (K >= 400) return set_error(RTTDA_E_ARG, "rttda_set_field: kick too strong for the Taylor series");
   }
 
+  AllocStream as(h->stream);
   h->free_batch();
   h->T = ntraj;
   h->pulses.assign(pulses, pulses + ntraj);

@@ -87,8 +87,12 @@ struct rttda_server {
 
 // Free a request's device resources and record its final state.
 void rttda_server::release(Request* r, int final_state) {
+  // stream-ordered frees: releasing one request does not wait for the others
   if (r->h) {
-    cudaStreamSynchronize(rttda::handle_stream(r->h));
+    cudaStream_t hs = rttda::handle_stream(r->h);
+    if (r->dev) cudaFreeAsync(r->dev, hs);
+    r->dev = nullptr;
+    cudaStreamSynchronize(hs);
     rttda_destroy(r->h);
     r->h = nullptr;
   }
@@ -151,7 +155,8 @@ bool rttda_server::admit_one() {
   if (st == RTTDA_OK) st = rttda_set_field(r->h, &q.pulse, 1);
   if (st == RTTDA_OK) {
     const size_t n = 2 * (size_t)(q.nsteps + 1) + 2 * (size_t)q.nfreq;
-    if (cudaMalloc((void**)&r->dev, n * sizeof(double)) != cudaSuccess ||
+    cudaStream_t hs = rttda::handle_stream(r->h);
+    if (cudaMallocAsync((void**)&r->dev, n * sizeof(double), hs) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
       st = RTTDA_E_OOM;
   }
