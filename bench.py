@@ -113,8 +113,6 @@ def workload_pulses(rb, name, mol):
                      direction=(0.0, 0.0, 1.0))], {"E0_au": E0}
     return [dict(kind=rb.KICK, E0=KAPPA, direction=d) for d in DIRS], {}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 CUDA-core peak from unit counts: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz.
-FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 
 def dist_info():
