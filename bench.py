@@ -300,6 +300,8 @@ PREC_INFO = {  # factor bytes, exchange planes, tensor products per K tile
     "bf16": dict(fb=2, planes=1, nprod=1, tensor=True),
     "bf16x3": dict(fb=4, planes=2, nprod=3, tensor=True),
     "bf16x2": dict(fb=4, planes=2, nprod=2, tensor=True, zplanes=1),
+    # Ozaki digits: 6 BF16 digit planes per operand, 21 digit pairs per K tile
+    "fp64oz": dict(fb=8, planes=6, nprod=21, tensor=True, zplanes=6),
 }
 
 
@@ -328,6 +330,11 @@ def algorithmic_work(prec: str, cls: str, T: int):
         return pi["nprod"] * 2.0 * M * N * K, eb * (zp * M * K + pi["planes"] * P * v * v)
     if cls == "coulomb":
         return 2 * 2.0 * P * o * v * C, 2.0 * P * o * v * (pi["fb"] if prec != "bf16x3" else 4)
+    if cls == "exchange_z" and prec == "fp64oz":
+        # Z build into int64 Z (written, read back by the digit split) plus
+        # its 6 BF16 digits; digits of B_oo and of the amplitudes read once
+        nz = P * o * v * C
+        return pi["nprod"] * 2.0 * P * o * o * v * C, (8 + 8 + 2 * 6) * nz + 2 * 6 * (P * o * o + o * v * C)
     if cls == "exchange_z":
         eb = 2 if pi["tensor"] else pi["fb"]
         zp = pi.get("zplanes", pi["planes"])
@@ -540,7 +547,8 @@ def run_gpu(args):
         cb = time_oracle(mol, rows_occ, args.cpu_steps, warmup=1)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
-    dtype = {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "bf16x2": "bf16x2"}[args.prec]
+    dtype = {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "bf16x2": "bf16x2",
+             "fp64oz": "f64 (exchange: Ozaki BF16 digits)"}[args.prec]
     cfg = base_config(args.prec, world, T)
     if pop_info:
         cfg["populations"] = pop_info
@@ -668,7 +676,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="absorption", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="bf16x2", choices=["fp64", "fp32", "bf16", "bf16x3", "bf16x2"])
+    ap.add_argument("--prec", default="bf16x2", choices=["fp64", "fp32", "bf16", "bf16x3", "bf16x2", "fp64oz"])
     ap.add_argument("--populations", type=int, default=0,
                     help="record overlaps with this many TI-TDA states (Davidson) at every step")
     ap.add_argument("--autocorrelation", action="store_true", help="record R(t) at every step")

@@ -76,9 +76,20 @@ typedef enum {
  *           lo*hi accumulated in FP32 (about 16 significant bits per
  *           operand); Coulomb and field in FP32 on CUDA cores.
  *   BF16X2: as BF16X3 for the factors and for Z = B_oo c, but Z enters the
- *           main contraction as one BF16 plane: products Z*B_hi + Z*B_lo. */
+ *           main contraction as one BF16 plane: products Z*B_hi + Z*B_lo.
+ *   FP64_OZ: FP64-accurate exchange on tcgen05 tensor cores by the Ozaki
+ *           scheme (exponent-aligned slicing, Ozaki, Ogita, Oishi and Rump,
+ *           Numer. Algorithms 59, 2012): in blocks of at most 512 K
+ *           elements every operand row is written as 6 BF16 digits of 7
+ *           bits under a common power of two, digit products are summed per
+ *           weight without rounding in FP32 and joined in int64, and blocks
+ *           are added in FP64.  Z = B_oo c is exact up to the digits' 42
+ *           bits; relative error of the exchange about 2^-42 of the block
+ *           scales.  Coulomb and field in FP64 (CUDA cores).  Requires
+ *           nocc <= 512 (RTTDA_E_ARG otherwise). */
 typedef enum {
-  RTTDA_FP64 = 0, RTTDA_FP32 = 1, RTTDA_TF32 = 2, RTTDA_BF16 = 3, RTTDA_BF16X3 = 4, RTTDA_BF16X2 = 5
+  RTTDA_FP64 = 0, RTTDA_FP32 = 1, RTTDA_TF32 = 2, RTTDA_BF16 = 3, RTTDA_BF16X3 = 4, RTTDA_BF16X2 = 5,
+  RTTDA_FP64_OZ = 6
 } rttda_prec;
 
 /* Pulse shapes E(t) (Sec. 2.2, Eqs. delta_pulse, continuous wave,
@@ -325,6 +336,7 @@ rttda_status rttda_set_integrator(rttda_t h, int integrator);
  *   main_kernel 0: SIMT (FP64 / FP32),
  *               1: tcgen05, 128-row tiles (BF16X3),
  *               2: tcgen05, wide-M tiles of main_mb x 128 rows (BF16, BF16X2),
+ *               3: tcgen05, Ozaki digit pairs on 128 x 64 tiles (FP64_OZ),
  * with main_bn output columns per tile, K tiles of main_kb BF16 and
  * main_splits split-K partials; Z^P = B^P_oo c is built for z_chunk values
  * of P at a time.  coulomb_kernel 0: SIMT, 1: tcgen05.
@@ -334,6 +346,7 @@ rttda_status rttda_set_integrator(rttda_t h, int integrator);
  * from the tuning cache of this process or of the RTTDA_TUNE_CACHE file,
  * 3: named by the environment variable RTTDA_WIDE_PLAN="BN,MB,KB" (an
  * unknown candidate there makes rttda_set_field fail with RTTDA_E_ARG).
+ * RTTDA_ZCHUNK=n caps z_chunk at n values of P (all precisions).
  * Errors: RTTDA_E_ARG (NULL), RTTDA_E_STATE (no batch yet). */
 typedef struct {
   int prec, ntraj;

@@ -26,8 +26,9 @@ lib = ct.CDLL(LIB_PATH)
 OK, E_ARG, E_OOM, E_CUDA, E_TIMEOUT, E_STATE, E_BUSY = range(7)
 STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_OOM", 3: "E_CUDA", 4: "E_TIMEOUT", 5: "E_STATE", 6: "E_BUSY"}
 # precisions (rttda_prec)
-FP64, FP32, TF32, BF16, BF16X3, BF16X2 = 0, 1, 2, 3, 4, 5
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3, "bf16x2": BF16X2}
+FP64, FP32, TF32, BF16, BF16X3, BF16X2, FP64_OZ = 0, 1, 2, 3, 4, 5, 6
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3, "bf16x2": BF16X2,
+              "fp64oz": FP64_OZ}
 # pulse kinds (rttda_pulse_kind)
 KICK, CW, GAUSS_TL, CHIRP, SIN2 = 0, 1, 2, 3, 4
 

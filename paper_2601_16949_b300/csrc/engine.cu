@@ -21,6 +21,7 @@
 #include "engine_internal.h"
 #include "kernels_simt.cuh"
 #include "tc_gemm.cuh"
+#include "ozaki.cuh"
 #include "coul_stream.cuh"
 
 using namespace rttda;
@@ -207,6 +208,23 @@ struct rttda_ctx {
   bool coul_tc = false;
   int SKc1 = 1, SKc2 = 1;
   CUtensorMap tmC1A, tmC1B, tmC2A, tmC2B;
+  // FP64-accurate exchange by BF16 digits (FP64_OZ): factor digits (set up
+  // at create), per-batch digits of the amplitudes and of Z, and the maps
+  bool oz = false;
+  __nv_bfloat16* oz_boo = nullptr;  // [digit][P*o][op]
+  int* oz_eoo = nullptr;            // [P*o] block exponents
+  __nv_bfloat16* oz_bvv = nullptr;  // [digit][P][v][vp]
+  int* oz_evv = nullptr;            // [v][P*nbp]
+  int oz_nbp = 1;                   // exactness blocks per P along b
+  __nv_bfloat16* oz_x = nullptr;    // [digit][C*vp][op]
+  int* oz_ex = nullptr;             // [C*vp]
+  long long* oz_zi = nullptr;       // [zchunk*o][C*vp] integer Z of the Z build
+  __nv_bfloat16* oz_z = nullptr;    // [digit][(zchunk, vp/64)][C*o][64]
+  int* oz_ez = nullptr;             // [C*o][zchunk*nbp]
+  size_t oz_zplane = 0;
+  int oz_pps = 1;                   // P per split of the main contraction
+  CUtensorMap tmOzX;
+  std::vector<CUtensorMap> tmOzBoo, tmOzZ, tmOzBvv;
 
   // host staging for the host-buffer entry points
   double* h_io = nullptr;  // device staging [T][N][2] + traces
@@ -241,6 +259,10 @@ rttda_ctx::~rttda_ctx() {
   dfree(mu_0);
   dfree(Bvv_tc);
   dfree(Boo_tc);
+  dfree(oz_boo);
+  dfree(oz_eoo);
+  dfree(oz_bvv);
+  dfree(oz_evv);
   dfree(Bov_tc);
   dfree(BovT_tc);
   dfree(d_err);
@@ -258,7 +280,8 @@ rttda_ctx::~rttda_ctx() {
 
 void rttda_ctx::free_batch() {
   void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xn, Xs, Xs2, acc, F, E, term,
-                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk, Xc, Wt, wpart_tc, Xf, f0_part};
+                obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk, Xc, Wt, wpart_tc, Xf, f0_part,
+                oz_x, oz_ex, oz_zi, oz_z, oz_ez};
   for (void* p : ps) dfree(p);
   d_pulses = nullptr;
   d_kappa = d_dirs = moo64 = mvv64 = m064 = nullptr;
@@ -271,6 +294,14 @@ void rttda_ctx::free_batch() {
   wpart_tc = nullptr;
   Xf = nullptr;
   f0_part = nullptr;
+  oz_x = nullptr;
+  oz_ex = nullptr;
+  oz_zi = nullptr;
+  oz_z = nullptr;
+  oz_ez = nullptr;
+  tmOzBoo.clear();
+  tmOzZ.clear();
+  tmOzBvv.clear();
   coul_tc = false;
   coul_stream = false;
   tmZA.clear();
@@ -506,6 +537,78 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
   }
 }
 
+// --- FP64-accurate exchange: Ozaki digits on the tensor cores ------------
+void oz_attr() {
+  static_assert(oz::smem_bytes() <= 232448, "shared memory per block exceeds 227 KB");
+  cudaFuncSetAttribute(oz::k_oz_gemm<oz::OZ_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz::smem_bytes());
+  cudaFuncSetAttribute(oz::k_oz_gemm<oz::OZ_VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz::smem_bytes());
+}
+
+template <int MODE>
+void oz_launch(const CUtensorMap& a, const CUtensorMap& b, const oz::Params& prm, cudaStream_t s) {
+  const long long tiles = cdiv(prm.N, oz::kBN) * cdiv(prm.M, tc::kBM) * prm.nsplit;
+  const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(tiles, kNumSM));
+  oz::k_oz_gemm<MODE><<<grid, tc::kThreads, oz::smem_bytes(), s>>>(a, b, prm);
+}
+
+// K_(col,i),a = sum_{P,b} Z^P_(col,i),b B^P_ab to FP64 accuracy: digits of
+// the stage amplitudes, then per chunk of P the Z build (Z^P = B^P_oo c as
+// integers, one exactness block since nocc <= 512), the digits of Z per
+// block of (P, b) and the main contraction into FP64 split-K partials.
+void exchange_oz(rttda_ctx* h, const double* X, cudaStream_t s) {
+  const int C = 2 * h->T, o = h->o, v = h->v, vp = h->vp, op = h->op;
+  {
+    Prof pr(h, RTTDA_KC_EXCHANGE_Z, s);
+    h->launches += 1;
+    oz::k_slice_x<<<blocks_for((long long)C * vp * 32, 256), 256, 0, s>>>(o, v, vp, op, C, X, h->oz_x,
+                                                                         (long long)C * vp * op, h->oz_ex);
+  }
+  for (int c = 0, p0 = 0; p0 < h->P; p0 += h->zchunk, ++c) {
+    const int pc = std::min(h->zchunk, h->P - p0);
+    {
+      Prof pr(h, RTTDA_KC_EXCHANGE_Z, s);
+      h->launches += 2;
+      oz::Params prm{};
+      prm.M = pc * o;
+      prm.N = C * vp;
+      prm.vt = (int)cdiv(op, oz::kKB);
+      prm.pc = 1;
+      prm.pps = 1;
+      prm.nsplit = 1;
+      prm.nbp = 1;
+      prm.out = h->oz_zi;
+      prm.ldo = (long long)C * vp;
+      prm.err = h->d_err;
+      oz_launch<oz::OZ_PLAIN>(h->tmOzBoo[c], h->tmOzX, prm, s);
+      const long long warps = (long long)C * o * pc * h->oz_nbp;
+      oz::k_slice_z<<<blocks_for(warps * 32, 256), 256, 0, s>>>(o, vp, C, pc, h->oz_nbp, p0, h->oz_zi, h->oz_eoo,
+                                                                h->oz_ex, h->oz_z, (long long)h->oz_zplane, h->oz_ez);
+    }
+    {
+      Prof pr(h, RTTDA_KC_EXCHANGE_MAIN, s);
+      h->launches += 1;
+      oz::Params prm{};
+      prm.M = C * o;
+      prm.N = v;
+      prm.vt = vp / oz::kKB;
+      prm.pc = pc;
+      prm.pps = h->oz_pps;
+      prm.nsplit = h->SK;
+      prm.nbp = h->oz_nbp;
+      prm.out = h->Kpart;
+      prm.ldo = v;
+      prm.split_stride = (long long)C * o * v;
+      prm.accum = c > 0 ? 1 : 0;
+      prm.ea = h->oz_ez;
+      prm.lde_a = (long long)pc * h->oz_nbp;
+      prm.eb = h->oz_evv + (size_t)p0 * h->oz_nbp;
+      prm.lde_b = (long long)h->P * h->oz_nbp;
+      prm.err = h->d_err;
+      oz_launch<oz::OZ_VV>(h->tmOzZ[c], h->tmOzBvv[c], prm, s);
+    }
+  }
+}
+
 // Coulomb on the FP32 streaming kernels: FP32 copy of the stage's amplitudes,
 // then both passes; column count as a template argument (2T in {2, ..., 12}).
 template <typename TF, int C>
@@ -712,10 +815,20 @@ struct Ops {
   }
 };
 
+// FP64_OZ: the FP64 paths with the exchange on Ozaki digits
+struct OpsOz : Ops<double, double, false> {
+  static void exchange(rttda_ctx* h, const double* X, cudaStream_t s) { exchange_oz(h, X, s); }
+  static void set_smem_limits() {
+    Ops<double, double, false>::set_smem_limits();
+    oz_attr();
+  }
+};
+
 template <typename F>
 void dispatch(int prec, F&& f) {
   switch (prec) {
     case RTTDA_FP64: f(Ops<double, double, false>{}); break;
+    case RTTDA_FP64_OZ: f(OpsOz{}); break;
     case RTTDA_FP32: f(Ops<float, float, false>{}); break;
     case RTTDA_BF16: f(Ops<__nv_bfloat16, float, true>{}); break;
     default: f(Ops<float, float, true>{}); break;  // RTTDA_BF16X3, RTTDA_BF16X2
@@ -932,6 +1045,18 @@ static size_t zbudget_bytes() {
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)6 << 30;
   return std::max<size_t>((size_t)256 << 20, std::min<size_t>((size_t)40 << 30, fr / 3));
+}
+
+// P per Z chunk: what the byte budget allows, at most RTTDA_ZCHUNK when that
+// environment variable holds a positive count (tests and experiments).
+static int zchunk_for(int P, size_t budget, size_t per_p) {
+  size_t zc = std::max<size_t>(1, std::min<size_t>(P, budget / std::max<size_t>(per_p, 1)));
+  const char* e = std::getenv("RTTDA_ZCHUNK");
+  if (e && *e) {
+    const long cap = std::atol(e);
+    if (cap > 0) zc = std::min<size_t>(zc, (size_t)cap);
+  }
+  return (int)zc;
 }
 
 // Split-K count for a persistent launch over `tiles` output tiles: the split
@@ -1206,7 +1331,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   CKS(dalloc(&h->Xt, xt * h->nplanes));
   // Z chunk: C*o rows of zchunk*vp BF16 per plane, at most ~2 GiB in total
   const size_t zper = (size_t)C * o * vp * 2 * h->zplanes;
-  h->zchunk = (int)std::max<size_t>(1, std::min<size_t>(P, zbudget_bytes() / std::max<size_t>(zper, 1)));
+  h->zchunk = zchunk_for(P, zbudget_bytes(), zper);
   h->zplane = (size_t)C * o * h->zchunk * vp;
   CKS(dalloc(&h->Zk, h->zplane * h->zplanes));
   // main contraction tiles.  BF16 and BF16X2 (Z is one plane): wide-M tiles
@@ -1284,6 +1409,75 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
 
 rttda_status rttda_ctx::alloc_tc(int C) { return ::alloc_tc(this, C); }
 
+// Buffers, split-K plan and TMA maps of the FP64-accurate exchange (FP64_OZ)
+// for C columns.  Main contraction: split-K over whole P, enough splits that
+// the (m, n) tiles times the splits fill the SMs once.
+static rttda_status alloc_oz(rttda_ctx* h, int C) {
+  const int o = h->o, v = h->v, P = h->P, vp = h->vp, op = h->op;
+  constexpr int S = oz::kS;
+  const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_64B;
+  CKS(dalloc(&h->oz_x, (size_t)S * C * vp * op));
+  CKS(dalloc(&h->oz_ex, (size_t)C * vp));
+  // Z chunk: the integer Z (8 bytes) and its digits (2 bytes each) per element
+  const size_t zper = (size_t)C * o * vp * (8 + 2 * S);
+  h->zchunk = zchunk_for(P, zbudget_bytes(), zper);
+  const int zc = h->zchunk;
+  CKS(dalloc(&h->oz_zi, (size_t)zc * o * C * vp));
+  h->oz_zplane = (size_t)C * o * zc * vp;
+  CKS(dalloc(&h->oz_z, h->oz_zplane * S));
+  CKS(dalloc(&h->oz_ez, (size_t)C * o * zc * h->oz_nbp));
+  const long long tiles = cdiv((long long)C * o, tc::kBM) * cdiv(v, oz::kBN);
+  const int sk = (int)std::max(1LL, std::min<long long>(zc, kNumSM / tiles));
+  h->oz_pps = (int)cdiv(zc, sk);
+  h->SK = (int)cdiv(zc, h->oz_pps);
+  char* p = nullptr;
+  CKS(dalloc_bytes((void**)&p, (size_t)h->SK * C * o * v * sizeof(double)));
+  h->Kpart = p;
+  h->plan = rttda_plan_info{};
+  h->plan.main_kernel = 3;
+  h->plan.main_bn = oz::kBN;
+  h->plan.main_mb = 1;
+  h->plan.main_kb = oz::kKB;
+  h->plan.main_splits = h->SK;
+  h->plan.z_chunk = zc;
+  {
+    // amplitude digits: B operand of the Z build, rows (col, b), K = j
+    const uint64_t dims[3] = {(uint64_t)op, (uint64_t)C * vp, (uint64_t)S};
+    const uint64_t str[2] = {(uint64_t)op * 2, (uint64_t)C * vp * op * 2};
+    const uint32_t box[3] = {(uint32_t)oz::kKB, (uint32_t)oz::kBN, 1};
+    CKS(bf16_map(&h->tmOzX, h->oz_x, 3, dims, str, box, sw));
+  }
+  for (int p0 = 0; p0 < P; p0 += zc) {
+    const int pc = std::min(zc, P - p0);
+    CUtensorMap mo, mz, mv;
+    {
+      // B_oo digits of the chunk: A of the Z build, rows (P, i), K = j
+      const uint64_t dims[3] = {(uint64_t)op, (uint64_t)pc * o, (uint64_t)S};
+      const uint64_t str[2] = {(uint64_t)op * 2, (uint64_t)P * o * op * 2};
+      const uint32_t box[3] = {(uint32_t)oz::kKB, (uint32_t)tc::kBM, 1};
+      CKS(bf16_map(&mo, h->oz_boo + (size_t)p0 * o * op, 3, dims, str, box, sw));
+    }
+    {
+      // Z digits: A of the main contraction, [digit][(P, b/64)][(col, i)][64]
+      const uint64_t dims[4] = {64, (uint64_t)C * o, (uint64_t)pc * (vp / 64), (uint64_t)S};
+      const uint64_t str[3] = {128, (uint64_t)C * o * 128, (uint64_t)h->oz_zplane * 2};
+      const uint32_t box[4] = {(uint32_t)oz::kKB, (uint32_t)tc::kBM, 1, 1};
+      CKS(bf16_map(&mz, h->oz_z, 4, dims, str, box, sw));
+    }
+    {
+      // B_vv digits of the chunk: B of the main contraction, (b, a, P, digit)
+      const uint64_t dims[4] = {(uint64_t)vp, (uint64_t)v, (uint64_t)pc, (uint64_t)S};
+      const uint64_t str[3] = {(uint64_t)vp * 2, (uint64_t)v * vp * 2, (uint64_t)P * v * vp * 2};
+      const uint32_t box[4] = {(uint32_t)oz::kKB, (uint32_t)oz::kBN, 1, 1};
+      CKS(bf16_map(&mv, h->oz_bvv + (size_t)p0 * v * vp, 4, dims, str, box, sw));
+    }
+    h->tmOzBoo.push_back(mo);
+    h->tmOzZ.push_back(mz);
+    h->tmOzBvv.push_back(mv);
+  }
+  return RTTDA_OK;
+}
+
 rttda_status rttda_ctx::alloc_batch() {
   const int C = 2 * T;
   const long long NC = N * C;
@@ -1303,7 +1497,7 @@ rttda_status rttda_ctx::alloc_batch() {
   } else {
     const int V = (int)(16 / fbytes);
     coul_vec = (ov % V) == 0 && C <= 12;
-    coul_stream = coul_vec && prec != RTTDA_FP64;
+    coul_stream = coul_vec && cbytes != 8;
     const size_t max_smem = 96 * 1024;
     if (coul_stream) {
       // pass 1 over (32-row blocks) x SW slices (a slice's FP32 amplitudes
@@ -1370,10 +1564,12 @@ rttda_status rttda_ctx::alloc_batch() {
     Jpart = p;
   }
   // exchange scratch: Z for a chunk of P (bounded size), split-K partials
-  if (!tc) {
+  if (oz) {
+    CKS(::alloc_oz(this, C));
+  } else if (!tc) {
     const size_t zper = (size_t)v * C * o * cbytes;
     const size_t zbudget = (size_t)1 << 30;
-    zchunk = (int)std::max<size_t>(1, std::min<size_t>(P, zbudget / std::max<size_t>(zper, 1)));
+    zchunk = zchunk_for(P, zbudget, zper);
     char* p = nullptr;
     CKS(dalloc_bytes((void**)&p, (size_t)zchunk * zper));
     Zt = p;
@@ -1483,6 +1679,29 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
     CKS(upload(B_oo, P * o * o, &h->Boo));
     CKS(upload(B_vv, P * v * v, &h->Bvv));
   }
+  if (h->oz) {
+    // Ozaki digits of B_oo (rows (P, i), K = j: one block, nocc <= 512) and
+    // of B_vv (rows (P, a), K = b in blocks of 512); the FP64 copies go
+    constexpr int S = oz::kS;
+    const size_t op = h->op, vp = h->vp;
+    h->oz_nbp = (int)cdiv(vp, oz::kBlk);
+    CKS(dalloc(&h->oz_boo, S * P * o * op));
+    CKS(dalloc(&h->oz_eoo, P * o));
+    CKS(dalloc(&h->oz_bvv, S * P * v * vp));
+    CKS(dalloc(&h->oz_evv, v * P * (size_t)h->oz_nbp));
+    const long long ro = (long long)(P * o), rv = (long long)(P * v);
+    oz::k_slice_rows<<<blocks_for(ro * 32, 256), 256, 0, h->stream>>>(
+        ro, ro, (int)o, (int)op, (const double*)h->Boo, (long long)o, h->oz_boo, (long long)op, ro * (long long)op,
+        h->oz_eoo, 1, 1);
+    oz::k_slice_rows<<<blocks_for(rv * h->oz_nbp * 32, 256), 256, 0, h->stream>>>(
+        rv, (long long)v, (int)v, (int)vp, (const double*)h->Bvv, (long long)v, h->oz_bvv, (long long)vp,
+        rv * (long long)vp, h->oz_evv, (long long)P * h->oz_nbp, h->oz_nbp);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    dfree(h->Boo);
+    dfree(h->Bvv);
+    h->Boo = h->Bvv = nullptr;
+  }
   CKS(upload64(eps_occ, o, &h->eps_o));
   CKS(upload64(eps_virt, v, &h->eps_v));
   CKS(upload64(mu_oo, 3 * o * o, &h->mu_oo));
@@ -1520,8 +1739,10 @@ rttda_status rttda_create(int nocc, int nvirt, int naux, const double* eps_occ, 
   if (!eps_occ || !eps_virt || !B_ov || !B_oo || !B_vv || !mu_oo || !mu_vv || !mu_0ov)
     return set_error(RTTDA_E_ARG, "rttda_create: NULL input array");
   if (prec != RTTDA_FP64 && prec != RTTDA_FP32 && prec != RTTDA_BF16 && prec != RTTDA_BF16X3 &&
-      prec != RTTDA_BF16X2)
+      prec != RTTDA_BF16X2 && prec != RTTDA_FP64_OZ)
     return set_error(RTTDA_E_ARG, "rttda_create: unsupported precision");
+  if (prec == RTTDA_FP64_OZ && nocc > oz::kBlk)
+    return set_error(RTTDA_E_ARG, "rttda_create: FP64_OZ needs nocc <= 512");
   if (!std::isfinite(c_x)) return set_error(RTTDA_E_ARG, "rttda_create: c_x not finite");
 
   rttda_ctx* h = new rttda_ctx();
@@ -1532,9 +1753,11 @@ rttda_status rttda_create(int nocc, int nvirt, int naux, const double* eps_occ, 
   h->N = 1 + h->ov;
   h->cx = c_x;
   h->prec = prec;
-  h->fbytes = prec == RTTDA_FP64 ? 8 : prec == RTTDA_BF16 ? 2 : 4;
-  h->cbytes = prec == RTTDA_FP64 ? 8 : 4;
+  const bool f64 = prec == RTTDA_FP64 || prec == RTTDA_FP64_OZ;
+  h->fbytes = f64 ? 8 : prec == RTTDA_BF16 ? 2 : 4;
+  h->cbytes = f64 ? 8 : 4;
   h->tc = prec == RTTDA_BF16 || prec == RTTDA_BF16X3 || prec == RTTDA_BF16X2;
+  h->oz = prec == RTTDA_FP64_OZ;
   h->nplanes = prec == RTTDA_BF16 ? 1 : 2;          // factor / amplitude planes
   h->nprod = prec == RTTDA_BF16 ? 1 : 3;            // Z = B_oo c products
   h->zplanes = prec == RTTDA_BF16X3 ? 2 : 1;        // Z planes kept
@@ -1564,13 +1787,17 @@ rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes) {
   size_t b = P * o * v * h->fbytes + (o + v + 3 * (o * o + v * v + o * v)) * 8;
   if (h->tc)
     b += (P * o * (size_t)h->op + P * (size_t)h->vp * h->vp) * 2 * h->nplanes;
+  else if (h->oz)
+    b += (P * o * (size_t)h->op + P * v * (size_t)h->vp) * 2 * oz::kS + (P * o + v * P * h->oz_nbp) * 4;
   else
     b += (P * o * o + P * v * v) * h->fbytes;
   if (h->T > 0) {
     const size_t C = 2 * h->T, NC = h->N * C;
-    b += NC * 8 * 6 + (size_t)P * C * h->cbytes + (size_t)h->SJ * h->ov * C * h->cbytes +
-         (size_t)h->zchunk * v * C * o * h->cbytes + (size_t)h->SK * C * o * v * h->cbytes +
-         (size_t)h->T * (o * o + v * v + o * v) * (8 + (h->prec == RTTDA_FP64 ? 0 : h->cbytes));
+    const size_t zb = h->oz ? (size_t)h->zchunk * C * o * h->vp * (8 + 2 * oz::kS) + C * (size_t)h->vp * h->op * 2 * oz::kS
+                            : (size_t)h->zchunk * v * C * o * h->cbytes;
+    b += NC * 8 * 6 + (size_t)P * C * h->cbytes + (size_t)h->SJ * h->ov * C * h->cbytes + zb +
+         (size_t)h->SK * C * o * v * h->cbytes +
+         (size_t)h->T * (o * o + v * v + o * v) * (8 + (h->cbytes == 8 ? 0 : h->cbytes));
   }
   *bytes = b;
   return RTTDA_OK;
@@ -1647,7 +1874,7 @@ rttda_status rttda_set_field(rttda_t h, const rttda_pulse* pulses, int ntraj) {
   k_dipole_dir<double><<<blocks_for(loo * ntraj, 256), 256, 0, s>>>(loo, ntraj, h->d_dirs, h->mu_oo, h->moo64);
   k_dipole_dir<double><<<blocks_for(lvv * ntraj, 256), 256, 0, s>>>(lvv, ntraj, h->d_dirs, h->mu_vv, h->mvv64);
   k_dipole_dir<double><<<blocks_for(lov * ntraj, 256), 256, 0, s>>>(lov, ntraj, h->d_dirs, h->mu_0, h->m064);
-  if (h->prec != RTTDA_FP64) {
+  if (h->cbytes != 8) {
     float* p = nullptr;
     CKS(dalloc(&p, loo * ntraj));
     h->mooC = p;
@@ -1926,16 +2153,22 @@ rttda_status spectrum_device(const double* trace_dev, long long ntr, long long n
 size_t estimate_bytes(int nocc, int nvirt, int naux, int ntraj, int prec, long nsteps) {
   const size_t o = nocc, v = nvirt, P = naux, T = ntraj, C = 2 * T, ov = o * v, N = 1 + ov;
   const bool tc = prec == RTTDA_BF16 || prec == RTTDA_BF16X3 || prec == RTTDA_BF16X2;
-  const size_t fb = prec == RTTDA_FP64 ? 8 : prec == RTTDA_BF16 ? 2 : 4, cb = prec == RTTDA_FP64 ? 8 : 4;
+  const bool ozk = prec == RTTDA_FP64_OZ, f64 = prec == RTTDA_FP64 || ozk;
+  const size_t fb = f64 ? 8 : prec == RTTDA_BF16 ? 2 : 4, cb = f64 ? 8 : 4;
   const size_t vp = (v + 63) / 64 * 64, op = (o + 7) / 8 * 8;
   const size_t planes = prec == RTTDA_BF16 ? 1 : 2, zplanes = prec == RTTDA_BF16X3 ? 2 : 1;
   size_t b = P * ov * fb + (o + v + 3 * (o * o + v * v + ov)) * 8;
-  b += tc ? (P * o * op + P * vp * vp + 2 * P * ov) * 2 * planes : (P * o * o + P * v * v) * fb;
+  if (ozk)  // digits of B_oo and B_vv (the FP64 copies are held while slicing)
+    b += (P * o * op + P * v * vp) * 2 * oz::kS + (P * o * o + P * v * v) * 8;
+  else
+    b += tc ? (P * o * op + P * vp * vp + 2 * P * ov) * 2 * planes : (P * o * o + P * v * v) * fb;
   b += N * C * 8 * 6 + T * (o * o + v * v + ov) * (8 + cb);               // state, dipole blocks
   b += (size_t)32 * P * C * cb + (size_t)16 * ov * C * cb;                 // Coulomb partials
   const size_t zcap = (size_t)40 << 30;
   if (tc)
     b += std::min(zcap, C * o * vp * 2 * zplanes * P) + C * vp * op * 2 * planes + (size_t)kNumSM * C * o * v * 4;
+  else if (ozk)
+    b += std::min(zcap, C * o * vp * (8 + 2 * oz::kS) * P) + C * vp * op * 2 * oz::kS + (size_t)kNumSM * C * o * v * 8;
   else
     b += std::min((size_t)1 << 30, v * C * o * cb * P) + (size_t)4 * kNumSM * C * o * v * cb;
   b += (2 * N * T * 2 + 2 * T * (size_t)(nsteps + 1)) * 8;                 // host-call staging
@@ -2128,8 +2361,8 @@ rttda_status rttda_plan(rttda_t h, rttda_plan_info* out) {
   g_last_error.clear();
   if (!h || !out) return set_error(RTTDA_E_ARG, "rttda_plan: NULL argument");
   if (h->T == 0) return set_error(RTTDA_E_STATE, "rttda_plan: no batch (call rttda_set_field first)");
-  rttda_plan_info p = h->tc ? h->plan : rttda_plan_info{};
-  if (!h->tc) {
+  rttda_plan_info p = h->tc || h->oz ? h->plan : rttda_plan_info{};
+  if (!h->tc && !h->oz) {
     p.main_bn = h->prec == RTTDA_FP64 ? Tile<double>::BN : Tile<float>::BN;
     p.main_mb = 1;
     p.main_kb = h->prec == RTTDA_FP64 ? Tile<double>::BK : Tile<float>::BK;

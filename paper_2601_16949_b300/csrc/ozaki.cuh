@@ -1,0 +1,513 @@
+// FP64-accurate contractions on the BF16 tensor cores by exponent-aligned
+// slicing: the Ozaki scheme (K. Ozaki, T. Ogita, S. Oishi, S. M. Rump,
+// "Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer.
+// Algorithms 59, 2012), here for the exchange term -c_x sum_P B^P_ij B^P_ab
+// of the A matrix elements (Sec. 2.2) when sigma must match FP64.
+//
+// Digits.  A block of values (one row of an operand over at most 512
+// consecutive K elements) with |x| < 2^e for all of its x is written as
+//     x = 2^e sum_{s<S} d_s 2^(-7(s+1)) + r,      |r| <= 2^(e - 7S - 1),
+// d_0 in [-128, 128] and d_s in [-64, 63] for s >= 1: small integers, exact
+// in BF16.  They come from the fixed-point integer F = round(x 2^(7S - e))
+// (|F| <= 2^(7S)) by centred base-128 division, in integer arithmetic only.
+// A value is handled as a pair (I, E) with x = I 2^E: an FP64 number as its
+// 53-bit significand and exponent, a product sum of this file as an int64
+// and the exponent its operands' blocks imply.
+//
+// Products.  Over one block, sum_k A[m][k] B[n][k] equals
+//     2^(ea + eb) sum_{s,t} 2^(-7(s+t+2)) sum_k d_s[m][k] g_t[n][k].
+// Pairs with s + t = g carry one weight, so the tensor cores sum each group
+// g < S in a TMEM accumulator of its own; pairs with s + t >= S are dropped
+// (the scheme's triangular truncation, relative size 2^(-7S) of the block's
+// scale).  A product of two digits is at most 2^14 in magnitude and group g
+// collects at most 2^14 (g <= 1) or (g + 3) 2^12 (g >= 2) per K element, so
+// for S = 6 and a block of at most 512 elements every partial sum is an
+// integer of magnitude <= 2^24: exact in FP32 in any order of addition.
+// The epilogue joins the groups exactly in int64,
+//     I = sum_g acc_g 2^(7(S-1-g)),        block value = I 2^(ea + eb - 7(S+1)),
+// and adds the block values of a K range in FP64 (or, for a contraction of
+// one block, stores I).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tc_gemm.cuh"
+
+namespace rttda {
+namespace oz {
+
+constexpr int kS = 6;                        // digits per value
+constexpr int kDigitBits = 7;
+constexpr int kFixBits = kS * kDigitBits;    // 42: fixed-point bits of F
+constexpr int kOutShift = kDigitBits * (kS + 1);  // 49: 2^(ea+eb-49) I
+constexpr int kKB = 32;                      // K tile: 32 BF16 = 64-byte rows, 64-byte swizzle
+constexpr int kBlkTiles = 16;                // K tiles per exactness block (512 elements)
+constexpr int kBlk = kKB * kBlkTiles;
+constexpr int kBN = 64;
+constexpr int kStages = 3;
+constexpr int kEmptyExp = -400;              // block exponent of an all-zero block
+constexpr int kASlice = tc::kBM * kKB * 2;   // one A digit plane of a K tile (8 KB)
+constexpr int kBSlice = kBN * kKB * 2;       // one B digit plane (4 KB)
+constexpr int kStageBytes = kS * (kASlice + kBSlice);
+constexpr uint32_t kTmemCols = 512;
+static_assert(kS * kBN <= (int)kTmemCols, "group accumulators exceed TMEM");
+static_assert(kStageBytes % 1024 == 0, "stage must keep 1024-byte alignment");
+static_assert(kBlk * 8 * 4096 <= (1 << 24), "a group sum of one block must stay exact in FP32");
+
+constexpr size_t smem_bytes() { return (size_t)kStages * kStageBytes + 1024 + 256; }
+
+// operand addressing
+enum : int {
+  OZ_PLAIN = 0,  // A [digit][row][k], B [digit][row][k]: 3-D maps (k, row, digit); out int64 I
+  OZ_VV = 1      // A = Z digits [digit][(P, b/64)][row][64]; B = B_vv digits [digit][P][a][b]; out FP64
+};
+
+struct Params {
+  int M, N;
+  int vt;        // K tiles per P (OZ_VV); all K tiles of the contraction (OZ_PLAIN)
+  int pc;        // P in this chunk (OZ_VV); 1 (OZ_PLAIN)
+  int pps;       // P per split
+  int nsplit;
+  int nbp;       // exactness blocks per P: ceil(vt / kBlkTiles)
+  void* out;     // OZ_VV: double [split][M][ldo]; OZ_PLAIN: long long [M][ldo]
+  long long ldo, split_stride;
+  int accum;     // OZ_VV: out += result (later chunks of P)
+  const int* ea;  // A block exponents ea[m * lde_a + block] (OZ_VV)
+  long long lde_a;
+  const int* eb;  // B block exponents eb[n * lde_b + block] (OZ_VV)
+  long long lde_b;
+  int* err;
+};
+
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+// 2^E as a double (E clamped to the normal range)
+__device__ __forceinline__ double exp2i(int E) {
+  E = max(-1022, min(1023, E));
+  return __longlong_as_double((long long)(E + 1023) << 52);
+}
+
+// ---------------------------------------------------------------------------
+// Digits of a value x = I 2^E in a block of exponent e (|x| < 2^e):
+// F = round(I 2^(E + 7S - e)), then d_{S-1}, ..., d_1 centred in [-64, 63]
+// and d_0 = what remains (|d_0| <= 128).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long fixed_point(long long I, int E, int e) {
+  if (I == 0) return 0;
+  const int sh = E + kFixBits - e;
+  const bool neg = I < 0;
+  const unsigned long long a = neg ? (unsigned long long)(-I) : (unsigned long long)I;
+  unsigned long long f;
+  if (sh >= 0)
+    f = a << sh;  // |I| < 2^(e-E) so that |F| < 2^(7S)
+  else if (sh <= -63)
+    f = 0;
+  else
+    f = (a + (1ull << (-sh - 1))) >> (-sh);
+  return neg ? -(long long)f : (long long)f;
+}
+
+__device__ __forceinline__ void digits(long long F, float (&d)[kS]) {
+#pragma unroll
+  for (int s = kS - 1; s >= 1; --s) {
+    const int q = (int)((F + 64) & 127) - 64;
+    F = (F - q) >> 7;
+    d[s] = (float)q;
+  }
+  d[0] = (float)F;
+}
+
+// Bits of |I| plus E: x = I 2^E lies below 2^(that) (INT_MIN-ish for I = 0).
+__device__ __forceinline__ int top_exp(long long I, int E) {
+  if (I == 0) return -0x40000000;
+  const unsigned long long a = I < 0 ? (unsigned long long)(-I) : (unsigned long long)I;
+  return 64 - __clzll((long long)a) + E;
+}
+
+__device__ __forceinline__ void f64_parts(double x, long long& I, int& E) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  long long m = b & 0xFFFFFFFFFFFFFll;
+  if (ex != 0) m |= 1ll << 52;
+  E = (ex != 0 ? ex : 1) - 1075;
+  I = b < 0 ? -m : m;
+}
+
+// ---------------------------------------------------------------------------
+// Slicing kernels.  One warp per block; lane l holds the block's elements
+// l, l + 32, ... (up to kBlk / 32 = 16 of them).
+// ---------------------------------------------------------------------------
+constexpr int kPerLane = kBlk / 32;
+
+__device__ __forceinline__ int warp_block_exp(int e) {
+  e = __reduce_max_sync(0xffffffffu, e);
+  return e < -0x20000000 ? kEmptyExp : e;
+}
+
+// Rows r of an FP64 matrix with the K elements of row r at src[r * lds + k]
+// (k < klen, zero beyond): digits [digit][r][ldd] (BF16, zero padded up to
+// kpad) and one exponent per (row, block of 512 along k), stored at
+// exps[(r % rin) * lde + (r / rin) * nblk + blk].  B_oo: rows (P, i), K = j,
+// rin = all rows, lde = nblk = 1.  B_vv: rows (P, a), K = b, rin = nvirt,
+// lde = naux * nblk (exponents [a][P][blk]).
+__global__ void __launch_bounds__(256) k_slice_rows(long long rows, long long rin, int klen, int kpad,
+                                                    const double* __restrict__ src, long long lds,
+                                                    __nv_bfloat16* __restrict__ dst, long long ldd, long long plane,
+                                                    int* __restrict__ exps, long long lde, int nblk) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= rows * nblk) return;
+  const long long r = wid / nblk;
+  const int blk = (int)(wid - r * nblk);
+  const int k0 = blk * kBlk;
+  long long I[kPerLane];
+  int E[kPerLane];
+  int emax = -0x40000000;
+#pragma unroll
+  for (int q = 0; q < kPerLane; ++q) {
+    const int k = k0 + lane + 32 * q;
+    I[q] = 0;
+    E[q] = 0;
+    if (k < klen) f64_parts(src[r * lds + k], I[q], E[q]);
+    emax = max(emax, top_exp(I[q], E[q]));
+  }
+  const int e = warp_block_exp(emax);
+  if (lane == 0) exps[(r % rin) * lde + (r / rin) * nblk + blk] = e;
+#pragma unroll
+  for (int q = 0; q < kPerLane; ++q) {
+    const int k = k0 + lane + 32 * q;
+    if (k >= kpad || k >= k0 + kBlk) continue;
+    float d[kS];
+    digits(fixed_point(I[q], E[q], e), d);
+#pragma unroll
+    for (int s = 0; s < kS; ++s) dst[(size_t)s * plane + r * ldd + k] = __float2bfloat16_rn(d[s]);
+  }
+}
+
+// Stage amplitudes for Z = B_oo c: rows (col, b) (b < vp; rows b >= v are
+// zero), K = j < o.  X[n * C + col] with n = 1 + j v + b.  Digits
+// [digit][col * vp + b][op], exponents ex[col * vp + b] (o <= 512: one block).
+__global__ void __launch_bounds__(256) k_slice_x(int o, int v, int vp, int op, int C, const double* __restrict__ X,
+                                                 __nv_bfloat16* __restrict__ dst, long long plane,
+                                                 int* __restrict__ ex) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)C * vp) return;
+  const int col = (int)(wid / vp), b = (int)(wid - (long long)col * vp);
+  long long I[kPerLane];
+  int E[kPerLane];
+  int emax = -0x40000000;
+#pragma unroll
+  for (int q = 0; q < kPerLane; ++q) {
+    const int j = lane + 32 * q;
+    I[q] = 0;
+    E[q] = 0;
+    if (j < o && b < v) f64_parts(X[(1 + (long long)j * v + b) * C + col], I[q], E[q]);
+    emax = max(emax, top_exp(I[q], E[q]));
+  }
+  const int e = warp_block_exp(emax);
+  if (lane == 0) ex[wid] = e;
+#pragma unroll
+  for (int q = 0; q < kPerLane; ++q) {
+    const int j = lane + 32 * q;
+    if (j >= op) continue;
+    float d[kS];
+    digits(fixed_point(I[q], E[q], e), d);
+#pragma unroll
+    for (int s = 0; s < kS; ++s) dst[(size_t)s * plane + wid * op + j] = __float2bfloat16_rn(d[s]);
+  }
+}
+
+// Z digits for the main contraction.  Zi[(P, i)][(col, b)] = I from the
+// Z build, with x = I 2^(eoo[P, i] + ex[col, b] - 49).  Rows (col, i), K =
+// (P, b): one warp per (row, P, block of 512 along b); lane l handles the
+// pairs b = 2l + 64q, 2l + 1 + 64q of the block.  Digits in the tile order
+// of the main contraction, [digit][(P, b/64)][col * o + i][64]; exponents
+// ez[(col * o + i) * (pc * nbp) + P * nbp + blk].
+__global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc, int nbp, int p0,
+                                                 const long long* __restrict__ Zi, const int* __restrict__ eoo,
+                                                 const int* __restrict__ ex, __nv_bfloat16* __restrict__ dst,
+                                                 long long plane, int* __restrict__ ez) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)C * o * pc * nbp;
+  if (wid >= nw) return;
+  // warp order: block fastest, then P, then row, so that neighbouring warps
+  // read neighbouring stretches of Zi
+  const int blk = (int)(wid % nbp);
+  const int P = (int)((wid / nbp) % pc);
+  const long long row = wid / ((long long)nbp * pc);
+  const int col = (int)(row / o), i = (int)(row - (long long)col * o);
+  const long long zrow = ((long long)P * o + i) * ((long long)C * vp) + (long long)col * vp;
+  const int eo = eoo[(long long)(p0 + P) * o + i];
+  constexpr int kPairs = kBlk / 64;  // pairs per lane
+  long long I[2 * kPairs];
+  int E[2 * kPairs];
+  int emax = -0x40000000;
+#pragma unroll
+  for (int q = 0; q < kPairs; ++q) {
+    const int b = blk * kBlk + 64 * q + 2 * lane;
+    I[2 * q] = I[2 * q + 1] = 0;
+    E[2 * q] = E[2 * q + 1] = 0;
+    if (b < vp) {
+      const longlong2 z = *reinterpret_cast<const longlong2*>(Zi + zrow + b);
+      I[2 * q] = z.x;
+      I[2 * q + 1] = z.y;
+      E[2 * q] = eo + ex[(long long)col * vp + b] - kOutShift;
+      E[2 * q + 1] = eo + ex[(long long)col * vp + b + 1] - kOutShift;
+    }
+    emax = max(emax, max(top_exp(I[2 * q], E[2 * q]), top_exp(I[2 * q + 1], E[2 * q + 1])));
+  }
+  const int e = warp_block_exp(emax);
+  if (lane == 0) ez[row * ((long long)pc * nbp) + (long long)P * nbp + blk] = e;
+  const int vt64 = vp / 64;
+#pragma unroll
+  for (int q = 0; q < kPairs; ++q) {
+    const int b = blk * kBlk + 64 * q + 2 * lane;
+    if (b >= vp) continue;
+    float d0[kS], d1[kS];
+    digits(fixed_point(I[2 * q], E[2 * q], e), d0);
+    digits(fixed_point(I[2 * q + 1], E[2 * q + 1], e), d1);
+    const size_t off = (((size_t)P * vt64 + (b >> 6)) * ((size_t)C * o) + (size_t)row) * 64 + (b & 63);
+#pragma unroll
+    for (int s = 0; s < kS; ++s)
+      *reinterpret_cast<__nv_bfloat162*>(dst + (size_t)s * plane + off) = __floats2bfloat162_rn(d0[s], d1[s]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The contraction kernel: persistent over (split, m tile, n tile) tiles of
+// 128 x 64; per K tile one pipeline stage holds the S digit planes of A and
+// of B; the MMA warp issues the S(S+1)/2 digit pairs of the tile into the
+// group accumulators g = s + t (TMEM columns g * 64 .. +63) and hands them
+// to the epilogue at the end of each exactness block.  Warp roles as in
+// the other tensor-core kernels: warp 0 TMA producer, warp 1 TMEM owner and
+// MMA issuer, warps 2..9 epilogue (TMEM lane quarter warp % 4, column half
+// (warp - 2) / 4).  Every wait is bounded (error code in *err).
+//
+// K tiles of a split: P in [split * pps, min(pc, (split + 1) * pps)), each
+// P with vt tiles; within a P a block ends every kBlkTiles tiles and at the
+// P's last tile, so blocks never straddle two P.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(tc::kThreads, 1)
+    k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* accf = empty + kStages;
+  uint64_t* acce = accf + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_n = (p.N + kBN - 1) / kBN;
+  const int tiles_m = (p.M + kBM - 1) / kBM;
+  const int ntiles = tiles_n * tiles_m * p.nsplit;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, kEpiWarps);
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto coords = [&](int t, int& n0, int& m0, int& kr0, int& kr1) {
+    n0 = (t % tiles_n) * kBN;
+    m0 = ((t / tiles_n) % tiles_m) * kBM;
+    const int split = t / (tiles_n * tiles_m);
+    const int P0 = split * p.pps, P1 = min(p.pc, P0 + p.pps);
+    kr0 = P0 * p.vt;
+    kr1 = max(P0, P1) * p.vt;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int it = 0;
+      bool alive = true;
+      for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+        int n0, m0, kr0, kr1;
+        coords(t, n0, m0, kr0, kr1);
+        for (int kr = kr0; kr < kr1; ++kr, ++it) {
+          const int s = it % kStages;
+          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, p.err, ERR_WAIT_EMPTY)) {
+            alive = false;
+            break;
+          }
+          uint8_t* st = smem + s * kStageBytes;
+          mbar_expect_tx(&full[s], (uint32_t)kStageBytes);
+          if (MODE == OZ_PLAIN) {
+#pragma unroll
+            for (int q = 0; q < kS; ++q) tma_load_3d(st + q * kASlice, &tmA, &full[s], kr * kKB, m0, q);
+#pragma unroll
+            for (int q = 0; q < kS; ++q)
+              tma_load_3d(st + kS * kASlice + q * kBSlice, &tmB, &full[s], kr * kKB, n0, q);
+          } else {
+            // Z digits in 64-wide tiles along (P, b): K tile kr is half kr & 1
+            // of tile kr / 2 (vt is even); B_vv digits at (b, a, P)
+            const int P = kr / p.vt, b0 = (kr - P * p.vt) * kKB;
+#pragma unroll
+            for (int q = 0; q < kS; ++q)
+              tma_load_4d(st + q * kASlice, &tmA, &full[s], (kr & 1) * kKB, m0, kr >> 1, q);
+#pragma unroll
+            for (int q = 0; q < kS; ++q)
+              tma_load_4d(st + kS * kASlice + q * kBSlice, &tmB, &full[s], b0, n0, P, q);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
+      int it = 0, nb = 0;
+      bool alive = true;
+      for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+        int n0, m0, kr0, kr1;
+        coords(t, n0, m0, kr0, kr1);
+        for (int kr = kr0; kr < kr1; ++kr, ++it) {
+          const int bt = kr % p.vt;
+          const bool bstart = (bt % kBlkTiles) == 0;
+          const bool bend = (bt % kBlkTiles) == kBlkTiles - 1 || bt == p.vt - 1;
+          if (bstart) {
+            // the epilogue has drained the group accumulators of the last block
+            if (!mbar_wait(acce, ((uint32_t)nb & 1u) ^ 1u, p.err, ERR_WAIT_ACC)) {
+              alive = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          const int s = it % kStages;
+          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          if (!mbar_wait(&full[s], ph, p.err, ERR_WAIT_FULL)) {
+            alive = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t base = smem_u32(smem + s * kStageBytes);
+          // pairs (sa, sb) with sa + sb < S; (0, g) comes first in group g
+#pragma unroll
+          for (int sa = 0; sa < kS; ++sa) {
+            const uint64_t adesc = sdesc_sw64(base + sa * kASlice);
+#pragma unroll
+            for (int sb = 0; sb < kS - sa; ++sb) {
+              const uint64_t bdesc = sdesc_sw64(base + kS * kASlice + sb * kBSlice);
+              const uint32_t d = tmem + (uint32_t)((sa + sb) * kBN);
+#pragma unroll
+              for (int k = 0; k < kKB / 16; ++k)
+                mma_bf16(d, adesc + 2 * k, bdesc + 2 * k, idesc, (!bstart || sa > 0 || k > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(&empty[s]);
+          if (bend) {
+            mma_commit(accf);
+            ++nb;
+          }
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..9) ----------------
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 32);
+    int nb = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int n0, m0, kr0, kr1;
+      coords(t, n0, m0, kr0, kr1);
+      const int m = m0 + row;
+      const int nbase = n0 + half * 32;
+      double acc[32];
+      long long ival[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        acc[j] = 0.0;
+        ival[j] = 0;
+      }
+      for (int kr = kr0; kr < kr1; ++kr) {
+        const int P = kr / p.vt, bt = kr - P * p.vt;
+        if (!((bt % kBlkTiles) == kBlkTiles - 1 || bt == p.vt - 1)) continue;
+        ok = mbar_wait(accf, (uint32_t)nb & 1u, p.err, ERR_WAIT_ACC);
+        ++nb;
+        tc_fence_after();
+        if (!ok) break;
+        const int blk = P * p.nbp + bt / kBlkTiles;
+        int ea = 0;
+        if (MODE == OZ_VV) ea = m < p.M ? __ldg(p.ea + (size_t)m * p.lde_a + blk) : kEmptyExp;
+#pragma unroll
+        for (int c8 = 0; c8 < 4; ++c8) {
+          uint32_t r[kS][8];
+#pragma unroll
+          for (int g = 0; g < kS; ++g) tmem_ld8_nowait(tl + (uint32_t)(g * kBN + c8 * 8), r[g]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            // I = sum_g acc_g 2^(7(S-1-g)) (Horner from the leading group)
+            long long I = __float2int_rn(__uint_as_float(r[0][j]));
+#pragma unroll
+            for (int g = 1; g < kS; ++g) I = I * 128 + __float2int_rn(__uint_as_float(r[g][j]));
+            if (MODE == OZ_VV) {
+              const int n = nbase + c8 * 8 + j;
+              const int eb = n < p.N ? __ldg(p.eb + (size_t)n * p.lde_b + blk) : kEmptyExp;
+              acc[c8 * 8 + j] = fma((double)I, exp2i(ea + eb - kOutShift), acc[c8 * 8 + j]);
+            } else {
+              ival[c8 * 8 + j] = I;
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce);
+      }
+      if (!ok) break;
+      if (m < p.M) {
+        if (MODE == OZ_VV) {
+          double* dst = reinterpret_cast<double*>(p.out) + (size_t)(t / (tiles_n * tiles_m)) * p.split_stride +
+                        (size_t)m * p.ldo;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = nbase + j;
+            if (n < p.N) dst[n] = p.accum ? dst[n] + acc[j] : acc[j];
+          }
+        } else {
+          long long* dst = reinterpret_cast<long long*>(p.out) + (size_t)m * p.ldo;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = nbase + j;
+            if (n < p.N) dst[n] = ival[j];
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+}  // namespace oz
+}  // namespace rttda
