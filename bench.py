@@ -51,10 +51,10 @@ NDIM = 1 + NOCC * NVIRT
 WORKLOAD = ""
 
 
-def set_workload(name: str) -> None:
+def set_workload(name: str, naux: int = 0) -> None:
     global NOCC, NVIRT, NAUX, DT, NDIM, WORKLOAD
     w = WORKLOADS[name]
-    NOCC, NVIRT, NAUX, DT = w["nocc"], w["nvirt"], w["naux"], w["dt"]
+    NOCC, NVIRT, NAUX, DT = w["nocc"], w["nvirt"], naux or w["naux"], w["dt"]
     NDIM = 1 + NOCC * NVIRT
     WORKLOAD = (f"{w['desc']}: nocc={NOCC} nvirt={NVIRT} naux={NAUX} (dim {NDIM}), RK4 dt={DT} au, c_x={CX}")
 
@@ -698,12 +698,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--naux", type=int, default=0,
+                    help="override the workload's naux (smaller cases for profiler captures; not a bench line)")
     ap.add_argument("--only-timed", action="store_true",
                     help="warm-up and timed steps only (for profiler captures): no per-kernel pass, "
                          "no FP64 comparison, no end-to-end or CPU legs")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
-    set_workload(args.workload)
+    set_workload(args.workload, args.naux)
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ and args.impl == "ours":
         # one process per GPU: relaunch under torch.distributed.run
         import socket

@@ -212,15 +212,15 @@ struct rttda_ctx {
   // at create), per-batch digits of the amplitudes and of Z, and the maps
   bool oz = false;
   __nv_bfloat16* oz_boo = nullptr;  // [digit][P*o][op]
-  int* oz_eoo = nullptr;            // [P*o] block exponents
+  short* oz_eoo = nullptr;          // [P*o] block exponents
   __nv_bfloat16* oz_bvv = nullptr;  // [digit][P][v][vp]
-  int* oz_evv = nullptr;            // [v][P*nbp]
+  short* oz_evv = nullptr;          // [P*nbp][vp] (columns a < v used)
   int oz_nbp = 1;                   // exactness blocks per P along b
   __nv_bfloat16* oz_x = nullptr;    // [digit][C*vp][op]
   int* oz_ex = nullptr;             // [C*vp]
   long long* oz_zi = nullptr;       // [zchunk*o][C*vp] integer Z of the Z build
   __nv_bfloat16* oz_z = nullptr;    // [digit][(zchunk, vp/64)][C*o][64]
-  int* oz_ez = nullptr;             // [C*o][zchunk*nbp]
+  int* oz_ez = nullptr;             // [zchunk*nbp][C*o]
   size_t oz_zplane = 0;
   int oz_pps = 1;                   // P per split of the main contraction
   CUtensorMap tmOzX;
@@ -539,16 +539,19 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
 
 // --- FP64-accurate exchange: Ozaki digits on the tensor cores ------------
 void oz_attr() {
-  static_assert(oz::smem_bytes() <= 232448, "shared memory per block exceeds 227 KB");
-  cudaFuncSetAttribute(oz::k_oz_gemm<oz::OZ_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz::smem_bytes());
-  cudaFuncSetAttribute(oz::k_oz_gemm<oz::OZ_VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz::smem_bytes());
+  static_assert(oz::smem_bytes<oz::OZ_PLAIN>() <= 232448, "shared memory per block exceeds 227 KB");
+  static_assert(oz::smem_bytes<oz::OZ_VV>() <= 232448, "shared memory per block exceeds 227 KB");
+  cudaFuncSetAttribute(oz::k_oz_gemm<oz::OZ_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)oz::smem_bytes<oz::OZ_PLAIN>());
+  cudaFuncSetAttribute(oz::k_oz_gemm<oz::OZ_VV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)oz::smem_bytes<oz::OZ_VV>());
 }
 
 template <int MODE>
 void oz_launch(const CUtensorMap& a, const CUtensorMap& b, const oz::Params& prm, cudaStream_t s) {
   const long long tiles = cdiv(prm.N, oz::kBN) * cdiv(prm.M, tc::kBM) * prm.nsplit;
   const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(tiles, kNumSM));
-  oz::k_oz_gemm<MODE><<<grid, tc::kThreads, oz::smem_bytes(), s>>>(a, b, prm);
+  oz::k_oz_gemm<MODE><<<grid, tc::kThreads, oz::smem_bytes<MODE>(), s>>>(a, b, prm);
 }
 
 // K_(col,i),a = sum_{P,b} Z^P_(col,i),b B^P_ab to FP64 accuracy: digits of
@@ -600,9 +603,9 @@ void exchange_oz(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.split_stride = (long long)C * o * v;
       prm.accum = c > 0 ? 1 : 0;
       prm.ea = h->oz_ez;
-      prm.lde_a = (long long)pc * h->oz_nbp;
-      prm.eb = h->oz_evv + (size_t)p0 * h->oz_nbp;
-      prm.lde_b = (long long)h->P * h->oz_nbp;
+      prm.lde_a = (long long)C * o;
+      prm.eb = h->oz_evv + (size_t)p0 * h->oz_nbp * vp;
+      prm.lde_b = vp;
       prm.err = h->d_err;
       oz_launch<oz::OZ_VV>(h->tmOzZ[c], h->tmOzBvv[c], prm, s);
     }
@@ -1688,14 +1691,14 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
     CKS(dalloc(&h->oz_boo, S * P * o * op));
     CKS(dalloc(&h->oz_eoo, P * o));
     CKS(dalloc(&h->oz_bvv, S * P * v * vp));
-    CKS(dalloc(&h->oz_evv, v * P * (size_t)h->oz_nbp));
+    CKS(dalloc(&h->oz_evv, vp * P * (size_t)h->oz_nbp));
     const long long ro = (long long)(P * o), rv = (long long)(P * v);
     oz::k_slice_rows<<<blocks_for(ro * 32, 256), 256, 0, h->stream>>>(
         ro, ro, (int)o, (int)op, (const double*)h->Boo, (long long)o, h->oz_boo, (long long)op, ro * (long long)op,
-        h->oz_eoo, 1, 1);
+        h->oz_eoo, ro, 1);
     oz::k_slice_rows<<<blocks_for(rv * h->oz_nbp * 32, 256), 256, 0, h->stream>>>(
         rv, (long long)v, (int)v, (int)vp, (const double*)h->Bvv, (long long)v, h->oz_bvv, (long long)vp,
-        rv * (long long)vp, h->oz_evv, (long long)P * h->oz_nbp, h->oz_nbp);
+        rv * (long long)vp, h->oz_evv, (long long)vp, h->oz_nbp);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     dfree(h->Boo);
@@ -1788,7 +1791,7 @@ rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes) {
   if (h->tc)
     b += (P * o * (size_t)h->op + P * (size_t)h->vp * h->vp) * 2 * h->nplanes;
   else if (h->oz)
-    b += (P * o * (size_t)h->op + P * v * (size_t)h->vp) * 2 * oz::kS + (P * o + v * P * h->oz_nbp) * 4;
+    b += (P * o * (size_t)h->op + P * v * (size_t)h->vp) * 2 * oz::kS + (P * o + (size_t)h->vp * P * h->oz_nbp) * 2;
   else
     b += (P * o * o + P * v * v) * h->fbytes;
   if (h->T > 0) {

@@ -48,7 +48,8 @@ constexpr int kKB = 32;                      // K tile: 32 BF16 = 64-byte rows, 
 constexpr int kBlkTiles = 16;                // K tiles per exactness block (512 elements)
 constexpr int kBlk = kKB * kBlkTiles;
 constexpr int kBN = 64;
-constexpr int kStages = 3;
+constexpr int kStagesVV = 3;     // main contraction: long K loops
+constexpr int kStagesPlain = 2;  // Z build (K = nocc): room for the store staging
 constexpr int kEmptyExp = -400;              // block exponent of an all-zero block
 constexpr int kASlice = tc::kBM * kKB * 2;   // one A digit plane of a K tile (8 KB)
 constexpr int kBSlice = kBN * kKB * 2;       // one B digit plane (4 KB)
@@ -57,8 +58,15 @@ constexpr uint32_t kTmemCols = 512;
 static_assert(kS * kBN <= (int)kTmemCols, "group accumulators exceed TMEM");
 static_assert(kStageBytes % 1024 == 0, "stage must keep 1024-byte alignment");
 static_assert(kBlk * 8 * 4096 <= (1 << 24), "a group sum of one block must stay exact in FP32");
+constexpr int kStgRow = 33;  // int64 words per staged row (32 + 1 against bank conflicts)
+constexpr int kStgWarpBytes = 32 * kStgRow * 8;
 
-constexpr size_t smem_bytes() { return (size_t)kStages * kStageBytes + 1024 + 256; }
+template <int MODE>
+constexpr int stages() { return MODE == 0 ? kStagesPlain : kStagesVV; }
+template <int MODE>
+constexpr size_t smem_bytes() {
+  return (size_t)stages<MODE>() * kStageBytes + (MODE == 0 ? (size_t)tc::kEpiWarps * kStgWarpBytes : 0) + 1024 + 256;
+}
 
 // operand addressing
 enum : int {
@@ -76,12 +84,18 @@ struct Params {
   void* out;     // OZ_VV: double [split][M][ldo]; OZ_PLAIN: long long [M][ldo]
   long long ldo, split_stride;
   int accum;     // OZ_VV: out += result (later chunks of P)
-  const int* ea;  // A block exponents ea[m * lde_a + block] (OZ_VV)
+  const int* ea;  // A block exponents ea[block * lde_a + m] (OZ_VV)
   long long lde_a;
-  const int* eb;  // B block exponents eb[n * lde_b + block] (OZ_VV)
+  const short* eb;  // B block exponents eb[block * lde_b + n] (OZ_VV; lde_b % 32 == 0)
   long long lde_b;
   int* err;
 };
+
+__device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
 
 __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -89,10 +103,19 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]
                : "r"(taddr));
 }
 
-// 2^E as a double (E clamped to the normal range)
-__device__ __forceinline__ double exp2i(int E) {
-  E = max(-1022, min(1023, E));
-  return __longlong_as_double((long long)(E + 1023) << 52);
+// I 2^E as a double, assembled from the bits of I (rounding toward zero,
+// relative error below 2^-52; zero below the normal range): no int-to-FP64
+// conversion, which B300 runs on its narrow FP64 pipe.
+__device__ __forceinline__ double scaled_i64(long long I, int E) {
+  if (I == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)I & 0x8000000000000000ull;
+  unsigned long long a = I < 0 ? 0ull - (unsigned long long)I : (unsigned long long)I;
+  const int lz = __clzll((long long)a);
+  a <<= lz;  // leading one at bit 63
+  const int ex = 63 - lz + E + 1023;
+  if (ex <= 0) return 0.0;
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)min(ex, 2046) << 52) |
+                                          ((a >> 11) & 0xFFFFFFFFFFFFFull)));
 }
 
 // ---------------------------------------------------------------------------
@@ -115,14 +138,28 @@ __device__ __forceinline__ long long fixed_point(long long I, int E, int e) {
   return neg ? -(long long)f : (long long)f;
 }
 
+// Adding 64 at each of the five low base-128 positions turns every centred
+// digit into a plain 7-bit field: with G = F + 64 (1 + 128 + ... + 128^4),
+// d_s = bits [7(5-s), 7(5-s) + 7) of G minus 64 (s >= 1) and d_0 = G >> 35.
+// The fields become floats without a conversion instruction: 2^23 + u has
+// the bit pattern 0x4B000000 | u for 0 <= u < 2^23.
+constexpr long long kDigitBias = 64LL * (1 + 128 + 16384 + 2097152 + 268435456);
+static_assert(kS == 6, "digits() unpacks six base-128 digits");
+
+__device__ __forceinline__ float field_digit(uint32_t u) {
+  return __uint_as_float(0x4B000000u | (u & 127u)) - 8388672.0f;  // u - 64
+}
+
 __device__ __forceinline__ void digits(long long F, float (&d)[kS]) {
-#pragma unroll
-  for (int s = kS - 1; s >= 1; --s) {
-    const int q = (int)((F + 64) & 127) - 64;
-    F = (F - q) >> 7;
-    d[s] = (float)q;
-  }
-  d[0] = (float)F;
+  const long long G = F + kDigitBias;
+  const uint32_t lo = (uint32_t)G;
+  const uint32_t hi = (uint32_t)((unsigned long long)G >> 32);
+  d[5] = field_digit(lo);
+  d[4] = field_digit(lo >> 7);
+  d[3] = field_digit(lo >> 14);
+  d[2] = field_digit(lo >> 21);
+  d[1] = field_digit(__funnelshift_r(lo, hi, 28));
+  d[0] = __int_as_float(0x4B400000 + ((int)hi >> 3)) - 12582912.0f;  // |d_0| <= 128
 }
 
 // Bits of |I| plus E: x = I 2^E lies below 2^(that) (INT_MIN-ish for I = 0).
@@ -155,13 +192,13 @@ __device__ __forceinline__ int warp_block_exp(int e) {
 // Rows r of an FP64 matrix with the K elements of row r at src[r * lds + k]
 // (k < klen, zero beyond): digits [digit][r][ldd] (BF16, zero padded up to
 // kpad) and one exponent per (row, block of 512 along k), stored at
-// exps[(r % rin) * lde + (r / rin) * nblk + blk].  B_oo: rows (P, i), K = j,
-// rin = all rows, lde = nblk = 1.  B_vv: rows (P, a), K = b, rin = nvirt,
-// lde = naux * nblk (exponents [a][P][blk]).
+// exps[((r / rin) * nblk + blk) * lde + r % rin].  B_oo: rows (P, i), K = j,
+// rin = all rows, nblk = 1.  B_vv: rows (P, a), K = b, rin = nvirt, lde =
+// the padded nvirt (exponents [P][blk][a]).
 __global__ void __launch_bounds__(256) k_slice_rows(long long rows, long long rin, int klen, int kpad,
                                                     const double* __restrict__ src, long long lds,
                                                     __nv_bfloat16* __restrict__ dst, long long ldd, long long plane,
-                                                    int* __restrict__ exps, long long lde, int nblk) {
+                                                    short* __restrict__ exps, long long lde, int nblk) {
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= rows * nblk) return;
@@ -180,7 +217,7 @@ __global__ void __launch_bounds__(256) k_slice_rows(long long rows, long long ri
     emax = max(emax, top_exp(I[q], E[q]));
   }
   const int e = warp_block_exp(emax);
-  if (lane == 0) exps[(r % rin) * lde + (r / rin) * nblk + blk] = e;
+  if (lane == 0) exps[((r / rin) * nblk + blk) * lde + r % rin] = (short)e;
 #pragma unroll
   for (int q = 0; q < kPerLane; ++q) {
     const int k = k0 + lane + 32 * q;
@@ -231,9 +268,9 @@ __global__ void __launch_bounds__(256) k_slice_x(int o, int v, int vp, int op, i
 // (P, b): one warp per (row, P, block of 512 along b); lane l handles the
 // pairs b = 2l + 64q, 2l + 1 + 64q of the block.  Digits in the tile order
 // of the main contraction, [digit][(P, b/64)][col * o + i][64]; exponents
-// ez[(col * o + i) * (pc * nbp) + P * nbp + blk].
+// ez[(P * nbp + blk) * (C * o) + col * o + i].
 __global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc, int nbp, int p0,
-                                                 const long long* __restrict__ Zi, const int* __restrict__ eoo,
+                                                 const long long* __restrict__ Zi, const short* __restrict__ eoo,
                                                  const int* __restrict__ ex, __nv_bfloat16* __restrict__ dst,
                                                  long long plane, int* __restrict__ ez) {
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -267,7 +304,7 @@ __global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc
     emax = max(emax, max(top_exp(I[2 * q], E[2 * q]), top_exp(I[2 * q + 1], E[2 * q + 1])));
   }
   const int e = warp_block_exp(emax);
-  if (lane == 0) ez[row * ((long long)pc * nbp) + (long long)P * nbp + blk] = e;
+  if (lane == 0) ez[((long long)P * nbp + blk) * ((long long)C * o) + row] = e;
   const int vt64 = vp / 64;
 #pragma unroll
   for (int q = 0; q < kPairs; ++q) {
@@ -285,8 +322,9 @@ __global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc
 
 // ---------------------------------------------------------------------------
 // The contraction kernel: persistent over (split, m tile, n tile) tiles of
-// 128 x 64; per K tile one pipeline stage holds the S digit planes of A and
-// of B; the MMA warp issues the S(S+1)/2 digit pairs of the tile into the
+// 128 x 64; per K tile one pipeline stage (3 stages for OZ_VV, 2 for
+// OZ_PLAIN, whose epilogue stages its int64 rows in shared memory) holds the
+// S digit planes of A and of B; the MMA warp issues the S(S+1)/2 digit pairs of the tile into the
 // group accumulators g = s + t (TMEM columns g * 64 .. +63) and hands them
 // to the epilogue at the end of each exactness block.  Warp roles as in
 // the other tensor-core kernels: warp 0 TMA producer, warp 1 TMEM owner and
@@ -301,11 +339,14 @@ template <int MODE>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p) {
   using namespace tc;
+  constexpr int ST = stages<MODE>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
-  uint64_t* empty = full + kStages;
-  uint64_t* accf = empty + kStages;
+  // [stages][store staging (OZ_PLAIN)][barriers]
+  uint8_t* stg_base = smem + ST * kStageBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(stg_base + (MODE == OZ_PLAIN ? kEpiWarps * kStgWarpBytes : 0));
+  uint64_t* empty = full + ST;
+  uint64_t* accf = empty + ST;
   uint64_t* acce = accf + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
 
@@ -315,7 +356,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
   const int ntiles = tiles_n * tiles_m * p.nsplit;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < ST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -347,8 +388,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         int n0, m0, kr0, kr1;
         coords(t, n0, m0, kr0, kr1);
         for (int kr = kr0; kr < kr1; ++kr, ++it) {
-          const int s = it % kStages;
-          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          const int s = it % ST;
+          const uint32_t ph = (uint32_t)(it / ST) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, p.err, ERR_WAIT_EMPTY)) {
             alive = false;
             break;
@@ -378,7 +419,6 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
       int it = 0, nb = 0;
       bool alive = true;
       for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
@@ -396,22 +436,28 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             }
             tc_fence_after();
           }
-          const int s = it % kStages;
-          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          const int s = it % ST;
+          const uint32_t ph = (uint32_t)(it / ST) & 1u;
           if (!mbar_wait(&full[s], ph, p.err, ERR_WAIT_FULL)) {
             alive = false;
             break;
           }
           tc_fence_after();
           const uint32_t base = smem_u32(smem + s * kStageBytes);
-          // pairs (sa, sb) with sa + sb < S; (0, g) comes first in group g
+          // A digit sa against the B digits sb = 0 .. S-1-sa, whose 64-row
+          // planes lie back to back and so form one B operand of
+          // (S - sa) * 64 rows: product (sa, sb) lands in accumulator
+          // columns (sa + sb) * 64, the columns of its group.  At most 256
+          // rows per MMA.  The MMA of sa = 0 writes every group first.
 #pragma unroll
           for (int sa = 0; sa < kS; ++sa) {
             const uint64_t adesc = sdesc_sw64(base + sa * kASlice);
 #pragma unroll
-            for (int sb = 0; sb < kS - sa; ++sb) {
-              const uint64_t bdesc = sdesc_sw64(base + kS * kASlice + sb * kBSlice);
-              const uint32_t d = tmem + (uint32_t)((sa + sb) * kBN);
+            for (int t0 = 0; t0 < kS - sa; t0 += 4) {
+              const int nt = min(4, kS - sa - t0);
+              const uint64_t bdesc = sdesc_sw64(base + kS * kASlice + t0 * kBSlice);
+              const uint32_t d = tmem + (uint32_t)((sa + t0) * kBN);
+              const uint32_t idesc = idesc_bf16(kBM, nt * kBN);
 #pragma unroll
               for (int k = 0; k < kKB / 16; ++k)
                 mma_bf16(d, adesc + 2 * k, bdesc + 2 * k, idesc, (!bstart || sa > 0 || k > 0) ? 1u : 0u);
@@ -438,51 +484,49 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       coords(t, n0, m0, kr0, kr1);
       const int m = m0 + row;
       const int nbase = n0 + half * 32;
-      double acc[32];
-      long long ival[32];
+      if constexpr (MODE == OZ_VV) {
+        double acc[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        acc[j] = 0.0;
-        ival[j] = 0;
-      }
-      for (int kr = kr0; kr < kr1; ++kr) {
-        const int P = kr / p.vt, bt = kr - P * p.vt;
-        if (!((bt % kBlkTiles) == kBlkTiles - 1 || bt == p.vt - 1)) continue;
-        ok = mbar_wait(accf, (uint32_t)nb & 1u, p.err, ERR_WAIT_ACC);
-        ++nb;
-        tc_fence_after();
-        if (!ok) break;
-        const int blk = P * p.nbp + bt / kBlkTiles;
-        int ea = 0;
-        if (MODE == OZ_VV) ea = m < p.M ? __ldg(p.ea + (size_t)m * p.lde_a + blk) : kEmptyExp;
+        for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+        for (int kr = kr0; kr < kr1; ++kr) {
+          const int P = kr / p.vt, bt = kr - P * p.vt;
+          if (!((bt % kBlkTiles) == kBlkTiles - 1 || bt == p.vt - 1)) continue;
+          const int blk = P * p.nbp + bt / kBlkTiles;
+          // the block's exponents, loaded while its MMAs still run
+          const int ea = m < p.M ? __ldg(p.ea + (size_t)blk * p.lde_a + m) : kEmptyExp;
+          uint4 eb4[4];  // 32 int16 exponents
+          const uint4* ebp = reinterpret_cast<const uint4*>(p.eb + (size_t)blk * p.lde_b + nbase);
 #pragma unroll
-        for (int c8 = 0; c8 < 4; ++c8) {
-          uint32_t r[kS][8];
+          for (int u = 0; u < 4; ++u) eb4[u] = __ldg(ebp + u);
+          ok = mbar_wait(accf, (uint32_t)nb & 1u, p.err, ERR_WAIT_ACC);
+          ++nb;
+          tc_fence_after();
+          if (!ok) break;
+          const int eab = ea - kOutShift;
 #pragma unroll
-          for (int g = 0; g < kS; ++g) tmem_ld8_nowait(tl + (uint32_t)(g * kBN + c8 * 8), r[g]);
-          tmem_wait_ld();
+          for (int c4 = 0; c4 < 8; ++c4) {
+            uint32_t r[kS][4];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            // I = sum_g acc_g 2^(7(S-1-g)) (Horner from the leading group)
-            long long I = __float2int_rn(__uint_as_float(r[0][j]));
+            for (int g = 0; g < kS; ++g) tmem_ld4_nowait(tl + (uint32_t)(g * kBN + c4 * 4), r[g]);
+            tmem_wait_ld();
+            const uint32_t w0 = (c4 & 1) ? eb4[c4 >> 1].z : eb4[c4 >> 1].x;
+            const uint32_t w1 = (c4 & 1) ? eb4[c4 >> 1].w : eb4[c4 >> 1].y;
+            const int ebj[4] = {(int)(short)(w0 & 0xFFFFu), (int)w0 >> 16, (int)(short)(w1 & 0xFFFFu), (int)w1 >> 16};
 #pragma unroll
-            for (int g = 1; g < kS; ++g) I = I * 128 + __float2int_rn(__uint_as_float(r[g][j]));
-            if (MODE == OZ_VV) {
-              const int n = nbase + c8 * 8 + j;
-              const int eb = n < p.N ? __ldg(p.eb + (size_t)n * p.lde_b + blk) : kEmptyExp;
-              acc[c8 * 8 + j] = fma((double)I, exp2i(ea + eb - kOutShift), acc[c8 * 8 + j]);
-            } else {
-              ival[c8 * 8 + j] = I;
+            for (int j = 0; j < 4; ++j) {
+              // I = sum_g acc_g 2^(7(S-1-g)) (Horner from the leading group)
+              long long I = __float2int_rn(__uint_as_float(r[0][j]));
+#pragma unroll
+              for (int g = 1; g < kS; ++g) I = I * 128 + __float2int_rn(__uint_as_float(r[g][j]));
+              acc[c4 * 4 + j] += scaled_i64(I, eab + ebj[j]);
             }
           }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce);
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(acce);
-      }
-      if (!ok) break;
-      if (m < p.M) {
-        if (MODE == OZ_VV) {
+        if (!ok) break;
+        if (m < p.M) {
           double* dst = reinterpret_cast<double*>(p.out) + (size_t)(t / (tiles_n * tiles_m)) * p.split_stride +
                         (size_t)m * p.ldo;
 #pragma unroll
@@ -490,14 +534,45 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             const int n = nbase + j;
             if (n < p.N) dst[n] = p.accum ? dst[n] + acc[j] : acc[j];
           }
-        } else {
-          long long* dst = reinterpret_cast<long long*>(p.out) + (size_t)m * p.ldo;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = nbase + j;
-            if (n < p.N) dst[n] = ival[j];
-          }
         }
+      } else {
+        // one block (K = nocc <= 512): the integers I, staged per warp in
+        // shared memory and stored row by row (32 consecutive words per row)
+        long long* stg = reinterpret_cast<long long*>(stg_base + (warp - 2) * kStgWarpBytes);
+        for (int kr = kr0; kr < kr1; ++kr) {
+          const int bt = kr % p.vt;
+          if (!((bt % kBlkTiles) == kBlkTiles - 1 || bt == p.vt - 1)) continue;
+          ok = mbar_wait(accf, (uint32_t)nb & 1u, p.err, ERR_WAIT_ACC);
+          ++nb;
+          tc_fence_after();
+          if (!ok) break;
+#pragma unroll
+          for (int c8 = 0; c8 < 4; ++c8) {
+            uint32_t r[kS][8];
+#pragma unroll
+            for (int g = 0; g < kS; ++g) tmem_ld8_nowait(tl + (uint32_t)(g * kBN + c8 * 8), r[g]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              long long I = __float2int_rn(__uint_as_float(r[0][j]));
+#pragma unroll
+              for (int g = 1; g < kS; ++g) I = I * 128 + __float2int_rn(__uint_as_float(r[g][j]));
+              stg[lane * kStgRow + c8 * 8 + j] = I;
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce);
+        }
+        if (!ok) break;
+        // lane l stores column nbase + l of the warp's 32 rows
+        long long* out = reinterpret_cast<long long*>(p.out);
+        const int n = nbase + lane;
+        const int mrow0 = m0 + q * 32;
+        for (int rr = 0; rr < 32; ++rr) {
+          if (mrow0 + rr < p.M && n < p.N) out[(size_t)(mrow0 + rr) * p.ldo + n] = stg[rr * kStgRow + lane];
+        }
+        __syncwarp();
       }
     }
   }
