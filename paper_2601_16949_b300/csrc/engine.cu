@@ -1610,7 +1610,8 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
     double*& p;
     ~Guard() { dfree(p); }
   } guard{stage};
-  if (h->prec != RTTDA_FP64) CKS(dalloc(&stage, std::max(stage_n, h->tc ? std::max(v * v, o * o) : (size_t)1)));
+  if (h->prec != RTTDA_FP64)
+    CKS(dalloc(&stage, std::max(stage_n, h->tc || h->oz ? std::max(v * v, o * o) : (size_t)1)));
   CKS(dalloc(&h->d_err, 1));
   CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   auto upload = [&](const double* src, size_t n, void** dst) -> rttda_status {
@@ -1678,32 +1679,43 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
         CK(cudaStreamSynchronize(h->stream));
       }
     }
-  } else {
-    CKS(upload(B_oo, P * o * o, &h->Boo));
-    CKS(upload(B_vv, P * v * v, &h->Bvv));
-  }
-  if (h->oz) {
+  } else if (h->oz) {
     // Ozaki digits of B_oo (rows (P, i), K = j: one block, nocc <= 512) and
-    // of B_vv (rows (P, a), K = b in blocks of 512); the FP64 copies go
+    // of B_vv (rows (P, a), K = b in blocks of 512), sliced slab by slab of
+    // whole P from a staging copy; no FP64 copy of these factors is kept
     constexpr int S = oz::kS;
-    const size_t op = h->op, vp = h->vp;
-    h->oz_nbp = (int)cdiv(vp, oz::kBlk);
+    const size_t op = h->op, vp = h->vp, nbp = (size_t)cdiv(vp, oz::kBlk);
+    h->oz_nbp = (int)nbp;
     CKS(dalloc(&h->oz_boo, S * P * o * op));
     CKS(dalloc(&h->oz_eoo, P * o));
     CKS(dalloc(&h->oz_bvv, S * P * v * vp));
-    CKS(dalloc(&h->oz_evv, vp * P * (size_t)h->oz_nbp));
-    const long long ro = (long long)(P * o), rv = (long long)(P * v);
-    oz::k_slice_rows<<<blocks_for(ro * 32, 256), 256, 0, h->stream>>>(
-        ro, ro, (int)o, (int)op, (const double*)h->Boo, (long long)o, h->oz_boo, (long long)op, ro * (long long)op,
-        h->oz_eoo, ro, 1);
-    oz::k_slice_rows<<<blocks_for(rv * h->oz_nbp * 32, 256), 256, 0, h->stream>>>(
-        rv, (long long)v, (int)v, (int)vp, (const double*)h->Bvv, (long long)v, h->oz_bvv, (long long)vp,
-        rv * (long long)vp, h->oz_evv, (long long)vp, h->oz_nbp);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(h->stream));
-    dfree(h->Boo);
-    dfree(h->Bvv);
-    h->Boo = h->Bvv = nullptr;
+    CKS(dalloc(&h->oz_evv, vp * P * nbp));
+    auto slice = [&](const double* src, size_t slab, bool vv) -> rttda_status {
+      const size_t per = std::max<size_t>(1, chunk / slab);
+      for (size_t p0 = 0; p0 < P; p0 += per) {
+        const size_t pc = std::min(per, P - p0);
+        CK(cudaMemcpyAsync(stage, src + p0 * slab, pc * slab * 8, cudaMemcpyDefault, h->stream));
+        if (vv) {
+          const long long rows = (long long)(pc * v);
+          oz::k_slice_rows<<<blocks_for(rows * (long long)nbp * 32, 256), 256, 0, h->stream>>>(
+              rows, (long long)v, (int)v, (int)vp, stage, (long long)v, h->oz_bvv + p0 * v * vp, (long long)vp,
+              (long long)(P * v * vp), h->oz_evv + p0 * nbp * vp, (long long)vp, (int)nbp);
+        } else {
+          const long long rows = (long long)(pc * o);
+          oz::k_slice_rows<<<blocks_for(rows * 32, 256), 256, 0, h->stream>>>(
+              rows, rows, (int)o, (int)op, stage, (long long)o, h->oz_boo + p0 * o * op, (long long)op,
+              (long long)(P * o * op), h->oz_eoo + p0 * o, rows, 1);
+        }
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->stream));
+      }
+      return RTTDA_OK;
+    };
+    CKS(slice(B_oo, o * o, false));
+    CKS(slice(B_vv, v * v, true));
+  } else {
+    CKS(upload(B_oo, P * o * o, &h->Boo));
+    CKS(upload(B_vv, P * v * v, &h->Bvv));
   }
   CKS(upload64(eps_occ, o, &h->eps_o));
   CKS(upload64(eps_virt, v, &h->eps_v));
@@ -2161,8 +2173,8 @@ size_t estimate_bytes(int nocc, int nvirt, int naux, int ntraj, int prec, long n
   const size_t vp = (v + 63) / 64 * 64, op = (o + 7) / 8 * 8;
   const size_t planes = prec == RTTDA_BF16 ? 1 : 2, zplanes = prec == RTTDA_BF16X3 ? 2 : 1;
   size_t b = P * ov * fb + (o + v + 3 * (o * o + v * v + ov)) * 8;
-  if (ozk)  // digits of B_oo and B_vv (the FP64 copies are held while slicing)
-    b += (P * o * op + P * v * vp) * 2 * oz::kS + (P * o * o + P * v * v) * 8;
+  if (ozk)  // digits of B_oo and B_vv
+    b += (P * o * op + P * v * vp) * 2 * oz::kS + (P * o + vp * P * ((vp + 511) / 512)) * 2;
   else
     b += tc ? (P * o * op + P * vp * vp + 2 * P * ov) * 2 * planes : (P * o * o + P * v * v) * fb;
   b += N * C * 8 * 6 + T * (o * o + v * v + ov) * (8 + cb);               // state, dipole blocks
