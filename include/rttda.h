@@ -85,7 +85,8 @@ typedef enum {
  *           weight without rounding in FP32 and joined in int64, and blocks
  *           are added in FP64.  Z = B_oo c is exact up to the digits' 42
  *           bits; relative error of the exchange about 2^-42 of the block
- *           scales.  Coulomb and field in FP64 (CUDA cores).  Requires
+ *           scales.  The Coulomb passes w = B_ov c and B_ov^T (2w) run on
+ *           the same digits; field in FP64 (CUDA cores).  Requires
  *           nocc <= 512 (RTTDA_E_ARG otherwise). */
 typedef enum {
   RTTDA_FP64 = 0, RTTDA_FP32 = 1, RTTDA_TF32 = 2, RTTDA_BF16 = 3, RTTDA_BF16X3 = 4, RTTDA_BF16X2 = 5,
@@ -339,7 +340,8 @@ rttda_status rttda_set_integrator(rttda_t h, int integrator);
  *               3: tcgen05, Ozaki digit pairs on 128 x 64 tiles (FP64_OZ),
  * with main_bn output columns per tile, K tiles of main_kb BF16 and
  * main_splits split-K partials; Z^P = B^P_oo c is built for z_chunk values
- * of P at a time.  coulomb_kernel 0: SIMT, 1: tcgen05.
+ * of P at a time.  coulomb_kernel 0: SIMT, 1: tcgen05, 2: tcgen05 Ozaki digits
+ * (FP64_OZ).
  * tuned 0: heuristic plan (or RTTDA_TUNE=0), 1: timed now (tune_ms[k] is the
  * fastest of five launches of candidate k in milliseconds, ncand
  * candidates), 2: taken

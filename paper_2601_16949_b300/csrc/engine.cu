@@ -220,9 +220,24 @@ struct rttda_ctx {
   int* oz_ex = nullptr;             // [C*vp]
   long long* oz_zi = nullptr;       // [zchunk*o][C*vp] integer Z of the Z build
   __nv_bfloat16* oz_z = nullptr;    // [digit][(zchunk, vp/64)][C*o][64]
-  int* oz_ez = nullptr;             // [zchunk*nbp][C*o]
+  short* oz_ez = nullptr;           // [zchunk*nbp][C*o]
   size_t oz_zplane = 0;
   int oz_pps = 1;                   // P per split of the main contraction
+  // Coulomb on digits: B_ov (rows P, K = ia) and its transpose (rows ia,
+  // K = P) set up at create; per batch the amplitudes (rows col, K = ia),
+  // the first pass's FP64 partials and the digits of 2w (rows col, K = P)
+  __nv_bfloat16* oz_bov = nullptr;   // [digit][P][ovp]
+  short* oz_ebov = nullptr;          // [nkb][P]
+  __nv_bfloat16* oz_bovt = nullptr;  // [digit][ov][Pp]
+  short* oz_ebovt = nullptr;         // [npb][ov]
+  int oz_ovp = 8, oz_Pp = 8, oz_nkb = 1, oz_npb = 1;
+  __nv_bfloat16* oz_xc = nullptr;    // [digit][cp][ovp]
+  short* oz_exc = nullptr;           // [nkb][cp]
+  double* oz_wpart = nullptr;        // [SW][P][C]
+  __nv_bfloat16* oz_w = nullptr;     // [digit][cp][Pp]
+  short* oz_ew = nullptr;            // [npb][cp]
+  int oz_cp = 64, oz_pps1 = 1, oz_pps2 = 1;
+  CUtensorMap tmOzBov, tmOzBovT, tmOzXc, tmOzW;
   CUtensorMap tmOzX;
   std::vector<CUtensorMap> tmOzBoo, tmOzZ, tmOzBvv;
 
@@ -263,6 +278,10 @@ rttda_ctx::~rttda_ctx() {
   dfree(oz_eoo);
   dfree(oz_bvv);
   dfree(oz_evv);
+  dfree(oz_bov);
+  dfree(oz_ebov);
+  dfree(oz_bovt);
+  dfree(oz_ebovt);
   dfree(Bov_tc);
   dfree(BovT_tc);
   dfree(d_err);
@@ -281,7 +300,7 @@ rttda_ctx::~rttda_ctx() {
 void rttda_ctx::free_batch() {
   void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xn, Xs, Xs2, acc, F, E, term,
                 obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk, Xc, Wt, wpart_tc, Xf, f0_part,
-                oz_x, oz_ex, oz_zi, oz_z, oz_ez};
+                oz_x, oz_ex, oz_zi, oz_z, oz_ez, oz_xc, oz_exc, oz_wpart, oz_w, oz_ew};
   for (void* p : ps) dfree(p);
   d_pulses = nullptr;
   d_kappa = d_dirs = moo64 = mvv64 = m064 = nullptr;
@@ -299,6 +318,11 @@ void rttda_ctx::free_batch() {
   oz_zi = nullptr;
   oz_z = nullptr;
   oz_ez = nullptr;
+  oz_xc = nullptr;
+  oz_exc = nullptr;
+  oz_wpart = nullptr;
+  oz_w = nullptr;
+  oz_ew = nullptr;
   tmOzBoo.clear();
   tmOzZ.clear();
   tmOzBvv.clear();
@@ -545,6 +569,8 @@ void oz_attr() {
                        (int)oz::smem_bytes<oz::OZ_PLAIN>());
   cudaFuncSetAttribute(oz::k_oz_gemm<oz::OZ_VV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)oz::smem_bytes<oz::OZ_VV>());
+  cudaFuncSetAttribute(oz::k_oz_gemm<oz::OZ_PLAIN64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)oz::smem_bytes<oz::OZ_PLAIN64>());
 }
 
 template <int MODE>
@@ -610,6 +636,47 @@ void exchange_oz(rttda_ctx* h, const double* X, cudaStream_t s) {
       oz_launch<oz::OZ_VV>(h->tmOzZ[c], h->tmOzBvv[c], prm, s);
     }
   }
+}
+
+// Coulomb 2 sum_jb (ia|jb) c_jb to FP64 accuracy on digits: w = B_ov c
+// (M = naux, K = nocc*nvirt, split-K partials), then J = B_ov^T (2w)
+// (M = nocc*nvirt, K = naux) into the FP64 partials the combine reads.
+void coulomb_oz(rttda_ctx* h, const double* X, cudaStream_t s) {
+  Prof pr(h, RTTDA_KC_COULOMB, s);
+  h->launches += 4;
+  const int C = 2 * h->T, P = h->P, cp = h->oz_cp;
+  const long long ov = h->ov;
+  oz::k_slice_xc<<<blocks_for((long long)cp * h->oz_nkb * 32, 256), 256, 0, s>>>(
+      ov, h->oz_ovp, C, cp, h->oz_nkb, X, h->oz_xc, (long long)cp * h->oz_ovp, h->oz_exc);
+  oz::Params prm{};
+  prm.M = P;
+  prm.N = C;
+  prm.vt = oz::kBlkTiles;
+  prm.pc = h->oz_nkb;
+  prm.pps = h->oz_pps1;
+  prm.nsplit = h->SW;
+  prm.nbp = 1;
+  prm.out = h->oz_wpart;
+  prm.ldo = C;
+  prm.split_stride = (long long)P * C;
+  prm.ea = h->oz_ebov;
+  prm.lde_a = P;
+  prm.eb = h->oz_exc;
+  prm.lde_b = cp;
+  prm.err = h->d_err;
+  oz_launch<oz::OZ_PLAIN64>(h->tmOzBov, h->tmOzXc, prm, s);
+  oz::k_slice_w<<<blocks_for((long long)cp * h->oz_npb * 32, 256), 256, 0, s>>>(
+      P, h->oz_Pp, C, cp, h->oz_npb, h->SW, h->oz_wpart, h->oz_w, (long long)cp * h->oz_Pp, h->oz_ew);
+  prm.M = (int)ov;
+  prm.pc = h->oz_npb;
+  prm.pps = h->oz_pps2;
+  prm.nsplit = h->SJ;
+  prm.out = h->Jpart;
+  prm.split_stride = ov * C;
+  prm.ea = h->oz_ebovt;
+  prm.lde_a = ov;
+  prm.eb = h->oz_ew;
+  oz_launch<oz::OZ_PLAIN64>(h->tmOzBovT, h->tmOzW, prm, s);
 }
 
 // Coulomb on the FP32 streaming kernels: FP32 copy of the stage's amplitudes,
@@ -820,6 +887,7 @@ struct Ops {
 
 // FP64_OZ: the FP64 paths with the exchange on Ozaki digits
 struct OpsOz : Ops<double, double, false> {
+  static void coulomb(rttda_ctx* h, const double* X, cudaStream_t s) { coulomb_oz(h, X, s); }
   static void exchange(rttda_ctx* h, const double* X, cudaStream_t s) { exchange_oz(h, X, s); }
   static void set_smem_limits() {
     Ops<double, double, false>::set_smem_limits();
@@ -1481,6 +1549,46 @@ static rttda_status alloc_oz(rttda_ctx* h, int C) {
   return RTTDA_OK;
 }
 
+// Coulomb on digits for C columns: split-K counts of both passes (whole
+// blocks of 512 per split, enough splits to fill the SMs once), buffers and
+// maps.
+static rttda_status alloc_oz_coul(rttda_ctx* h, int C) {
+  constexpr int S = oz::kS;
+  const int P = h->P;
+  const long long ov = h->ov;
+  const int cp = (int)cdiv(C, oz::kBN) * oz::kBN;
+  h->oz_cp = cp;
+  auto splits = [](long long tiles, int nblk, int& pps) {
+    const int sk = (int)std::max(1LL, std::min<long long>(nblk, kNumSM / std::max(1LL, tiles)));
+    pps = (int)cdiv(nblk, sk);
+    return (int)cdiv(nblk, pps);
+  };
+  h->SW = splits(cdiv(P, tc::kBM) * (cp / oz::kBN), h->oz_nkb, h->oz_pps1);
+  h->SJ = splits(cdiv(ov, tc::kBM) * (cp / oz::kBN), h->oz_npb, h->oz_pps2);
+  CKS(dalloc(&h->oz_xc, (size_t)S * cp * h->oz_ovp));
+  CKS(dalloc(&h->oz_exc, (size_t)h->oz_nkb * cp));
+  CKS(dalloc(&h->oz_wpart, (size_t)h->SW * P * C));
+  CKS(dalloc(&h->oz_w, (size_t)S * cp * h->oz_Pp));
+  CKS(dalloc(&h->oz_ew, (size_t)h->oz_npb * cp));
+  char* p = nullptr;
+  CKS(dalloc_bytes((void**)&p, (size_t)h->SJ * ov * C * sizeof(double)));
+  h->Jpart = p;
+  CKS(dalloc_bytes((void**)&p, sizeof(double)));  // SIMT pass-1 scratch is unused here
+  h->w = p;
+  const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_64B;
+  auto map3 = [&](CUtensorMap* m, const void* base, uint64_t k, uint64_t rows, uint32_t boxr) {
+    const uint64_t dims[3] = {k, rows, (uint64_t)S};
+    const uint64_t str[2] = {k * 2, rows * k * 2};
+    const uint32_t box[3] = {(uint32_t)oz::kKB, boxr, 1};
+    return bf16_map(m, base, 3, dims, str, box, sw);
+  };
+  CKS(map3(&h->tmOzBov, h->oz_bov, (uint64_t)h->oz_ovp, (uint64_t)P, tc::kBM));
+  CKS(map3(&h->tmOzXc, h->oz_xc, (uint64_t)h->oz_ovp, (uint64_t)cp, oz::kBN));
+  CKS(map3(&h->tmOzBovT, h->oz_bovt, (uint64_t)h->oz_Pp, (uint64_t)ov, tc::kBM));
+  CKS(map3(&h->tmOzW, h->oz_w, (uint64_t)h->oz_Pp, (uint64_t)cp, oz::kBN));
+  return RTTDA_OK;
+}
+
 rttda_status rttda_ctx::alloc_batch() {
   const int C = 2 * T;
   const long long NC = N * C;
@@ -1495,7 +1603,9 @@ rttda_status rttda_ctx::alloc_batch() {
   CKS(dalloc(&d_step, 1));
   // Coulomb scratch
   coul_tc = tc && Bov_tc != nullptr && C >= 16;
-  if (coul_tc) {
+  if (oz) {
+    CKS(::alloc_oz_coul(this, C));
+  } else if (coul_tc) {
     CKS(alloc_coul_tc(this, C));
   } else {
     const int V = (int)(16 / fbytes);
@@ -1659,6 +1769,31 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
     return RTTDA_OK;
   };
   CKS(upload(B_ov, P * o * v, &h->Bov));
+  if (h->oz) {
+    // Ozaki digits of B_ov (rows P, K = ia) and of its transpose (rows ia,
+    // K = P) for the Coulomb passes; the FP64 copy goes afterwards
+    constexpr int S = oz::kS;
+    const long long ovl = (long long)(o * v);
+    h->oz_ovp = (int)(cdiv(ovl, 8) * 8);
+    h->oz_Pp = (int)(cdiv((long long)P, 8) * 8);
+    h->oz_nkb = (int)cdiv(ovl, oz::kBlk);
+    h->oz_npb = (int)cdiv((long long)P, oz::kBlk);
+    CKS(dalloc(&h->oz_bov, S * P * (size_t)h->oz_ovp));
+    CKS(dalloc(&h->oz_ebov, (size_t)h->oz_nkb * P));
+    CKS(dalloc(&h->oz_bovt, S * (size_t)ovl * h->oz_Pp));
+    CKS(dalloc(&h->oz_ebovt, (size_t)h->oz_npb * ovl));
+    const double* B = (const double*)h->Bov;
+    oz::k_slice_rows<<<blocks_for((long long)P * h->oz_nkb * 32, 256), 256, 0, h->stream>>>(
+        (long long)P, (long long)P, (int)ovl, h->oz_ovp, B, ovl, 1, h->oz_bov, (long long)h->oz_ovp,
+        (long long)P * h->oz_ovp, h->oz_ebov, (long long)P, h->oz_nkb);
+    oz::k_slice_rows<<<blocks_for(ovl * h->oz_npb * 32, 256), 256, 0, h->stream>>>(
+        ovl, ovl, (int)P, h->oz_Pp, B, 1, ovl, h->oz_bovt, (long long)h->oz_Pp, ovl * h->oz_Pp, h->oz_ebovt, ovl,
+        h->oz_npb);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    dfree(h->Bov);
+    h->Bov = nullptr;
+  }
   if (h->tc) {
     CKS(pack(B_oo, o * o, o * (size_t)h->op, false, &h->Boo_tc));
     CKS(pack(B_vv, v * v, (size_t)h->vp * h->vp, true, &h->Bvv_tc));
@@ -1698,12 +1833,12 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
         if (vv) {
           const long long rows = (long long)(pc * v);
           oz::k_slice_rows<<<blocks_for(rows * (long long)nbp * 32, 256), 256, 0, h->stream>>>(
-              rows, (long long)v, (int)v, (int)vp, stage, (long long)v, h->oz_bvv + p0 * v * vp, (long long)vp,
+              rows, (long long)v, (int)v, (int)vp, stage, (long long)v, 1, h->oz_bvv + p0 * v * vp, (long long)vp,
               (long long)(P * v * vp), h->oz_evv + p0 * nbp * vp, (long long)vp, (int)nbp);
         } else {
           const long long rows = (long long)(pc * o);
           oz::k_slice_rows<<<blocks_for(rows * 32, 256), 256, 0, h->stream>>>(
-              rows, rows, (int)o, (int)op, stage, (long long)o, h->oz_boo + p0 * o * op, (long long)op,
+              rows, rows, (int)o, (int)op, stage, (long long)o, 1, h->oz_boo + p0 * o * op, (long long)op,
               (long long)(P * o * op), h->oz_eoo + p0 * o, rows, 1);
         }
         CK(cudaGetLastError());
@@ -1799,11 +1934,12 @@ rttda_status rttda_create_device(int nocc, int nvirt, int naux, const double* ep
 rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes) {
   if (!h || !bytes) return set_error(RTTDA_E_ARG, "rttda_memory_bytes: NULL argument");
   const size_t o = h->o, v = h->v, P = h->P;
-  size_t b = P * o * v * h->fbytes + (o + v + 3 * (o * o + v * v + o * v)) * 8;
+  size_t b = (h->oz ? 0 : P * o * v * h->fbytes) + (o + v + 3 * (o * o + v * v + o * v)) * 8;
   if (h->tc)
     b += (P * o * (size_t)h->op + P * (size_t)h->vp * h->vp) * 2 * h->nplanes;
   else if (h->oz)
-    b += (P * o * (size_t)h->op + P * v * (size_t)h->vp) * 2 * oz::kS + (P * o + (size_t)h->vp * P * h->oz_nbp) * 2;
+    b += (P * o * (size_t)h->op + P * v * (size_t)h->vp + P * (size_t)h->oz_ovp + (size_t)h->ov * h->oz_Pp) * 2 * oz::kS +
+         (P * o + (size_t)h->vp * P * h->oz_nbp + (size_t)h->oz_nkb * P + (size_t)h->oz_npb * h->ov) * 2;
   else
     b += (P * o * o + P * v * v) * h->fbytes;
   if (h->T > 0) {
@@ -2386,7 +2522,7 @@ rttda_status rttda_plan(rttda_t h, rttda_plan_info* out) {
   }
   p.prec = (int)h->prec;
   p.ntraj = h->T;
-  p.coulomb_kernel = h->coul_tc ? 1 : 0;
+  p.coulomb_kernel = h->oz ? 2 : h->coul_tc ? 1 : 0;
   *out = p;
   return RTTDA_OK;
 }

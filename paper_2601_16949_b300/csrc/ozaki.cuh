@@ -58,21 +58,24 @@ constexpr uint32_t kTmemCols = 512;
 static_assert(kS * kBN <= (int)kTmemCols, "group accumulators exceed TMEM");
 static_assert(kStageBytes % 1024 == 0, "stage must keep 1024-byte alignment");
 static_assert(kBlk * 8 * 4096 <= (1 << 24), "a group sum of one block must stay exact in FP32");
+// operand addressing
+enum : int {
+  OZ_PLAIN = 0,    // A [digit][row][k], B [digit][row][k]: 3-D maps (k, row, digit); one block, out int64 I
+  OZ_VV = 1,       // A = Z digits [digit][(P, b/64)][row][64]; B = B_vv digits [digit][P][a][b]; out FP64
+  OZ_PLAIN64 = 2   // 3-D maps as OZ_PLAIN over many blocks (a "P" below is one block); out FP64
+};
+
 constexpr int kStgRow = 33;  // int64 words per staged row (32 + 1 against bank conflicts)
 constexpr int kStgWarpBytes = 32 * kStgRow * 8;
 
 template <int MODE>
-constexpr int stages() { return MODE == 0 ? kStagesPlain : kStagesVV; }
+constexpr int stages() { return MODE == OZ_PLAIN ? kStagesPlain : kStagesVV; }
 template <int MODE>
 constexpr size_t smem_bytes() {
-  return (size_t)stages<MODE>() * kStageBytes + (MODE == 0 ? (size_t)tc::kEpiWarps * kStgWarpBytes : 0) + 1024 + 256;
+  return (size_t)stages<MODE>() * kStageBytes + (MODE == OZ_PLAIN ? (size_t)tc::kEpiWarps * kStgWarpBytes : 0) +
+         1024 + 256;
 }
 
-// operand addressing
-enum : int {
-  OZ_PLAIN = 0,  // A [digit][row][k], B [digit][row][k]: 3-D maps (k, row, digit); out int64 I
-  OZ_VV = 1      // A = Z digits [digit][(P, b/64)][row][64]; B = B_vv digits [digit][P][a][b]; out FP64
-};
 
 struct Params {
   int M, N;
@@ -84,9 +87,9 @@ struct Params {
   void* out;     // OZ_VV: double [split][M][ldo]; OZ_PLAIN: long long [M][ldo]
   long long ldo, split_stride;
   int accum;     // OZ_VV: out += result (later chunks of P)
-  const int* ea;  // A block exponents ea[block * lde_a + m] (OZ_VV)
+  const short* ea;  // A block exponents ea[block * lde_a + m] (OZ_VV, OZ_PLAIN64)
   long long lde_a;
-  const short* eb;  // B block exponents eb[block * lde_b + n] (OZ_VV; lde_b % 32 == 0)
+  const short* eb;  // B block exponents eb[block * lde_b + n] (OZ_VV, OZ_PLAIN64; lde_b % 32 == 0)
   long long lde_b;
   int* err;
 };
@@ -189,14 +192,14 @@ __device__ __forceinline__ int warp_block_exp(int e) {
   return e < -0x20000000 ? kEmptyExp : e;
 }
 
-// Rows r of an FP64 matrix with the K elements of row r at src[r * lds + k]
+// Rows r of an FP64 matrix with element k of row r at src[r * lds + k * ldk]
 // (k < klen, zero beyond): digits [digit][r][ldd] (BF16, zero padded up to
 // kpad) and one exponent per (row, block of 512 along k), stored at
 // exps[((r / rin) * nblk + blk) * lde + r % rin].  B_oo: rows (P, i), K = j,
 // rin = all rows, nblk = 1.  B_vv: rows (P, a), K = b, rin = nvirt, lde =
 // the padded nvirt (exponents [P][blk][a]).
 __global__ void __launch_bounds__(256) k_slice_rows(long long rows, long long rin, int klen, int kpad,
-                                                    const double* __restrict__ src, long long lds,
+                                                    const double* __restrict__ src, long long lds, long long ldk,
                                                     __nv_bfloat16* __restrict__ dst, long long ldd, long long plane,
                                                     short* __restrict__ exps, long long lde, int nblk) {
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(256) k_slice_rows(long long rows, long long ri
     const int k = k0 + lane + 32 * q;
     I[q] = 0;
     E[q] = 0;
-    if (k < klen) f64_parts(src[r * lds + k], I[q], E[q]);
+    if (k < klen) f64_parts(src[r * lds + (long long)k * ldk], I[q], E[q]);
     emax = max(emax, top_exp(I[q], E[q]));
   }
   const int e = warp_block_exp(emax);
@@ -263,6 +266,80 @@ __global__ void __launch_bounds__(256) k_slice_x(int o, int v, int vp, int op, i
   }
 }
 
+// Stage amplitudes for the Coulomb pass w_P = sum_ia B^P_ia c_ia: rows col
+// (< cp; rows col >= C are zero), K = ia < ov in blocks of 512, element
+// X[(1 + ia) * C + col].  Digits [digit][col][ovp], exponents
+// ex[blk * cp + col]; one warp per (col, block).
+__global__ void __launch_bounds__(256) k_slice_xc(long long ov, int ovp, int C, int cp, int nkb,
+                                                  const double* __restrict__ X, __nv_bfloat16* __restrict__ dst,
+                                                  long long plane, short* __restrict__ ex) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)cp * nkb) return;
+  const int col = (int)(wid / nkb), blk = (int)(wid - (long long)col * nkb);
+  long long I[kPerLane];
+  int E[kPerLane];
+  int emax = -0x40000000;
+#pragma unroll
+  for (int q = 0; q < kPerLane; ++q) {
+    const long long ia = (long long)blk * kBlk + lane + 32 * q;
+    I[q] = 0;
+    E[q] = 0;
+    if (ia < ov && col < C) f64_parts(X[(1 + ia) * C + col], I[q], E[q]);
+    emax = max(emax, top_exp(I[q], E[q]));
+  }
+  const int e = warp_block_exp(emax);
+  if (lane == 0) ex[(long long)blk * cp + col] = (short)e;
+#pragma unroll
+  for (int q = 0; q < kPerLane; ++q) {
+    const long long ia = (long long)blk * kBlk + lane + 32 * q;
+    if (ia >= ovp) continue;
+    float d[kS];
+    digits(fixed_point(I[q], E[q], e), d);
+#pragma unroll
+    for (int s = 0; s < kS; ++s) dst[(size_t)s * plane + (long long)col * ovp + ia] = __float2bfloat16_rn(d[s]);
+  }
+}
+
+// The Coulomb intermediate 2 w: rows col (< cp), K = P in blocks of 512,
+// 2 w[P][col] = 2 sum_s wpart[s][P][col] (the nsp split-K partials of the
+// first pass, added in order).  Digits [digit][col][Pp], exponents
+// ew[blk * cp + col].
+__global__ void __launch_bounds__(256) k_slice_w(int P, int Pp, int C, int cp, int npb, int nsp,
+                                                 const double* __restrict__ wpart, __nv_bfloat16* __restrict__ dst,
+                                                 long long plane, short* __restrict__ ew) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)cp * npb) return;
+  const int col = (int)(wid / npb), blk = (int)(wid - (long long)col * npb);
+  long long I[kPerLane];
+  int E[kPerLane];
+  int emax = -0x40000000;
+#pragma unroll
+  for (int q = 0; q < kPerLane; ++q) {
+    const int Pi = blk * kBlk + lane + 32 * q;
+    I[q] = 0;
+    E[q] = 0;
+    if (Pi < P && col < C) {
+      double a = 0.0;
+      for (int sp = 0; sp < nsp; ++sp) a += wpart[((size_t)sp * P + Pi) * C + col];
+      f64_parts(2.0 * a, I[q], E[q]);
+    }
+    emax = max(emax, top_exp(I[q], E[q]));
+  }
+  const int e = warp_block_exp(emax);
+  if (lane == 0) ew[(long long)blk * cp + col] = (short)e;
+#pragma unroll
+  for (int q = 0; q < kPerLane; ++q) {
+    const int Pi = blk * kBlk + lane + 32 * q;
+    if (Pi >= Pp) continue;
+    float d[kS];
+    digits(fixed_point(I[q], E[q], e), d);
+#pragma unroll
+    for (int s = 0; s < kS; ++s) dst[(size_t)s * plane + (size_t)col * Pp + Pi] = __float2bfloat16_rn(d[s]);
+  }
+}
+
 // Z digits for the main contraction.  Zi[(P, i)][(col, b)] = I from the
 // Z build, with x = I 2^(eoo[P, i] + ex[col, b] - 49).  Rows (col, i), K =
 // (P, b): one warp per (row, P, block of 512 along b); lane l handles the
@@ -272,7 +349,7 @@ __global__ void __launch_bounds__(256) k_slice_x(int o, int v, int vp, int op, i
 __global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc, int nbp, int p0,
                                                  const long long* __restrict__ Zi, const short* __restrict__ eoo,
                                                  const int* __restrict__ ex, __nv_bfloat16* __restrict__ dst,
-                                                 long long plane, int* __restrict__ ez) {
+                                                 long long plane, short* __restrict__ ez) {
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const long long nw = (long long)C * o * pc * nbp;
@@ -304,7 +381,7 @@ __global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc
     emax = max(emax, max(top_exp(I[2 * q], E[2 * q]), top_exp(I[2 * q + 1], E[2 * q + 1])));
   }
   const int e = warp_block_exp(emax);
-  if (lane == 0) ez[((long long)P * nbp + blk) * ((long long)C * o) + row] = e;
+  if (lane == 0) ez[((long long)P * nbp + blk) * ((long long)C * o) + row] = (short)e;
   const int vt64 = vp / 64;
 #pragma unroll
   for (int q = 0; q < kPairs; ++q) {
@@ -396,7 +473,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
           }
           uint8_t* st = smem + s * kStageBytes;
           mbar_expect_tx(&full[s], (uint32_t)kStageBytes);
-          if (MODE == OZ_PLAIN) {
+          if (MODE != OZ_VV) {
 #pragma unroll
             for (int q = 0; q < kS; ++q) tma_load_3d(st + q * kASlice, &tmA, &full[s], kr * kKB, m0, q);
 #pragma unroll
@@ -484,7 +561,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       coords(t, n0, m0, kr0, kr1);
       const int m = m0 + row;
       const int nbase = n0 + half * 32;
-      if constexpr (MODE == OZ_VV) {
+      if constexpr (MODE != OZ_PLAIN) {
         double acc[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) acc[j] = 0.0;
