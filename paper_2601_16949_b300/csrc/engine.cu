@@ -220,16 +220,16 @@ struct rttda_ctx {
   int* oz_ex = nullptr;             // [C*vp]
   long long* oz_zi = nullptr;       // [zchunk*o][C*vp] integer Z of the Z build
   __nv_bfloat16* oz_z = nullptr;    // [digit][(zchunk, vp/64)][C*o][64]
-  short* oz_ez = nullptr;           // [zchunk*nbp][C*o]
+  int* oz_ez = nullptr;             // [zchunk*nbp][C*o] block exponents of Z
   size_t oz_zplane = 0;
   int oz_pps = 1;                   // P per split of the main contraction
   // Coulomb on digits: B_ov (rows P, K = ia) and its transpose (rows ia,
   // K = P) set up at create; per batch the amplitudes (rows col, K = ia),
   // the first pass's FP64 partials and the digits of 2w (rows col, K = P)
   __nv_bfloat16* oz_bov = nullptr;   // [digit][P][ovp]
-  short* oz_ebov = nullptr;          // [nkb][P]
+  int* oz_ebov = nullptr;            // [nkb][P]
   __nv_bfloat16* oz_bovt = nullptr;  // [digit][ov][Pp]
-  short* oz_ebovt = nullptr;         // [npb][ov]
+  int* oz_ebovt = nullptr;           // [npb][ov]
   int oz_ovp = 8, oz_Pp = 8, oz_nkb = 1, oz_npb = 1;
   __nv_bfloat16* oz_xc = nullptr;    // [digit][cp][ovp]
   short* oz_exc = nullptr;           // [nkb][cp]
@@ -577,13 +577,14 @@ template <int MODE>
 void oz_launch(const CUtensorMap& a, const CUtensorMap& b, const oz::Params& prm, cudaStream_t s) {
   const long long tiles = cdiv(prm.N, oz::kBN) * cdiv(prm.M, tc::kBM) * prm.nsplit;
   const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(tiles, kNumSM));
-  oz::k_oz_gemm<MODE><<<grid, tc::kThreads, oz::smem_bytes<MODE>(), s>>>(a, b, prm);
+  oz::k_oz_gemm<MODE><<<grid, oz::kThreads, oz::smem_bytes<MODE>(), s>>>(a, b, prm);
 }
 
 // K_(col,i),a = sum_{P,b} Z^P_(col,i),b B^P_ab to FP64 accuracy: digits of
 // the stage amplitudes, then per chunk of P the Z build (Z^P = B^P_oo c as
-// integers, one exactness block since nocc <= 512), the digits of Z per
-// block of (P, b) and the main contraction into FP64 split-K partials.
+// exact integers, one exactness block since nocc <= 512), the digits of Z per
+// block of (row, P, b / 512) and the main contraction into FP64 split-K
+// partials.
 void exchange_oz(rttda_ctx* h, const double* X, cudaStream_t s) {
   const int C = 2 * h->T, o = h->o, v = h->v, vp = h->vp, op = h->op;
   {
@@ -1783,10 +1784,10 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
     CKS(dalloc(&h->oz_bovt, S * (size_t)ovl * h->oz_Pp));
     CKS(dalloc(&h->oz_ebovt, (size_t)h->oz_npb * ovl));
     const double* B = (const double*)h->Bov;
-    oz::k_slice_rows<<<blocks_for((long long)P * h->oz_nkb * 32, 256), 256, 0, h->stream>>>(
+    oz::k_slice_rows<int><<<blocks_for((long long)P * h->oz_nkb * 32, 256), 256, 0, h->stream>>>(
         (long long)P, (long long)P, (int)ovl, h->oz_ovp, B, ovl, 1, h->oz_bov, (long long)h->oz_ovp,
         (long long)P * h->oz_ovp, h->oz_ebov, (long long)P, h->oz_nkb);
-    oz::k_slice_rows<<<blocks_for(ovl * h->oz_npb * 32, 256), 256, 0, h->stream>>>(
+    oz::k_slice_rows<int><<<blocks_for(ovl * h->oz_npb * 32, 256), 256, 0, h->stream>>>(
         ovl, ovl, (int)P, h->oz_Pp, B, 1, ovl, h->oz_bovt, (long long)h->oz_Pp, ovl * h->oz_Pp, h->oz_ebovt, ovl,
         h->oz_npb);
     CK(cudaGetLastError());
@@ -1832,12 +1833,12 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
         CK(cudaMemcpyAsync(stage, src + p0 * slab, pc * slab * 8, cudaMemcpyDefault, h->stream));
         if (vv) {
           const long long rows = (long long)(pc * v);
-          oz::k_slice_rows<<<blocks_for(rows * (long long)nbp * 32, 256), 256, 0, h->stream>>>(
+          oz::k_slice_rows<short><<<blocks_for(rows * (long long)nbp * 32, 256), 256, 0, h->stream>>>(
               rows, (long long)v, (int)v, (int)vp, stage, (long long)v, 1, h->oz_bvv + p0 * v * vp, (long long)vp,
               (long long)(P * v * vp), h->oz_evv + p0 * nbp * vp, (long long)vp, (int)nbp);
         } else {
           const long long rows = (long long)(pc * o);
-          oz::k_slice_rows<<<blocks_for(rows * 32, 256), 256, 0, h->stream>>>(
+          oz::k_slice_rows<short><<<blocks_for(rows * 32, 256), 256, 0, h->stream>>>(
               rows, rows, (int)o, (int)op, stage, (long long)o, 1, h->oz_boo + p0 * o * op, (long long)op,
               (long long)(P * o * op), h->oz_eoo + p0 * o, rows, 1);
         }

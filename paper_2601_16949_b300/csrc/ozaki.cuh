@@ -26,8 +26,8 @@
 // integer of magnitude <= 2^24: exact in FP32 in any order of addition.
 // The epilogue joins the groups exactly in int64,
 //     I = sum_g acc_g 2^(7(S-1-g)),        block value = I 2^(ea + eb - 7(S+1)),
-// and adds the block values of a K range in FP64 (or, for a contraction of
-// one block, stores I).
+// and adds the block values of a K range in FP64 (or, for the Z build, a
+// contraction of one block, stores I).
 #pragma once
 
 #include <cuda.h>
@@ -48,8 +48,11 @@ constexpr int kKB = 32;                      // K tile: 32 BF16 = 64-byte rows, 
 constexpr int kBlkTiles = 16;                // K tiles per exactness block (512 elements)
 constexpr int kBlk = kKB * kBlkTiles;
 constexpr int kBN = 64;
-constexpr int kStagesVV = 3;     // main contraction: long K loops
+constexpr int kStagesVV = 3;     // long K loops
 constexpr int kStagesPlain = 2;  // Z build (K = nocc): room for the store staging
+constexpr int kEpiWarps = 16;                    // four per TMEM lane quarter, 16 columns each
+constexpr int kThreads = 64 + 32 * kEpiWarps;   // producer + MMA warp + epilogue
+constexpr int kCW = kBN * 4 / kEpiWarps;        // columns per epilogue thread
 constexpr int kEmptyExp = -400;              // block exponent of an all-zero block
 constexpr int kASlice = tc::kBM * kKB * 2;   // one A digit plane of a K tile (8 KB)
 constexpr int kBSlice = kBN * kKB * 2;       // one B digit plane (4 KB)
@@ -58,36 +61,36 @@ constexpr uint32_t kTmemCols = 512;
 static_assert(kS * kBN <= (int)kTmemCols, "group accumulators exceed TMEM");
 static_assert(kStageBytes % 1024 == 0, "stage must keep 1024-byte alignment");
 static_assert(kBlk * 8 * 4096 <= (1 << 24), "a group sum of one block must stay exact in FP32");
-// operand addressing
+// operand addressing and epilogue
 enum : int {
   OZ_PLAIN = 0,    // A [digit][row][k], B [digit][row][k]: 3-D maps (k, row, digit); one block, out int64 I
   OZ_VV = 1,       // A = Z digits [digit][(P, b/64)][row][64]; B = B_vv digits [digit][P][a][b]; out FP64
   OZ_PLAIN64 = 2   // 3-D maps as OZ_PLAIN over many blocks (a "P" below is one block); out FP64
 };
 
-constexpr int kStgRow = 33;  // int64 words per staged row (32 + 1 against bank conflicts)
+constexpr int kStgRow = kCW + 1;  // int64 words per staged row (+1 against bank conflicts)
 constexpr int kStgWarpBytes = 32 * kStgRow * 8;
 
 template <int MODE>
 constexpr int stages() { return MODE == OZ_PLAIN ? kStagesPlain : kStagesVV; }
 template <int MODE>
 constexpr size_t smem_bytes() {
-  return (size_t)stages<MODE>() * kStageBytes + (MODE == OZ_PLAIN ? (size_t)tc::kEpiWarps * kStgWarpBytes : 0) +
-         1024 + 256;
+  return (size_t)stages<MODE>() * kStageBytes + (MODE == OZ_PLAIN ? (size_t)kEpiWarps * kStgWarpBytes : 0) + 1024 +
+         256;
 }
 
 
 struct Params {
   int M, N;
-  int vt;        // K tiles per P (OZ_VV); all K tiles of the contraction (OZ_PLAIN)
-  int pc;        // P in this chunk (OZ_VV); 1 (OZ_PLAIN)
+  int vt;        // K tiles per P (OZ_VV, OZ_PLAIN64); all K tiles of the contraction (OZ_PLAIN)
+  int pc;        // P in this chunk (OZ_VV); blocks (OZ_PLAIN64); 1 (OZ_PLAIN)
   int pps;       // P per split
   int nsplit;
   int nbp;       // exactness blocks per P: ceil(vt / kBlkTiles)
-  void* out;     // OZ_VV: double [split][M][ldo]; OZ_PLAIN: long long [M][ldo]
+  void* out;     // OZ_VV, OZ_PLAIN64: double [split][M][ldo]; OZ_PLAIN: long long [M][ldo]
   long long ldo, split_stride;
-  int accum;     // OZ_VV: out += result (later chunks of P)
-  const short* ea;  // A block exponents ea[block * lde_a + m] (OZ_VV, OZ_PLAIN64)
+  int accum;     // out += result (later chunks of P)
+  const int* ea;    // A block exponents ea[block * lde_a + m] (OZ_VV, OZ_PLAIN64)
   long long lde_a;
   const short* eb;  // B block exponents eb[block * lde_b + n] (OZ_VV, OZ_PLAIN64; lde_b % 32 == 0)
   long long lde_b;
@@ -126,19 +129,13 @@ __device__ __forceinline__ double scaled_i64(long long I, int E) {
 // F = round(I 2^(E + 7S - e)), then d_{S-1}, ..., d_1 centred in [-64, 63]
 // and d_0 = what remains (|d_0| <= 128).
 // ---------------------------------------------------------------------------
+// Rounding half up (arithmetic shift of I + half); |I 2^(E-e)| <= 1 keeps
+// |F| <= 2^(7S).
 __device__ __forceinline__ long long fixed_point(long long I, int E, int e) {
-  if (I == 0) return 0;
   const int sh = E + kFixBits - e;
-  const bool neg = I < 0;
-  const unsigned long long a = neg ? (unsigned long long)(-I) : (unsigned long long)I;
-  unsigned long long f;
-  if (sh >= 0)
-    f = a << sh;  // |I| < 2^(e-E) so that |F| < 2^(7S)
-  else if (sh <= -63)
-    f = 0;
-  else
-    f = (a + (1ull << (-sh - 1))) >> (-sh);
-  return neg ? -(long long)f : (long long)f;
+  if (sh >= 0) return (long long)((unsigned long long)I << sh);
+  if (sh <= -63) return 0;
+  return (I + (1ll << (-sh - 1))) >> (-sh);
 }
 
 // Adding 64 at each of the five low base-128 positions turns every centred
@@ -165,11 +162,12 @@ __device__ __forceinline__ void digits(long long F, float (&d)[kS]) {
   d[0] = __int_as_float(0x4B400000 + ((int)hi >> 3)) - 12582912.0f;  // |d_0| <= 128
 }
 
-// Bits of |I| plus E: x = I 2^E lies below 2^(that) (INT_MIN-ish for I = 0).
+// Bits of |I| (of |I| - 1 for negative I) plus E: |x| = |I 2^E| <= 2^(that),
+// with equality only for x = -2^(that), whose fixed-point form -2^(7S) still
+// has a leading digit of -128 (-2^30 for I = 0).
 __device__ __forceinline__ int top_exp(long long I, int E) {
   if (I == 0) return -0x40000000;
-  const unsigned long long a = I < 0 ? (unsigned long long)(-I) : (unsigned long long)I;
-  return 64 - __clzll((long long)a) + E;
+  return 64 - __clzll(I ^ (I >> 63)) + E;
 }
 
 __device__ __forceinline__ void f64_parts(double x, long long& I, int& E) {
@@ -198,10 +196,11 @@ __device__ __forceinline__ int warp_block_exp(int e) {
 // exps[((r / rin) * nblk + blk) * lde + r % rin].  B_oo: rows (P, i), K = j,
 // rin = all rows, nblk = 1.  B_vv: rows (P, a), K = b, rin = nvirt, lde =
 // the padded nvirt (exponents [P][blk][a]).
+template <typename TE>
 __global__ void __launch_bounds__(256) k_slice_rows(long long rows, long long rin, int klen, int kpad,
                                                     const double* __restrict__ src, long long lds, long long ldk,
                                                     __nv_bfloat16* __restrict__ dst, long long ldd, long long plane,
-                                                    short* __restrict__ exps, long long lde, int nblk) {
+                                                    TE* __restrict__ exps, long long lde, int nblk) {
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= rows * nblk) return;
@@ -220,7 +219,7 @@ __global__ void __launch_bounds__(256) k_slice_rows(long long rows, long long ri
     emax = max(emax, top_exp(I[q], E[q]));
   }
   const int e = warp_block_exp(emax);
-  if (lane == 0) exps[((r / rin) * nblk + blk) * lde + r % rin] = (short)e;
+  if (lane == 0) exps[((r / rin) * nblk + blk) * lde + r % rin] = (TE)e;
 #pragma unroll
   for (int q = 0; q < kPerLane; ++q) {
     const int k = k0 + lane + 32 * q;
@@ -349,7 +348,7 @@ __global__ void __launch_bounds__(256) k_slice_w(int P, int Pp, int C, int cp, i
 __global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc, int nbp, int p0,
                                                  const long long* __restrict__ Zi, const short* __restrict__ eoo,
                                                  const int* __restrict__ ex, __nv_bfloat16* __restrict__ dst,
-                                                 long long plane, short* __restrict__ ez) {
+                                                 long long plane, int* __restrict__ ez) {
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const long long nw = (long long)C * o * pc * nbp;
@@ -381,7 +380,7 @@ __global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc
     emax = max(emax, max(top_exp(I[2 * q], E[2 * q]), top_exp(I[2 * q + 1], E[2 * q + 1])));
   }
   const int e = warp_block_exp(emax);
-  if (lane == 0) ez[((long long)P * nbp + blk) * ((long long)C * o) + row] = (short)e;
+  if (lane == 0) ez[((long long)P * nbp + blk) * ((long long)C * o) + row] = e;
   const int vt64 = vp / 64;
 #pragma unroll
   for (int q = 0; q < kPairs; ++q) {
@@ -405,7 +404,9 @@ __global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc
 // group accumulators g = s + t (TMEM columns g * 64 .. +63) and hands them
 // to the epilogue at the end of each exactness block.  Warp roles as in
 // the other tensor-core kernels: warp 0 TMA producer, warp 1 TMEM owner and
-// MMA issuer, warps 2..9 epilogue (TMEM lane quarter warp % 4, column half
+// MMA issuer, warps 2..17 epilogue (TMEM lane quarter warp % 4, columns
+// 16 ((warp - 2) / 4) .. +15; sixteen warps so that the integer work of the
+// drain, which stalls the MMAs of the next block, has latency cover)
 // (warp - 2) / 4).  Every wait is bounded (error code in *err).
 //
 // K tiles of a split: P in [split * pps, min(pc, (split + 1) * pps)), each
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc
 // P's last tile, so blocks never straddle two P.
 // ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(tc::kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p) {
   using namespace tc;
   constexpr int ST = stages<MODE>();
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(accf, 1);
-    mbar_init(acce, kEpiWarps);
+    mbar_init(acce, oz::kEpiWarps);
     mbar_fence_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
@@ -551,37 +552,37 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
   } else {
     // ---------------- epilogue (warps 2..9) ----------------
     const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int cg = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 32);
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cg * kCW);
     int nb = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int n0, m0, kr0, kr1;
       coords(t, n0, m0, kr0, kr1);
       const int m = m0 + row;
-      const int nbase = n0 + half * 32;
+      const int nbase = n0 + cg * kCW;
       if constexpr (MODE != OZ_PLAIN) {
-        double acc[32];
+        double acc[kCW];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+        for (int j = 0; j < kCW; ++j) acc[j] = 0.0;
         for (int kr = kr0; kr < kr1; ++kr) {
           const int P = kr / p.vt, bt = kr - P * p.vt;
           if (!((bt % kBlkTiles) == kBlkTiles - 1 || bt == p.vt - 1)) continue;
           const int blk = P * p.nbp + bt / kBlkTiles;
           // the block's exponents, loaded while its MMAs still run
           const int ea = m < p.M ? __ldg(p.ea + (size_t)blk * p.lde_a + m) : kEmptyExp;
-          uint4 eb4[4];  // 32 int16 exponents
+          uint4 eb4[kCW / 8];  // int16 exponents of the thread's columns
           const uint4* ebp = reinterpret_cast<const uint4*>(p.eb + (size_t)blk * p.lde_b + nbase);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) eb4[u] = __ldg(ebp + u);
+          for (int u = 0; u < kCW / 8; ++u) eb4[u] = __ldg(ebp + u);
           ok = mbar_wait(accf, (uint32_t)nb & 1u, p.err, ERR_WAIT_ACC);
           ++nb;
           tc_fence_after();
           if (!ok) break;
           const int eab = ea - kOutShift;
 #pragma unroll
-          for (int c4 = 0; c4 < 8; ++c4) {
+          for (int c4 = 0; c4 < kCW / 4; ++c4) {
             uint32_t r[kS][4];
 #pragma unroll
             for (int g = 0; g < kS; ++g) tmem_ld4_nowait(tl + (uint32_t)(g * kBN + c4 * 4), r[g]);
@@ -607,14 +608,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
           double* dst = reinterpret_cast<double*>(p.out) + (size_t)(t / (tiles_n * tiles_m)) * p.split_stride +
                         (size_t)m * p.ldo;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < kCW; ++j) {
             const int n = nbase + j;
             if (n < p.N) dst[n] = p.accum ? dst[n] + acc[j] : acc[j];
           }
         }
       } else {
         // one block (K = nocc <= 512): the integers I, staged per warp in
-        // shared memory and stored row by row (32 consecutive words per row)
+        // shared memory and stored two rows at a time (16 consecutive words
+        // per row)
         long long* stg = reinterpret_cast<long long*>(stg_base + (warp - 2) * kStgWarpBytes);
         for (int kr = kr0; kr < kr1; ++kr) {
           const int bt = kr % p.vt;
@@ -624,17 +626,17 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
           tc_fence_after();
           if (!ok) break;
 #pragma unroll
-          for (int c8 = 0; c8 < 4; ++c8) {
-            uint32_t r[kS][8];
+          for (int c4 = 0; c4 < kCW / 4; ++c4) {
+            uint32_t r[kS][4];
 #pragma unroll
-            for (int g = 0; g < kS; ++g) tmem_ld8_nowait(tl + (uint32_t)(g * kBN + c8 * 8), r[g]);
+            for (int g = 0; g < kS; ++g) tmem_ld4_nowait(tl + (uint32_t)(g * kBN + c4 * 4), r[g]);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 4; ++j) {
               long long I = __float2int_rn(__uint_as_float(r[0][j]));
 #pragma unroll
               for (int g = 1; g < kS; ++g) I = I * 128 + __float2int_rn(__uint_as_float(r[g][j]));
-              stg[lane * kStgRow + c8 * 8 + j] = I;
+              stg[lane * kStgRow + c4 * 4 + j] = I;
             }
           }
           tc_fence_before();
@@ -642,12 +644,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
           if (lane == 0) mbar_arrive(acce);
         }
         if (!ok) break;
-        // lane l stores column nbase + l of the warp's 32 rows
         long long* out = reinterpret_cast<long long*>(p.out);
-        const int n = nbase + lane;
+        const int n = nbase + (lane & (kCW - 1));
         const int mrow0 = m0 + q * 32;
-        for (int rr = 0; rr < 32; ++rr) {
-          if (mrow0 + rr < p.M && n < p.N) out[(size_t)(mrow0 + rr) * p.ldo + n] = stg[rr * kStgRow + lane];
+        for (int rr = lane / kCW; rr < 32; rr += 32 / kCW) {
+          if (mrow0 + rr < p.M && n < p.N)
+            out[(size_t)(mrow0 + rr) * p.ldo + n] = stg[rr * kStgRow + (lane & (kCW - 1))];
         }
         __syncwarp();
       }
