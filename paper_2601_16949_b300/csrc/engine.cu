@@ -174,6 +174,7 @@ struct rttda_ctx {
   int zplanes = 1, nprod_main = 1;  // Z planes kept; products in the main contraction
   int wide_mb = 0;                   // >0: main contraction on the wide-M kernel with this many 128-row blocks
   int wide_kb = 32;                  // K tile width of the wide-M kernel (32 or 64 BF16)
+  bool wide_tr = false;              // wide kernel with the contraction transposed (rows a)
   int integrator = RTTDA_INT_RK4;    // rttda_integrator
   // projectors (Eq. populations) and the overlaps of the last propagation
   int nproj = 0;
@@ -390,25 +391,62 @@ void tc_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm
   tc::k_tc_gemm<BN, ST, BM, EP><<<grid, tc::kThreads, tc::smem_bytes<BN, ST, EP>(), s>>>(a, b, z ? *z : a, prm);
 }
 
-template <int BN, int MB, int NBP, int ST, int KB>
+template <int BN, int MB, int NBP, int ST, int KB, bool TR = false>
 void wide_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s) {
   const long long tiles = cdiv(prm.N, BN) * cdiv(prm.M, (long long)tc::kBM * MB) * prm.nsplit;
   const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(tiles, kNumSM));
-  tc::k_tc_wide<BN, MB, NBP, ST, KB><<<grid, tc::kThreads, tc::wide_smem_bytes<BN, MB, NBP, ST, KB>(), s>>>(a, b, prm);
+  tc::k_tc_wide<BN, MB, NBP, ST, KB, TR>
+      <<<grid, tc::kThreads, tc::wide_smem_bytes<BN, MB, NBP, ST, KB, TR>(), s>>>(a, b, prm);
 }
 
-template <int BN, int MB, int NBP, int ST, int KB>
+template <int BN, int MB, int NBP, int ST, int KB, bool TR = false>
 void wide_attr() {
-  static_assert(tc::wide_smem_bytes<BN, MB, NBP, ST, KB>() <= 232448, "shared memory per block exceeds 227 KB");
-  cudaFuncSetAttribute(tc::k_tc_wide<BN, MB, NBP, ST, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)tc::wide_smem_bytes<BN, MB, NBP, ST, KB>());
+  static_assert(tc::wide_smem_bytes<BN, MB, NBP, ST, KB, TR>() <= 232448, "shared memory per block exceeds 227 KB");
+  cudaFuncSetAttribute(tc::k_tc_wide<BN, MB, NBP, ST, KB, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::wide_smem_bytes<BN, MB, NBP, ST, KB, TR>());
+}
+
+// Transposed wide configurations (rows a in two 128-row blocks, columns
+// (col, i) in tiles of BN, K tiles of 32): BN in {64, 96, 128, 160, 192,
+// 256}; 4 stages with both B_vv planes, 6 with one.
+constexpr int kTrBN[6] = {64, 96, 128, 160, 192, 256};
+
+template <int NBP>
+void wide_tr_launch(int bn, const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s) {
+  constexpr int ST = NBP == 2 ? 4 : 6;
+  switch (bn) {
+    case 64: wide_launch<64, 2, NBP, ST, 32, true>(a, b, prm, s); break;
+    case 96: wide_launch<96, 2, NBP, ST, 32, true>(a, b, prm, s); break;
+    case 128: wide_launch<128, 2, NBP, ST, 32, true>(a, b, prm, s); break;
+    case 160: wide_launch<160, 2, NBP, ST, 32, true>(a, b, prm, s); break;
+    case 192: wide_launch<192, 2, NBP, ST, 32, true>(a, b, prm, s); break;
+    default: wide_launch<256, 2, NBP, ST, 32, true>(a, b, prm, s); break;
+  }
+}
+
+template <int NBP>
+void wide_tr_attr() {
+  constexpr int ST = NBP == 2 ? 4 : 6;
+  wide_attr<64, 2, NBP, ST, 32, true>();
+  wide_attr<96, 2, NBP, ST, 32, true>();
+  wide_attr<128, 2, NBP, ST, 32, true>();
+  wide_attr<160, 2, NBP, ST, 32, true>();
+  wide_attr<192, 2, NBP, ST, 32, true>();
+  wide_attr<256, 2, NBP, ST, 32, true>();
 }
 
 // The wide-M configurations: (BN, MB) in {(160, 3), (192, 2)}, one or two B
 // planes, K tiles of 64 (128-byte rows) or 32 (64-byte rows, twice the
 // stages).  Stage counts fill the 227 KB of shared memory.
 void wide_dispatch(int bn, int mb, int nbp, int kb, const CUtensorMap& a, const CUtensorMap& b,
-                   const tc::Params& prm, cudaStream_t s) {
+                   const tc::Params& prm, cudaStream_t s, bool tr = false) {
+  if (tr) {
+    if (nbp == 2)
+      wide_tr_launch<2>(bn, a, b, prm, s);
+    else
+      wide_tr_launch<1>(bn, a, b, prm, s);
+    return;
+  }
   const bool w3 = bn == 160 && mb == 3;
   if (kb == 32) {
     if (nbp == 2) {
@@ -451,6 +489,8 @@ void set_tc_smem_limits() {
   wide_attr<192, 2, 2, 2, 64>();
   wide_attr<160, 3, 1, 3, 64>();
   wide_attr<192, 2, 1, 4, 64>();
+  wide_tr_attr<2>();
+  wide_tr_attr<1>();
 }
 
 // Batched Coulomb on tensor cores: w = B_ov c (split-K over ia), then
@@ -537,8 +577,9 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       h->launches += 1;
       tc::Params prm{};
       const int kb = h->wide_mb ? h->wide_kb : tc::kBK;
-      prm.M = C * o;
-      prm.N = v;
+      // wide_tr: rows a, columns (col, i), partials written transposed
+      prm.M = h->wide_tr ? v : C * o;
+      prm.N = h->wide_tr ? C * o : v;
       prm.kt_total = pc * (vp / kb);
       prm.kt_per_split = h->tc_kper[c];
       prm.nsplit = h->SK;
@@ -551,7 +592,7 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
       prm.err = h->d_err;
       if (h->wide_mb) {
         // wide-M tiles: MB accumulators share each B tile; both B planes per stage
-        wide_dispatch(h->tc_bn, h->wide_mb, h->nprod_main, h->wide_kb, h->tmMA[c], h->tmMB[c], prm, s);
+        wide_dispatch(h->tc_bn, h->wide_mb, h->nprod_main, h->wide_kb, h->tmMA[c], h->tmMB[c], prm, s, h->wide_tr);
       } else switch (h->tc_bn) {
         case 128: tc_launch<128, 7, tc::BMODE_VV, tc::EPI_PARTIAL>(h->tmMA[c], h->tmMB[c], prm, s); break;
         case 224: tc_launch<224, 5, tc::BMODE_VV, tc::EPI_PARTIAL>(h->tmMA[c], h->tmMB[c], prm, s); break;
@@ -1195,8 +1236,9 @@ static rttda_status alloc_coul_tc(rttda_ctx* h, int C) {
 
 // ---------------------------------------------------------------------------
 // Autotuner of the main exchange contraction (wide-M kernel).  Candidates:
-// (BN, MB) in {(160, 3), (192, 2)} x K tile {32, 64}, each with the split-K
-// count of choose_splits.  Each candidate runs the contraction over the
+// (BN, MB) in {(160, 3), (192, 2)} x K tile {32, 64}, plus the transposed
+// kernel (rows a, MB = 2, K tile 32) with the column tile of least padding
+// for the C*o columns, each with the split-K count of choose_splits.  Each candidate runs the contraction over the
 // first Z chunk (filled with hashed values, so that the tensor cores see
 // data-like operands and power) once to warm up and then five times,
 // interleaved with the others, timed with CUDA events on the handle's
@@ -1204,11 +1246,19 @@ static rttda_status alloc_coul_tc(rttda_ctx* h, int C) {
 // and, when RTTDA_TUNE_CACHE names a file, in that file (one JSON object per
 // line).  RTTDA_TUNE=0 skips the timing and takes the first candidate with
 // the least padded work and K tile 32; RTTDA_WIDE_PLAN="BN,MB,KB" names the
-// candidate to use (for tests and experiments).
+// candidate to use, "BN,2,32,t" a transposed plan with column tile BN (for
+// tests and experiments).
 // ---------------------------------------------------------------------------
 struct WidePlan {
   int bn = 160, mb = 3, kb = 32, sk = 1;
+  int tr = 0;  // 1: transposed (rows a, MB = 2, K tile 32)
 };
+
+static bool tr_bn_ok(int bn) {
+  for (int x : kTrBN)
+    if (x == bn) return true;
+  return false;
+}
 
 static std::mutex g_tune_mu;
 static std::map<std::string, WidePlan> g_tune_cache;
@@ -1221,7 +1271,7 @@ static std::string tune_key(int o, int v, int vp, int pc, int C, int nprod, int 
   return k.str();
 }
 
-// {"key": "...", "bn": B, "mb": M, "kb": K, "sk": S}
+// {"key": "...", "bn": B, "mb": M, "kb": K, "sk": S, "tr": T}
 static void tune_file_load() {
   const char* f = std::getenv("RTTDA_TUNE_CACHE");
   if (g_tune_file_loaded || !f || !*f) return;
@@ -1242,8 +1292,10 @@ static void tune_file_load() {
     num("mb", w.mb);
     num("kb", w.kb);
     num("sk", w.sk);
-    const bool valid = ((w.bn == 160 && w.mb == 3) || (w.bn == 192 && w.mb == 2)) && (w.kb == 32 || w.kb == 64) &&
-                       w.sk >= 1 && w.sk <= 64;
+    num("tr", w.tr);
+    const bool valid = w.tr ? (tr_bn_ok(w.bn) && w.mb == 2 && w.kb == 32 && w.sk >= 1 && w.sk <= 64)
+                            : (((w.bn == 160 && w.mb == 3) || (w.bn == 192 && w.mb == 2)) && (w.kb == 32 || w.kb == 64) &&
+                               w.sk >= 1 && w.sk <= 64);
     if (valid) g_tune_cache[line.substr(ks, ke - ks)] = w;
   }
 }
@@ -1253,23 +1305,27 @@ static void tune_file_append(const std::string& key, const WidePlan& w) {
   if (!f || !*f) return;
   std::ofstream out(f, std::ios::app);
   out << "{\"key\": \"" << key << "\", \"bn\": " << w.bn << ", \"mb\": " << w.mb << ", \"kb\": " << w.kb
-      << ", \"sk\": " << w.sk << "}\n";
+      << ", \"sk\": " << w.sk << ", \"tr\": " << w.tr << "}\n";
 }
 
-static rttda_status wide_maps(rttda_ctx* h, int C, int pc, int p0, int bn, int kb, CUtensorMap* ma, CUtensorMap* mb) {
+// Operand maps of the main contraction: Z tiles (rows (col, i)) and B^P_vv
+// planes (rows a).  Normal: A = Z with 128-row boxes, B = B_vv with bn-row
+// boxes; transposed (tr): A = B_vv with 128-row boxes, B = Z with bn-row boxes.
+static rttda_status wide_maps(rttda_ctx* h, int C, int pc, int p0, int bn, int kb, CUtensorMap* ma, CUtensorMap* mb,
+                              bool tr = false) {
   const int o = h->o, vp = h->vp, P = h->P;
   const CUtensorMapSwizzle sw = kb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
   {
     const uint64_t dims[4] = {64, (uint64_t)C * o, (uint64_t)pc * (vp / 64), (uint64_t)h->zplanes};
     const uint64_t str[3] = {128, (uint64_t)C * o * 128, (uint64_t)h->zplane * 2};
-    const uint32_t box[4] = {(uint32_t)kb, 128, 1, 1};
-    CKS(bf16_map(ma, h->Zk, 4, dims, str, box, sw));
+    const uint32_t box[4] = {(uint32_t)kb, tr ? (uint32_t)bn : 128u, 1, 1};
+    CKS(bf16_map(tr ? mb : ma, h->Zk, 4, dims, str, box, sw));
   }
   {
     const uint64_t dims[4] = {(uint64_t)vp, (uint64_t)vp, (uint64_t)pc, (uint64_t)h->nplanes};
     const uint64_t str[3] = {(uint64_t)vp * 2, (uint64_t)vp * vp * 2, (uint64_t)P * vp * vp * 2};
-    const uint32_t box[4] = {(uint32_t)kb, (uint32_t)bn, 1, 1};
-    CKS(bf16_map(mb, h->Bvv_tc + (size_t)p0 * vp * vp, 4, dims, str, box, sw));
+    const uint32_t box[4] = {(uint32_t)kb, tr ? 128u : (uint32_t)bn, 1, 1};
+    CKS(bf16_map(tr ? ma : mb, h->Bvv_tc + (size_t)p0 * vp * vp, 4, dims, str, box, sw));
   }
   return RTTDA_OK;
 }
@@ -1304,12 +1360,43 @@ static rttda_status tune_wide(rttda_ctx* h, int C, WidePlan& out) {
       c.w.sk = choose_splits(tiles, (long long)h->zchunk * (vp / kb));
       cands.push_back(c);
     }
+  auto tr_plan = [&](int bn) {
+    WidePlan w;
+    w.tr = 1;
+    w.bn = bn;
+    w.mb = 2;
+    w.kb = 32;
+    w.sk = choose_splits(cdiv((long long)v, 2LL * tc::kBM) * cdiv(M, (long long)bn), (long long)h->zchunk * (vp / 32));
+    return w;
+  };
+  {
+    // transposed candidate: the column tile that pads C*o least (ties to the wider)
+    int best_bn = kTrBN[0];
+    long long bestp = -1;
+    for (int bn : kTrBN) {
+      const long long padded = cdiv(M, (long long)bn) * bn;
+      if (bestp < 0 || padded <= bestp) {
+        bestp = padded;
+        best_bn = bn;
+      }
+    }
+    Cand c;
+    c.w = tr_plan(best_bn);
+    cands.push_back(c);
+  }
   const char* force = std::getenv("RTTDA_WIDE_PLAN");
   if (force && *force) {
     int fb = 0, fm = 0, fk = 0;
-    if (std::sscanf(force, "%d,%d,%d", &fb, &fm, &fk) == 3)
+    char ft = 0;
+    const int nf = std::sscanf(force, "%d,%d,%d,%c", &fb, &fm, &fk, &ft);
+    if (nf == 4 && ft == 't' && fm == 2 && fk == 32 && tr_bn_ok(fb)) {
+      out = tr_plan(fb);
+      h->plan.tuned = 3;
+      return RTTDA_OK;
+    }
+    if (nf == 3)
       for (const Cand& c : cands)
-        if (c.w.bn == fb && c.w.mb == fm && c.w.kb == fk) {
+        if (!c.w.tr && c.w.bn == fb && c.w.mb == fm && c.w.kb == fk) {
           out = c.w;
           h->plan.tuned = 3;
           return RTTDA_OK;
@@ -1345,12 +1432,12 @@ static rttda_status tune_wide(rttda_ctx* h, int C, WidePlan& out) {
   k_fill_hash_bf16<<<4 * kNumSM, 256, 0, h->stream>>>((long long)(h->zplane * h->zplanes), 0.05f, h->Zk);
   std::vector<CUtensorMap> ma(cands.size()), mb(cands.size());
   for (size_t i = 0; i < cands.size(); ++i)
-    CKS(wide_maps(h, C, pc, 0, cands[i].w.bn, cands[i].w.kb, &ma[i], &mb[i]));
+    CKS(wide_maps(h, C, pc, 0, cands[i].w.bn, cands[i].w.kb, &ma[i], &mb[i], cands[i].w.tr != 0));
   auto launch = [&](size_t i) {
     const WidePlan& w = cands[i].w;
     tc::Params prm{};
-    prm.M = (int)M;
-    prm.N = v;
+    prm.M = w.tr ? v : (int)M;
+    prm.N = w.tr ? (int)M : v;
     prm.kt_total = pc * (vp / w.kb);
     prm.kt_per_split = (int)cdiv(prm.kt_total, w.sk);
     prm.nsplit = w.sk;
@@ -1361,7 +1448,7 @@ static rttda_status tune_wide(rttda_ctx* h, int C, WidePlan& out) {
     prm.split_stride = M * v;
     prm.accum = 0;
     prm.err = h->d_err;
-    wide_dispatch(w.bn, w.mb, h->nprod_main, w.kb, ma[i], mb[i], prm, h->stream);
+    wide_dispatch(w.bn, w.mb, h->nprod_main, w.kb, ma[i], mb[i], prm, h->stream, w.tr != 0);
   };
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -1412,6 +1499,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   const long long M = (long long)C * o;
   int kb = tc::kBK;  // main K tile width
   h->wide_mb = 0;
+  h->wide_tr = false;
   h->plan = rttda_plan_info{};
   if (h->nprod_main <= 2) {
     WidePlan wp;
@@ -1419,6 +1507,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
     h->tc_bn = wp.bn;
     h->wide_mb = wp.mb;
     h->wide_kb = kb = wp.kb;
+    h->wide_tr = wp.tr != 0;
     h->SK = wp.sk;
   } else {
     int best = 256;
@@ -1434,7 +1523,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
     h->SK = choose_splits(cdiv(M, tc::kBM) * cdiv(v, best), (long long)h->zchunk * (vp / kb));
   }
   const int best = h->tc_bn;
-  h->plan.main_kernel = h->wide_mb ? 2 : 1;
+  h->plan.main_kernel = h->wide_tr ? 4 : h->wide_mb ? 2 : 1;
   h->plan.main_bn = best;
   h->plan.main_mb = h->wide_mb ? h->wide_mb : 1;
   h->plan.main_kb = kb;
@@ -1468,7 +1557,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
       CKS(bf16_map(&zs, h->Zk, 4, dims, str, sbox, CU_TENSOR_MAP_SWIZZLE_128B));
     }
     // main contraction operands: Z tiles and B^P_vv tiles of K-tile width kb
-    CKS(wide_maps(h, C, pc, p0, best, kb, &ma, &mb));
+    CKS(wide_maps(h, C, pc, p0, best, kb, &ma, &mb, h->wide_tr));
     h->tmZA.push_back(za);
     h->tmMA.push_back(ma);
     h->tmZS.push_back(zs);

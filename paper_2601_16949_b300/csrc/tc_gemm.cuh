@@ -635,13 +635,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 // K tiles are numbered in units of KB along (P, b): tile kr covers
 // b = (kr % (vp/KB)) * KB .. +KB of P = kr / (vp/KB).  Z is stored in
 // 64-wide b tiles, so a 32-wide K tile is the half (kr & 1) of Z tile kr/2.
+//
+// TR (transposed): the same contraction with the operands swapped, for
+// batches whose C*o rows fill 128-row tiles poorly (one trajectory): rows
+// are a (A = the NBP B_vv planes, MB 128-row blocks each), columns are
+// (col, i) (B = one Z plane of BN rows), and the epilogue writes the
+// partials transposed, out[split][(col, i)][a], the layout the combine
+// reads; a warp then stores 32 consecutive a of one (col, i).
 // ---------------------------------------------------------------------------
-template <int BN, int MB, int NBP, int KB>
+template <int BN, int MB, int NBP, int KB, bool TR = false>
 struct WideCfg {
   static constexpr int kRowBytes = KB * 2;
   static constexpr int kABlock = kBM * kRowBytes;   // one 128-row A tile
   static constexpr int kBBytes = BN * kRowBytes;    // one B plane
-  static constexpr int kStageBytes = MB * kABlock + NBP * kBBytes;
+  static constexpr int kATiles = TR ? MB * NBP : MB;
+  static constexpr int kBTiles = TR ? 1 : NBP;
+  static constexpr int kStageBytes = kATiles * kABlock + kBTiles * kBBytes;
   static constexpr int kCols = MB * BN;
   static constexpr uint32_t kTmemCols = kCols <= 32 ? 32 : kCols <= 64 ? 64 : kCols <= 128 ? 128
                                         : kCols <= 256 ? 256 : 512;
@@ -651,15 +660,15 @@ struct WideCfg {
   static_assert(KB == 64 || KB == 32, "K tile of 64 or 32 BF16");
 };
 
-template <int BN, int MB, int NBP, int STAGES, int KB>
+template <int BN, int MB, int NBP, int STAGES, int KB, bool TR = false>
 constexpr size_t wide_smem_bytes() {
-  return (size_t)STAGES * WideCfg<BN, MB, NBP, KB>::kStageBytes + 1024 + 256;
+  return (size_t)STAGES * WideCfg<BN, MB, NBP, KB, TR>::kStageBytes + 1024 + 256;
 }
 
-template <int BN, int MB, int NBP, int STAGES, int KB>
+template <int BN, int MB, int NBP, int STAGES, int KB, bool TR = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_wide(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p) {
-  using CF = WideCfg<BN, MB, NBP, KB>;
+  using CF = WideCfg<BN, MB, NBP, KB, TR>;
   constexpr int TM = kBM * MB;  // rows per tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -714,12 +723,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint8_t* st = smem + s * CF::kStageBytes;
           mbar_expect_tx(&full[s], CF::kStageBytes);
           const int zt = KB == 64 ? kr : kr >> 1, zx = KB == 64 ? 0 : (kr & 1) * KB;
-#pragma unroll
-          for (int b = 0; b < MB; ++b) tma_load_4d(st + b * CF::kABlock, &tmA, &full[s], zx, m0 + b * kBM, zt, 0);
           const int P = kr / p.vtiles, b0 = (kr % p.vtiles) * KB;
+          if (TR) {
+            // A: plane q, row block b of B_vv at (b0, a, P); B: the Z tile
 #pragma unroll
-          for (int q = 0; q < NBP; ++q)
-            tma_load_4d(st + MB * CF::kABlock + q * CF::kBBytes, &tmB, &full[s], b0, n0, P, q);
+            for (int q = 0; q < NBP; ++q)
+#pragma unroll
+              for (int b = 0; b < MB; ++b)
+                tma_load_4d(st + (q * MB + b) * CF::kABlock, &tmA, &full[s], b0, m0 + b * kBM, P, q);
+            tma_load_4d(st + MB * NBP * CF::kABlock, &tmB, &full[s], zx, n0, zt, 0);
+          } else {
+#pragma unroll
+            for (int b = 0; b < MB; ++b) tma_load_4d(st + b * CF::kABlock, &tmA, &full[s], zx, m0 + b * kBM, zt, 0);
+#pragma unroll
+            for (int q = 0; q < NBP; ++q)
+              tma_load_4d(st + MB * CF::kABlock + q * CF::kBBytes, &tmB, &full[s], b0, n0, P, q);
+          }
         }
       }
     }
@@ -746,10 +765,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t base = smem_u32(smem + s * CF::kStageBytes);
 #pragma unroll
           for (int q = 0; q < NBP; ++q) {
-            const uint64_t bdesc = sdesc_k<KB>(base + MB * CF::kABlock + q * CF::kBBytes);
+            const uint64_t bdesc = sdesc_k<KB>(base + CF::kATiles * CF::kABlock + (TR ? 0 : q) * CF::kBBytes);
 #pragma unroll
             for (int b = 0; b < MB; ++b) {
-              const uint64_t adesc = sdesc_k<KB>(base + b * CF::kABlock);
+              const uint64_t adesc = sdesc_k<KB>(base + (TR ? q * MB + b : b) * CF::kABlock);
 #pragma unroll
               for (int k = 0; k < KB / 16; ++k)
                 mma_bf16(tmem + b * BN, adesc + 2 * k, bdesc + 2 * k, idesc,
@@ -776,7 +795,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       for (int b = 0; b < MB; ++b) {
         const int m = m0 + b * kBM + row;
-        float* dst = p.out + (size_t)split * p.split_stride + (size_t)m * p.ldo;
+        // TR: element (m = a, n = (col, i)) goes to out[n][a] (ldo = nvirt)
+        float* dst = p.out + (size_t)split * p.split_stride + (TR ? (size_t)m : (size_t)m * p.ldo);
+        const size_t nstride = TR ? (size_t)p.ldo : 1;
         for (int ci = half; ci < BN / 32; ci += 2) {
           const int c = ci * 32;
           uint32_t r[32];
@@ -787,7 +808,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int n = n0 + c + j;
               if (n < p.N) {
                 const float x = has_k ? __uint_as_float(r[j]) : 0.0f;
-                dst[n] = p.accum ? dst[n] + x : x;
+                float* d = dst + (size_t)n * nstride;
+                *d = p.accum ? *d + x : x;
               }
             }
           }

@@ -140,16 +140,19 @@ def test_batched_sigma_with_tensorcore_coulomb(rb, prec, tol2e, shape):
     prop.close()
 
 
-WIDE_PLANS = ["160,3,32", "160,3,64", "192,2,32", "192,2,64"]
+WIDE_PLANS = ["160,3,32", "160,3,64", "192,2,32", "192,2,64",
+              "64,2,32,t", "192,2,32,t", "256,2,32,t"]   # t: transposed (rows a, columns (col, i))
 
 
 @pytest.mark.parametrize("prec,tol", [("bf16x2", 1e-2), ("bf16", 3e-2)])
 def test_every_wide_plan_gives_the_same_exchange(rb, prec, tol, monkeypatch):
     """Exchange only (no Coulomb factors, orbital energies or field): each
-    wide-M plan of the main contraction (tile width x row blocks x K tile)
-    computes the same sum up to FP32 summation order, and matches the FP64
-    exchange within the BF16 rounding of Z.  o=64 with 3 trajectories gives
-    3 row blocks; v=128 is ragged for both tile widths."""
+    wide-M plan of the main contraction (tile width x row blocks x K tile,
+    normal or transposed) computes the same sum up to FP32 summation order,
+    and matches the FP64 exchange within the BF16 rounding of Z.  o=64 with
+    3 trajectories gives 3 row blocks; v=128 is ragged for both tile widths;
+    the transposed plans tile the 384 columns (col, i) by 64, 192 and 256
+    (ragged)."""
     mol = synth.molecule(64, 128, 40, seed=31)
     mol["B_ov"][:] = 0.0
     mol["eps_occ"][:] = 0.0
@@ -161,8 +164,8 @@ def test_every_wide_plan_gives_the_same_exchange(rb, prec, tol, monkeypatch):
         prop = rb.Propagator(mol, 1.0, prec)
         prop.set_field([dict(kind=0, E0=0.0)] * 3)
         info = rb.rttda_plan(prop.h)
-        assert info["tuned"] == 3 and info["main_kernel"] == 2
-        assert (info["main_bn"], info["main_mb"], info["main_kb"]) == tuple(int(x) for x in plan.split(","))
+        assert info["tuned"] == 3 and info["main_kernel"] == (4 if plan.endswith(",t") else 2)
+        assert (info["main_bn"], info["main_mb"], info["main_kb"]) == tuple(int(x) for x in plan.split(",")[:3])
         outs.append(_sigma_gpu(rb, prop, c, 0.5))
         prop.close()
     A = orc.build_A(mol, 1.0)
@@ -180,9 +183,9 @@ def test_wide_plan_tuner_times_every_candidate(rb, monkeypatch):
     prop = rb.Propagator(mol, 0.2, "bf16x2")
     prop.set_field(PULSES)
     info = rb.rttda_plan(prop.h)
-    assert info["main_kernel"] == 2 and info["tuned"] in (1, 2) and info["ntraj"] == 3
+    assert info["main_kernel"] in (2, 4) and info["tuned"] in (1, 2) and info["ntraj"] == 3
     if info["tuned"] == 1:
-        assert info["ncand"] == 4 and all(t > 0 for t in info["tune_ms"])
+        assert info["ncand"] == 5 and all(t > 0 for t in info["tune_ms"])
     # the tuned plan is cached for the shape: a second handle reuses it
     p2 = rb.Propagator(mol, 0.2, "bf16x2")
     p2.set_field(PULSES)
@@ -200,3 +203,28 @@ def test_wide_plan_tuner_times_every_candidate(rb, monkeypatch):
         p3.set_field(PULSES)
     assert e.value.status == rb.E_ARG
     p3.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16"])
+def test_transposed_plan_for_one_trajectory(rb, prec, monkeypatch):
+    """One trajectory: the C*o = 74 columns fill a transposed tile of 96
+    (ragged); rows a = 150 span two 128-row blocks (ragged).  The transposed
+    and the normal plans give the same sigma up to FP32 summation order, and
+    both match the oracle within the BF16 tolerance."""
+    mol = synth.molecule(37, 150, 20, seed=12)
+    pulses = [dict(kind=2, E0=0.05, omega=0.9, t0=1.0, fwhm=1.5, direction=(0, 1, 0))]
+    c = synth.random_state(1 + 37 * 150, 1, seed=9)
+    outs = {}
+    for plan in ("160,3,32", "96,2,32,t", "128,2,32,t"):
+        monkeypatch.setenv("RTTDA_WIDE_PLAN", plan)
+        prop = rb.Propagator(mol, 0.2, prec)
+        prop.set_field(pulses)
+        assert rb.rttda_plan(prop.h)["main_kernel"] == (4 if plan.endswith(",t") else 2)
+        outs[plan] = _sigma_gpu(rb, prop, c, 0.8)
+        prop.close()
+    ref = oracle_sigma(mol, 0.2, pulses, c, 0.8)
+    scale = np.max(np.abs(ref))
+    tol = 1e-2 if prec == "bf16x2" else 3e-2
+    for plan, got in outs.items():
+        assert np.max(np.abs(got - outs["160,3,32"])) <= 2e-5 * scale, plan
+        assert np.max(np.abs(got - ref)) <= tol * scale, plan
