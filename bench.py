@@ -307,10 +307,12 @@ PREC_INFO = {  # factor bytes, exchange planes, tensor products per K tile
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant kernel, from one ncu --set full capture of that kernel on this
-# workload.  Keyed by (workload, precision, kernel class, BN, MB, K tile):
+# workload.  Keyed by (workload, precision, kernel class, main kernel kind
+# (2 wide-M, 4 transposed), BN, MB, K tile):
 # the number holds only for that kernel and plan.
 PROFILED_TRAFFIC = {
-    ("absorption", "bf16x2", "exchange_main", 160, 3, 32): 1.780069e9 + 4.38272e6,
+    ("absorption", "bf16x2", "exchange_main", 2, 160, 3, 32): 1.780069e9 + 4.38272e6,
+    ("absorption", "bf16x2", "exchange_main", 4, 192, 2, 32): 1.766210e9 + 3.739392e6,
 }
 
 
@@ -533,7 +535,7 @@ def run_gpu(args):
     # step plus the call's first half step
     nsig = 4 * kp if args.integrator == "rk4" else 2 * kp + 1
     roof = roofline(args.prec, dom, prof[dom], T, peaks, nsig)
-    tkey = (args.workload, args.prec, dom, plan["main_bn"], plan["main_mb"], plan["main_kb"])
+    tkey = (args.workload, args.prec, dom, plan["main_kernel"], plan["main_bn"], plan["main_mb"], plan["main_kb"])
     if tkey in PROFILED_TRAFFIC and plan["z_chunk"] >= NAUX:
         roof["traffic"] = PROFILED_TRAFFIC[tkey]
         roof["traffic_source"] = "ncu capture of this kernel and plan (one launch = one sigma build)"

@@ -338,6 +338,9 @@ rttda_status rttda_set_integrator(rttda_t h, int integrator);
  *               1: tcgen05, 128-row tiles (BF16X3),
  *               2: tcgen05, wide-M tiles of main_mb x 128 rows (BF16, BF16X2),
  *               3: tcgen05, Ozaki digit pairs on 128 x 64 tiles (FP64_OZ),
+ *               4: tcgen05, wide tiles with the contraction transposed: rows a
+ *                  (main_mb x 128), columns (trajectory column, i) (BF16,
+ *                  BF16X2; the tuner's choice when faster),
  * with main_bn output columns per tile, K tiles of main_kb BF16 and
  * main_splits split-K partials; Z^P = B^P_oo c is built for z_chunk values
  * of P at a time.  coulomb_kernel 0: SIMT, 1: tcgen05, 2: tcgen05 Ozaki digits
@@ -346,8 +349,9 @@ rttda_status rttda_set_integrator(rttda_t h, int integrator);
  * fastest of five launches of candidate k in milliseconds, ncand
  * candidates), 2: taken
  * from the tuning cache of this process or of the RTTDA_TUNE_CACHE file,
- * 3: named by the environment variable RTTDA_WIDE_PLAN="BN,MB,KB" (an
- * unknown candidate there makes rttda_set_field fail with RTTDA_E_ARG).
+ * 3: named by the environment variable RTTDA_WIDE_PLAN="BN,MB,KB" or, for
+ * main_kernel 4, "BN,2,32,t" (an unknown candidate there makes
+ * rttda_set_field fail with RTTDA_E_ARG).
  * RTTDA_ZCHUNK=n caps z_chunk at n values of P (all precisions).
  * Errors: RTTDA_E_ARG (NULL), RTTDA_E_STATE (no batch yet). */
 typedef struct {
