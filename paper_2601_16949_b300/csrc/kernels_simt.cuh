@@ -552,15 +552,20 @@ __global__ void __launch_bounds__(256) k_field(int o, int v, int T, const double
 
 // The same product with one output per thread, for batches too small to give
 // the register-tiled kernel enough blocks: grid (ceil(v/32), ceil(o/8), T),
-// block (32, 8): thread (a, i).
+// block (32, 8): thread (a, i).  With so few blocks per SM the tile loads
+// are latency-bound, so the tiles are double-buffered: the global loads of
+// tile k+1 are issued into registers before tile k is consumed from shared
+// memory, one barrier per tile.  The b and j phases share one buffer.
 template <typename TM_, typename TC>
 __global__ void __launch_bounds__(256) k_field_small(int o, int v, int T, const double* __restrict__ X,
                                                const TM_* __restrict__ moo, const TM_* __restrict__ mvv,
                                                const TM_* __restrict__ m0, double* __restrict__ F) {
-  __shared__ TC sx[8][32][2];    // X[i0+ii][b0+bb]
-  __shared__ TC sm[32][33];      // mu_vv[b0+bb][a0+aa]
-  __shared__ TC so[32][9];       // mu_oo[j0+jj][i0+ii]
-  __shared__ TC sy[32][32][2];   // X[j0+jj][a0+aa]
+  // phase b: [buf] sx[8][32][2] (X[i0+ii][b0+bb]) + sm[32][33] (mu_vv[b0+bb][a0+aa])
+  // phase j: [buf] so[32][9] (mu_oo[j0+jj][i0+ii]) + sy[32][32][2] (X[j0+jj][a0+aa])
+  constexpr int kSX = 8 * 32 * 2, kSM = 32 * 33, kSO = 32 * 9, kSY = 32 * 32 * 2;
+  constexpr int kBufB = kSX + kSM, kBufJ = kSO + kSY;
+  constexpr int kBuf = kBufB > kBufJ ? kBufB : kBufJ;
+  __shared__ TC sbuf[2 * kBuf];
   const int C = 2 * T;
   const int t = blockIdx.z;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
@@ -571,47 +576,94 @@ __global__ void __launch_bounds__(256) k_field_small(int o, int v, int T, const 
   const TM_* Mz = m0 + (size_t)t * o * v;
   const double* Xt = X + 2 * t;
   TC fr = 0, fi = 0;
-  for (int b0 = 0; b0 < v; b0 += 32) {
-    {
-      const int ii = ty, bb = tx;
-      const bool ok = (i0 + ii < o) && (b0 + bb < v);
-      const size_t row = 1 + (size_t)(i0 + ii) * v + b0 + bb;
-      sx[ii][bb][0] = ok ? (TC)Xt[row * C] : TC(0);
-      sx[ii][bb][1] = ok ? (TC)Xt[row * C + 1] : TC(0);
-    }
-    for (int e = tid; e < 32 * 32; e += 256) {
-      const int bb = e / 32, aa = e % 32;
-      sm[bb][aa] = (b0 + bb < v && a0 + aa < v) ? cvt<TC>(Mv[(size_t)(b0 + bb) * v + a0 + aa]) : TC(0);
-    }
+  {
+    // phase b: F_ia += sum_b X_ib mu_ab
+    TC rx[2], rm[4];
+    auto fetch = [&](int b0) {
+      const bool ok = (i0 + ty < o) && (b0 + tx < v);
+      const size_t row = 1 + (size_t)(i0 + ty) * v + b0 + tx;
+      rx[0] = ok ? (TC)Xt[row * C] : TC(0);
+      rx[1] = ok ? (TC)Xt[row * C + 1] : TC(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + 256 * q, bb = e / 32, aa = e % 32;
+        rm[q] = (b0 + bb < v && a0 + aa < v) ? cvt<TC>(Mv[(size_t)(b0 + bb) * v + a0 + aa]) : TC(0);
+      }
+    };
+    auto put = [&](int buf) {
+      TC* sx = sbuf + buf * kBuf;
+      TC* sm = sx + kSX;
+      sx[(ty * 32 + tx) * 2] = rx[0];
+      sx[(ty * 32 + tx) * 2 + 1] = rx[1];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + 256 * q;
+        sm[(e / 32) * 33 + e % 32] = rm[q];
+      }
+    };
+    const int nb = (v + 31) / 32;
+    fetch(0);
+    put(0);
     __syncthreads();
+    for (int k = 0; k < nb; ++k) {
+      if (k + 1 < nb) fetch((k + 1) * 32);
+      const TC* sx = sbuf + (k & 1) * kBuf;
+      const TC* sm = sx + kSX;
 #pragma unroll 8
-    for (int bb = 0; bb < 32; ++bb) {
-      const TC mv = sm[bb][tx];
-      fr = fma(sx[ty][bb][0], mv, fr);
-      fi = fma(sx[ty][bb][1], mv, fi);
+      for (int bb = 0; bb < 32; ++bb) {
+        const TC mv = sm[bb * 33 + tx];
+        fr = fma(sx[(ty * 32 + bb) * 2], mv, fr);
+        fi = fma(sx[(ty * 32 + bb) * 2 + 1], mv, fi);
+      }
+      if (k + 1 < nb) put((k + 1) & 1);
+      __syncthreads();
     }
-    __syncthreads();
   }
-  for (int j0 = 0; j0 < o; j0 += 32) {
-    for (int e = tid; e < 32 * 8; e += 256) {
-      const int jj = e / 8, ii = e % 8;
-      so[jj][ii] = (j0 + jj < o && i0 + ii < o) ? cvt<TC>(Mo[(size_t)(j0 + jj) * o + i0 + ii]) : TC(0);
-    }
-    for (int e = tid; e < 32 * 32; e += 256) {
-      const int jj = e / 32, aa = e % 32;
-      const bool ok = (j0 + jj < o) && (a0 + aa < v);
-      const size_t row = 1 + (size_t)(j0 + jj) * v + a0 + aa;
-      sy[jj][aa][0] = ok ? (TC)Xt[row * C] : TC(0);
-      sy[jj][aa][1] = ok ? (TC)Xt[row * C + 1] : TC(0);
-    }
+  {
+    // phase j: F_ia -= sum_j mu_ji X_ja
+    TC ro, ry[4][2];
+    auto fetch = [&](int j0) {
+      {
+        const int jj = tid / 8, ii = tid % 8;  // 256 threads = 32 x 8 entries
+        ro = (j0 + jj < o && i0 + ii < o) ? cvt<TC>(Mo[(size_t)(j0 + jj) * o + i0 + ii]) : TC(0);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + 256 * q, jj = e / 32, aa = e % 32;
+        const bool ok = (j0 + jj < o) && (a0 + aa < v);
+        const size_t row = 1 + (size_t)(j0 + jj) * v + a0 + aa;
+        ry[q][0] = ok ? (TC)Xt[row * C] : TC(0);
+        ry[q][1] = ok ? (TC)Xt[row * C + 1] : TC(0);
+      }
+    };
+    auto put = [&](int buf) {
+      TC* so = sbuf + buf * kBuf;
+      TC* sy = so + kSO;
+      so[(tid / 8) * 9 + tid % 8] = ro;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + 256 * q;
+        sy[e * 2] = ry[q][0];
+        sy[e * 2 + 1] = ry[q][1];
+      }
+    };
+    const int nj = (o + 31) / 32;
+    fetch(0);
+    put(0);
     __syncthreads();
+    for (int k = 0; k < nj; ++k) {
+      if (k + 1 < nj) fetch((k + 1) * 32);
+      const TC* so = sbuf + (k & 1) * kBuf;
+      const TC* sy = so + kSO;
 #pragma unroll 8
-    for (int jj = 0; jj < 32; ++jj) {
-      const TC mo = so[jj][ty];
-      fr = fma(-mo, sy[jj][tx][0], fr);
-      fi = fma(-mo, sy[jj][tx][1], fi);
+      for (int jj = 0; jj < 32; ++jj) {
+        const TC mo = so[jj * 9 + ty];
+        fr = fma(-mo, sy[(jj * 32 + tx) * 2], fr);
+        fi = fma(-mo, sy[(jj * 32 + tx) * 2 + 1], fi);
+      }
+      if (k + 1 < nj) put((k + 1) & 1);
+      __syncthreads();
     }
-    __syncthreads();
   }
   if (a < v && i < o) {
     const TC mz = cvt<TC>(Mz[(size_t)i * v + a]);
