@@ -1178,7 +1178,7 @@ static int zchunk_for(int P, size_t budget, size_t per_p) {
 static int choose_splits(long long tiles, long long kt) {
   int best = 1;
   double best_score = -1.0;
-  for (int sk = 1; sk <= 64; ++sk) {
+  for (int sk = 1; sk <= kNumSM; ++sk) {
     if (sk > 1 && kt / sk < 16) break;
     const double x = (double)(tiles * sk) / kNumSM;
     const double score = x / std::ceil(x) - 0.002 * sk;
@@ -1293,9 +1293,9 @@ static void tune_file_load() {
     num("kb", w.kb);
     num("sk", w.sk);
     num("tr", w.tr);
-    const bool valid = w.tr ? (tr_bn_ok(w.bn) && w.mb == 2 && w.kb == 32 && w.sk >= 1 && w.sk <= 64)
+    const bool valid = w.tr ? (tr_bn_ok(w.bn) && w.mb == 2 && w.kb == 32 && w.sk >= 1 && w.sk <= kNumSM)
                             : (((w.bn == 160 && w.mb == 3) || (w.bn == 192 && w.mb == 2)) && (w.kb == 32 || w.kb == 64) &&
-                               w.sk >= 1 && w.sk <= 64);
+                               w.sk >= 1 && w.sk <= kNumSM);
     if (valid) g_tune_cache[line.substr(ks, ke - ks)] = w;
   }
 }
