@@ -103,12 +103,6 @@ __device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t (&r)[4]
                : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-}
-
 // I 2^E as a double, assembled from the bits of I (rounding toward zero,
 // relative error below 2^-52; zero below the normal range): no int-to-FP64
 // conversion, which B300 runs on its narrow FP64 pipe.
@@ -398,16 +392,17 @@ __global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc
 
 // ---------------------------------------------------------------------------
 // The contraction kernel: persistent over (split, m tile, n tile) tiles of
-// 128 x 64; per K tile one pipeline stage (3 stages for OZ_VV, 2 for
-// OZ_PLAIN, whose epilogue stages its int64 rows in shared memory) holds the
-// S digit planes of A and of B; the MMA warp issues the S(S+1)/2 digit pairs of the tile into the
-// group accumulators g = s + t (TMEM columns g * 64 .. +63) and hands them
-// to the epilogue at the end of each exactness block.  Warp roles as in
-// the other tensor-core kernels: warp 0 TMA producer, warp 1 TMEM owner and
-// MMA issuer, warps 2..17 epilogue (TMEM lane quarter warp % 4, columns
-// 16 ((warp - 2) / 4) .. +15; sixteen warps so that the integer work of the
-// drain, which stalls the MMAs of the next block, has latency cover)
-// (warp - 2) / 4).  Every wait is bounded (error code in *err).
+// 128 x 64; per K tile one pipeline stage (3 stages for OZ_VV and
+// OZ_PLAIN64, 2 for OZ_PLAIN, whose epilogue stages its int64 rows in shared
+// memory) holds the S digit planes of A and of B; the MMA warp issues the
+// S(S+1)/2 digit pairs of the tile into the group accumulators g = s + t
+// (TMEM columns g * 64 .. +63) and hands them to the epilogue at the end of
+// each exactness block.  Warp roles as in the other tensor-core kernels:
+// warp 0 TMA producer, warp 1 TMEM owner and MMA issuer, warps 2..17
+// epilogue (TMEM lane quarter warp % 4, columns 16 ((warp - 2) / 4) .. +15;
+// sixteen warps so that the integer work of the drain, which stalls the
+// MMAs of the next block, has latency cover).  Every wait is bounded (error
+// code in *err).
 //
 // K tiles of a split: P in [split * pps, min(pc, (split + 1) * pps)), each
 // P with vt tiles; within a P a block ends every kBlkTiles tiles and at the
@@ -550,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..9) ----------------
+    // ---------------- epilogue (warps 2..17) ----------------
     const int q = warp & 3;
     const int cg = (warp - 2) >> 2;
     const int row = q * 32 + lane;
