@@ -575,28 +575,34 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++nb;
           tc_fence_after();
           if (!ok) break;
-          const int eab = ea - kOutShift;
+          // join the groups into integers and release the accumulators;
+          // the FP64 additions then overlap the next block's MMAs
+          long long Iv[kCW];
 #pragma unroll
           for (int c4 = 0; c4 < kCW / 4; ++c4) {
             uint32_t r[kS][4];
 #pragma unroll
             for (int g = 0; g < kS; ++g) tmem_ld4_nowait(tl + (uint32_t)(g * kBN + c4 * 4), r[g]);
             tmem_wait_ld();
-            const uint32_t w0 = (c4 & 1) ? eb4[c4 >> 1].z : eb4[c4 >> 1].x;
-            const uint32_t w1 = (c4 & 1) ? eb4[c4 >> 1].w : eb4[c4 >> 1].y;
-            const int ebj[4] = {(int)(short)(w0 & 0xFFFFu), (int)w0 >> 16, (int)(short)(w1 & 0xFFFFu), (int)w1 >> 16};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               // I = sum_g acc_g 2^(7(S-1-g)) (Horner from the leading group)
               long long I = __float2int_rn(__uint_as_float(r[0][j]));
 #pragma unroll
               for (int g = 1; g < kS; ++g) I = I * 128 + __float2int_rn(__uint_as_float(r[g][j]));
-              acc[c4 * 4 + j] += scaled_i64(I, eab + ebj[j]);
+              Iv[c4 * 4 + j] = I;
             }
           }
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(acce);
+          const int eab = ea - kOutShift;
+#pragma unroll
+          for (int j = 0; j < kCW; ++j) {
+            const uint32_t w = (j & 4) ? ((j & 2) ? eb4[j >> 3].w : eb4[j >> 3].z) : ((j & 2) ? eb4[j >> 3].y : eb4[j >> 3].x);
+            const int ebj = (j & 1) ? (int)w >> 16 : (int)(short)(w & 0xFFFFu);
+            acc[j] += scaled_i64(Iv[j], eab + ebj);
+          }
         }
         if (!ok) break;
         if (m < p.M) {
