@@ -67,7 +67,9 @@ typedef enum {
  * every mode.
  *   FP64:   all contractions in FP64 (CUDA cores).
  *   FP32:   factors and contractions in FP32 (CUDA cores).
- *   TF32:   reserved (rejected with RTTDA_E_ARG by this version).
+ *   TF32:   not provided (RTTDA_E_ARG): on B300 TF32 runs at half the BF16
+ *           tensor rate with 4-byte operands; BF16X2 is faster and more
+ *           accurate.
  *   BF16:   exchange on tcgen05 tensor cores with BF16 factors and BF16
  *           activations, FP32 accumulation; Coulomb with BF16 factors and
  *           FP32 arithmetic; field in FP32.

@@ -1978,6 +1978,8 @@ rttda_status rttda_create(int nocc, int nvirt, int naux, const double* eps_occ, 
   if (nocc < 1 || nvirt < 1 || naux < 1) return set_error(RTTDA_E_ARG, "rttda_create: nocc, nvirt, naux must be >= 1");
   if (!eps_occ || !eps_virt || !B_ov || !B_oo || !B_vv || !mu_oo || !mu_vv || !mu_0ov)
     return set_error(RTTDA_E_ARG, "rttda_create: NULL input array");
+  if (prec == RTTDA_TF32)
+    return set_error(RTTDA_E_ARG, "rttda_create: TF32 is not provided (BF16X2 is faster and more accurate on B300)");
   if (prec != RTTDA_FP64 && prec != RTTDA_FP32 && prec != RTTDA_BF16 && prec != RTTDA_BF16X3 &&
       prec != RTTDA_BF16X2 && prec != RTTDA_FP64_OZ)
     return set_error(RTTDA_E_ARG, "rttda_create: unsupported precision");

@@ -50,6 +50,10 @@ def test_create_rejects_bad_sizes_without_gpu(rb):
     assert st == rb.E_ARG
     st = rb.lib.rttda_create(2, 3, 4, p, p, p, p, p, p, p, p, 0.2, 7, ct.byref(h))
     assert st == rb.E_ARG
+    st = rb.lib.rttda_create(2, 3, 4, p, p, p, p, p, p, p, p, 0.2, rb.TF32, ct.byref(h))
+    assert st == rb.E_ARG and b"TF32" in rb.lib.rttda_last_error()
+    st = rb.lib.rttda_create(513, 3, 4, p, p, p, p, p, p, p, p, 0.2, rb.FP64_OZ, ct.byref(h))
+    assert st == rb.E_ARG and b"512" in rb.lib.rttda_last_error()
 
 
 def test_spectrum_rejects_bad_arguments_without_gpu(rb):
