@@ -125,3 +125,41 @@ def test_fp64oz_rejects_nocc_above_512(rb):
     with pytest.raises(rb.RTTDAError) as e:
         rb.Propagator(mol, 0.2, "fp64oz")
     assert e.value.status == rb.E_ARG
+
+
+def test_fp64oz_split_operator_and_resume(rb):
+    """The split-operator stepper on the digit path: driven batch from a
+    given state against the oracle's split operator, and a bitwise resume."""
+    mol = synth.molecule(4, 9, 11, seed=2)
+    pulses = [dict(kind=1, E0=0.03, omega=0.7, direction=(0, 0, 1)),
+              dict(kind=3, E0=0.04, omega=0.6, t0=1.5, fwhm=2.5, beta=0.3, direction=(0, 1, 1))]
+    c0 = synth.random_state(1 + 4 * 9, len(pulses), seed=4)
+    a = rb.Propagator(mol, 0.3, "fp64oz", integrator="sso")
+    a.set_field(pulses)
+    c, dip, nrm = a.propagate(0.05, 150, c0=c0)
+    refs = oracle_runs(mol, 0.3, pulses, 0.05, 150, c0=c0, integrator="sso")
+    for t, ref in enumerate(refs):
+        assert np.max(np.abs(c[t] - ref.c)) < 1e-11, t
+        assert np.max(np.abs(nrm[t] - ref.norm)) < 1e-12, t
+    a.propagate(0.05, 80, c0=c0)
+    c_full = a.resume(0.05, 40)[0]
+    b = rb.Propagator(mol, 0.3, "fp64oz", integrator="sso")
+    b.set_field(pulses)
+    b.propagate(0.05, 80, c0=c0)
+    state, t_now = b.get_state()
+    b.set_state(state, t_now)
+    assert np.array_equal(b.resume(0.05, 40)[0], c_full)
+    a.close()
+    b.close()
+
+
+def test_fp64oz_eigenstates_match_dense_diagonalisation(rb):
+    """Davidson on the digit path's sigma finds the dense eigenpairs."""
+    mol = synth.molecule(5, 12, 17, seed=21)
+    prop = rb.Propagator(mol, 0.2, "fp64oz")
+    prop.set_field([dict(kind=0, E0=1e-3, direction=(0, 0, 1))])
+    w, X, iters = prop.eigenstates(6, tol=1e-9, max_iter=300)
+    w_ref, X_ref = orc.ti_states(orc.build_A(mol, 0.2), 6)
+    assert np.max(np.abs(w - w_ref)) < 1e-10, (w, w_ref)
+    assert np.max(np.abs(np.abs(np.sum(X * X_ref, axis=1)) - 1.0)) < 1e-9
+    prop.close()
