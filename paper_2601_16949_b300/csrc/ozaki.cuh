@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(256) k_slice_w(int P, int Pp, int C, int cp, i
 // pairs b = 2l + 64q, 2l + 1 + 64q of the block.  Digits in the tile order
 // of the main contraction, [digit][(P, b/64)][col * o + i][64]; exponents
 // ez[(P * nbp + blk) * (C * o) + col * o + i].
-__global__ void __launch_bounds__(256, 2) k_slice_z(int o, int vp, int C, int pc, int nbp, int p0,
+__global__ void __launch_bounds__(256, 4) k_slice_z(int o, int vp, int C, int pc, int nbp, int p0,
                                                  const long long* __restrict__ Zi, const short* __restrict__ eoo,
                                                  const int* __restrict__ ex, __nv_bfloat16* __restrict__ dst,
                                                  long long plane, int* __restrict__ ez) {
