@@ -10,9 +10,9 @@
 //   * no FP64 arithmetic in the stream: the stage's amplitudes are converted
 //     to FP32 once per stage (k_prep_xf), and the FP64 pipe is a small
 //     fraction of the FP32 rate;
-//   * 16-byte loads with eight of them in flight per thread and two or more
-//     CTAs per SM (at most 128 registers per thread), so that 64 KB or more
-//     per SM are in flight;
+//   * 16-byte loads with eight of them in flight per thread and three CTAs
+//     per SM for up to six columns (two above), so that 64-96 KB per SM are
+//     in flight;
 //   * pass 1 stages its slice of FP32 amplitudes in shared memory once per
 //     CTA and reuses it for 32 factor rows.
 // Partial sums (pass 1 over ia slices, pass 2 over chunks of P) are added in
@@ -30,7 +30,13 @@ namespace stream {
 
 constexpr int kThreads = 256;
 constexpr int kW1Rows = 32;              // pass 1: factor rows per CTA (4 per warp)
-constexpr int kMinBlocksPerSM = 2;       // register cap: 128 per thread
+// CTAs per SM the register budget is sized for: three (85 registers) for
+// up to six columns, two (128 registers) above, where the per-thread
+// accumulators grow with C
+template <int C>
+constexpr int min_blocks_w() { return C <= 6 ? 3 : 2; }
+template <int C>
+constexpr int min_blocks_j() { return C <= 6 ? 3 : 2; }
 constexpr int kW1SmemBytes = 48 * 1024;  // pass 1 amplitude slice
 
 template <typename TF>
@@ -69,7 +75,7 @@ __global__ void __launch_bounds__(256) k_prep_xf(long long n, int C, const doubl
 // slice * C * 4 <= kW1SmemBytes.
 // ---------------------------------------------------------------------------
 template <typename TF, int C>
-__global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
+__global__ void __launch_bounds__(kThreads, min_blocks_w<C>())
     k_coul_w_stream(const TF* __restrict__ Bov, const float* __restrict__ Xf, int P, long long ov, int slice,
                     float* __restrict__ wpart) {
   constexpr int V = 16 / sizeof(TF);
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 // Jpart[s][ia][col] = 2 x partial sum.  Requires ov % V == 0.
 // ---------------------------------------------------------------------------
 template <typename TF, int C>
-__global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
+__global__ void __launch_bounds__(kThreads, min_blocks_j<C>())
     k_coul_J_stream(const TF* __restrict__ Bov, const float* __restrict__ wpart, int nw, int P, long long ov,
                     int pchunk, float* __restrict__ Jpart) {
   constexpr int V = 16 / sizeof(TF);
