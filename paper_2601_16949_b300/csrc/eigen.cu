@@ -317,7 +317,7 @@ extern "C" rttda_status rttda_eigenstates(rttda_t h, int k, double tol, int max_
     int added = 0;
     for (int q = 0; q < nu; ++q) {
       double* tq = dT.p + (size_t)q * N;
-      // against the vectors added in this round, then normalise
+      // against the vectors added in this iteration, then normalise
       for (int pass = 0; pass < 2; ++pass) {
         if (added > 0) {
           k_dots<<<dim3(added, 1), 256, 0, s>>>(N, dV.p + (size_t)m * N, tq, 1, dc1.p);
