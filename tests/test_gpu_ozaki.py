@@ -163,3 +163,44 @@ def test_fp64oz_eigenstates_match_dense_diagonalisation(rb):
     assert np.max(np.abs(w - w_ref)) < 1e-10, (w, w_ref)
     assert np.max(np.abs(np.abs(np.sum(X * X_ref, axis=1)) - 1.0)) < 1e-9
     prop.close()
+
+
+def _extreme_digit_value(sign):
+    """A value in (-1, 1) whose six centred base-128 digits are all at the
+    largest magnitude the split produces for a block maximum of 1:
+    +-(127, 63, 63, 63, 63, 63)."""
+    F = 127 * 128 ** 5 + 63 * sum(128 ** k for k in range(5))
+    return sign * F / 2.0 ** 42
+
+
+@pytest.mark.parametrize("pattern", ["equal", "alternating"])
+def test_fp64oz_group_sums_at_their_bound_stay_exact(rb, pattern):
+    """Exactness of the tensor-core group sums at their worst case.  With
+    nocc = 1, nvirt = 512 (one exactness block of 512 b per P), B_oo = 1 and
+    every amplitude and B_vv entry at +-(127, 63, 63, 63, 63, 63), the
+    digit-pair sums of the main contraction reach (g + 3) 2^12 x 512 per
+    group: 2^23.96 for g = 5, 2^23 for the leading groups.  A rounded partial
+    sum in a leading group would show as a relative error near 1e-7; the
+    dropped pairs (s + t >= 6) allow about 2^-44."""
+    o, v, P = 1, 512, 1
+    x = _extreme_digit_value(1.0)
+    sgn = np.ones(v) if pattern == "equal" else np.where(np.arange(v) % 2 == 0, 1.0, -1.0)
+    mol = dict(nocc=o, nvirt=v, naux=P,
+               eps_occ=np.zeros(o), eps_virt=np.zeros(v),
+               B_ov=np.zeros((P, o, v)), B_oo=np.ones((P, o, o)),
+               B_vv=np.full((P, v, v), x), mu_oo=np.zeros((3, o, o)),
+               mu_vv=np.zeros((3, v, v)), mu_0ov=np.zeros((3, o, v)))
+    c = np.zeros((1, 1 + v), dtype=complex)
+    c[0, 1:] = x * sgn
+    pulses = [dict(kind=1, E0=0.0, omega=0.5, direction=(0, 0, 1))]
+    prop = rb.Propagator(mol, 1.0, "fp64oz")
+    prop.set_field(pulses)
+    got = _sigma_gpu(rb, prop, c, 0.0)
+    prop.close()
+    ref = oracle_sigma(mol, 1.0, pulses, c, 0.0)
+    exact = -x * x * np.sum(sgn)   # every row a: -c_x sum_b x_b B_ab
+    scale = x * x * v
+    assert np.max(np.abs(ref[0, 1:] - exact)) <= 1e-14 * scale   # the oracle, up to FP64 summation
+    assert abs(got[0, 0]) == 0.0
+    err = np.max(np.abs(got[0, 1:] - exact)) / scale
+    assert err <= 1e-12, err
