@@ -27,6 +27,7 @@ CASES = [  # (nocc, nvirt, naux, prec, pulse, nsteps, seed)
     (9, 64, 36, "bf16x2", dict(kind=4, E0=0.02, omega=0.9, duration=8.0, direction=(1, 0, 0)), 420, 2),
     (4, 130, 52, "bf16x3", dict(kind=0, E0=2e-3, direction=(0, 1, 0)), 250, 3),
     (12, 48, 30, "fp32", dict(kind=2, E0=0.03, omega=0.7, t0=3.0, fwhm=2.0, direction=(0, 1, 1)), 360, 4),
+    (5, 40, 24, "fp64oz", dict(kind=3, E0=0.02, omega=0.8, t0=2.0, fwhm=2.5, beta=0.2, direction=(1, 0, 1)), 200, 5),
 ]
 
 
