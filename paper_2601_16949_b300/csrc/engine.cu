@@ -535,13 +535,25 @@ void coulomb_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
   }
 }
 
-void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s) {
+// BF16 planes of the stage's amplitudes for the Z build; with_xf: the same
+// launch writes the FP32 copy the streaming Coulomb reads (ov x C <= the
+// plane grid, since vp >= v and op >= o).
+void prep_xt(rttda_ctx* h, const double* X, bool with_xf, cudaStream_t s) {
+  const int C = 2 * h->T;
+  const long long tot = (long long)C * h->vp * h->op;
+  k_prep_xt<<<blocks_for(tot, 256), 256, 0, s>>>(h->o, h->v, h->vp, h->op, C, X, h->Xt,
+                                                h->nplanes > 1 ? h->Xt + tot : nullptr,
+                                                with_xf ? h->ov * C : 0, with_xf ? h->Xf : nullptr);
+}
+
+// xt_done: the planes of X are already in Xt (written with the Coulomb's
+// FP32 copy by one launch).
+void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s, bool xt_done = false) {
   const int C = 2 * h->T, o = h->o, v = h->v, vp = h->vp, op = h->op;
-  {
+  if (!xt_done) {
     Prof pr(h, RTTDA_KC_EXCHANGE_Z, s);
     h->launches += 1;
-    const long long tot = (long long)C * vp * op;
-    k_prep_xt<<<blocks_for(tot, 256), 256, 0, s>>>(o, v, vp, op, C, X, h->Xt, h->nplanes > 1 ? h->Xt + tot : nullptr);
+    prep_xt(h, X, false, s);
   }
   for (int c = 0, p0 = 0; p0 < h->P; p0 += h->zchunk, ++c) {
     const int pc = std::min(h->zchunk, h->P - p0);
@@ -724,9 +736,10 @@ void coulomb_oz(rttda_ctx* h, const double* X, cudaStream_t s) {
 // Coulomb on the FP32 streaming kernels: FP32 copy of the stage's amplitudes,
 // then both passes; column count as a template argument (2T in {2, ..., 12}).
 template <typename TF, int C>
-void coul_stream_launch_c(rttda_ctx* h, const double* X, cudaStream_t s) {
+void coul_stream_launch_c(rttda_ctx* h, const double* X, bool xf_done, cudaStream_t s) {
   const long long nx = h->ov * C;
-  stream::k_prep_xf<<<(unsigned)std::min<long long>(cdiv(nx, 256), 8 * kNumSM), 256, 0, s>>>(nx, C, X, h->Xf);
+  if (!xf_done)
+    stream::k_prep_xf<<<(unsigned)std::min<long long>(cdiv(nx, 256), 8 * kNumSM), 256, 0, s>>>(nx, C, X, h->Xf);
   stream::k_coul_w_stream<TF, C><<<dim3((unsigned)cdiv(h->P, stream::kW1Rows), h->SW), stream::kThreads,
                                    (size_t)h->wslice * C * sizeof(float), s>>>((const TF*)h->Bov, h->Xf, h->P, h->ov,
                                                                                h->wslice, (float*)h->w);
@@ -737,14 +750,14 @@ void coul_stream_launch_c(rttda_ctx* h, const double* X, cudaStream_t s) {
 }
 
 template <typename TF>
-void coul_stream_launch(rttda_ctx* h, int C, const double* X, cudaStream_t s) {
+void coul_stream_launch(rttda_ctx* h, int C, const double* X, bool xf_done, cudaStream_t s) {
   switch (C) {
-    case 2: coul_stream_launch_c<TF, 2>(h, X, s); break;
-    case 4: coul_stream_launch_c<TF, 4>(h, X, s); break;
-    case 6: coul_stream_launch_c<TF, 6>(h, X, s); break;
-    case 8: coul_stream_launch_c<TF, 8>(h, X, s); break;
-    case 10: coul_stream_launch_c<TF, 10>(h, X, s); break;
-    default: coul_stream_launch_c<TF, 12>(h, X, s); break;
+    case 2: coul_stream_launch_c<TF, 2>(h, X, xf_done, s); break;
+    case 4: coul_stream_launch_c<TF, 4>(h, X, xf_done, s); break;
+    case 6: coul_stream_launch_c<TF, 6>(h, X, xf_done, s); break;
+    case 8: coul_stream_launch_c<TF, 8>(h, X, xf_done, s); break;
+    case 10: coul_stream_launch_c<TF, 10>(h, X, xf_done, s); break;
+    default: coul_stream_launch_c<TF, 12>(h, X, xf_done, s); break;
   }
 }
 
@@ -816,10 +829,14 @@ template <typename TF, typename TC, bool XTC>
 struct Ops {
   using TL = Tile<TC>;
 
-  static void coulomb(rttda_ctx* h, const double* X, cudaStream_t s) {
+  // Returns whether it also wrote the exchange's BF16 planes of X (only when
+  // asked with prep_xt, on the tensor-core exchange with the streaming
+  // Coulomb: one launch writes them and the FP32 copy); the caller then
+  // passes that to exchange() on the same X.
+  static bool coulomb(rttda_ctx* h, const double* X, cudaStream_t s, bool prep_xt_too = false) {
     if (XTC && h->coul_tc) {
       coulomb_tc(h, X, s);
-      return;
+      return false;
     }
     Prof pr(h, RTTDA_KC_COULOMB, s);
     h->launches += 2;
@@ -827,8 +844,10 @@ struct Ops {
     if constexpr (!std::is_same<TF, double>::value) {
       if (h->coul_stream) {
         h->launches += 1;  // the FP32 amplitude copy
-        coul_stream_launch<TF>(h, C, X, s);
-        return;
+        const bool fused = XTC && prep_xt_too;
+        if (fused) prep_xt(h, X, true, s);
+        coul_stream_launch<TF>(h, C, X, fused, s);
+        return fused;
       }
     }
     if (h->coul_vec) {
@@ -840,7 +859,7 @@ struct Ops {
       const size_t smem = (size_t)h->pchunkJ * C * sizeof(TC);
       k_coul_J_vec<TF, TC, 6><<<g, 256, smem, s>>>((const TF*)h->Bov, (const TC*)h->w, h->SW, h->P, h->ov, C,
                                                   h->pchunkJ, (TC*)h->Jpart);
-      return;
+      return false;
     }
     constexpr int PB = 8;
     k_coul_w<TF, TC, 8, PB><<<dim3(blocks_for(h->P, PB), h->SW), 256, 0, s>>>((const TF*)h->Bov, X, h->P, h->ov, C,
@@ -849,11 +868,12 @@ struct Ops {
     const size_t smem = (size_t)h->pchunkJ * C * sizeof(TC);
     k_coul_J<TF, TC, 8><<<g, 256, smem, s>>>((const TF*)h->Bov, (const TC*)h->w, h->SW, h->P, h->ov, C,
                                             h->pchunkJ, (TC*)h->Jpart);
+    return false;
   }
 
-  static void exchange(rttda_ctx* h, const double* X, cudaStream_t s) {
+  static void exchange(rttda_ctx* h, const double* X, cudaStream_t s, bool xt_done = false) {
     if (XTC) {
-      exchange_tc(h, X, s);
+      exchange_tc(h, X, s, xt_done);
       return;
     }
     const int C = 2 * h->T, o = h->o, v = h->v;
@@ -898,24 +918,26 @@ struct Ops {
   }
 
   static void combine(rttda_ctx* h, int mode, int stage, bool use_field, double dt, const double* Xin,
-                      double* Xnext, double* sig_out, cudaStream_t s) {
+                      double* Xnext, double* sig_out, cudaStream_t s, long long* step_ctr = nullptr) {
     Prof pr(h, RTTDA_KC_COMBINE, s);
     h->launches += 1;
     const int C = 2 * h->T;
     k_combine<TC><<<blocks_for(h->N * 2 * h->T, 256), 256, 0, s>>>(
         mode, stage, h->N, h->o, h->v, h->T, h->eps_o, h->eps_v, h->cx, (const TC*)h->Jpart, h->SJ,
         (const TC*)h->Kpart, h->SK, (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn, Xin,
-        Xnext, h->acc, sig_out);
+        Xnext, h->acc, sig_out, step_ctr);
   }
 
   // split-operator sub-step on the stage input X (in place); see k_sso_update
-  static void sso_update(rttda_ctx* h, int mode, int stage, bool use_field, double dt, double* X, cudaStream_t s) {
+  static void sso_update(rttda_ctx* h, int mode, int stage, bool use_field, double dt, double* X, cudaStream_t s,
+                         long long* step_ctr = nullptr) {
     Prof pr(h, RTTDA_KC_COMBINE, s);
     h->launches += 1;
     const int C = 2 * h->T;
     k_sso_update<TC><<<blocks_for(h->N * h->T, 256), 256, 0, s>>>(
         mode, stage, h->N, h->o, h->v, h->T, h->eps_o, h->eps_v, h->cx, (const TC*)h->Jpart, h->SJ,
-        (const TC*)h->Kpart, h->SK, (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn, X);
+        (const TC*)h->Kpart, h->SK, (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn, X,
+        step_ctr);
   }
 
   static void set_smem_limits() {
@@ -929,8 +951,11 @@ struct Ops {
 
 // FP64_OZ: the FP64 paths with the exchange on Ozaki digits
 struct OpsOz : Ops<double, double, false> {
-  static void coulomb(rttda_ctx* h, const double* X, cudaStream_t s) { coulomb_oz(h, X, s); }
-  static void exchange(rttda_ctx* h, const double* X, cudaStream_t s) { exchange_oz(h, X, s); }
+  static bool coulomb(rttda_ctx* h, const double* X, cudaStream_t s, bool = false) {
+    coulomb_oz(h, X, s);
+    return false;
+  }
+  static void exchange(rttda_ctx* h, const double* X, cudaStream_t s, bool = false) { exchange_oz(h, X, s); }
   static void set_smem_limits() {
     Ops<double, double, false>::set_smem_limits();
     oz_attr();
@@ -993,7 +1018,8 @@ void enqueue_acf(rttda_ctx* h, const double* X, long long ld, long long step_off
 template <typename O>
 void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, double* dip, double* nrm, long long ld,
                   long long offset, cudaStream_t s) {
-  h->launches += 2;  // efield + step counter
+  // the step counter advances in the last stage's combine
+  h->launches += 1;
   k_efield<<<1, 128, 0, s>>>(h->T, h->d_pulses, h->d_step, base, t_off, dt, h->E);
   for (int st = 0; st < 4; ++st) {
     // stage inputs alternate between two buffers (the combine reads one and
@@ -1007,11 +1033,10 @@ void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, doub
       enqueue_project(h, h->Xn, ld, offset, s);
       enqueue_acf(h, h->Xn, ld, offset, s);
     }
-    O::coulomb(h, xin, s);
-    O::exchange(h, xin, s);
-    O::combine(h, 0, st, fld, dt, xin, xnext, nullptr, s);
+    const bool xt = O::coulomb(h, xin, s, true);
+    O::exchange(h, xin, s, xt);
+    O::combine(h, 0, st, fld, dt, xin, xnext, nullptr, s, st == 3 ? h->d_step : nullptr);
   }
-  k_step_inc<<<1, 1, 0, s>>>(h->d_step);
 }
 
 // One symplectic split-operator step (Sec. 2.2): two sigma builds, each on one
@@ -1022,7 +1047,8 @@ void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, doub
 template <typename O>
 void enqueue_step_sso(rttda_ctx* h, O, long long base, double t_off, double dt, double* dip, double* nrm,
                       long long ld, long long offset, cudaStream_t s) {
-  h->launches += 2;  // efield + step counter
+  // the step counter advances in the second half's update
+  h->launches += 1;
   k_efield<<<1, 128, 0, s>>>(h->T, h->d_pulses, h->d_step, base, t_off, dt, h->E);
   const bool fld = h->any_field;
   if (dip) {
@@ -1033,11 +1059,10 @@ void enqueue_step_sso(rttda_ctx* h, O, long long base, double t_off, double dt, 
   enqueue_acf(h, h->Xn, ld, offset, s);
   for (int half = 0; half < 2; ++half) {
     if (fld) O::field(h, h->Xs, s);
-    O::coulomb(h, h->Xs, s);
-    O::exchange(h, h->Xs, s);
-    O::sso_update(h, half == 0 ? 1 : 2, half == 0 ? 1 : 3, fld, dt, h->Xs, s);
+    const bool xt = O::coulomb(h, h->Xs, s, true);
+    O::exchange(h, h->Xs, s, xt);
+    O::sso_update(h, half == 0 ? 1 : 2, half == 0 ? 1 : 3, fld, dt, h->Xs, s, half == 1 ? h->d_step : nullptr);
   }
-  k_step_inc<<<1, 1, 0, s>>>(h->d_step);
 }
 
 // First half step of the split operator at the start of a propagation:
@@ -1048,8 +1073,8 @@ void enqueue_sso_prologue(rttda_ctx* h, O, long long base, double t_off, double 
   k_efield<<<1, 128, 0, s>>>(h->T, h->d_pulses, h->d_step, base, t_off, dt, h->E);
   const bool fld = h->any_field;
   if (fld) O::field(h, h->Xs, s);
-  O::coulomb(h, h->Xs, s);
-  O::exchange(h, h->Xs, s);
+  const bool xt = O::coulomb(h, h->Xs, s, true);
+  O::exchange(h, h->Xs, s, xt);
   O::sso_update(h, 0, 0, fld, dt, h->Xs, s);
 }
 

@@ -725,7 +725,7 @@ __global__ void k_efield(int T, const PulseDev* __restrict__ pulses, const long 
   }
 }
 
-__global__ void k_step_inc(long long* step) { *step += 1; }
+
 
 // ---------------------------------------------------------------------------
 // sigma assembly and RK4 stage update (one thread per amplitude row n).
@@ -768,7 +768,11 @@ __global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long 
                                                  const double* __restrict__ F, const double* __restrict__ E,
                                                  int use_field, double dt, double* __restrict__ Xn,
                                                  const double* __restrict__ Xs, double* __restrict__ Xs_next,
-                                                 double* __restrict__ acc, double* __restrict__ sig_out) {
+                                                 double* __restrict__ acc, double* __restrict__ sig_out,
+                                                 long long* __restrict__ step_ctr) {
+  // step_ctr (the last stage of a step): advance the step counter; nothing in
+  // this kernel reads it and everything of the step before it already has.
+  if (step_ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
   // one thread per (trajectory t, part q, row n), n fastest.  Xs is this
   // stage's input and is only read; the next stage's input goes to Xs_next.  sigma_q is the
   // real (q = 0) or imaginary (q = 1) part; k = -i sigma swaps them, so the
@@ -844,7 +848,9 @@ __global__ void __launch_bounds__(256) k_sso_update(int mode, int stage, long lo
                                                     const TC* __restrict__ Kpart, int SK, long long Kstride,
                                                     const double* __restrict__ F, const double* __restrict__ E,
                                                     int use_field, double dt, double* __restrict__ Xn,
-                                                    double* __restrict__ X) {
+                                                    double* __restrict__ X, long long* __restrict__ step_ctr) {
+  // step_ctr: as in k_combine, for the last sub-step of a step
+  if (step_ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int n32 = (int)N;
   if (e >= n32 * T) return;
@@ -1214,10 +1220,14 @@ __global__ void k_pack_oo(int pc, int o, int op, const double* __restrict__ src,
 }
 
 // Amplitudes -> Xt[plane][(col, b)][j] = X[1 + j v + b][col] (K-major B
-// operand of Z^P = B^P_oo c), zero for b >= v or j >= o.
+// operand of Z^P = B^P_oo c), zero for b >= v or j >= o.  With Xf, the same
+// launch also writes the FP32 amplitudes of the streaming Coulomb,
+// Xf[e] = X[C + e] for e < nxf (one launch fewer per stage).
 __global__ void k_prep_xt(int o, int v, int vp, int op, int C, const double* __restrict__ X,
-                          __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+                          __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long nxf = 0,
+                          float* __restrict__ Xf = nullptr) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nxf) Xf[e] = (float)X[C + e];
   const long long tot = (long long)C * vp * op;
   if (e >= tot) return;
   const int j = (int)(e % op);
