@@ -1078,6 +1078,40 @@ void enqueue_sso_prologue(rttda_ctx* h, O, long long base, double t_off, double 
   O::sso_update(h, 0, 0, fld, dt, h->Xs, s);
 }
 
+// Turn every kernel-to-kernel edge of the captured step into a programmatic
+// edge (the successor is launched once every CTA of its predecessor has
+// started; it then waits in pdl_entry for the predecessor's completion).
+// RTTDA_PDL=0 keeps ordinary edges.
+cudaError_t make_edges_programmatic(cudaGraph_t g) {
+  const char* e = std::getenv("RTTDA_PDL");
+  if (e && std::atoi(e) == 0) return cudaSuccess;
+  size_t n = 0;
+  cudaError_t ce = cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &n);
+  if (ce != cudaSuccess || n == 0) return ce;
+  std::vector<cudaGraphNode_t> from(n), to(n);
+  std::vector<cudaGraphEdgeData> ed(n);
+  ce = cudaGraphGetEdges(g, from.data(), to.data(), ed.data(), &n);
+  if (ce != cudaSuccess) return ce;
+  for (size_t k = 0; k < n; ++k) {
+    cudaGraphNodeType ta, tb;
+    if ((ce = cudaGraphNodeGetType(from[k], &ta)) != cudaSuccess) return ce;
+    if ((ce = cudaGraphNodeGetType(to[k], &tb)) != cudaSuccess) return ce;
+    if (ta != cudaGraphNodeTypeKernel || tb != cudaGraphNodeTypeKernel ||
+        ed[k].type != cudaGraphDependencyTypeDefault || ed[k].from_port != cudaGraphKernelNodePortDefault)
+      continue;
+    cudaGraphEdgeData pe{};
+    pe.from_port = cudaGraphKernelNodePortProgrammatic;
+    pe.type = cudaGraphDependencyTypeProgrammatic;
+    if ((ce = cudaGraphRemoveDependencies(g, &from[k], &to[k], &ed[k], 1)) != cudaSuccess) return ce;
+    if ((ce = cudaGraphAddDependencies(g, &from[k], &to[k], &pe, 1)) != cudaSuccess) {
+      // put the ordinary edge back so the graph stays ordered
+      cudaGraphAddDependencies(g, &from[k], &to[k], &ed[k], 1);
+      return ce;
+    }
+  }
+  return cudaSuccess;
+}
+
 rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, double* dip, double* nrm,
                        long long ld, long long offset, cudaStream_t s) {
   // stage times are t_off + (base + k + c_s) dt with an integer base when the
@@ -1114,6 +1148,11 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
     h->launches = l0 + h->launches_per_step * nsteps;
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (ce != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    ce = make_edges_programmatic(graph);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return set_error(RTTDA_E_CUDA, std::string("graph edges: ") + cudaGetErrorString(ce));
+    }
     ce = cudaGraphInstantiate(&exec, graph, 0);
     if (ce != cudaSuccess) {
       cudaGraphDestroy(graph);
