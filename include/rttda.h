@@ -98,7 +98,12 @@ typedef enum {
 /* Pulse shapes E(t) (Sec. 2.2, Eqs. delta_pulse, continuous wave,
  * transform_limited, chirped_pulse) plus a sin^2 envelope:
  *   KICK     : E0 delta(t); applied exactly as c(0+) = exp(+i E0 M_d) c(0)
- *              at the start of rttda_propagate, E = 0 afterwards.
+ *              at the start of rttda_propagate, E = 0 afterwards.  Taylor
+ *              series accumulated in FP64; its first-order term from FP64
+ *              products in every precision, the higher terms from the field
+ *              products of the precision (FP32 in FP32, BF16, BF16X2,
+ *              BF16X3: about n 2^-24 x^2 / 2 for x = E0 ||M_d||_2, n = nocc
+ *              + nvirt + 1).
  *   CW       : E0 sin(omega t)
  *   GAUSS_TL : E0 exp(-(t-t0)^2 / (2 s^2)) sin(omega (t-t0)), s = fwhm/2.35482
  *   CHIRP    : E0 exp(-(t-t0)^2 / (2 s^2)) sin((omega + beta (t-t0)/2)(t-t0))

@@ -973,15 +973,25 @@ void dispatch(int prec, F&& f) {
   }
 }
 
-// Exact kick exp(+i kappa M_d) on h->Xn (FP64 field products).
+// Exact kick exp(+i kappa M_d) on h->Xn: Taylor terms accumulated in FP64.
+// The first-order term, which carries the whole linear response, always
+// takes FP64 field products.  The higher terms (each at most x^k / k! of
+// the state for x the bound on |kappa M_d|) take the field products of the
+// precision's sigma build when that is FP32, where B300's FP64 pipe would
+// make them cost as much as a few time steps.
 void enqueue_kick(rttda_ctx* h, cudaStream_t s) {
   Prof pr(h, RTTDA_KC_KICK, s);
   h->launches += 4 * h->kick_terms;
   const long long NT = h->N * h->T;
   cudaMemcpyAsync(h->term, h->Xn, sizeof(double) * NT * 2, cudaMemcpyDeviceToDevice, s);
   for (int k = 1; k <= h->kick_terms; ++k) {
-    launch_field<double, double>(h, h->term, h->moo64, h->mvv64, h->m064, s);
-    launch_field0<double, double>(h, h->term, h->m064, s);
+    if (k == 1 || h->cbytes == 8) {
+      launch_field<double, double>(h, h->term, h->moo64, h->mvv64, h->m064, s);
+      launch_field0<double, double>(h, h->term, h->m064, s);
+    } else {
+      launch_field<float, float>(h, h->term, (const float*)h->mooC, (const float*)h->mvvC, (const float*)h->m0C, s);
+      launch_field0<float, float>(h, h->term, (const float*)h->m0C, s);
+    }
     k_kick_term<<<blocks_for(NT, 256), 256, 0, s>>>(h->N, h->T, h->d_kappa, 1.0 / k, h->F, h->term, h->Xn);
   }
 }

@@ -24,16 +24,25 @@ def rb():
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("integrator", ["rk4", "sso"])
-def test_zero_steps_returns_the_kicked_state(rb, prec, integrator):
+@pytest.mark.parametrize("kappa", [0.01, 0.3])
+def test_zero_steps_returns_the_kicked_state(rb, prec, integrator, kappa):
+    """The kicked state: the Taylor series of exp(i kappa M_d) accumulated in
+    FP64, its first-order term from FP64 field products in every precision.
+    In the precisions whose field products are FP32 the terms of order >= 2
+    take FP32 products, so the state is exact to FP64 rounding plus FP32
+    rounding of those terms: n eps_32 (x^2 / 2) e^x for x = kappa ||M_d||_2
+    and inner length n <= o + v + 1."""
     mol = synth.molecule(3, 8, 5, seed=2)
-    pulses = [dict(kind=0, E0=0.01, direction=(0, 1, 0))]
+    pulses = [dict(kind=0, E0=kappa, direction=(0, 1, 0))]
     prop = rb.Propagator(mol, 0.2, prec, integrator=integrator)
     prop.set_field(pulses)
     c, dip, nrm = prop.propagate(0.05, 0)
     ref = oracle_runs(mol, 0.2, pulses, 0.05, 0)[0]
     assert dip.shape == (1, 1) and nrm.shape == (1, 1)
-    assert np.max(np.abs(c[0] - ref.c)) < 1e-12       # the kick runs in FP64 in every precision
-    assert abs(nrm[0, 0] - ref.norm[0]) < 1e-12
+    x = kappa * np.linalg.norm(orc.build_M(*orc.dipole_along(mol, (0, 1, 0))), 2)
+    ktol = 1e-12 if prec == "fp64" else 1e-12 + (3 + 8 + 1) * 2.0 ** -24 * x * x / 2 * np.exp(x)
+    assert np.max(np.abs(c[0] - ref.c)) < ktol
+    assert abs(nrm[0, 0] - ref.norm[0]) < 2 * ktol
     tol = 1e-12 if prec == "fp64" else 1e-6
     assert abs(dip[0, 0] - ref.dipole[0]) < tol * max(1.0, abs(ref.dipole[0]))
     # resuming zero steps changes nothing
