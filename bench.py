@@ -311,8 +311,7 @@ PREC_INFO = {  # factor bytes, exchange planes, tensor products per K tile
 # (2 wide-M, 4 transposed), BN, MB, K tile):
 # the number holds only for that kernel and plan.
 PROFILED_TRAFFIC = {
-    ("absorption", "bf16x2", "exchange_main", 2, 160, 3, 32): 1.780069e9 + 4.38272e6,
-    ("absorption", "bf16x2", "exchange_main", 4, 192, 2, 32): 1.766210e9 + 3.739392e6,
+    ("absorption", "bf16x2", "exchange_main", 4, 192, 2, 32): 1.766175e9 + 3.553792e6,
 }
 
 
