@@ -1088,13 +1088,13 @@ void enqueue_sso_prologue(rttda_ctx* h, O, long long base, double t_off, double 
   O::sso_update(h, 0, 0, fld, dt, h->Xs, s);
 }
 
-// Turn every kernel-to-kernel edge of the captured step into a programmatic
-// edge (the successor is launched once every CTA of its predecessor has
-// started; it then waits in pdl_entry for the predecessor's completion).
-// RTTDA_PDL=0 keeps ordinary edges.
+// With RTTDA_PDL=1, turn every kernel-to-kernel edge of the captured step
+// into a programmatic edge (the successor is launched once every CTA of its
+// predecessor has started; it then waits in pdl_entry for the
+// predecessor's completion).  Off by default: ordinary edges.
 cudaError_t make_edges_programmatic(cudaGraph_t g) {
   const char* e = std::getenv("RTTDA_PDL");
-  if (e && std::atoi(e) == 0) return cudaSuccess;
+  if (!e || std::atoi(e) != 1) return cudaSuccess;
   size_t n = 0;
   cudaError_t ce = cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &n);
   if (ce != cudaSuccess || n == 0) return ce;
