@@ -194,7 +194,12 @@ rttda_status rttda_propagate(rttda_t h, const double* c0, double dt, long nsteps
 /* As rttda_propagate, but every buffer is device memory and the work is
  * enqueued on `stream` (a cudaStream_t; NULL = the handle's own stream).
  * Returns after enqueueing; results are valid once the stream reaches them.
- * The buffers must stay allocated until then. */
+ * The buffers must stay allocated until then.  The steps run as one CUDA
+ * graph per step, replayed; the handle keeps the executable graph between
+ * calls and updates its parameters, so that calls on handles with their
+ * own streams run concurrently (instantiating a graph allocates device
+ * memory, which would order the call against every stream's work;
+ * RTTDA_GRAPH_CACHE=0 instantiates per call). */
 rttda_status rttda_propagate_device(rttda_t h, const double* c0_dev, double dt, long nsteps,
                                     double* c_out_dev, double* dipole_dev, double* norm_dev,
                                     void* stream);

@@ -153,6 +153,7 @@ struct rttda_ctx {
   double* obs_part = nullptr;
   double* Xq = nullptr;  // sigma entry input
   long long* d_step = nullptr;
+  cudaGraphExec_t step_exec = nullptr;  // the step graph kept between calls
   void* w = nullptr;
   void* Jpart = nullptr;
   void* Zt = nullptr;
@@ -261,6 +262,7 @@ struct rttda_ctx {
 
 rttda_ctx::~rttda_ctx() {
   if (stream) cudaStreamSynchronize(stream);
+  if (step_exec) cudaGraphExecDestroy(step_exec);
   AllocStream as(stream);
   for (auto& v : prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
@@ -1163,16 +1165,40 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
       cudaGraphDestroy(graph);
       return set_error(RTTDA_E_CUDA, std::string("graph edges: ") + cudaGetErrorString(ce));
     }
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    if (ce != cudaSuccess) {
-      cudaGraphDestroy(graph);
-      return set_error(RTTDA_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    // Keep the executable step graph of the handle and give it this call's
+    // parameters with cudaGraphExecUpdate (launches in flight keep theirs);
+    // a new one is instantiated only when the update is refused (a different
+    // topology).  Instantiating allocates device memory, which CUDA orders
+    // against the work of every stream: with an instantiation per call, the
+    // steps of concurrent handles (the server's requests) never overlapped.
+    // RTTDA_GRAPH_CACHE=0 instantiates per call.
+    const char* gc = std::getenv("RTTDA_GRAPH_CACHE");
+    const bool keep = !(gc && std::atoi(gc) == 0);
+    if (keep && h->step_exec) {
+      cudaGraphExecUpdateResultInfo info{};
+      if (cudaGraphExecUpdate(h->step_exec, graph, &info) == cudaSuccess) {
+        exec = h->step_exec;
+      } else {
+        cudaGetLastError();
+        cudaGraphExecDestroy(h->step_exec);
+      }
+      h->step_exec = nullptr;
+    }
+    if (!exec) {
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_error(RTTDA_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+      }
     }
     for (long k = 0; k < nsteps; ++k) {
       ce = cudaGraphLaunch(exec, s);
       if (ce != cudaSuccess) break;
     }
-    cudaGraphExecDestroy(exec);
+    if (keep && ce == cudaSuccess)
+      h->step_exec = exec;
+    else
+      cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
   }
