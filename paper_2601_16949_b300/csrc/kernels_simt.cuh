@@ -736,8 +736,6 @@ __global__ void k_efield(int T, const PulseDev* __restrict__ pulses, const long 
   }
 }
 
-
-
 // ---------------------------------------------------------------------------
 // sigma assembly and RK4 stage update (one thread per amplitude row n).
 //   sigma_n = (e_a - e_i) X_n + J_n - c_x K_n - E_t F_n      (n = ia)
