@@ -1168,10 +1168,11 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
     // Keep the executable step graph of the handle and give it this call's
     // parameters with cudaGraphExecUpdate (launches in flight keep theirs);
     // a new one is instantiated only when the update is refused (a different
-    // topology).  Instantiating allocates device memory, which CUDA orders
-    // against the work of every stream: with an instantiation per call, the
-    // steps of concurrent handles (the server's requests) never overlapped.
-    // RTTDA_GRAPH_CACHE=0 instantiates per call.
+    // topology).  With an instantiation per call, the steps of concurrent
+    // handles (the server's requests) were measured not to overlap at all;
+    // instantiation allocates device memory, which keeps commands of
+    // different streams from running concurrently.  RTTDA_GRAPH_CACHE=0
+    // instantiates per call.
     const char* gc = std::getenv("RTTDA_GRAPH_CACHE");
     const bool keep = !(gc && std::atoi(gc) == 0);
     if (keep && h->step_exec) {
