@@ -124,10 +124,13 @@ typedef struct {
   double dir[3];     /* polarisation d (normalised by the library)         */
 } rttda_pulse;
 
-/* ABI version of the loaded library (RTTDA_ABI_VERSION it was built with). */
+/* ABI version of the loaded library (RTTDA_ABI_VERSION it was built with).
+ * Library utility, no counterpart in the paper; cannot fail. */
 int rttda_abi_version(void);
 
-/* Message describing the last failure on the calling thread ("" if none). */
+/* Message describing the last failure on the calling thread ("" if none).
+ * Library utility, no counterpart in the paper; cannot fail.  The string is
+ * owned by the library and valid until the thread's next call. */
 const char* rttda_last_error(void);
 
 /* Create a handle for one molecule and upload its factors.
@@ -157,14 +160,16 @@ rttda_status rttda_create(int nocc, int nvirt, int naux,
 /* As rttda_create, but every array argument is device memory of the current
  * device (FP64, same layouts), e.g. factors produced on the GPU; they are
  * read during the call and may be freed when it returns.  Needed for
- * molecules whose FP64 factors do not fit in host memory. */
+ * molecules whose FP64 factors do not fit in host memory.
+ * Errors: as rttda_create. */
 rttda_status rttda_create_device(int nocc, int nvirt, int naux,
                                  const double* eps_occ, const double* eps_virt,
                                  const double* B_ov, const double* B_oo, const double* B_vv,
                                  const double* mu_oo, const double* mu_vv, const double* mu_0ov,
                                  double c_x, int prec, rttda_t* out);
 
-/* Device memory the handle holds right now, in bytes. */
+/* Device memory the handle holds right now, in bytes (library utility, no
+ * counterpart in the paper).  Errors: RTTDA_E_ARG (NULL argument). */
 rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes);
 
 /* Set the batch: one pulse per trajectory (Eq. e_field, Eqs. e_fields).
@@ -206,26 +211,37 @@ rttda_status rttda_propagate_device(rttda_t h, const double* c0_dev, double dt, 
 
 /* Wait for the work enqueued on `stream` (NULL = the handle's stream) and
  * report device-side failures: RTTDA_E_TIMEOUT if a bounded wait inside a
- * tensor-core kernel ran out (the results of that call are invalid). */
+ * tensor-core kernel ran out (the results of that call are invalid).
+ * Library utility, no counterpart in the paper.
+ * Errors: RTTDA_E_ARG (NULL handle), RTTDA_E_CUDA, RTTDA_E_TIMEOUT. */
 rttda_status rttda_sync(rttda_t h, void* stream);
 
-/* Continue from the handle's current state and time (no kick).  Buffers as
+/* Continue from the handle's current state and time (no kick): the same
+ * integration of Eq. ode_rt_tda as rttda_propagate, from t_now.  Buffers as
  * in rttda_propagate; entry 0 of each trace is the current state.
- * Errors: RTTDA_E_STATE if there is no state (nothing propagated or set). */
+ * Errors: those of rttda_propagate, and RTTDA_E_STATE if there is no state
+ * (nothing propagated or set). */
 rttda_status rttda_resume(rttda_t h, double dt, long nsteps,
                           double* c_out, double* dipole_trace, double* norm_trace);
 
-/* Checkpoint: copy the current state [ntraj][n][2] and time to the host. */
+/* Checkpoint: copy the current state [ntraj][n][2] and time to the host
+ * (c host, written; t may be NULL).  Library feature, no counterpart in the
+ * paper.  Errors: RTTDA_E_ARG (NULL h or c), RTTDA_E_STATE (no state),
+ * RTTDA_E_CUDA. */
 rttda_status rttda_get_state(rttda_t h, double* c, double* t);
 
-/* Restore: set the current state [ntraj][n][2] (host) and time t. */
+/* Restore: set the current state [ntraj][n][2] (host, copied) and time t.
+ * Library feature, no counterpart in the paper.  Errors: RTTDA_E_ARG (NULL,
+ * t not finite), RTTDA_E_STATE (no rttda_set_field yet), RTTDA_E_CUDA. */
 rttda_status rttda_set_state(rttda_t h, const double* c, double t);
 
 /* One evaluation of sigma = H(t) c for the whole batch (Eq. e_field with
  * Eq. sigmas; the field term uses each trajectory's pulse at time t; a kick
  * contributes nothing for t > 0).  c_dev and sigma_dev are device
  * [ntraj][n][2]; enqueued on `stream` (NULL = handle stream).  The handle's
- * propagation state is not touched. */
+ * propagation state is not touched.
+ * Errors: RTTDA_E_ARG (NULL, t not finite), RTTDA_E_STATE (no
+ * rttda_set_field yet), RTTDA_E_CUDA. */
 rttda_status rttda_sigma(rttda_t h, const double* c_dev, double t, double* sigma_dev, void* stream);
 
 /* Absorption spectrum from dipole traces (dipole-trace analogue of
@@ -236,7 +252,10 @@ rttda_status rttda_sigma(rttda_t h, const double* c_dev, double t, double* sigma
  *   trace     host [ntraces][npts]; npts >= 2; kappa != 0; gamma >= 0.
  *   omega_out host [nfreq] (may be NULL): w_j = wmin + j (wmax-wmin)/(nfreq-1).
  *   S_out     host [nfreq].
- * Computed on the GPU (FP64).  No handle needed. */
+ * Computed on the GPU (FP64).  No handle needed.
+ * Errors: RTTDA_E_ARG (NULL trace or S_out, ntraces < 1, npts < 2, nfreq < 1
+ * or > 2^30, dt <= 0, kappa 0 or not finite, gamma < 0), RTTDA_E_OOM,
+ * RTTDA_E_CUDA. */
 rttda_status rttda_spectrum(const double* trace, long ntraces, long npts, double dt,
                             double kappa, double gamma, double wmin, double wmax,
                             long nfreq, double* omega_out, double* S_out);
@@ -259,12 +278,15 @@ enum {
  * graph) with a CUDA event pair around every kernel-class launch; the
  * counters restart.  rttda_profile_read waits for the recorded events, writes
  * the summed milliseconds ms[RTTDA_NUM_KERNEL_CLASSES] and the number of
- * timed launches per class launches[...] (either may be NULL) and resets. */
+ * timed launches per class launches[...] (either may be NULL) and resets.
+ * The per-class analogue of the paper's per-task wall-clock totals (Table
+ * timings).  Errors: RTTDA_E_ARG (NULL handle), RTTDA_E_CUDA. */
 rttda_status rttda_profile(rttda_t h, int enable);
 rttda_status rttda_profile_read(rttda_t h, double* ms, long long* launches);
 
 /* Kernels this handle has enqueued so far (*total) and in one RK4 step of
- * the last propagation (*per_step).  Either pointer may be NULL. */
+ * the last propagation (*per_step).  Either pointer may be NULL.  Library
+ * utility, no counterpart in the paper.  Errors: RTTDA_E_ARG (NULL handle). */
 rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step);
 
 /* Lowest excited states of the TI-TDA problem A X_i = w_i X_i (Sec. 2.1,
@@ -291,7 +313,7 @@ rttda_status rttda_eigenstates(rttda_t h, int k, double tol, int max_iter, doubl
  * Errors: RTTDA_E_ARG (k < 0, k > 4096, NULL X), RTTDA_E_OOM. */
 rttda_status rttda_set_projectors(rttda_t h, int k, const double* X);
 
-/* Overlaps of the last rttda_propagate / rttda_resume call:
+/* Overlaps (Eq. populations) of the last rttda_propagate / rttda_resume call:
  * out[ntraj][npts][k][2] (host or device; re, im), npts = nsteps + 1 of
  * that call.  Synchronises the handle.
  * Errors: RTTDA_E_ARG (NULL, npts mismatch), RTTDA_E_STATE (no projectors,
@@ -302,10 +324,11 @@ rttda_status rttda_get_overlaps(rttda_t h, double* out, long npts);
  * R_t(t_n) = X_t^dagger(eps) X_t(eps + t_n), with eps right after the kick
  * (the state a fresh propagation starts from, kick applied).  enable != 0:
  * every fresh propagation stores its X(eps) and every propagation or resume
- * records R for its steps n = 0..nsteps; 0 turns it off. */
+ * records R for its steps n = 0..nsteps; 0 turns it off.
+ * Errors: RTTDA_E_ARG (NULL handle). */
 rttda_status rttda_set_autocorrelation(rttda_t h, int enable);
 
-/* R of the last call: out[ntraj][npts][2] (host or device; re, im),
+/* R (Eq. time_correlation_function) of the last call: out[ntraj][npts][2] (host or device; re, im),
  * npts = nsteps + 1 of that call.  Synchronises the handle.
  * Errors: RTTDA_E_ARG (NULL, npts mismatch), RTTDA_E_STATE (off, or no
  * fresh propagation since it was enabled). */
@@ -344,7 +367,7 @@ typedef enum { RTTDA_INT_RK4 = 0, RTTDA_INT_SSO = 1 } rttda_integrator;
 rttda_status rttda_set_integrator(rttda_t h, int integrator);
 
 /* Execution plan of the sigma build chosen for the current batch (after
- * rttda_set_field).  The exchange main contraction sum_{P,b} Z^P_ib B^P_ab
+ * rttda_set_field; library introspection, no counterpart in the paper).  The exchange main contraction sum_{P,b} Z^P_ib B^P_ab
  * (Sec. 2.2, exchange part of the A matrix elements) runs on
  *   main_kernel 0: SIMT (FP64 / FP32),
  *               1: tcgen05, 128-row tiles (BF16X3),
@@ -397,7 +420,11 @@ rttda_status rttda_plan(rttda_t h, rttda_plan_info* out);
  * call outside any stream capture.  All calls share the one array and each
  * call overwrites the part it reads before reading it; calls whose work may
  * overlap on the GPU (different streams, or several host threads) race on
- * it and must be serialised by the caller.  Returns after enqueueing. */
+ * it and must be serialised by the caller.  Returns after enqueueing.
+ * The operation is the Coulomb part of Eq. A_matrix_element2 in the
+ * factorised form above.  Errors: RTTDA_E_ARG (a size < 1, NULL pointer,
+ * naux*2*ntraj > 2^20, ntraj > 65535, device index above the library's
+ * limit), RTTDA_E_CUDA. */
 rttda_status rttda_coulomb_noalloc(int nocc, int nvirt, int naux, const double* B_ov_dev, const double* c_dev,
                                    int ntraj, double* sigma_dev, void* stream);
 
@@ -406,10 +433,14 @@ rttda_status rttda_coulomb_noalloc(int nocc, int nvirt, int naux, const double* 
  * flag that nothing sets; the kernel then records the expiry and returns, as
  * the tensor-core kernels do when one of their pipeline waits runs out.
  * Returns RTTDA_E_TIMEOUT when the wait ran out (the expected outcome); the
- * CUDA context stays usable.  The paper has no counterpart. */
+ * CUDA context stays usable.  The paper has no counterpart.
+ * Errors: RTTDA_E_ARG (limit_s outside [1e-3, 2]), RTTDA_E_CUDA; and
+ * RTTDA_E_TIMEOUT as above. */
 rttda_status rttda_selftest_wait(double limit_s);
 
-/* Free every resource of the handle (NULL is ignored). */
+/* Free every resource of the handle (NULL is ignored); waits for the
+ * handle's own stream first.  Work the caller enqueued on other streams
+ * must be finished before.  Cannot fail. */
 void rttda_destroy(rttda_t h);
 
 #ifdef __cplusplus

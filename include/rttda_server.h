@@ -70,32 +70,41 @@ typedef struct {
  * Errors: RTTDA_E_ARG, RTTDA_E_CUDA (no usable device). */
 rttda_status rttda_server_create(size_t hbm_budget, int max_active, long chunk_steps, rttda_server_t* out);
 
-/* Queue a request; *id receives its identifier.  RTTDA_E_ARG for invalid
- * fields (sizes, NULL arrays, pulse as in rttda_set_field, nsteps, nfreq). */
+/* Queue a request; *id receives its identifier.
+ * Errors: RTTDA_E_ARG (NULL argument; invalid fields: sizes, NULL arrays,
+ * pulse kind, dt, nsteps, nfreq, the spectrum window, E0 = 0). */
 rttda_status rttda_server_submit(rttda_server_t s, const rttda_request* req, long* id);
 
 /* Non-blocking status.  *state gets an rttda_request_state.  When the
  * request is DONE and the pointers are not NULL: spectrum[nfreq],
  * omega[nfreq], dipole[nsteps+1] receive its results and *latency_s its
- * time to spectrum.  A FAILED request's reason is in rttda_last_error(). */
+ * time to spectrum.  A FAILED request's reason is in rttda_last_error().
+ * Errors: RTTDA_E_ARG (NULL s or state, unknown id). */
 rttda_status rttda_server_poll(rttda_server_t s, long id, int* state, double* spectrum, double* omega,
                                double* dipole, double* latency_s);
 
 /* Block until the request leaves PENDING/ACTIVE or timeout_s elapses
- * (RTTDA_E_TIMEOUT; the request keeps running). */
+ * (RTTDA_E_TIMEOUT; the request keeps running).
+ * Errors: RTTDA_E_ARG (NULL s, timeout_s < 0, unknown id), RTTDA_E_TIMEOUT. */
 rttda_status rttda_server_wait(rttda_server_t s, long id, double timeout_s);
 
 /* Cancel a pending or active request (an active one stops after its chunk
- * in flight and releases its memory). */
+ * in flight and releases its memory).
+ * Errors: RTTDA_E_ARG (NULL s, unknown id). */
 rttda_status rttda_server_cancel(rttda_server_t s, long id);
 
+/* Counters and latency percentiles of the requests so far (the serving
+ * metrics: p50/p99 time to spectrum, trajectory-steps).
+ * Errors: RTTDA_E_ARG (NULL argument). */
 rttda_status rttda_server_stats_get(rttda_server_t s, rttda_server_stats* st);
 
 /* Device bytes a handle with this shape and precision needs for ntraj
- * trajectories and nsteps-long host traces (upper estimate). */
+ * trajectories and nsteps-long host traces (upper estimate; host arithmetic,
+ * no GPU work).  Errors: RTTDA_E_ARG (NULL bytes, a size < 1, nsteps < 0). */
 rttda_status rttda_estimate_bytes(int nocc, int nvirt, int naux, int ntraj, int prec, long nsteps, size_t* bytes);
 
-/* Stop the scheduler (active requests are cancelled) and free everything. */
+/* Stop the scheduler (active requests are cancelled) and free everything
+ * (NULL is ignored).  Cannot fail. */
 void rttda_server_destroy(rttda_server_t s);
 
 #ifdef __cplusplus
