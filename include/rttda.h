@@ -6,17 +6,17 @@
  * Approximation" (arXiv 2601.16949).  The library propagates complex
  * amplitudes c in the ground-plus-singles basis {|0>, |ia>} under
  *
- *     i dc/dt = H(t) c,   H(t) = A - E(t) M_d            (Eqs. ode_rt_tda, e_field)
+ *     i dc/dt = H(t) c,   H(t) = A - E(t) M_d            (Eqs. (11), (16))
  *
  * with A_00 = 0, A_0,ia = 0 (Sec. 2.1, last paragraph) and, on the singles
- * block (structure of Eq. A_matrix_element2, two-electron part written in
+ * block (structure of Eq. (3), two-electron part written in
  * three-index factorised form for this library),
  *
  *     A_ia,jb = d_ij d_ab (e_a - e_i) + 2 sum_P B^P_ia B^P_jb
  *                                     - c_x sum_P B^P_ij B^P_ab.
  *
  * M_d is the CSF-basis dipole matrix along the unit polarisation d, built
- * from MO-basis blocks by the Slater-Condon rules (Eqs. sc1-sc6):
+ * from MO-basis blocks by the Slater-Condon rules (Eqs. (19a)-(19f)):
  * M_0,ia = <0|mu_d|ia>, M_ia,ia = mu_aa - mu_ii, M_ia,ib = mu_ab,
  * M_ia,ja = -mu_ji, zero otherwise (the constant <Phi0|mu|Phi0> is dropped).
  *
@@ -95,8 +95,8 @@ typedef enum {
   RTTDA_FP64_OZ = 6
 } rttda_prec;
 
-/* Pulse shapes E(t) (Sec. 2.2, Eqs. delta_pulse, continuous wave,
- * transform_limited, chirped_pulse) plus a sin^2 envelope:
+/* Pulse shapes E(t) (Sec. 2.2, Eqs. (18a), (18b),
+ * (18c), (18d)) plus a sin^2 envelope:
  *   KICK     : E0 delta(t); applied exactly as c(0+) = exp(+i E0 M_d) c(0)
  *              at the start of rttda_propagate, E = 0 afterwards.  Taylor
  *              series accumulated in FP64; its first-order term from FP64
@@ -134,8 +134,8 @@ int rttda_abi_version(void);
 const char* rttda_last_error(void);
 
 /* Create a handle for one molecule and upload its factors.
- * Defines A (Eq. A_matrix_element2, factorised as above) and the dipole
- * blocks of the Slater-Condon rules (Eqs. sc2-sc5).
+ * Defines A (Eq. (3), factorised as above) and the dipole
+ * blocks of the Slater-Condon rules (Eqs. (19b)-(19e)).
  *   nocc, nvirt, naux >= 1.
  *   eps_occ[nocc], eps_virt[nvirt]       orbital energies (Ha).
  *   B_ov[naux][nocc][nvirt]               B^P_ia.
@@ -144,7 +144,7 @@ const char* rttda_last_error(void);
  *   mu_oo[3][nocc][nocc], mu_vv[3][nvirt][nvirt]  MO dipole blocks (x,y,z),
  *                                         symmetric.
  *   mu_0ov[3][nocc][nvirt]                <0|mu_x|ia> (pass sqrt(2) <i|mu|a>
- *                                         for MO-basis input, Eq. sc2).
+ *                                         for MO-basis input, Eq. (19b)).
  *   c_x                                   exchange scaling.
  *   prec                                  rttda_prec.
  * All arrays are host FP64 and are copied (and cast to the working
@@ -172,7 +172,7 @@ rttda_status rttda_create_device(int nocc, int nvirt, int naux,
  * counterpart in the paper).  Errors: RTTDA_E_ARG (NULL argument). */
 rttda_status rttda_memory_bytes(rttda_t h, size_t* bytes);
 
-/* Set the batch: one pulse per trajectory (Eq. e_field, Eqs. e_fields).
+/* Set the batch: one pulse per trajectory (Eq. (16), Eqs. (18)).
  * ntraj >= 1; pulses[ntraj] (host).  Builds mu_d = sum_x d_x mu_x per
  * trajectory on the device.  Discards any propagated state.
  * Errors: RTTDA_E_ARG (ntraj < 1, (1 + nocc*nvirt) * 2 * ntraj >= 2^31,
@@ -217,7 +217,7 @@ rttda_status rttda_propagate_device(rttda_t h, const double* c0_dev, double dt, 
 rttda_status rttda_sync(rttda_t h, void* stream);
 
 /* Continue from the handle's current state and time (no kick): the same
- * integration of Eq. ode_rt_tda as rttda_propagate, from t_now.  Buffers as
+ * integration of Eq. (11) as rttda_propagate, from t_now.  Buffers as
  * in rttda_propagate; entry 0 of each trace is the current state.
  * Errors: those of rttda_propagate, and RTTDA_E_STATE if there is no state
  * (nothing propagated or set). */
@@ -235,8 +235,8 @@ rttda_status rttda_get_state(rttda_t h, double* c, double* t);
  * t not finite), RTTDA_E_STATE (no rttda_set_field yet), RTTDA_E_CUDA. */
 rttda_status rttda_set_state(rttda_t h, const double* c, double t);
 
-/* One evaluation of sigma = H(t) c for the whole batch (Eq. e_field with
- * Eq. sigmas; the field term uses each trajectory's pulse at time t; a kick
+/* One evaluation of sigma = H(t) c for the whole batch (Eq. (16) with
+ * Eq. (17); the field term uses each trajectory's pulse at time t; a kick
  * contributes nothing for t > 0).  c_dev and sigma_dev are device
  * [ntraj][n][2]; enqueued on `stream` (NULL = handle stream).  The handle's
  * propagation state is not touched.
@@ -245,7 +245,7 @@ rttda_status rttda_set_state(rttda_t h, const double* c, double t);
 rttda_status rttda_sigma(rttda_t h, const double* c_dev, double t, double* sigma_dev, void* stream);
 
 /* Absorption spectrum from dipole traces (dipole-trace analogue of
- * Eq. fourier_transform, averaged over traces as in Eq. spectrum_average):
+ * Eq. (21), averaged over traces as in Eq. (23)):
  *   S(w) = (1/ntraces) sum_tr (w/kappa) sum_k w_k (mu_k - mu_0)
  *          exp(-gamma t_k) sin(w t_k) dt,
  * trapezoid weights w_k (1/2 at both ends), t_k = k dt.
@@ -264,7 +264,7 @@ rttda_status rttda_spectrum(const double* trace, long ntraces, long npts, double
  * group of the class).  EXCHANGE_MAIN is the long-K contraction
  * sum_{P,b} Z^P_ib B^P_ab; EXCHANGE_Z builds Z^P = B^P_oo c. */
 enum {
-  RTTDA_KC_FIELD = 0,          /* M_d c (Slater-Condon rules, Eqs. sc2-sc5)   */
+  RTTDA_KC_FIELD = 0,          /* M_d c (Slater-Condon rules, Eqs. (19b)-(19e))   */
   RTTDA_KC_COULOMB = 1,        /* both Coulomb passes                         */
   RTTDA_KC_EXCHANGE_Z = 2,     /* Z^P = B^P_oo c                              */
   RTTDA_KC_EXCHANGE_MAIN = 3,  /* sum_{P,b} Z^P_ib B^P_ab                     */
@@ -290,8 +290,8 @@ rttda_status rttda_profile_read(rttda_t h, double* ms, long long* launches);
 rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step);
 
 /* Lowest excited states of the TI-TDA problem A X_i = w_i X_i (Sec. 2.1,
- * Eq. casida_tda; A without the field, in the handle's precision), for the
- * population projections of Eq. populations.  Davidson iteration on the
+ * Eq. (2); A without the field, in the handle's precision), for the
+ * population projections of Eq. (22).  Davidson iteration on the
  * library's sigma build (up to 2*ntraj vectors per build, so a batch must be
  * set with rttda_set_field first), diagonal preconditioner e_a - e_i, stop
  * when every residual norm |A X_i - w_i X_i| < tol.
@@ -305,7 +305,7 @@ rttda_status rttda_launch_stats(rttda_t h, long long* total, long long* per_step
  * RTTDA_E_CUDA. */
 rttda_status rttda_eigenstates(rttda_t h, int k, double tol, int max_iter, double* evals, double* evecs, int* iters);
 
-/* Projectors for overlap and population recording (Eq. populations,
+/* Projectors for overlap and population recording (Eq. (22),
  * P_i(t) = |X_i^T c(t)|^2 with real state vectors X_i).  X: host or device
  * [k][1 + nocc*nvirt] FP64, copied.  Later propagations record, for every
  * trajectory t, step n = 0..nsteps and projector i, the complex overlap
@@ -313,14 +313,14 @@ rttda_status rttda_eigenstates(rttda_t h, int k, double tol, int max_iter, doubl
  * Errors: RTTDA_E_ARG (k < 0, k > 4096, NULL X), RTTDA_E_OOM. */
 rttda_status rttda_set_projectors(rttda_t h, int k, const double* X);
 
-/* Overlaps (Eq. populations) of the last rttda_propagate / rttda_resume call:
+/* Overlaps (Eq. (22)) of the last rttda_propagate / rttda_resume call:
  * out[ntraj][npts][k][2] (host or device; re, im), npts = nsteps + 1 of
  * that call.  Synchronises the handle.
  * Errors: RTTDA_E_ARG (NULL, npts mismatch), RTTDA_E_STATE (no projectors,
  * or no propagation since they were set). */
 rttda_status rttda_get_overlaps(rttda_t h, double* out, long npts);
 
-/* Autocorrelation recording (Eq. time_correlation_function):
+/* Autocorrelation recording (Eq. (20)):
  * R_t(t_n) = X_t^dagger(eps) X_t(eps + t_n), with eps right after the kick
  * (the state a fresh propagation starts from, kick applied).  enable != 0:
  * every fresh propagation stores its X(eps) and every propagation or resume
@@ -328,14 +328,14 @@ rttda_status rttda_get_overlaps(rttda_t h, double* out, long npts);
  * Errors: RTTDA_E_ARG (NULL handle). */
 rttda_status rttda_set_autocorrelation(rttda_t h, int enable);
 
-/* R (Eq. time_correlation_function) of the last call: out[ntraj][npts][2] (host or device; re, im),
+/* R (Eq. (20)) of the last call: out[ntraj][npts][2] (host or device; re, im),
  * npts = nsteps + 1 of that call.  Synchronises the handle.
  * Errors: RTTDA_E_ARG (NULL, npts mismatch), RTTDA_E_STATE (off, or no
  * fresh propagation since it was enabled). */
 rttda_status rttda_get_autocorrelation(rttda_t h, double* out, long npts);
 
 /* The paper's spectrum from autocorrelation records (Sec. 3.1 with Eqs.
- * time_correlation_function, fourier_transform, spectrum_average): each
+ * (20), (21), (23)): each
  * record R(t_j), t_j = j dt, j < npts, is mirrored (R(-t) = conj R(t), 2
  * npts - 1 points), multiplied by a Hann window peaked at t = 0, padded with
  * npad zeros, and transformed, F(w) = sum_m win_m R(t_m) e^{+i w t_m} dt; the
@@ -355,7 +355,7 @@ rttda_status rttda_spectrum_autocorr(const double* R, long ntraces, long npts, d
  *                  builds per step);
  *   RTTDA_INT_SSO  second-order symplectic split operator on
  *                  dq/dt = H p, dp/dt = -H q with c = q + i p (Sec. 2.2,
- *                  Eq. x_real_imagiary; convergence Sec. 3.4):
+ *                  Eq. (12); convergence Sec. 3.4):
  *                    p_{n+1/2} = p_n - dt/2 H(t_n) q_n,
  *                    q_{n+1} = q_n + dt H(t_n + dt/2) p_{n+1/2},
  *                    p_{n+1} = p_{n+1/2} - dt/2 H(t_n + dt) q_{n+1};
@@ -421,8 +421,7 @@ rttda_status rttda_plan(rttda_t h, rttda_plan_info* out);
  * call overwrites the part it reads before reading it; calls whose work may
  * overlap on the GPU (different streams, or several host threads) race on
  * it and must be serialised by the caller.  Returns after enqueueing.
- * The operation is the Coulomb part of Eq. A_matrix_element2 in the
- * factorised form above.  Errors: RTTDA_E_ARG (a size < 1, NULL pointer,
+ * The paper has no counterpart for this entry point.  Errors: RTTDA_E_ARG (a size < 1, NULL pointer,
  * naux*2*ntraj > 2^20, ntraj > 65535, device index above the library's
  * limit), RTTDA_E_CUDA. */
 rttda_status rttda_coulomb_noalloc(int nocc, int nvirt, int naux, const double* B_ov_dev, const double* c_dev,

@@ -3,7 +3,7 @@
  *
  * Serving pattern for the RT-TDA hot path (real-time TDA propagation,
  * arXiv 2601.16949, Sec. 2.2 "Propagation Algorithm", followed by the
- * spectrum of Eq. fourier_transform on the dipole trace): many independent
+ * spectrum of Eq. (21) on the dipole trace): many independent
  * propagation requests, each with its own molecule (nocc, nvirt, naux), pulse
  * and length, arrive over time.  A scheduler thread admits a request when
  * its device-memory footprint fits the budget and an active slot is free,

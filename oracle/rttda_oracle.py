@@ -9,24 +9,24 @@ What it computes (Knoll & Levine, "Simulating Electron Dynamics with
 GPU-Accelerated Real-Time Tamm-Dancoff Approximation", arXiv 2601.16949):
 
 * Basis {|0>, |ia>}; the singles index is 1 + i*nvirt + a ("virtuals run
-  fastest", Sec. 2.1 after Eq. A_matrix_element2).  |0> is the Kohn-Sham
+  fastest", Sec. 2.1 after Eq. (3)).  |0> is the Kohn-Sham
   ground state added to the basis (Sec. 2.1, last paragraph).
 * A is built explicitly as a dense real symmetric matrix:
       A_00 = 0, A_0,ia = 0                                (Sec. 2.1, Brillouin)
       A_ia,jb = d_ij d_ab (e_a - e_i) + 2 (ia|jb) - c_x (ij|ab)
   with (pq|rs) = sum_P B^P_pq B^P_rs.  The structure follows
-  Eq. A_matrix_element2; the RI-factorised Coulomb/exchange pair in place of
+  Eq. (3); the RI-factorised Coulomb/exchange pair in place of
   (ia|jb) + (ia|f_xc|jb) is this project's synthetic workload.
 * The dipole matrix in the CSF basis follows the Slater-Condon rules
-  (Eqs. sc1-sc6), with the constant <Phi0|mu|Phi0> dropped from the diagonal
+  (Eqs. (19a)-(19f)), with the constant <Phi0|mu|Phi0> dropped from the diagonal
   (it is a multiple of the identity):
-      M_00 = 0, M_0,ia = <0|mu|ia> (input; sqrt(2) mu_ia for MO input, sc2)
-      M_ia,ia = mu_aa - mu_ii (sc3), M_ia,ib = mu_ab (sc4),
-      M_ia,ja = -mu_ji (sc5), every other element 0 (sc6).
-* H(t) = A - E(t) M_d with M_d = sum_x d_x M_x (Eq. e_field) and
-  i dc/dt = H(t) c (Eq. ode_rt_tda).
-* Pulses: Eqs. delta_pulse, continuous wave, transform_limited,
-  chirped_pulse (sigma = FWHM / 2.35482), plus a sin^2 envelope
+      M_00 = 0, M_0,ia = <0|mu|ia> (input; sqrt(2) mu_ia for MO input, Eq. (19b))
+      M_ia,ia = mu_aa - mu_ii (Eq. (19c)), M_ia,ib = mu_ab (Eq. (19d)),
+      M_ia,ja = -mu_ji (Eq. (19e)), every other element 0 (Eq. (19f)).
+* H(t) = A - E(t) M_d with M_d = sum_x d_x M_x (Eq. (16)) and
+  i dc/dt = H(t) c (Eq. (11)).
+* Pulses: Eqs. (18a), (18b), (18c),
+  (18d) (sigma = FWHM / 2.35482), plus a sin^2 envelope
   E0 sin^2(pi t / tau) sin(omega t) on [0, tau].
 * The delta kick E0 delta(t) is applied exactly, c(0+) = exp(+i kappa M_d) c(0),
   by a Taylor series; E(t) = 0 afterwards.
@@ -36,13 +36,13 @@ GPU-Accelerated Real-Time Tamm-Dancoff Approximation", arXiv 2601.16949):
   Sec. 3.4) on dq/dt = H p, dp/dt = -H q (sso_step).
 * Observables after every step: mu_d(t_n) = Re c^dagger M_d c and |c|^2;
   populations P_i(t) = |X_i^T c(t)|^2 of the TI-TDA states X_i (eigenvectors
-  of A's singles block, Eq. populations).
+  of A's singles block, Eq. (22)).
 * Spectrum: S(w) = (w / kappa) Im sum_n w_n (mu_n - mu_0) exp((i w - g) t_n) dt
-  with trapezoid weights, the dipole-trace analogue of Eq. fourier_transform;
-  several polarisations are averaged as in Eq. spectrum_average.  The
+  with trapezoid weights, the dipole-trace analogue of Eq. (21);
+  several polarisations are averaged as in Eq. (23).  The
   paper's own mode (spectrum_autocorr): autocorrelation R(t) (Eq.
-  time_correlation_function), mirrored, Hann window, zero padding, FFT,
-  w Re F[R] (Eq. fourier_transform), averaged and normalised to the highest
+  (20)), mirrored, Hann window, zero padding, FFT,
+  w Re F[R] (Eq. (21)), averaged and normalised to the highest
   peak (Sec. 3.1).
 
 Pins: every function here is checked against the paper or against
@@ -57,10 +57,10 @@ from dataclasses import dataclass, field as dc_field
 
 import numpy as np
 
-# Pulse kinds (Eqs. delta_pulse ... chirped_pulse, plus sin^2).
+# Pulse kinds (Eqs. (18a)-(18d), plus sin^2).
 KICK, CW, GAUSS_TL, CHIRP, SIN2 = 0, 1, 2, 3, 4
 
-# sigma = FWHM / 2.35482 (Sec. 2.2, after Eq. chirped_pulse).
+# sigma = FWHM / 2.35482 (Sec. 2.2, after Eq. (18d)).
 FWHM_TO_SIGMA = 2.35482
 
 
@@ -89,12 +89,12 @@ def csf_index(i: int, a: int, nvirt: int) -> int:
 
 
 def dim(nocc: int, nvirt: int) -> int:
-    """N_CSF + 1 (Eq. number_of_csfs plus the ground state)."""
+    """N_CSF + 1 (Eq. (13) plus the ground state)."""
     return 1 + nocc * nvirt
 
 
 # ---------------------------------------------------------------------------
-# A matrix (Eq. A_matrix_element2 with the RI-factorised two-electron part)
+# A matrix (Eq. (3) with the RI-factorised two-electron part)
 # ---------------------------------------------------------------------------
 
 def eri_ovov(B_ov: np.ndarray) -> np.ndarray:
@@ -169,11 +169,11 @@ def A_block(mol: dict, c_x: float, i0: int, i1: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Dipole matrix (Eqs. sc1-sc6)
+# Dipole matrix (Eqs. (19a)-(19f))
 # ---------------------------------------------------------------------------
 
 def dipole_along(mol: dict, direction) -> tuple:
-    """mu_d = sum_x d_x mu_x for the three MO blocks (Eq. e_field: mu . d)."""
+    """mu_d = sum_x d_x mu_x for the three MO blocks (Eq. (16): mu . d)."""
     d = np.asarray(direction, dtype=np.float64)
     mu_oo = np.einsum("x,xij->ij", d, mol["mu_oo"])
     mu_vv = np.einsum("x,xab->ab", d, mol["mu_vv"])
@@ -189,15 +189,15 @@ def build_M(mu_oo: np.ndarray, mu_vv: np.ndarray, m0: np.ndarray) -> np.ndarray:
     for i in range(o):
         for a in range(v):
             k = csf_index(i, a, v)
-            M[0, k] = M[k, 0] = m0[i, a]                          # sc2
-            M[k, k] = mu_vv[a, a] - mu_oo[i, i]                   # sc3 minus sc1
+            M[0, k] = M[k, 0] = m0[i, a]                          # Eq. (19b)
+            M[k, k] = mu_vv[a, a] - mu_oo[i, i]                   # Eq. (19c) minus (19a)
             for b in range(v):
                 if b != a:
-                    M[k, csf_index(i, b, v)] = mu_vv[a, b]        # sc4
+                    M[k, csf_index(i, b, v)] = mu_vv[a, b]        # Eq. (19d)
             for j in range(o):
                 if j != i:
-                    M[k, csf_index(j, a, v)] = -mu_oo[j, i]       # sc5
-    return M                                                       # sc6: rest 0
+                    M[k, csf_index(j, a, v)] = -mu_oo[j, i]       # Eq. (19e)
+    return M                                                       # Eq. (19f): rest 0
 
 
 def M_rows(mu_oo, mu_vv, m0, rows) -> np.ndarray:
@@ -219,7 +219,7 @@ def M_rows(mu_oo, mu_vv, m0, rows) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Pulses (Eqs. delta_pulse, continuous wave, transform_limited, chirped_pulse)
+# Pulses (Eqs. (18a), (18b), (18c), (18d))
 # ---------------------------------------------------------------------------
 
 def field(p: Pulse, t: float) -> float:
@@ -259,7 +259,7 @@ def kick(M: np.ndarray, kappa: float, c: np.ndarray, tol: float = 1e-18) -> np.n
 
 
 def sigma(A: np.ndarray, M: np.ndarray, E: float, c: np.ndarray) -> np.ndarray:
-    """sigma = H(t) c = (A - E(t) M) c (Eq. e_field with Eq. sigmas).
+    """sigma = H(t) c = (A - E(t) M) c (Eq. (16) with Eq. (17)).
 
     A and M are real, so the real and imaginary parts of c are multiplied
     separately (numpy would otherwise copy A to complex for every product)."""
@@ -320,7 +320,7 @@ def propagate(A, M, p: Pulse, c0, dt: float, nsteps: int, keep_every: int = 0) -
 # ---------------------------------------------------------------------------
 # Symplectic split-operator integrator (Sec. 2.2; convergence study Sec. 3.4)
 # ---------------------------------------------------------------------------
-# With c = q + i p (Eq. x_real_imagiary) and a real symmetric H(t), the
+# With c = q + i p (Eq. (12)) and a real symmetric H(t), the
 # equation of motion i dc/dt = H(t) c is the pair dq/dt = H p, dp/dt = -H q
 # (Sec. 2.2).  The second-order symmetric splitting takes half a step of the
 # p-flow, a whole step of the q-flow and again half a step of the p-flow;
@@ -362,11 +362,11 @@ def propagate_sso(A, M, p: Pulse, c0, dt: float, nsteps: int) -> Trajectory:
 
 
 # ---------------------------------------------------------------------------
-# Stationary states and populations (Sec. 2.2, Eq. populations)
+# Stationary states and populations (Sec. 2.2, Eq. (22))
 # ---------------------------------------------------------------------------
 
 def ti_states(A: np.ndarray, k: int) -> tuple:
-    """The k lowest excited TI-TDA states (Sec. 2.1, Eq. casida_tda): the
+    """The k lowest excited TI-TDA states (Sec. 2.1, Eq. (2)): the
     eigenpairs of A's singles block, as full-length vectors with a zero
     ground component.  (The ground row and column of A are zero, so |0> is
     an eigenvector with eigenvalue 0 that is left out.)"""
@@ -382,16 +382,16 @@ def overlaps(X: np.ndarray, c: np.ndarray) -> np.ndarray:
 
 
 def populations(X: np.ndarray, c: np.ndarray) -> np.ndarray:
-    """P_i = |X_i^T c|^2 (Eq. populations)."""
+    """P_i = |X_i^T c|^2 (Eq. (22))."""
     return np.abs(overlaps(X, c)) ** 2
 
 
 # ---------------------------------------------------------------------------
-# Spectrum (Eq. fourier_transform on the dipole trace; Eq. spectrum_average)
+# Spectrum (Eq. (21) on the dipole trace; Eq. (23))
 # ---------------------------------------------------------------------------
 
 def autocorrelation(c_eps: np.ndarray, states) -> np.ndarray:
-    """R(t_n) = X^dagger(eps) X(eps + t_n) (Eq. time_correlation_function) for
+    """R(t_n) = X^dagger(eps) X(eps + t_n) (Eq. (20)) for
     the states of a run started right after the kick (c_eps = its first)."""
     return np.array([np.vdot(c_eps, c) for c in states])
 
@@ -405,8 +405,8 @@ def autocorr_grid(npts: int, dt: float, npad: int, nfreq: int) -> np.ndarray:
 
 def spectrum_autocorr(R, dt: float, npad: int, nfreq: int, normalize: bool = True) -> np.ndarray:
     """Absorption spectrum from autocorrelation functions, the paper's way
-    (Sec. 3.1 with Eqs. time_correlation_function, fourier_transform and
-    spectrum_average): each R(t) (t >= 0) is mirrored to negative times with
+    (Sec. 3.1 with Eqs. (20), (21) and
+    (23)): each R(t) (t >= 0) is mirrored to negative times with
     R(-t) = conj(R(t)), multiplied by a Hann window over the mirrored record
     (peak at t = 0), padded with npad zeros and Fourier transformed,
     F(w) = sum_m w_m R(t_m) exp(+i w t_m) dt; the spectrum is w Re F(w) on the

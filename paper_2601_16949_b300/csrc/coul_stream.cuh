@@ -61,7 +61,6 @@ __device__ __forceinline__ void unpack16(const uint4& u, float (&b)[16 / sizeof(
 // not needed by the Coulomb term).
 __global__ void __launch_bounds__(256) k_prep_xf(long long n, int C, const double* __restrict__ X,
                                                  float* __restrict__ Xf) {
-  pdl_entry();
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     Xf[e] = (float)X[C + e];
 }
@@ -79,7 +78,6 @@ template <typename TF, int C>
 __global__ void __launch_bounds__(kThreads, min_blocks_w<C>())
     k_coul_w_stream(const TF* __restrict__ Bov, const float* __restrict__ Xf, int P, long long ov, int slice,
                     float* __restrict__ wpart) {
-  pdl_entry();
   constexpr int V = 16 / sizeof(TF);
   static_assert(C % 2 == 0 && C <= 12, "C = 2T <= 12");
   extern __shared__ __align__(16) float xs[];  // [slice][C]
@@ -167,7 +165,6 @@ template <typename TF, int C>
 __global__ void __launch_bounds__(kThreads, min_blocks_j<C>())
     k_coul_J_stream(const TF* __restrict__ Bov, const float* __restrict__ wpart, int nw, int P, long long ov,
                     int pchunk, float* __restrict__ Jpart) {
-  pdl_entry();
   constexpr int V = 16 / sizeof(TF);
   constexpr int U = 8;
   static_assert(C % 2 == 0 && C <= 12, "C = 2T <= 12");

@@ -1,6 +1,6 @@
-// Lowest eigenpairs of A (TI-TDA states, Sec. 2.1 Eq. casida_tda) by the
+// Lowest eigenpairs of A (TI-TDA states, Sec. 2.1 Eq. (2)) by the
 // Davidson method on the library's own sigma build, for population
-// projections (Eq. populations).
+// projections (Eq. (22)).
 //
 // A is real symmetric; its ground row and column are zero (A_00 = 0,
 // A_0,ia = 0), so the excited states live in the singles block and every

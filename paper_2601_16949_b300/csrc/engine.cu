@@ -177,14 +177,14 @@ struct rttda_ctx {
   int wide_kb = 32;                  // K tile width of the wide-M kernel (32 or 64 BF16)
   bool wide_tr = false;              // wide kernel with the contraction transposed (rows a)
   int integrator = RTTDA_INT_RK4;    // rttda_integrator
-  // projectors (Eq. populations) and the overlaps of the last propagation
+  // projectors (Eq. (22)) and the overlaps of the last propagation
   int nproj = 0;
   double* d_proj = nullptr;   // [nproj][N]
   double* d_ovl = nullptr;    // [T][ovl_ld][nproj][2]
   double* d_proj_part = nullptr;
   long long ovl_ld = 0, ovl_cap = 0, proj_rows = 1, part_cap = 0;
   int proj_G = 1;
-  // autocorrelation R(t) = X(eps)^dagger X(eps + t) (Eq. time_correlation_function)
+  // autocorrelation R(t) = X(eps)^dagger X(eps + t) (Eq. (20))
   bool acf_on = false;
   double* d_xeps = nullptr;   // [N][2T] state right after the kick of the last fresh propagation
   double* d_acf = nullptr;    // [T][acf_ld][2]
@@ -919,6 +919,21 @@ struct Ops {
     }
   }
 
+  // The field product of the step's start, which also feeds the dipole
+  // expectation: FP64-accurate in every precision.  The modes whose field
+  // products are FP32 take it in double-float arithmetic from the FP64
+  // dipole blocks (ground row in FP64); the FP64 modes take their own.
+  static void field_obs(rttda_ctx* h, const double* X, cudaStream_t s) {
+    if (std::is_same<TC, double>::value) {
+      field(h, X, s);
+      return;
+    }
+    Prof pr(h, RTTDA_KC_FIELD, s);
+    h->launches += 3;
+    launch_field<double, df32>(h, X, h->moo64, h->mvv64, h->m064, s);
+    launch_field0<double, double>(h, X, h->m064, s);
+  }
+
   static void combine(rttda_ctx* h, int mode, int stage, bool use_field, double dt, const double* Xin,
                       double* Xnext, double* sig_out, cudaStream_t s, long long* step_ctr = nullptr) {
     Prof pr(h, RTTDA_KC_COMBINE, s);
@@ -1039,7 +1054,10 @@ void enqueue_step(rttda_ctx* h, O, long long base, double t_off, double dt, doub
     double* xin = (st % 2 == 0) ? h->Xs : h->Xs2;
     double* xnext = (st % 2 == 0) ? h->Xs2 : h->Xs;
     const bool fld = h->any_field;
-    if (st == 0 || fld) O::field(h, xin, s);
+    if (st == 0)
+      O::field_obs(h, xin, s);  // xin holds c_n: also the observables' M_d c_n
+    else if (fld)
+      O::field(h, xin, s);
     if (st == 0 && dip) enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
     if (st == 0) {
       enqueue_project(h, h->Xn, ld, offset, s);
@@ -1064,7 +1082,7 @@ void enqueue_step_sso(rttda_ctx* h, O, long long base, double t_off, double dt, 
   k_efield<<<1, 128, 0, s>>>(h->T, h->d_pulses, h->d_step, base, t_off, dt, h->E);
   const bool fld = h->any_field;
   if (dip) {
-    O::field(h, h->Xn, s);
+    O::field_obs(h, h->Xn, s);
     enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
   }
   enqueue_project(h, h->Xn, ld, offset, s);
@@ -1088,40 +1106,6 @@ void enqueue_sso_prologue(rttda_ctx* h, O, long long base, double t_off, double 
   const bool xt = O::coulomb(h, h->Xs, s, true);
   O::exchange(h, h->Xs, s, xt);
   O::sso_update(h, 0, 0, fld, dt, h->Xs, s);
-}
-
-// With RTTDA_PDL=1, turn every kernel-to-kernel edge of the captured step
-// into a programmatic edge (the successor is launched once every CTA of its
-// predecessor has started; it then waits in pdl_entry for the
-// predecessor's completion).  Off by default: ordinary edges.
-cudaError_t make_edges_programmatic(cudaGraph_t g) {
-  const char* e = std::getenv("RTTDA_PDL");
-  if (!e || std::atoi(e) != 1) return cudaSuccess;
-  size_t n = 0;
-  cudaError_t ce = cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &n);
-  if (ce != cudaSuccess || n == 0) return ce;
-  std::vector<cudaGraphNode_t> from(n), to(n);
-  std::vector<cudaGraphEdgeData> ed(n);
-  ce = cudaGraphGetEdges(g, from.data(), to.data(), ed.data(), &n);
-  if (ce != cudaSuccess) return ce;
-  for (size_t k = 0; k < n; ++k) {
-    cudaGraphNodeType ta, tb;
-    if ((ce = cudaGraphNodeGetType(from[k], &ta)) != cudaSuccess) return ce;
-    if ((ce = cudaGraphNodeGetType(to[k], &tb)) != cudaSuccess) return ce;
-    if (ta != cudaGraphNodeTypeKernel || tb != cudaGraphNodeTypeKernel ||
-        ed[k].type != cudaGraphDependencyTypeDefault || ed[k].from_port != cudaGraphKernelNodePortDefault)
-      continue;
-    cudaGraphEdgeData pe{};
-    pe.from_port = cudaGraphKernelNodePortProgrammatic;
-    pe.type = cudaGraphDependencyTypeProgrammatic;
-    if ((ce = cudaGraphRemoveDependencies(g, &from[k], &to[k], &ed[k], 1)) != cudaSuccess) return ce;
-    if ((ce = cudaGraphAddDependencies(g, &from[k], &to[k], &pe, 1)) != cudaSuccess) {
-      // put the ordinary edge back so the graph stays ordered
-      cudaGraphAddDependencies(g, &from[k], &to[k], &ed[k], 1);
-      return ce;
-    }
-  }
-  return cudaSuccess;
 }
 
 rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, double* dip, double* nrm,
@@ -1160,11 +1144,6 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
     h->launches = l0 + h->launches_per_step * nsteps;
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (ce != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-    ce = make_edges_programmatic(graph);
-    if (ce != cudaSuccess) {
-      cudaGraphDestroy(graph);
-      return set_error(RTTDA_E_CUDA, std::string("graph edges: ") + cudaGetErrorString(ce));
-    }
     // Keep the executable step graph of the handle and give it this call's
     // parameters with cudaGraphExecUpdate (launches in flight keep theirs);
     // a new one is instantiated only when the update is refused (a different
@@ -1204,7 +1183,7 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
     if (ce != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
   }
   if (dip) {
-    dispatch(h->prec, [&](auto ops) { decltype(ops)::field(h, h->Xn, s); });
+    dispatch(h->prec, [&](auto ops) { decltype(ops)::field_obs(h, h->Xn, s); });
     enqueue_observe(h, h->Xn, dip, nrm, ld, offset, s);
   }
   enqueue_project(h, h->Xn, ld, offset, s);

@@ -6,7 +6,6 @@
 // contraction because A and M_d are real symmetric.
 #pragma once
 
-#include "pdl.cuh"
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -14,7 +13,7 @@
 namespace rttda {
 
 // ---------------------------------------------------------------------------
-// Pulses (Sec. 2.2, Eqs. delta_pulse ... chirped_pulse, plus sin^2)
+// Pulses (Sec. 2.2, Eqs. (18a)-(18d), plus sin^2)
 // ---------------------------------------------------------------------------
 struct PulseDev {
   int kind;                       // 0 kick, 1 CW, 2 Gaussian TL, 3 chirp, 4 sin^2
@@ -52,6 +51,51 @@ __device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 x) { re
 template <>
 __device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
 
+// Double-float ("float-float") numbers for the field product of the
+// observables in the FP32 modes: a value is the unevaluated sum hi + lo of
+// two floats (about 48 significant bits).  A multiply-add uses Dekker's exact
+// product (p + e = a.hi b.hi, e from one FMA) and Knuth's two-sum for the
+// addition of p to the running hi part; the remaining error terms are summed
+// into lo.  The accumulator is not renormalised after every addition (lo
+// only collects rounding errors, so its own rounding stays below 2^-24 of
+// them).  Every step uses the _rn intrinsics so that the compiler neither
+// contracts nor reorders the error-free transformations.  On B300 this runs
+// on the FP32 pipe at about five times the rate of FP64 multiply-adds.
+struct df32 {
+  float hi, lo;
+  df32() = default;
+  __device__ __forceinline__ explicit df32(double x) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+  }
+  __device__ __forceinline__ df32(int x) : hi((float)x), lo(0.0f) {}
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ df32 operator-() const {
+    df32 r;
+    r.hi = -hi;
+    r.lo = -lo;
+    return r;
+  }
+};
+
+// the built-in float and double overloads stay visible beside this one
+using ::fma;
+
+// a * b + c in double-float
+__device__ __forceinline__ df32 fma(df32 a, df32 b, df32 c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);          // exact: a.hi b.hi = p + e
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float sh = __fadd_rn(p, c.hi);          // two-sum of p and c.hi
+  const float bb = __fsub_rn(sh, p);
+  const float err = __fadd_rn(__fsub_rn(p, __fsub_rn(sh, bb)), __fsub_rn(c.hi, bb));
+  df32 r;
+  r.hi = sh;
+  r.lo = __fadd_rn(__fadd_rn(err, e), c.lo);
+  return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll
@@ -86,7 +130,6 @@ __device__ __forceinline__ T block_sum(T x, T* scratch) {
 template <typename TF, typename TC, int CG, int PB>
 __global__ void __launch_bounds__(256) k_coul_w(const TF* __restrict__ Bov, const double* __restrict__ X, int P,
                                                 long long ov, int C, TC* __restrict__ wpart) {
-  pdl_entry();
   // grid (ceil(P/PB), nsplit_ia): block (pb, s) reduces rows p0..p0+PB over
   // the s-th slice of ia and writes wpart[s][p][col] (summed in pass 2).
   __shared__ TC red[32];
@@ -133,7 +176,6 @@ __global__ void __launch_bounds__(256) k_coul_w(const TF* __restrict__ Bov, cons
 template <typename TF, typename TC, int CG>
 __global__ void __launch_bounds__(256) k_coul_J(const TF* __restrict__ Bov, const TC* __restrict__ w, int nw,
                                                 int P, long long ov, int C, int pchunk, TC* __restrict__ Jpart) {
-  pdl_entry();
   extern __shared__ unsigned char smem_raw[];
   TC* ws = reinterpret_cast<TC*>(smem_raw);
   const int s = blockIdx.y;
@@ -209,7 +251,6 @@ template <typename TF, typename TC, int CG>
 __global__ void __launch_bounds__(256, 3) k_coul_w_vec(const TF* __restrict__ Bov, const double* __restrict__ X,
                                                        int P, long long ov, int C, int slice,
                                                        TC* __restrict__ wpart) {
-  pdl_entry();
   constexpr int V = Vec16<TF>::V;
   constexpr int RPW = 4;
   extern __shared__ unsigned char smem_raw[];
@@ -288,7 +329,6 @@ template <typename TF, typename TC, int CG>
 __global__ void __launch_bounds__(256) k_coul_J_vec(const TF* __restrict__ Bov, const TC* __restrict__ w, int nw,
                                                     int P, long long ov, int C, int pchunk,
                                                     TC* __restrict__ Jpart) {
-  pdl_entry();
   constexpr int V = Vec16<TF>::V;
   extern __shared__ unsigned char smem_raw[];
   TC* ws = reinterpret_cast<TC*>(smem_raw);
@@ -341,7 +381,6 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     k_gemm_tn(int M, int N, long long K, const TA* __restrict__ A, long long lda, long long strideA,
               const TB* __restrict__ B, long long ldb, long long strideB, TC* __restrict__ D, long long ldd,
               long long strideD, long long splitStrideD, int nsplit, long long kper, int accumulate) {
-  pdl_entry();
   constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
   constexpr int LA = (BK * BM) / NT, LB = (BK * BN) / NT;
   static_assert((BK * BM) % NT == 0 && (BK * BN) % NT == 0, "tile/threads mismatch");
@@ -440,7 +479,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 
 // ---------------------------------------------------------------------------
 // Field product F = M_d X for every trajectory (Slater-Condon rules, Eqs.
-// sc2-sc5), singles rows:
+// (19b)-(19e)), singles rows:
 //   F_ia = m_ia X_0 + sum_b mu_ab X_ib - sum_j mu_ji X_ja
 // Two small GEMMs per trajectory (X mu_vv and mu_oo^T X, real and imaginary
 // parts together) with register tiles: a block computes 32 i x 64 a (both
@@ -453,7 +492,6 @@ template <typename TM_, typename TC>
 __global__ void __launch_bounds__(256) k_field(int o, int v, int T, const double* __restrict__ X,
                                                const TM_* __restrict__ moo, const TM_* __restrict__ mvv,
                                                const TM_* __restrict__ m0, double* __restrict__ F) {
-  pdl_entry();
   constexpr int BI = 32, BA = 64, BK = 16;
   __shared__ TC xi[2][BK][BI + 1];   // X[i0+ii][k0+kk] (re, im): A operand of X mu_vv
   __shared__ TC mv[BK][BA];          // mu_vv[k0+kk][a0+aa]
@@ -567,7 +605,6 @@ template <typename TM_, typename TC>
 __global__ void __launch_bounds__(256) k_field_small(int o, int v, int T, const double* __restrict__ X,
                                                const TM_* __restrict__ moo, const TM_* __restrict__ mvv,
                                                const TM_* __restrict__ m0, double* __restrict__ F) {
-  pdl_entry();
   // phase b: [buf] sx[8][32][2] (X[i0+ii][b0+bb]) + sm[32][33] (mu_vv[b0+bb][a0+aa])
   // phase j: [buf] so[32][9] (mu_oo[j0+jj][i0+ii]) + sy[32][32][2] (X[j0+jj][a0+aa])
   constexpr int kSX = 8 * 32 * 2, kSM = 32 * 33, kSO = 32 * 9, kSY = 32 * 32 * 2;
@@ -684,13 +721,12 @@ __global__ void __launch_bounds__(256) k_field_small(int o, int v, int T, const 
 }
 
 // Ground row of the field product: F_0 = sum_ia m_ia X_ia (Hermitian
-// partner of sc2).  Two passes with a fixed order: block (g, t) sums the
+// partner of Eq. (19b)).  Two passes with a fixed order: block (g, t) sums the
 // rows of chunk g (part[(t G + g) 2 + re/im], accumulated in TC), then one
 // block adds the G chunk sums of every trajectory in order.
 template <typename TM_, typename TC>
 __global__ void __launch_bounds__(256) k_field0(long long ov, int T, long long rows, const double* __restrict__ X,
                                                 const TM_* __restrict__ m0, double* __restrict__ part) {
-  pdl_entry();
   __shared__ TC red[32];
   const int C = 2 * T, g = blockIdx.x, t = blockIdx.y, G = gridDim.x;
   const TM_* Mz = m0 + (size_t)t * ov;
@@ -710,7 +746,6 @@ __global__ void __launch_bounds__(256) k_field0(long long ov, int T, long long r
 }
 
 __global__ void k_field0_final(int G, int T, const double* __restrict__ part, double* __restrict__ F) {
-  pdl_entry();
   for (int e = threadIdx.x; e < 2 * T; e += blockDim.x) {
     const int t = e >> 1, r = e & 1;
     double sum = 0.0;
@@ -727,7 +762,6 @@ __global__ void k_field0_final(int G, int T, const double* __restrict__ part, do
 // ---------------------------------------------------------------------------
 __global__ void k_efield(int T, const PulseDev* __restrict__ pulses, const long long* __restrict__ step,
                          long long base, double t_off, double dt, double* __restrict__ E) {
-  pdl_entry();
   const double cs[4] = {0.0, 0.5, 0.5, 1.0};
   const long long n = base + *step;
   for (int e = threadIdx.x; e < 4 * T; e += blockDim.x) {
@@ -779,7 +813,6 @@ __global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long 
                                                  const double* __restrict__ Xs, double* __restrict__ Xs_next,
                                                  double* __restrict__ acc, double* __restrict__ sig_out,
                                                  long long* __restrict__ step_ctr) {
-  pdl_entry();
   // step_ctr (the last stage of a step): advance the step counter; nothing in
   // this kernel reads it and everything of the step before it already has.
   if (step_ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
@@ -859,7 +892,6 @@ __global__ void __launch_bounds__(256) k_sso_update(int mode, int stage, long lo
                                                     const double* __restrict__ F, const double* __restrict__ E,
                                                     int use_field, double dt, double* __restrict__ Xn,
                                                     double* __restrict__ X, long long* __restrict__ step_ctr) {
-  pdl_entry();
   // step_ctr: as in k_combine, for the last sub-step of a step
   if (step_ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -899,7 +931,6 @@ __global__ void __launch_bounds__(256) k_obs_partial(long long N, int T, long lo
                                                      const double* __restrict__ X,
                                                      const double* __restrict__ F,
                                                      double* __restrict__ part) {
-  pdl_entry();
   __shared__ double red[32];
   const int C = 2 * T;
   const long long r0 = (long long)blockIdx.x * rows_per_block;
@@ -926,7 +957,6 @@ __global__ void __launch_bounds__(256) k_obs_partial(long long N, int T, long lo
 __global__ void k_obs_final(int G, int T, const double* __restrict__ part, const long long* __restrict__ step,
                             long long step_offset, long long ld, double* __restrict__ dip,
                             double* __restrict__ nrm) {
-  pdl_entry();
   const long long k = *step + step_offset;
   for (int t = threadIdx.x; t < T; t += blockDim.x) {
     double mu = 0.0, nr = 0.0;
@@ -940,7 +970,7 @@ __global__ void k_obs_final(int G, int T, const double* __restrict__ part, const
 }
 
 // ---------------------------------------------------------------------------
-// Overlaps with K real projectors (Eq. populations: P_i(t) = |X_i^T c(t)|^2):
+// Overlaps with K real projectors (Eq. (22): P_i(t) = |X_i^T c(t)|^2):
 // o[t][i] = sum_n Pj_i[n] c_t[n], complex (column 2t real part, 2t+1
 // imaginary part).  Pass 1: block (g, i) sums the rows of chunk g for up to
 // eight columns at a time, warp shuffles then a fixed-order sum over warps
@@ -950,7 +980,6 @@ __global__ void k_obs_final(int G, int T, const double* __restrict__ part, const
 __global__ void __launch_bounds__(256) k_proj_partial(long long N, int C, int K, long long rows,
                                                       const double* __restrict__ Pj, const double* __restrict__ X,
                                                       double* __restrict__ part) {
-  pdl_entry();
   __shared__ double ws[8][8];
   const int g = blockIdx.x, i = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -984,7 +1013,6 @@ __global__ void __launch_bounds__(256) k_proj_partial(long long N, int C, int K,
 
 __global__ void k_proj_final(int G, int C, int K, const double* __restrict__ part, const long long* __restrict__ step,
                              long long step_offset, long long ld, double* __restrict__ ovl) {
-  pdl_entry();
   const long long k = *step + step_offset;
   for (int e = threadIdx.x; e < K * C; e += blockDim.x) {
     const int i = e / C, col = e % C;
@@ -1000,7 +1028,6 @@ __global__ void k_proj_final(int G, int C, int K, const double* __restrict__ par
 // ---------------------------------------------------------------------------
 __global__ void k_kick_term(long long N, int T, const double* __restrict__ kappa, double inv_k,
                             const double* __restrict__ F, double* __restrict__ term, double* __restrict__ out) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * T) return;
   const long long n = e / T;
@@ -1020,7 +1047,6 @@ __global__ void k_kick_term(long long N, int T, const double* __restrict__ kappa
 // Layout changes between the ABI ([t][n][2]) and the device ([n][t][2]).
 // ---------------------------------------------------------------------------
 __global__ void k_abi_to_dev(long long N, int T, const double* __restrict__ in, double* __restrict__ X) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * T) return;
   const long long n = e / T;
@@ -1030,7 +1056,6 @@ __global__ void k_abi_to_dev(long long N, int T, const double* __restrict__ in, 
 }
 
 __global__ void k_dev_to_abi(long long N, int T, const double* __restrict__ X, double* __restrict__ out) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * T) return;
   const int t = (int)(e / N);
@@ -1041,7 +1066,6 @@ __global__ void k_dev_to_abi(long long N, int T, const double* __restrict__ X, d
 
 // |0> for every trajectory.
 __global__ void k_ground(long long N, int T, double* __restrict__ X) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * 2 * T) return;
   X[e] = (e < 2 * T && (e % 2) == 0) ? 1.0 : 0.0;
@@ -1052,13 +1076,11 @@ __global__ void k_ground(long long N, int T, double* __restrict__ X) {
 // ---------------------------------------------------------------------------
 template <typename TD>
 __global__ void k_cast(long long n, const double* __restrict__ src, TD* __restrict__ dst) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) dst[e] = static_cast<TD>(src[e]);
 }
 template <>
 __global__ void k_cast<__nv_bfloat16>(long long n, const double* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) dst[e] = __double2bfloat16(src[e]);
 }
@@ -1066,7 +1088,6 @@ __global__ void k_cast<__nv_bfloat16>(long long n, const double* __restrict__ sr
 // Timing filler for the autotuner: BF16 values in [-scale, scale) from an
 // integer hash of the index (operands that toggle like real data).
 __global__ void k_fill_hash_bf16(long long n, float scale, __nv_bfloat16* __restrict__ dst) {
-  pdl_entry();
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     uint32_t x = (uint32_t)e * 0x9E3779B1u ^ (uint32_t)(e >> 32);
     x ^= x >> 16;
@@ -1076,11 +1097,10 @@ __global__ void k_fill_hash_bf16(long long n, float scale, __nv_bfloat16* __rest
   }
 }
 
-// out[t][e] = sum_x d[t][x] src[x][e]  (mu_d = mu . d, Eq. e_field)
+// out[t][e] = sum_x d[t][x] src[x][e]  (mu_d = mu . d, Eq. (16))
 template <typename TD>
 __global__ void k_dipole_dir(long long len, int T, const double* __restrict__ dirs, const double* __restrict__ src,
                              TD* __restrict__ out) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= len * T) return;
   const int t = (int)(e / len);
@@ -1097,7 +1117,6 @@ __global__ void __launch_bounds__(256) k_spectrum(const double* __restrict__ tra
                                                   double dt, double kappa, double gamma, double wmin,
                                                   double dw, double* __restrict__ om_out,
                                                   double* __restrict__ S) {
-  pdl_entry();
   __shared__ double red[32];
   const long long j = blockIdx.x;
   const double w = wmin + dw * (double)j;
@@ -1120,14 +1139,13 @@ __global__ void __launch_bounds__(256) k_spectrum(const double* __restrict__ tra
 
 // ---------------------------------------------------------------------------
 // Autocorrelation R_t = sum_n conj(E_t[n]) c_t[n] of each trajectory's state
-// with its own stored state E = X(eps) (Eq. time_correlation_function), same
+// with its own stored state E = X(eps) (Eq. (20)), same
 // [N][2T] layout.  Pass 1: block (g, t) over the rows of chunk g, warp
 // shuffles and a fixed-order sum over warps -> part[(g T + t) 2 + re/im].
 // Pass 2: acf[(t ld + k) 2 + re/im] with k = *step + step_offset.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_acf_partial(long long N, int T, long long rows, const double* __restrict__ E,
                                                      const double* __restrict__ X, double* __restrict__ part) {
-  pdl_entry();
   __shared__ double ws[8][2];
   const int g = blockIdx.x, t = blockIdx.y, C = 2 * T;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1155,7 +1173,6 @@ __global__ void __launch_bounds__(256) k_acf_partial(long long N, int T, long lo
 
 __global__ void k_acf_final(int G, int T, const double* __restrict__ part, const long long* __restrict__ step,
                             long long step_offset, long long ld, double* __restrict__ acf) {
-  pdl_entry();
   const long long k = *step + step_offset;
   for (int e = threadIdx.x; e < 2 * T; e += blockDim.x) {
     const int t = e >> 1, r = e & 1;
@@ -1178,7 +1195,6 @@ __global__ void k_acf_final(int G, int T, const double* __restrict__ part, const
 __global__ void __launch_bounds__(256) k_spectrum_acf(const double* __restrict__ R, long long ntr, long long npts,
                                                       double dt, long long npad, double* __restrict__ om_out,
                                                       double* __restrict__ S) {
-  pdl_entry();
   __shared__ double red[32];
   const long long k = blockIdx.x;
   const double two_pi = 6.283185307179586476925286766559;
@@ -1218,7 +1234,6 @@ __device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& h, __nv_bflo
 // B^P_ab [pc][v][v] (FP64) -> planes [plane][P][vp][vp], slab p0..p0+pc
 __global__ void k_pack_vv(int pc, int v, int vp, const double* __restrict__ src, __nv_bfloat16* __restrict__ hi,
                           __nv_bfloat16* __restrict__ lo) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long tot = (long long)pc * vp * vp;
   if (e >= tot) return;
@@ -1235,7 +1250,6 @@ __global__ void k_pack_vv(int pc, int v, int vp, const double* __restrict__ src,
 // B^P_ij [pc][o][o] (FP64) -> planes [plane][(P, i)][op]
 __global__ void k_pack_oo(int pc, int o, int op, const double* __restrict__ src, __nv_bfloat16* __restrict__ hi,
                           __nv_bfloat16* __restrict__ lo) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long tot = (long long)pc * o * op;
   if (e >= tot) return;
@@ -1255,7 +1269,6 @@ __global__ void k_pack_oo(int pc, int o, int op, const double* __restrict__ src,
 __global__ void k_prep_xt(int o, int v, int vp, int op, int C, const double* __restrict__ X,
                           __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long nxf = 0,
                           float* __restrict__ Xf = nullptr) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < nxf) Xf[e] = (float)X[C + e];
   const long long tot = (long long)C * vp * op;
@@ -1281,7 +1294,6 @@ namespace rttda {
 __global__ void k_pack_ov(int pc, int p0, int P, long long ov, const double* __restrict__ src,
                           __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                           __nv_bfloat16* __restrict__ thi, __nv_bfloat16* __restrict__ tlo, long long plane) {
-  pdl_entry();
   __shared__ double tile[32][33];
   const long long ia0 = (long long)blockIdx.x * 32;
   const int pb = blockIdx.y * 32;
@@ -1318,7 +1330,6 @@ __global__ void k_pack_ov(int pc, int p0, int P, long long ov, const double* __r
 // w = B_ov X), via a 32 (ia) x C tile.  grid ceil(ov/32), block 256.
 __global__ void k_prep_xc(long long ov, int C, const double* __restrict__ X, __nv_bfloat16* __restrict__ hi,
                           __nv_bfloat16* __restrict__ lo) {
-  pdl_entry();
   extern __shared__ double xt[];  // [32][C + 1]
   const long long ia0 = (long long)blockIdx.x * 32;
   for (int e = threadIdx.x; e < 32 * C; e += blockDim.x) {
@@ -1344,7 +1355,6 @@ __global__ void k_prep_xc(long long ov, int C, const double* __restrict__ X, __n
 // in), split into BF16 hi/lo.
 __global__ void k_prep_wt(int P, int C, int nsplit, const float* __restrict__ wpart, __nv_bfloat16* __restrict__ hi,
                           __nv_bfloat16* __restrict__ lo) {
-  pdl_entry();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)P * C) return;
   const int c = (int)(e / P), p = (int)(e % P);

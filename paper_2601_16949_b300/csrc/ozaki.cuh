@@ -30,7 +30,6 @@
 // contraction of one block, stores I).
 #pragma once
 
-#include "pdl.cuh"
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -196,7 +195,6 @@ __global__ void __launch_bounds__(256) k_slice_rows(long long rows, long long ri
                                                     const double* __restrict__ src, long long lds, long long ldk,
                                                     __nv_bfloat16* __restrict__ dst, long long ldd, long long plane,
                                                     TE* __restrict__ exps, long long lde, int nblk) {
-  pdl_entry();
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= rows * nblk) return;
@@ -233,7 +231,6 @@ __global__ void __launch_bounds__(256) k_slice_rows(long long rows, long long ri
 __global__ void __launch_bounds__(256) k_slice_x(int o, int v, int vp, int op, int C, const double* __restrict__ X,
                                                  __nv_bfloat16* __restrict__ dst, long long plane,
                                                  int* __restrict__ ex) {
-  pdl_entry();
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= (long long)C * vp) return;
@@ -269,7 +266,6 @@ __global__ void __launch_bounds__(256) k_slice_x(int o, int v, int vp, int op, i
 __global__ void __launch_bounds__(256) k_slice_xc(long long ov, int ovp, int C, int cp, int nkb,
                                                   const double* __restrict__ X, __nv_bfloat16* __restrict__ dst,
                                                   long long plane, short* __restrict__ ex) {
-  pdl_entry();
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= (long long)cp * nkb) return;
@@ -305,7 +301,6 @@ __global__ void __launch_bounds__(256) k_slice_xc(long long ov, int ovp, int C, 
 __global__ void __launch_bounds__(256) k_slice_w(int P, int Pp, int C, int cp, int npb, int nsp,
                                                  const double* __restrict__ wpart, __nv_bfloat16* __restrict__ dst,
                                                  long long plane, short* __restrict__ ew) {
-  pdl_entry();
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= (long long)cp * npb) return;
@@ -348,7 +343,6 @@ __global__ void __launch_bounds__(256, 4) k_slice_z(int o, int vp, int C, int pc
                                                  const long long* __restrict__ Zi, const short* __restrict__ eoo,
                                                  const int* __restrict__ ex, __nv_bfloat16* __restrict__ dst,
                                                  long long plane, int* __restrict__ ez) {
-  pdl_entry();
   const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const long long nw = (long long)C * o * pc * nbp;
@@ -417,7 +411,6 @@ __global__ void __launch_bounds__(256, 4) k_slice_z(int o, int vp, int C, int pc
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p) {
-  pdl_entry();
   using namespace tc;
   constexpr int ST = stages<MODE>();
   extern __shared__ uint8_t smem_raw[];

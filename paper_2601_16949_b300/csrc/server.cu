@@ -43,7 +43,7 @@ struct Request {
   rttda_request req{};
   std::vector<double> eps_o, eps_v, Bov, Boo, Bvv, moo, mvv, m0;  // owned copies until admission
   int state = RTTDA_REQ_PENDING;
-  bool cancel = false;
+  std::atomic<bool> cancel{false};  // written by rttda_server_cancel, read by the scheduler thread
   double t_submit = 0.0, t_done = 0.0;
   rttda_t h = nullptr;
   double* dev = nullptr;  // [dip nsteps+1][nrm nsteps+1][omega nfreq][S nfreq]

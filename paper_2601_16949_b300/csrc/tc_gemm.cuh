@@ -19,7 +19,6 @@
 // records an error code in *err and leaves its loops.
 #pragma once
 
-#include "pdl.cuh"
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -320,7 +319,6 @@ template <int BN, int STAGES, int BMODE, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmZ, const Params p) {
-  pdl_entry();
   // MERGED: a stage holds A hi, A lo and B hi of one K tile and the MMA warp
   // issues every product of the tile from it (products (hi,hi), (lo,hi),
   // i.e. nprod <= 2 with alo); otherwise one stage per product
@@ -670,7 +668,6 @@ constexpr size_t wide_smem_bytes() {
 template <int BN, int MB, int NBP, int STAGES, int KB, bool TR = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_wide(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p) {
-  pdl_entry();
   using CF = WideCfg<BN, MB, NBP, KB, TR>;
   constexpr int TM = kBM * MB;  // rows per tile
   extern __shared__ uint8_t smem_raw[];

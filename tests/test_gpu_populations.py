@@ -1,5 +1,5 @@
 """TI-TDA eigenstates (Davidson on the library's sigma) and population /
-overlap recording (Eq. populations) against the FP64 oracle."""
+overlap recording (Eq. (22)) against the FP64 oracle."""
 import numpy as np
 import pytest
 

@@ -156,7 +156,7 @@ def _dot(x, y):
 
 def test_M_matches_brute_force_slater_determinants():
     """Singlet CSFs from determinants; <I|mu|J> by second quantisation.
-    Checks sc2 (sqrt 2), sc3, sc4, sc5 (sign) and sc6 (zeros) at once."""
+    Checks Eqs. (19b) (sqrt 2), (19c), (19d), (19e) (sign) and (19f) (zeros) at once."""
     o, v = 2, 3
     nmo = o + v
     rng = np.random.default_rng(7)
@@ -489,7 +489,7 @@ def test_autocorr_spectrum_peaks_at_state_energies_with_weights():
     """R(t) = sum_i |b_i|^2 exp(-i E_i t) for a state b expanded in
     eigenstates (exact for a stationary H): peaks at w = E_i on the grid,
     heights proportional to E_i |b_i|^2 (the w prefactor of Eq.
-    fourier_transform), the Hann window's peak value being the same for
+    (21)), the Hann window's peak value being the same for
     every line; the |0> line at w = 0 is removed by the w factor."""
     dt, n, npad = 0.1, 3001, 50000
     grid = orc.autocorr_grid(n, dt, npad, 4000)
@@ -663,7 +663,7 @@ def test_spectrum_sum_equals_geometric_series(gamma):
 
 
 def test_field_sign_matches_linear_response_convolution():
-    """H = A - E(t) M (Eq. e_field) fixes the sign of the first-order dipole
+    """H = A - E(t) M (Eq. (16)) fixes the sign of the first-order dipole
     response: delta mu(t) = int_0^t chi(t - t') E(t') dt' with
     chi(tau) = 2 sum_n (v_n . m)^2 sin(lambda_n tau) from the eigenpairs."""
     mol = small_mol(2, 3, 4, seed=13)

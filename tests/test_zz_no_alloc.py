@@ -1,4 +1,5 @@
-"""The allocation-free Coulomb entry point, checked against rttda_sigma.
+"""The allocation-free Coulomb entry point, checked against rttda_sigma and
+against the oracle's explicit matrix.
 
 rttda_coulomb_noalloc serves callers that may not allocate GPU memory while
 they run (their device memory belongs to their own pool or has a fixed
@@ -9,6 +10,7 @@ other test already; it also passes alone in a fresh process.
 import numpy as np
 import pytest
 
+from oracle import rttda_oracle as orc
 from paper_2601_16949_b300 import synth
 from tests._util import to_ri
 
@@ -36,6 +38,7 @@ def test_noalloc_coulomb_matches_sigma_on_two_calls():
     prop = rb.Propagator(mol, 0.2, "fp64")
     prop.set_field(pulses)
     n = prop.n
+    A = orc.build_A(mol, 0.2)
     B = torch.tensor(mol["B_ov"].reshape(P, o * v), dtype=torch.float64, device="cuda")
     for call in range(2):
         c = synth.random_state(n, 3, seed=30 + call)
@@ -50,6 +53,11 @@ def test_noalloc_coulomb_matches_sigma_on_two_calls():
         r, g = ref.cpu().numpy(), out.cpu().numpy()
         assert np.all(np.isfinite(g))
         assert np.max(np.abs(g - r)) <= 1e-13 * np.max(np.abs(r)), call
+        # the oracle: with zero orbital energies and exchange factors, A is
+        # the Coulomb block 2 B_ov^T B_ov alone (ground row and column zero)
+        want = (A @ c.T).T
+        got = g[..., 0] + 1j * g[..., 1]
+        assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want)), call
     prop.close()
 
 
