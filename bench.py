@@ -1,10 +1,18 @@
 #!/usr/bin/env python
 """RT-TDA benchmark: trajectory-steps/s of the batched sigma build + RK4 stepper.
 
-Workload (linear absorption): nocc=64, nvirt=448, naux=1536 (dim 28673),
-synthetic factors (seeded generator), three trajectories kicked along x, y, z
-(kappa = 1e-3) from |0>, RK4 dt = 0.05 au.  One "step" is one RK4 step of the
-whole batch (four sigma builds per trajectory, observables included).
+Default workload (the batched field scan): nocc=128, nvirt=768, naux=3072
+(dim 98305), synthetic factors drawn on the GPU with a seeded generator,
+32 trajectories driven by sin^2 pulses (400 au, z-polarised) at
+omega = lambda_min(A) and lambda_min/2 with amplitudes log-spaced 1e-3 to
+5e-2 au, RK4 dt = 0.04 au, plain BF16 factors with FP32 accumulation and an
+FP64 amplitude state.  One "step" is one RK4 step of the whole batch (four
+sigma builds per trajectory, observables included).  lambda_min(A) is the
+lowest eigenvalue of the FP64-accurate sigma build (Davidson).
+
+Other workloads (--workload): linear absorption (nocc=64, nvirt=448,
+naux=1536, x/y/z kicks), the large system (nocc=256, nvirt=1536,
+naux=4096, one z kick) and the shape of the paper's smallest timing system.
 
 Default: 1 GPU.  Under torchrun each rank propagates its own batch (weak
 scaling, no data-path collective); timing is the max over ranks.
@@ -29,14 +37,12 @@ METRIC = "RT-TDA trajectory-steps/s vs plain FP64 path at stated dipole err; p50
 UNIT = "trajectory-steps/s"
 CX, KAPPA, SEED = 0.2, 1e-3, 0
 DIRS = [(1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)]
-# workloads: the linear-absorption one is the default bench line; the others
-# are the batched field scan and the large system
 WORKLOADS = {
-    "absorption": dict(nocc=64, nvirt=448, naux=1536, dt=0.05,
-                       desc="linear absorption: 3 trajectories (x/y/z kicks, kappa=1e-3) per GPU"),
     "fieldscan": dict(nocc=128, nvirt=768, naux=3072, dt=0.04,
                       desc=("batched field scan: 32 sin^2 pulses (400 au) per GPU at omega = lambda_min(A) and "
-                            "lambda_min/2, amplitudes log-spaced 1e-3..5e-2, z-polarised")),
+                            "lambda_min/2, amplitudes log-spaced 1e-3..5e-2 au, z-polarised")),
+    "absorption": dict(nocc=64, nvirt=448, naux=1536, dt=0.05,
+                       desc="linear absorption: 3 trajectories (x/y/z kicks, kappa=1e-3) per GPU"),
     "large": dict(nocc=256, nvirt=1536, naux=4096, dt=0.05, desc="large system: one z kick kappa=1e-3"),
     # the shape of the paper's smallest timing system (Indigo: 68 occupied, 252
     # virtual orbitals) with a synthetic RI basis of 3 x 320 functions, driven
@@ -46,72 +52,50 @@ WORKLOADS = {
                          desc=("paper timing-study shape: one transform-limited pulse, 2.5 eV carrier, "
                                "5e11 W/cm2 peak, FWHM 0.91 fs, centred at 50 au")),
 }
-NOCC, NVIRT, NAUX, DT = 64, 448, 1536, 0.05
-NDIM = 1 + NOCC * NVIRT
-WORKLOAD = ""
+# workloads whose FP64 factors are drawn on the GPU (host generation takes
+# minutes, or the factors do not fit in host memory)
+DEVICE_FACTORS = ("fieldscan", "large")
+NOCC = NVIRT = NAUX = NDIM = 0
+DT = 0.0
+WORKLOAD = NAME = ""
 
 
 def set_workload(name: str, naux: int = 0) -> None:
-    global NOCC, NVIRT, NAUX, DT, NDIM, WORKLOAD
+    global NOCC, NVIRT, NAUX, DT, NDIM, WORKLOAD, NAME
     w = WORKLOADS[name]
     NOCC, NVIRT, NAUX, DT = w["nocc"], w["nvirt"], naux or w["naux"], w["dt"]
     NDIM = 1 + NOCC * NVIRT
+    NAME = name
     WORKLOAD = (f"{w['desc']}: nocc={NOCC} nvirt={NVIRT} naux={NAUX} (dim {NDIM}), RK4 dt={DT} au, c_x={CX}")
 
 
-set_workload("absorption")
+set_workload("fieldscan")
 
 
-def lowest_eigenvalue(rb, mol, iters=60):
-    """lambda_min of A by Lanczos with full reorthogonalisation, using the
-    library's sigma (a kicked trajectory has E = 0 for t > 0, so sigma = A c)."""
-    import torch
-    prop = rb.Propagator(mol, CX, "bf16x3")
-    prop.set_field([dict(kind=rb.KICK, E0=KAPPA, direction=(0.0, 0.0, 1.0))])
-    n = prop.n
-    rng = np.random.default_rng(7)
-    q = rng.standard_normal(n)
-    q[0] = 0.0
-    q /= np.linalg.norm(q)
-    Q, alpha, beta = [q], [], []
-    cd = torch.zeros((1, n, 2), dtype=torch.float64, device="cuda")
-    sd = torch.zeros_like(cd)
-    for k in range(iters):
-        cd[0, :, 0] = torch.from_numpy(Q[-1])
-        cd[0, :, 1] = 0.0
-        rb.rttda_sigma(prop.h, cd.data_ptr(), 1.0, sd.data_ptr(), 0)
-        rb.rttda_sync(prop.h)
-        w = sd[0, :, 0].cpu().numpy()
-        a = float(w @ Q[-1])
-        w = w - a * Q[-1] - (beta[-1] * Q[-2] if beta else 0.0)
-        for qq in Q:
-            w -= (w @ qq) * qq
-        alpha.append(a)
-        b = float(np.linalg.norm(w))
-        if b < 1e-12 or k == iters - 1:
-            break
-        beta.append(b)
-        Q.append(w / b)
-    prop.close()
-    Tm = np.diag(alpha) + np.diag(beta[:len(alpha) - 1], 1) + np.diag(beta[:len(alpha) - 1], -1)
-    return float(np.linalg.eigvalsh(Tm)[0])
+def make_molecule(name: str, device: bool):
+    from paper_2601_16949_b300 import synth
+    if device:
+        return synth.molecule_device(NOCC, NVIRT, NAUX, seed=SEED)
+    return synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
 
 
-def workload_pulses(rb, name, mol):
+def workload_pulses(name: str, lam: float | None = None):
+    """The workload's pulses (binding pulse dicts; kinds as in rttda.h).
+    The field scan needs lambda_min(A) (lam)."""
     if name == "fieldscan":
-        lam = lowest_eigenvalue(rb, mol)
         amps = np.exp(np.linspace(np.log(1e-3), np.log(5e-2), 16))
-        return [dict(kind=rb.SIN2, E0=float(a), omega=w, duration=400.0, direction=(0.0, 0.0, 1.0))
-                for w in (lam, 0.5 * lam) for a in amps], {"lambda_min": lam}
+        return [dict(kind=4, E0=float(a), omega=w, duration=400.0, direction=(0.0, 0.0, 1.0))
+                for w in (lam, 0.5 * lam) for a in amps]
     if name == "large":
-        return [dict(kind=rb.KICK, E0=KAPPA, direction=(0.0, 0.0, 1.0))], {}
+        return [dict(kind=0, E0=KAPPA, direction=(0.0, 0.0, 1.0))]
     if name == "paper_timing":
         ev = 1.0 / 27.211386245988                   # Hartree per eV
         fs = 1.0 / 2.4188843265857e-2                # au of time per fs
         E0 = float(np.sqrt(5e11 / 3.50944758e16))    # peak field from the intensity (au)
-        return [dict(kind=rb.GAUSS_TL, E0=E0, omega=2.5 * ev, t0=50.0, fwhm=0.91 * fs,
-                     direction=(0.0, 0.0, 1.0))], {"E0_au": E0}
-    return [dict(kind=rb.KICK, E0=KAPPA, direction=d) for d in DIRS], {}
+        return [dict(kind=2, E0=E0, omega=2.5 * ev, t0=50.0, fwhm=0.91 * fs, direction=(0.0, 0.0, 1.0))]
+    return [dict(kind=0, E0=KAPPA, direction=d) for d in DIRS]
+
+
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -157,81 +141,182 @@ class Ranks:
             self.torch.distributed.destroy_process_group()
 
 
-def base_config(prec: str, world: int, T: int = 3) -> dict:
-    return {"workload": WORKLOAD, "precision": prec, "trajectories_per_gpu": T,
+def base_config(prec: str, world: int, T: int) -> dict:
+    return {"workload": WORKLOAD, "workload_name": NAME, "precision": prec, "trajectories_per_gpu": T,
             "global_trajectories": T * world, "parallelism": f"trajectory replicas x{world}",
-            "l2": "inputs larger than L2: every stage streams the B_vv planes (>1 GB) and B_ov",
+            "l2": "inputs larger than L2: every stage streams the B_vv factors (>1 GB) and B_ov",
             "seed": SEED}
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
+def host_rows_molecule(mol, rows):
+    """numpy copy of what the oracle needs for A_rows / M_rows on `rows`.
+    Host molecules pass through.  From a GPU molecule: every array in full
+    except B_vv, which is copied only at the virtual indices a of the sampled
+    rows (A_rows reads B_vv[:, a, :] for those a alone); the rest of that
+    array is never touched, so its zero pages are never allocated."""
+    if not hasattr(mol["B_vv"], "is_cuda"):
+        return mol
+    out = {k: mol[k] for k in ("nocc", "nvirt", "naux")}
+    for k in ("eps_occ", "eps_virt", "B_ov", "B_oo", "mu_oo", "mu_vv", "mu_0ov"):
+        out[k] = mol[k].cpu().numpy()
+    P, v = mol["naux"], mol["nvirt"]
+    bvv = np.zeros((P, v, v))
+    for a in sorted({(int(k) - 1) % v for k in rows if k > 0}):
+        bvv[:, a, :] = mol["B_vv"][:, a, :].cpu().numpy()
+    out["B_vv"] = bvv
+    return out
+
+
 class OracleSample:
-    """Dense sigma = H(t)c of the oracle on a block of rows of the explicit A.
+    """The oracle's sigma = H(t)c on a sample of rows of the explicit A.
 
-    The block is the rows of the first `nocc_rows` occupied orbitals (all
-    virtuals); one sampled step is the oracle's sigma on that block for all
-    three trajectories, four times (one RK4 step), and the full step is that
-    time scaled by (rows of A) / (rows in the block).  Building A is setup,
-    as rttda_create is for the GPU."""
+    `nrows` rows of the dim x dim matrices A and M_d (drawn uniformly with a
+    fixed seed) are built from the definitions (set-up, as rttda_create is
+    for the GPU); one sampled step is the oracle's sigma on those rows for
+    every trajectory at the four RK4 stage times, and the full step is that
+    time scaled by dim / nrows."""
 
-    def __init__(self, mol, nocc_rows: int):
+    def __init__(self, mol, pulses, nrows: int):
         from oracle import rttda_oracle as orc
         self.orc = orc
-        self.rows = np.arange(1, 1 + nocc_rows * NVIRT)
-        self.A = orc.A_block(mol, CX, 0, nocc_rows)
-        self.M = [orc.M_rows(*orc.dipole_along(mol, d), self.rows) for d in DIRS]
         rng = np.random.default_rng(1)
-        self.c = [rng.standard_normal(NDIM) + 1j * rng.standard_normal(NDIM) for _ in DIRS]
+        self.rows = np.sort(rng.choice(NDIM, size=min(nrows, NDIM), replace=False))
+        hm = host_rows_molecule(mol, self.rows)
+        self.A = orc.A_rows(hm, CX, self.rows)
+        self.pulses, self.M, mcache = [], [], {}
+        for p in pulses:
+            d = tuple(float(x) for x in p["direction"])
+            if d not in mcache:
+                u = np.asarray(d) / np.linalg.norm(d)
+                mcache[d] = orc.M_rows(*orc.dipole_along(hm, u), self.rows)
+            self.M.append(mcache[d])
+            self.pulses.append(orc.Pulse(kind=p["kind"], E0=p["E0"], omega=p.get("omega", 0.0),
+                                         t0=p.get("t0", 0.0), fwhm=p.get("fwhm", 1.0),
+                                         duration=p.get("duration", 0.0), direction=d))
+        self.c = [rng.standard_normal(NDIM) + 1j * rng.standard_normal(NDIM) for _ in pulses]
+        self.t = 0.0
 
     def step(self):
-        for k in range(3):
+        for k, p in enumerate(self.pulses):
             c = self.c[k]
-            for _ in range(4):
-                sg = self.orc.sigma(self.A, self.M[k], 0.0, c)
+            for cs in (0.0, 0.5, 0.5, 1.0):
+                sg = self.orc.sigma(self.A, self.M[k], self.orc.field(p, self.t + cs * DT), c)
                 c[self.rows] = c[self.rows] + (-1j * DT) * sg * 1e-6
+        self.t += DT
 
     def scale(self) -> float:
         return NDIM / len(self.rows)
 
-    @staticmethod
-    def cores() -> int:
-        try:
-            from threadpoolctl import threadpool_info
-            n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
-            return max(n) if n else 1
-        except Exception:
-            return 1
+    def save(self, path: str) -> None:
+        np.savez(path, rows=self.rows, A=self.A, M=np.stack(self.M), c=np.stack(self.c),
+                 pulses=json.dumps([p.__dict__ for p in self.pulses]))
+
+    @classmethod
+    def load(cls, path: str) -> "OracleSample":
+        from oracle import rttda_oracle as orc
+        z = np.load(path)
+        s = cls.__new__(cls)
+        s.orc, s.rows, s.A, s.t = orc, z["rows"], z["A"], 0.0
+        s.M, s.c = list(z["M"]), list(z["c"])
+        s.pulses = [orc.Pulse(**{k: (tuple(v) if isinstance(v, list) else v) for k, v in p.items()})
+                    for p in json.loads(str(z["pulses"]))]
+        return s
 
 
-def time_oracle(mol, nocc_rows: int, nsteps: int, warmup: int = 1):
-    s = OracleSample(mol, nocc_rows)
+def sample_rows() -> int:
+    """Rows of the oracle sample: a few seconds of CPU work per sampled step."""
+    return {"fieldscan": 24, "large": 8}.get(NAME, 256)
+
+
+def blas_threads() -> int:
+    """Threads the oracle's BLAS runs on: threadpoolctl's count when it is
+    installed, else the CPUs this process may use (OpenBLAS's default)."""
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return max(n)
+    except Exception:
+        pass
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle(sample: OracleSample, nsteps: int, warmup: int = 1) -> dict:
+    """Trajectory-steps/s of the oracle on its row sample, in this process
+    (its BLAS on all cores unless the environment limits it)."""
     for _ in range(warmup):
-        s.step()
+        sample.step()
     t0 = time.perf_counter()
     for _ in range(nsteps):
-        s.step()
+        sample.step()
     dt_sample = (time.perf_counter() - t0) / nsteps
-    full_step = dt_sample * s.scale()
-    return {"value": 3.0 / full_step, "unit": UNIT, "cores": OracleSample.cores(), "kind": "oracle",
-            "sample": (f"oracle dense sigma on {len(s.rows)} of {NDIM} rows of A (occupied 0..{nocc_rows - 1}), "
-                       f"3 trajectories x 4 sigma per step, {nsteps} sampled steps, scaled x{s.scale():.2f} "
-                       "to a full RK4 step; building A excluded as setup"),
+    T = len(sample.pulses)
+    full_step = dt_sample * sample.scale()
+    return {"value": T / full_step, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": (f"oracle sigma on {len(sample.rows)} of {NDIM} rows of the explicit A and M_d (rows drawn "
+                       f"with a fixed seed), {T} trajectories x 4 sigma per RK4 step, {nsteps} sampled steps, "
+                       f"scaled x{sample.scale():.1f} to a full step; building the rows excluded as set-up"),
             "ms_per_step": full_step * 1e3}
+
+
+def time_oracle_one_core(sample: OracleSample, nsteps: int) -> dict:
+    """The same timing in a child process whose BLAS is limited to one thread
+    (the thread count of a loaded BLAS cannot be changed from numpy)."""
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "sample.npz")
+        sample.save(path)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--time-oracle-sample", path,
+                              "--cpu-steps", str(nsteps), "--workload", NAME, "--naux", str(NAUX)],
+                             env=env, capture_output=True, text=True, timeout=900)
+        if out.returncode != 0:
+            return {"error": out.stderr[-500:]}
+        return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_pulses(mol):
+    """The workload's pulses for the oracle arm.  The field scan's carrier
+    frequency is set from the lowest orbital-energy gap here: the oracle
+    cannot diagonalise A at this size, and the frequency does not change the
+    cost of its sigma."""
+    if NAME != "fieldscan":
+        return workload_pulses(NAME)
+    eo, ev = mol["eps_occ"], mol["eps_virt"]
+    gap = float(ev.min() - eo.max()) if not hasattr(ev, "is_cuda") else float((ev.min() - eo.max()).item())
+    return workload_pulses(NAME, gap)
 
 
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
-    from paper_2601_16949_b300 import synth
-    mol = synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
-    base = time_oracle(mol, 2, args.steps, warmup=args.warmup)
+    device = False
+    if NAME in DEVICE_FACTORS:
+        try:
+            import torch
+            device = torch.cuda.is_available()
+        except Exception:
+            device = False
+    mol = make_molecule(NAME, device)
+    pulses = reference_pulses(mol)
+    sample = OracleSample(mol, pulses, sample_rows())
+    del mol
+    base = time_oracle(sample, args.steps, warmup=args.warmup)
+    T = len(pulses)
     line = {"metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": base["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": base_config("fp64 (CPU oracle)", 1), "impl": "reference",
+            "config": base_config("fp64 (CPU oracle)", 1, T), "impl": "reference",
             "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -251,7 +336,7 @@ class ClockSampler:
         self.proc = None
 
     def __enter__(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
         if self.uuid:
             cmd += ["-i", self.uuid]
         try:
@@ -304,23 +389,34 @@ PREC_INFO = {  # factor bytes, exchange planes, tensor products per K tile
     "fp64oz": dict(fb=8, planes=6, nprod=21, tensor=True, zplanes=6),
 }
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the dominant kernel, from one ncu --set full capture of that kernel on this
-# workload.  Keyed by (workload, precision, kernel class, main kernel kind
-# (2 wide-M, 4 transposed), BN, MB, K tile):
-# the number holds only for that kernel and plan.
-PROFILED_TRAFFIC = {
-    ("absorption", "bf16x2", "exchange_main", 4, 192, 2, 32): 1.766175e9 + 3.553792e6,
-}
+
+def profiled_traffic(prec: str, cls: str, plan: dict):
+    """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
+    launch of a kernel class, from the committed ncu summary table
+    profiles/dram_traffic.txt, for this workload, precision and plan; None
+    when the table has no capture of exactly this kernel and plan."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    want = [NAME, str(NAUX), prec, cls, str(plan.get("main_kernel")), str(plan.get("main_bn")),
+            str(plan.get("main_mb")), str(plan.get("main_kb")), str(plan.get("main_splits"))]
+    for line in open(TRAFFIC_FILE):
+        f = line.split("#", 1)[0].split()
+        if len(f) >= 11 and f[:9] == want:
+            return {"bytes": float(f[9]), "source": f"profiles/{f[10]}"}
+    return None
 
 
 def algorithmic_work(prec: str, cls: str, T: int):
-    """(flop, bytes) of one launch of a kernel class on this workload.
+    """(method flop, hardware flop, bytes) of one sigma build's launches of a
+    kernel class.
 
-    exchange_main: sum_{P,b} Z^P_(col,i),b B^P_ab, M = 2T*nocc, N = nvirt,
-    K = naux*nvirt; bytes = Z and B_vv read once (all planes).  Flops count
-    every tensor product of the split (nprod x 2MNK)."""
+    exchange_main: K_(col,i),a = sum_{P,b} Z^P_(col,i),b B^P_ab with
+    M = 2T nocc, N = nvirt, K = naux nvirt: the method's flop are 2MNK (one
+    product, the P o v^2 C multiply-adds of the exchange); the hardware
+    executes nprod products of the precision's hi/lo split; bytes = Z and
+    B_vv read once (all planes)."""
     pi = PREC_INFO[prec]
     C = 2 * T
     o, v, P = NOCC, NVIRT, NAUX
@@ -328,54 +424,55 @@ def algorithmic_work(prec: str, cls: str, T: int):
         M, N, K = C * o, v, P * v
         eb = 2 if pi["tensor"] else pi["fb"]
         zp = pi.get("zplanes", pi["planes"])
-        return pi["nprod"] * 2.0 * M * N * K, eb * (zp * M * K + pi["planes"] * P * v * v)
+        f = 2.0 * M * N * K
+        return f, pi["nprod"] * f, eb * (zp * M * K + pi["planes"] * P * v * v)
     if cls == "coulomb":
-        return 2 * 2.0 * P * o * v * C, 2.0 * P * o * v * (pi["fb"] if prec != "bf16x3" else 4)
+        f = 2 * 2.0 * P * o * v * C
+        return f, f, 2.0 * P * o * v * (pi["fb"] if prec != "bf16x3" else 4)
     if cls == "exchange_z" and prec == "fp64oz":
-        # Z build into int64 Z (written, read back by the digit split) plus
-        # its 6 BF16 digits; digits of B_oo and of the amplitudes read once
         nz = P * o * v * C
-        return pi["nprod"] * 2.0 * P * o * o * v * C, (8 + 8 + 2 * 6) * nz + 2 * 6 * (P * o * o + o * v * C)
+        f = 2.0 * P * o * o * v * C
+        return f, pi["nprod"] * f, (8 + 8 + 2 * 6) * nz + 2 * 6 * (P * o * o + o * v * C)
     if cls == "exchange_z":
         eb = 2 if pi["tensor"] else pi["fb"]
         zp = pi.get("zplanes", pi["planes"])
         nz = 3 if prec in ("bf16x3", "bf16x2") else pi["nprod"]
-        return nz * 2.0 * P * o * o * v * C, eb * (zp * P * o * v * C + pi["planes"] * P * o * o)
-    return None, None
+        f = 2.0 * P * o * o * v * C
+        return f, nz * f, eb * (zp * P * o * v * C + pi["planes"] * P * o * o)
+    return None, None, None
 
 
-def roofline(prec: str, cls: str, prof_entry, T: int, peaks: dict, nsigma: int) -> dict:
+def roofline(prec: str, cls: str, prof_entry, T: int, peaks: dict, nsigma: int, plan: dict) -> dict:
     """Roofline of one kernel class.  The unit is one sigma build (one RK4
     stage): when the exchange is chunked over P, a stage is several launches
     of the class, so work and time are both taken per stage (the sum over
     its launches), which keeps achieved = work / duration for any chunking.
 
-    The class is timed inside a long run of steps, so the tensor peak is the
-    sustained (power-capped) measured bf16 rate; the burst rate is reported
-    beside it."""
+    achieved counts the method's flop (one product); frac is taken against
+    the burst bf16 peak, with the fraction of the sustained (power-capped)
+    peak beside it, and the hardware rate (every product of the split)."""
     ms, n = prof_entry
-    flop, byts = algorithmic_work(prec, cls, T)
+    flop, hw_flop, byts = algorithmic_work(prec, cls, T)
     hbm = peaks.get("hbm_gbs", 6400.0)
     bf16_burst = peaks.get("bf16_tflops", 1800.0)
-    bf16 = peaks.get("bf16_tflops_sustained", 1400.0)
+    bf16_sus = peaks.get("bf16_tflops_sustained", 1400.0)
     out = {"kernel": cls, "unit_of_work": "one sigma build (all launches of the class in one RK4 stage)",
            "avg_launch_ms": ms / max(n, 1), "launches_timed": n, "sigma_builds_timed": nsigma,
            "launches_per_sigma": n / max(nsigma, 1), "ms_per_sigma": ms / max(nsigma, 1), "traffic": None,
-           "flop_per_sigma": flop, "bytes_per_sigma": byts}
+           "flop_per_sigma": flop, "hardware_flop_per_sigma": hw_flop, "bytes_per_sigma": byts}
     if flop is None or n == 0:
         out.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None})
         return out
     sec = ms / nsigma / 1e3
     pi = PREC_INFO[prec]
     if pi["tensor"]:
-        cpeak, cunit = bf16, "TFLOP/s"
-        csrc = "of measured: bf16 sustained (MEASURED_PEAKS.json bf16_tflops_sustained)"
-        cbound = "tensor"
+        cpeak, cunit, cbound = bf16_burst, "TFLOP/s", "tensor"
+        csrc = "of measured: bf16 burst (MEASURED_PEAKS.json bf16_tflops)"
     else:
-        lanes = 128 if prec == "fp32" else 64
+        lanes = 128 if prec == "fp32" else 2
         cpeak = 148 * lanes * 2 * 2.032e9 / 1e12
         cunit, cbound = "TFLOP/s", "alu"
-        csrc = f"derived: 148 SM x {lanes} {'FP32' if prec == 'fp32' else 'FP64'} FMA/clk x 2 x 2032 MHz"
+        csrc = (f"derived: 148 SM x {lanes} {'FP32' if prec == 'fp32' else 'FP64'} FMA/clk x 2 x 2032 MHz")
     t_comp = flop / (cpeak * 1e12)
     t_mem = byts / (hbm * 1e9)
     if t_mem >= t_comp:
@@ -387,30 +484,76 @@ def roofline(prec: str, cls: str, prof_entry, T: int, peaks: dict, nsigma: int) 
     out["frac"] = out["achieved"] / out["peak"]
     out["other_bound_frac"] = (flop / sec / 1e12 / cpeak) if out["bound"] == "hbm" else (byts / sec / 1e9 / hbm)
     if pi["tensor"]:
-        out["tensor_frac_of_burst"] = flop / sec / 1e12 / bf16_burst
+        out["frac_of_sustained"] = flop / sec / 1e12 / bf16_sus
+        out["hardware_tflops"] = hw_flop / sec / 1e12
+    tr = profiled_traffic(prec, cls, plan)
+    if tr is not None:
+        out["traffic"] = tr["bytes"] * out["launches_per_sigma"]
+        out["traffic_source"] = tr["source"] + " (ncu dram__bytes_read.sum + dram__bytes_write.sum, this plan)"
+        out["traffic_over_algorithmic"] = out["traffic"] / byts
     return out
 
 
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+ACC_STEPS = 20     # horizon of the accuracy probe against the FP64-accurate path
+ACC_STATES = 4     # lowest excitation energies compared (spectral peak positions)
+
+
+def davidson(rb, prop, k, tol, max_iter=200):
+    w, _, it = prop.eigenstates(k, tol=tol, max_iter=max_iter, allow_unconverged=True)
+    return np.asarray(w), it
+
+
+def kick_probe(rb, prop, nsteps):
+    """Dipole and norm traces of one z-kicked trajectory (kappa = 1e-3) on
+    the handle's molecule, for accuracy comparisons."""
+    prop.set_field([dict(kind=rb.KICK, E0=KAPPA, direction=(0.0, 0.0, 1.0))])
+    _, dip, nrm = prop.propagate(DT, nsteps, want_state=False)
+    return dip[0], nrm[0]
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
     ranks = Ranks("nccl", "cuda")
     from paper_2601_16949_b300 import binding as rb
-    from paper_2601_16949_b300 import synth
     barrier, max_over_ranks = ranks.barrier, ranks.max
+    dev = torch.device("cuda", local)
 
-    if args.workload in ("large", "fieldscan"):
-        # FP64 factors of this size take minutes to draw on the host (or do
-        # not fit there): draw them on the GPU
-        mol = synth.molecule_device(NOCC, NVIRT, NAUX, seed=SEED)
-        args.no_cpu_baseline = True
+    mol = make_molecule(NAME, NAME in DEVICE_FACTORS)
+    wl_info = {}
+    accuracy = None
+    ref = None
+    if not (args.no_accuracy or args.only_timed):
+        # FP64-accurate reference (Ozaki digits on the tensor cores): the
+        # lowest excitation energies by Davidson (the positions of the
+        # lowest spectral peaks) and a kicked probe trajectory
+        t0 = time.perf_counter()
+        poz = rb.Propagator(mol, CX, "fp64oz")
+        poz.set_field([dict(kind=rb.KICK, E0=KAPPA, direction=(0.0, 0.0, 1.0))] * 2)
+        w_oz, it_oz = davidson(rb, poz, ACC_STATES, 1e-8)
+        d_oz, n_oz = kick_probe(rb, poz, args.acc_steps)
+        poz.close()
+        ref = {"w": w_oz, "it": it_oz, "dip": d_oz, "nrm": n_oz, "s": time.perf_counter() - t0}
+    if NAME == "fieldscan":
+        if args.lambda_min > 0.0:
+            lam, src = args.lambda_min, "given on the command line"
+        elif ref is not None:
+            lam = float(ref["w"][0])
+            src = "Davidson on the FP64-accurate (Ozaki-digit) sigma build"
+        else:
+            p3 = rb.Propagator(mol, CX, "bf16x3")
+            p3.set_field([dict(kind=rb.KICK, E0=KAPPA, direction=(0.0, 0.0, 1.0))] * 2)
+            lam = float(davidson(rb, p3, 1, 1e-6)[0][0])
+            p3.close()
+            src = "Davidson on the BF16X3 sigma build"
+        wl_info = {"lambda_min": lam, "lambda_min_source": src}
+        pulses = workload_pulses(NAME, lam)
     else:
-        mol = synth.molecule(NOCC, NVIRT, NAUX, seed=SEED)
-    pulses, wl_info = workload_pulses(rb, args.workload, mol)
+        pulses = workload_pulses(NAME)
     T, K, W = len(pulses), args.steps, args.warmup
     prop = rb.Propagator(mol, CX, args.prec, integrator=args.integrator)
     prop.set_field(pulses)
@@ -429,7 +572,6 @@ def run_gpu(args):
             pop_info["autocorrelation"] = "recorded at every step, inside the timed region"
     if args.autocorrelation:
         rb.rttda_set_autocorrelation(h, True)
-    dev = torch.device("cuda", local)
     c_out = torch.zeros((T, NDIM, 2), dtype=torch.float64, device=dev)
     dip = torch.zeros((T, K + 1), dtype=torch.float64, device=dev)
     nrm = torch.zeros((T, K + 1), dtype=torch.float64, device=dev)
@@ -468,11 +610,11 @@ def run_gpu(args):
     rb.rttda_sync(h, sptr)
     ms = max_over_ranks(ev0.elapsed_time(ev1))
     value = world * T * K / (ms / 1e3)
-    dip32 = dip.cpu().numpy()
     if args.only_timed:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-                              "warmup": W, "ms_per_step": ms / K, "mode": "only-timed", "prec": args.prec}))
+                              "warmup": W, "ms_per_step": ms / K, "mode": "only-timed", "prec": args.prec,
+                              "workload": NAME, "naux": NAUX, "plan": plan}), flush=True)
         prop.close()
         ranks.close()
         return 0
@@ -485,27 +627,6 @@ def run_gpu(args):
     torch.cuda.synchronize()
     prof = rb.rttda_profile_read(h)
     rb.rttda_profile(h, False)
-
-    # plain FP64 single-trajectory path on the same molecule (the batch's
-    # last trajectory)
-    p64 = rb.Propagator(mol, CX, "fp64", integrator=args.integrator)
-    p64.set_field([pulses[-1]])
-    k64 = max(2, min(args.fp64_steps, K))
-    d64 = torch.zeros((1, k64 + 1), dtype=torch.float64, device=dev)
-    n64 = torch.zeros_like(d64)
-    c64 = torch.zeros((1, NDIM, 2), dtype=torch.float64, device=dev)
-    rb.rttda_propagate_device(p64.h, 0, DT, 1, c64.data_ptr(), d64.data_ptr(), n64.data_ptr(), sptr)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    rb.rttda_propagate_device(p64.h, 0, DT, k64, c64.data_ptr(), d64.data_ptr(), n64.data_ptr(), sptr)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    fp64_rate = k64 / (e0.elapsed_time(e1) / 1e3)
-    d64h = d64.cpu().numpy()[0]
-    ref = d64h - d64h[0]
-    dip_err = float(np.max(np.abs(dip32[T - 1, :k64 + 1] - d64h)) / max(np.max(np.abs(ref)), 1e-300))
-    p64.close()
 
     # end to end through the host-buffer ABI: per step, H2D of the state from
     # pinned memory (rttda_set_state), one RK4 step, D2H of state and traces
@@ -527,6 +648,46 @@ def run_gpu(args):
            "h2d_bytes_per_step": T * NDIM * 16, "d2h_bytes_per_step": T * NDIM * 16 + 2 * T * 2 * 8,
            "steps": ke, "call": "rttda_set_state + rttda_resume(nsteps=1) per step, pinned host buffers"}
 
+    # accuracy of this precision against the FP64-accurate reference:
+    # lowest excitation energies and the kicked probe (same handle, new batch)
+    if ref is not None:
+        tol = {"bf16": 1e-3, "bf16x2": 1e-5}.get(args.prec, 1e-7)
+        w_p, it_p = davidson(rb, prop, ACC_STATES, tol)
+        d_p, n_p = kick_probe(rb, prop, args.acc_steps)
+        dd = ref["dip"] - ref["dip"][0]
+        accuracy = {
+            "reference": "fp64oz (FP64-accurate Ozaki-digit sigma build on the same molecule)",
+            "peak_shift_ha": float(np.max(np.abs(w_p - ref["w"]))),
+            "peak_shift_method": (f"lowest {ACC_STATES} excitation energies (the positions of the lowest spectral "
+                                  "peaks of a kicked spectrum) by Davidson on each precision's own sigma build"),
+            "excitation_energies_ha": w_p.tolist(), "reference_excitation_energies_ha": ref["w"].tolist(),
+            "davidson_iterations": [int(it_p), int(ref["it"])],
+            "norm_drift": float(np.max(np.abs(n_p - ref["nrm"]))),
+            "dipole_rel_err": float(np.max(np.abs(d_p - ref["dip"])) / max(np.max(np.abs(dd)), 1e-300)),
+            "probe": f"z kick kappa={KAPPA} from |0>, {args.acc_steps} RK4 steps of {DT} au (truncated horizon)",
+            "gates": {"peak_shift_ha": 1e-4, "norm_drift": 1e-6},
+            "reference_seconds": ref["s"]}
+        accuracy["passes_gates"] = bool(accuracy["peak_shift_ha"] <= 1e-4 and accuracy["norm_drift"] <= 1e-6)
+    prop.close()
+
+    # plain FP64 single-trajectory path on the same molecule (the batch's
+    # last trajectory)
+    p64 = rb.Propagator(mol, CX, "fp64", integrator=args.integrator)
+    p64.set_field([pulses[-1]])
+    k64 = max(2, min(args.fp64_steps, K))
+    d64 = torch.zeros((1, k64 + 1), dtype=torch.float64, device=dev)
+    n64 = torch.zeros_like(d64)
+    c64 = torch.zeros((1, NDIM, 2), dtype=torch.float64, device=dev)
+    rb.rttda_propagate_device(p64.h, 0, DT, 1, c64.data_ptr(), d64.data_ptr(), n64.data_ptr(), sptr)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rb.rttda_propagate_device(p64.h, 0, DT, k64, c64.data_ptr(), d64.data_ptr(), n64.data_ptr(), sptr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_rate = k64 / (e0.elapsed_time(e1) / 1e3)
+    p64.close()
+
     # roofline of the dominant kernel class
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     ms_cls = {k: v[0] for k, v in prof.items()}
@@ -534,20 +695,24 @@ def run_gpu(args):
     # sigma builds in the profiled call: 4 per RK4 step; 2 per split-operator
     # step plus the call's first half step
     nsig = 4 * kp if args.integrator == "rk4" else 2 * kp + 1
-    roof = roofline(args.prec, dom, prof[dom], T, peaks, nsig)
-    tkey = (args.workload, args.prec, dom, plan["main_kernel"], plan["main_bn"], plan["main_mb"], plan["main_kb"])
-    if tkey in PROFILED_TRAFFIC and plan["z_chunk"] >= NAUX:
-        roof["traffic"] = PROFILED_TRAFFIC[tkey]
-        roof["traffic_source"] = "ncu capture of this kernel and plan (one launch = one sigma build)"
+    roof = roofline(args.prec, dom, prof[dom], T, peaks, nsig, plan)
     roof["class_ms_share"] = {k: round(v / max(sum(ms_cls.values()), 1e-30), 4) for k, v in ms_cls.items()}
     roof["class_ms_per_step"] = {k: round(v / kp, 4) for k, v in ms_cls.items()}
+    roof["classes"] = {k: roofline(args.prec, k, prof[k], T, peaks, nsig, plan)
+                       for k in ("coulomb", "exchange_z") if k in prof and prof[k][1] > 0}
+    for k in list(roof["classes"]):
+        roof["classes"][k] = {kk: roof["classes"][k].get(kk) for kk in
+                              ("bound", "achieved", "peak", "unit", "frac", "ms_per_sigma", "traffic",
+                               "traffic_over_algorithmic")}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        # row block of the explicit A of at most ~1 GB
-        rows_occ = int(max(1, min(8, (1 << 27) // (NVIRT * NDIM))))
-        cb = time_oracle(mol, rows_occ, args.cpu_steps, warmup=1)
-        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        sample = OracleSample(mol, pulses, sample_rows())
+        allc = time_oracle(sample, args.cpu_steps, warmup=1)
+        one = time_oracle_one_core(sample, args.cpu_steps)
+        cpu = {k: allc[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["single_core"] = {k: one.get(k) for k in ("value", "cores", "error") if k in one}
+        cpu["host_cpus"] = os.cpu_count()
 
     dtype = {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "bf16x2": "bf16x2",
              "fp64oz": "f64 (exchange: Ozaki BF16 digits)"}[args.prec]
@@ -558,18 +723,17 @@ def run_gpu(args):
         cfg["autocorrelation"] = "recorded at every step, inside the timed region"
     cfg["integrator"] = {"rk4": "classical RK4 (4 sigma builds per step)",
                          "sso": "symplectic split operator (2 sigma builds per step)"}[args.integrator]
+    cfg["factors"] = ("drawn on the GPU (seeded Philox)" if NAME in DEVICE_FACTORS else "drawn on the host (seeded PCG64)")
     cfg.update(wl_info)
     cfg.update({"fp64_path_traj_steps_per_s": fp64_rate, "speedup_vs_fp64_path": value / world / fp64_rate,
                 "fp64_path": f"plain FP64, one trajectory (the batch's last), {k64} timed steps",
-                "dipole_rel_err_vs_fp64": dip_err, "dipole_err_horizon_steps": k64,
                 "launches_per_step": per_step, "plan": plan})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": dtype, "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu,
-            "e2e": e2e, "gpu_launches": int(launches1 - launches0), "clocks": clk.summary()}
+            "dtype": dtype, "data": "synthetic", "config": cfg, "accuracy": accuracy, "roofline": roof,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches1 - launches0), "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    prop.close()
     ranks.close()
     return 0
 
@@ -674,11 +838,11 @@ def run_serving(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="absorption", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="bf16x2", choices=["fp64", "fp32", "bf16", "bf16x3", "bf16x2", "fp64oz"])
+    ap.add_argument("--workload", default="fieldscan", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "bf16", "bf16x3", "bf16x2", "fp64oz"])
     ap.add_argument("--populations", type=int, default=0,
                     help="record overlaps with this many TI-TDA states (Davidson) at every step")
     ap.add_argument("--autocorrelation", action="store_true", help="record R(t) at every step")
@@ -696,10 +860,17 @@ def main():
     ap.add_argument("--serving-budget-gb", type=float, default=64.0)
     ap.add_argument("--serving-chunk", type=int, default=200)
     ap.add_argument("--serving-seed", type=int, default=5)
-    ap.add_argument("--fp64-steps", type=int, default=4)
-    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy leg against the FP64-accurate (Ozaki-digit) path")
+    ap.add_argument("--acc-steps", type=int, default=ACC_STEPS,
+                    help="RK4 steps of the kicked accuracy probe")
+    ap.add_argument("--time-oracle-sample", default="", help=argparse.SUPPRESS)
+    ap.add_argument("--lambda-min", type=float, default=0.0,
+                    help="field scan: use this lambda_min(A) instead of solving for it (profiler captures)")
     ap.add_argument("--naux", type=int, default=0,
                     help="override the workload's naux (smaller cases for profiler captures; not a bench line)")
     ap.add_argument("--only-timed", action="store_true",
@@ -717,6 +888,10 @@ def main():
         cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
                "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
         return subprocess.call(cmd)
+    if args.time_oracle_sample:
+        r = time_oracle(OracleSample.load(args.time_oracle_sample), args.cpu_steps, warmup=0)
+        print(json.dumps(r), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.accuracy:

@@ -291,14 +291,20 @@ def rttda_set_integrator(h, integrator) -> None:
     _check(lib.rttda_set_integrator(h, code), "rttda_set_integrator")
 
 
-def rttda_eigenstates(h, k: int, dim: int = 0, tol: float = 1e-8, max_iter: int = 200):
+def rttda_eigenstates(h, k: int, dim: int = 0, tol: float = 1e-8, max_iter: int = 200,
+                      allow_unconverged: bool = False):
     """(evals[k], evecs[k][dim] or None when dim = 0, iterations): the k
-    lowest TI-TDA states of A (dim = 1 + nocc * nvirt)."""
+    lowest TI-TDA states of A (dim = 1 + nocc * nvirt).  With
+    allow_unconverged, RTTDA_E_STATE (tolerance not reached within max_iter)
+    returns the last estimates and iterations = -max_iter instead of raising."""
     n = ct.c_int()
     ev = np.zeros(k)
     vecs = np.zeros((k, dim)) if dim else None
-    _check(lib.rttda_eigenstates(h, int(k), float(tol), int(max_iter), _ptr(ev),
-                                 _ptr(vecs) if vecs is not None else None, ct.byref(n)), "rttda_eigenstates")
+    st = lib.rttda_eigenstates(h, int(k), float(tol), int(max_iter), _ptr(ev),
+                               _ptr(vecs) if vecs is not None else None, ct.byref(n))
+    if allow_unconverged and st == E_STATE:
+        return ev, vecs, -int(max_iter)
+    _check(st, "rttda_eigenstates")
     return ev, vecs, n.value
 
 
@@ -471,8 +477,8 @@ class Propagator:
         c = None if c_out is None else c_out[..., 0] + 1j * c_out[..., 1]
         return c, dip, nrm
 
-    def eigenstates(self, k, tol=1e-8, max_iter=200):
-        return rttda_eigenstates(self.h, k, self.n, tol, max_iter)
+    def eigenstates(self, k, tol=1e-8, max_iter=200, allow_unconverged=False):
+        return rttda_eigenstates(self.h, k, self.n, tol, max_iter, allow_unconverged)
 
     def set_projectors(self, X):
         rttda_set_projectors(self.h, X)

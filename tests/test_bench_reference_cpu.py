@@ -1,6 +1,6 @@
 """The benchmark's reference arm on the CPU: `bench.py --impl reference` times
-the FP64 oracle on a bounded row sample of the linear-absorption workload
-and prints one JSON line with the benchmark's metric, unit and direction,
+the FP64 oracle on a bounded row sample of a workload (here the linear-
+absorption one, whose factors the host draws in seconds) and prints one JSON line with the benchmark's metric, unit and direction,
 `impl`, a `cpu_baseline` describing the run and an `e2e` object with no
 host-device traffic."""
 import json
@@ -12,7 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_contract_line():
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "absorption",
+                          "--steps", "1", "--warmup", "3"],
                          cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.strip().startswith("{")]

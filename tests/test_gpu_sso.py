@@ -73,7 +73,9 @@ def test_sso_resume_is_bitwise(rb, prec):
     b.close()
 
 
-@pytest.mark.parametrize("prec,dip_tol", [("bf16x3", 2e-4), ("bf16x2", 1e-2), ("fp32", 1e-5)])
+# about 10x the measured relative dipole error after 400 steps (7e-9, 3e-7,
+# 7e-10 with the FP64-accurate observable)
+@pytest.mark.parametrize("prec,dip_tol", [("bf16x3", 1e-7), ("bf16x2", 3e-6), ("fp32", 1e-8)])
 def test_sso_reduced_precision_against_oracle(rb, prec, dip_tol):
     mol = synth.molecule(8, 64, 48, seed=5)
     pulses = [dict(kind=0, E0=1e-3, direction=d) for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1))]
@@ -85,7 +87,7 @@ def test_sso_reduced_precision_against_oracle(rb, prec, dip_tol):
         d = ref.dipole - ref.dipole[0]
         rel = np.max(np.abs(dip[t] - ref.dipole)) / np.max(np.abs(d))
         assert rel < dip_tol, (prec, t, rel)
-        assert np.max(np.abs(nrm[t] - ref.norm)) < 1e-6, (prec, t)
+        assert np.max(np.abs(nrm[t] - ref.norm)) < 1e-9, (prec, t)
     prop.close()
 
 

@@ -41,7 +41,9 @@ def _two_electron_part(mol, c_x, c):
     return np.array([A2 @ ck for ck in c])
 
 
-@pytest.mark.parametrize("prec,tol2e", [("bf16x3", 2e-4), ("bf16x2", 1e-2), ("bf16", 3e-2)])
+# per-element error bounds relative to the two-electron scale, about 5-8x
+# the largest error measured on these shapes (6e-6, 5e-4, 3e-3)
+@pytest.mark.parametrize("prec,tol2e", [("bf16x3", 5e-5), ("bf16x2", 3e-3), ("bf16", 2e-2)])
 @pytest.mark.parametrize("shape", [(3, 5, 7), (17, 70, 33), (64, 128, 40), (9, 192, 130)])
 def test_sigma_tensorcore_matches_oracle(rb, prec, tol2e, shape):
     mol = synth.molecule(*shape, seed=12)
@@ -75,7 +77,9 @@ def test_bf16x3_exchange_only_matches_oracle_tightly(rb):
     prop.close()
 
 
-@pytest.mark.parametrize("prec,dip_tol", [("bf16x3", 2e-4), ("bf16x2", 1e-2), ("bf16", 5e-2)])
+# relative dipole error after 400 steps, about 10x the measured error
+# (7e-9, 1.5e-7, 3.1e-5 with the FP64-accurate observable)
+@pytest.mark.parametrize("prec,dip_tol", [("bf16x3", 1e-7), ("bf16x2", 2e-6), ("bf16", 3e-4)])
 def test_tensorcore_propagation_against_oracle(rb, prec, dip_tol):
     mol = synth.molecule(8, 64, 48, seed=5)
     pulses = [dict(kind=0, E0=1e-3, direction=d) for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1))]
@@ -88,7 +92,7 @@ def test_tensorcore_propagation_against_oracle(rb, prec, dip_tol):
         d = ref.dipole - ref.dipole[0]
         rel = np.max(np.abs(dip[t] - ref.dipole)) / np.max(np.abs(d))
         assert rel < dip_tol, (prec, t, rel)
-        assert np.max(np.abs(nrm[t] - ref.norm)) < 1e-6, (prec, t)
+        assert np.max(np.abs(nrm[t] - ref.norm)) < 1e-9, (prec, t)
     prop.close()
 
 
@@ -120,7 +124,9 @@ def test_bf16x3_config2_sampled_rows(rb):
         assert np.all(err <= 2e-4 * s2e + 2e-6 * sall + 1e-300), (k, np.max(err / np.maximum(s2e, 1e-300)))
 
 
-@pytest.mark.parametrize("prec,tol2e", [("bf16x3", 2e-4), ("bf16x2", 1e-2), ("bf16", 3e-2)])
+# per-element error bounds relative to the two-electron scale, about 5-8x
+# the largest error measured on these shapes (6e-6, 5e-4, 3e-3)
+@pytest.mark.parametrize("prec,tol2e", [("bf16x3", 5e-5), ("bf16x2", 3e-3), ("bf16", 2e-2)])
 @pytest.mark.parametrize("shape", [(4, 70, 40), (8, 64, 48)])
 def test_batched_sigma_with_tensorcore_coulomb(rb, prec, tol2e, shape):
     """Eight or more trajectories (16+ real columns) route the Coulomb passes
