@@ -184,6 +184,40 @@ def test_M_matches_brute_force_slater_determinants():
     assert np.allclose(Mo, Mb - e0 * np.eye(n), atol=1e-13)
 
 
+def test_dipole_along_matches_brute_force_for_a_mixed_direction():
+    """Eq. (16)'s mu . d for a polarisation mixing all three axes: the CSF
+    dipole matrix built by second quantisation from the combined MO operator
+    sum_x d_x mu_x equals build_M of dipole_along's blocks (a dropped or
+    transposed component, or a wrong block, fails)."""
+    o, v = 2, 3
+    nmo = o + v
+    rng = np.random.default_rng(11)
+    mus = []
+    for _ in range(3):
+        m = rng.standard_normal((nmo, nmo))
+        mus.append(0.5 * (m + m.T))
+    mol = {"nocc": o, "nvirt": v,
+           "mu_oo": np.array([m[:o, :o] for m in mus]),
+           "mu_vv": np.array([m[o:, o:] for m in mus]),
+           "mu_0ov": np.array([math.sqrt(2.0) * m[:o, o:] for m in mus])}
+    d = np.array([0.36, -0.48, 0.8])
+    h = sum(d[x] * mus[x] for x in range(3))
+    ground = 0
+    for i in range(o):
+        ground |= (1 << (2 * i)) | (1 << (2 * i + 1))
+    csfs = [{ground: 1.0}]
+    for i in range(o):
+        for a in range(v):
+            e = np.zeros((nmo, nmo))
+            e[o + a, i] = 1.0
+            st = _apply_one_body({ground: 1.0}, e)
+            csfs.append({det: c / math.sqrt(2.0) for det, c in st.items()})
+    n = len(csfs)
+    Mb = np.array([[_dot(csfs[x], _apply_one_body(csfs[y], h)) for y in range(n)] for x in range(n)])
+    Mo = orc.build_M(*orc.dipole_along(mol, d))
+    assert np.allclose(Mo, Mb - Mb[0, 0] * np.eye(n), atol=1e-13)
+
+
 def test_M_two_level_and_sparsity():
     mu_oo = np.array([[0.3]])
     mu_vv = np.array([[-0.2]])
@@ -588,9 +622,32 @@ def test_spectrum_matches_closed_form_integral():
 
 
 def test_frequency_resolution_matches_paper():
+    """Sec. 3.1 gives 0.057 eV for a 3000 au record, i.e. 2 pi / T.  On the
+    oracle's spectrum of such a record (undamped), two equal lines 2 pi / T
+    apart are resolved: a single line's spectrum vanishes pi / T from its
+    centre, so at their midpoint both vanish; the two maxima sit about that
+    far apart (each pushed out by the other's side lobe).  Lines a quarter
+    of that apart merge into one peak."""
     T, dt, res_ev = np.loadtxt(os.path.join(GOLDEN, "energy_resolution.txt"))
-    assert abs(2 * math.pi / T * HARTREE_EV - res_ev) < 5e-4
-    del dt
+    res = 2 * math.pi / T
+    assert abs(res * HARTREE_EV - res_ev) < 5e-4
+    t = dt * np.arange(int(round(T / dt)) + 1)
+    w1 = 0.5
+
+    def lines(sep):
+        trace = np.sin(w1 * t) + np.sin((w1 + sep) * t)
+        om = np.linspace(w1 - 1.5 * res, w1 + sep + 1.5 * res, 601)
+        S = orc.spectrum(trace, dt, 1.0, 0.0, om)
+        peaks = [k for k in range(1, len(om) - 1) if S[k] > S[k - 1] and S[k] >= S[k + 1] and S[k] > 0.5 * S.max()]
+        return om, S, peaks
+
+    om, S, peaks = lines(res)
+    assert len(peaks) == 2
+    mid = np.argmin(np.abs(om - (w1 + 0.5 * res)))
+    assert abs(S[mid]) < 0.05 * S.max()
+    assert abs(om[peaks[1]] - om[peaks[0]] - res) < 0.2 * res
+    _, _, peaks = lines(0.25 * res)
+    assert len(peaks) == 1
 
 
 def test_kicked_dipole_is_linear_response_and_peaks_at_eigenvalues():
