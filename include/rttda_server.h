@@ -9,9 +9,12 @@
  * its device-memory footprint fits the budget and an active slot is free,
  * keeps its factors and amplitudes resident on the GPU, and advances every
  * active request in chunks of RK4 steps on its own CUDA stream, so the work
- * of different requests overlaps on the device.  A finished request's dipole
- * trace is turned into a spectrum on the GPU; its memory is then released
- * and the next request is admitted.
+ * of different requests overlaps on the device.  Small requests in the BF16
+ * precision (nocc <= 64, nvirt <= 256, naux <= 2048) are instead stepped
+ * together: one persistent kernel per chunk advances every such active
+ * request at once (see rttda_server_set_grouping).  A finished request's
+ * dipole trace is turned into a spectrum on the GPU; its memory is then
+ * released and the next request is admitted.
  *
  * Conventions are those of rttda.h.  All functions are thread-safe.
  */
@@ -92,6 +95,23 @@ rttda_status rttda_server_wait(rttda_server_t s, long id, double timeout_s);
  * in flight and releases its memory).
  * Errors: RTTDA_E_ARG (NULL s, unknown id). */
 rttda_status rttda_server_cancel(rttda_server_t s, long id);
+
+/* Grouped stepping of small BF16 requests (on by default).  With enable != 0
+ * every admitted request with prec = RTTDA_BF16, nocc <= 64, nvirt <= 256
+ * and naux <= 2048 is advanced, chunk by chunk, by one persistent
+ * cooperative kernel that steps all such active requests together (about
+ * forty launches per RK4 step of each request become one launch per chunk
+ * of the group).  Its numerics are those of the BF16 path (BF16 factors and
+ * contraction inputs, FP32 accumulation on the warp-level tensor-core
+ * instructions, FP64 state, FP64-accurate dipole expectation); a request's
+ * results are bitwise the same whichever requests share its group, but not
+ * bitwise equal to a plain rttda_propagate in the BF16 precision, whose
+ * contractions sum in another order.  With enable = 0 they get handles like
+ * every other request.  Applies to requests admitted afterwards.  The
+ * serving pattern of the workload (Sec. 2.2 propagation served as
+ * continuous batching) has no counterpart in the paper.
+ * Errors: RTTDA_E_ARG (NULL s). */
+rttda_status rttda_server_set_grouping(rttda_server_t s, int enable);
 
 /* Counters and latency percentiles of the requests so far (the serving
  * metrics: p50/p99 time to spectrum, trajectory-steps).

@@ -113,13 +113,14 @@ lib.rttda_server_submit.argtypes = [_h, ct.POINTER(rttda_request), ct.POINTER(ct
 lib.rttda_server_poll.argtypes = [_h, ct.c_long, ct.POINTER(ct.c_int), _dp, _dp, _dp, _dp]
 lib.rttda_server_wait.argtypes = [_h, ct.c_long, ct.c_double]
 lib.rttda_server_cancel.argtypes = [_h, ct.c_long]
+lib.rttda_server_set_grouping.argtypes = [_h, ct.c_int]
 lib.rttda_server_stats_get.argtypes = [_h, ct.POINTER(rttda_server_stats)]
 lib.rttda_estimate_bytes.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_long,
                                      ct.POINTER(ct.c_size_t)]
 lib.rttda_server_destroy.argtypes = [_h]
 lib.rttda_server_destroy.restype = None
 for _name in ("rttda_server_create", "rttda_server_submit", "rttda_server_poll", "rttda_server_wait",
-              "rttda_server_cancel", "rttda_server_stats_get", "rttda_estimate_bytes"):
+              "rttda_server_cancel", "rttda_server_set_grouping", "rttda_server_stats_get", "rttda_estimate_bytes"):
     getattr(lib, _name).restype = ct.c_int
 lib.rttda_selftest_wait.argtypes = [ct.c_double]
 lib.rttda_selftest_wait.restype = ct.c_int
@@ -425,6 +426,10 @@ def rttda_server_wait(srv, rid, timeout_s) -> None:
 
 def rttda_server_cancel(srv, rid) -> None:
     _check(lib.rttda_server_cancel(srv, int(rid)), "rttda_server_cancel")
+
+
+def rttda_server_set_grouping(srv, enable: bool) -> None:
+    _check(lib.rttda_server_set_grouping(srv, int(bool(enable))), "rttda_server_set_grouping")
 
 
 def rttda_server_stats_get(srv) -> dict:

@@ -488,6 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      drain_loads(full, it, ST);
     }
   } else if (warp == 1) {
     if (lane == 0) {

