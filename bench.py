@@ -779,59 +779,134 @@ def run_accuracy(args):
 
 
 def run_serving(args):
-    """Continuous-batching trace (scaled-down serving workload): Poisson
-    arrivals, a random molecule, pulse and length per request, admitted by
-    footprint; reports p50/p99 time-to-spectrum and trajectory-steps/s."""
+    """Continuous-batching trace: Poisson arrivals, a random molecule, pulse
+    and length per request, admitted by footprint; reports p50/p99
+    time-to-spectrum and trajectory-steps/s.
+
+    sizes "full" draws the serving workload's molecules (nocc U[16,192],
+    nvirt U[64,1024] with nvirt >= 4 nocc, naux = 4 nvirt) with factors drawn
+    on the GPU and handed to the server as device arrays (host FP64 factors
+    of the largest would take 34 GB each); sizes "small" draws nocc U[16,48],
+    nvirt U[64,192] on the host.  Device factors of a request exist from its
+    arrival until the server admits it; to bound that memory the trace keeps
+    at most --serving-pending such requests waiting in the server, later
+    arrivals wait on the host, and their time to spectrum counts from the
+    arrival."""
     import torch
     from paper_2601_16949_b300 import binding as rb
     from paper_2601_16949_b300 import synth
     torch.cuda.set_device(0)
     rng = np.random.default_rng(args.serving_seed)
     n = args.serving_requests
+    full = args.serving_sizes == "full"
     arrivals = np.cumsum(rng.exponential(1.0 / args.serving_rate, n))
     spec = dict(gamma=1e-3, wmin=0.1, wmax=3.0, nfreq=512)
-    reqs = []
+    shapes = []
     for k in range(n):
         while True:
-            o = int(rng.integers(16, 49))
-            v = int(rng.integers(64, 193))
+            o = int(rng.integers(16, 193 if full else 49))
+            v = int(rng.integers(64, 1025 if full else 193))
             if v >= 4 * o:
                 break
-        P = 4 * v
-        steps = int(rng.integers(200, 2001))
+        steps = int(rng.integers(args.serving_steps_min, args.serving_steps_max + 1))
         if rng.random() < 0.5:
             pulse = dict(kind=rb.KICK, E0=1e-3, direction=(0.0, 0.0, 1.0))
         else:
             pulse = dict(kind=rb.SIN2, E0=float(np.exp(rng.uniform(np.log(1e-3), np.log(5e-2)))),
                          omega=float(rng.uniform(0.4, 2.5)), duration=0.8 * steps * DT, direction=(0.0, 0.0, 1.0))
-        mol = synth.molecule(o, v, P, seed=1000 + k)
-        reqs.append((mol, rb.make_request(mol, CX, args.prec, pulse, DT, steps, **spec), steps))
+        shapes.append((o, v, 4 * v, steps, pulse))
+
+    def make(k):
+        o, v, P, steps, pulse = shapes[k]
+        mol = synth.molecule_device(o, v, P, seed=1000 + k) if full else synth.molecule(o, v, P, seed=1000 + k)
+        return rb.make_request(mol, CX, args.prec, pulse, DT, steps, **spec), mol
+
     srv = rb.rttda_server_create(int(args.serving_budget_gb * (1 << 30)), args.serving_slots, args.serving_chunk)
-    ids = []
+    rb.rttda_server_set_grouping(srv, bool(args.serving_grouping))
+    ids, sub_t = [None] * n, [0.0] * n
+    held = {}   # request index -> its device molecule, until admitted
     t0 = time.perf_counter()
-    for k, (mol, q, steps) in enumerate(reqs):
-        delay = arrivals[k] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        ids.append(rb.rttda_server_submit(srv, q))
+    nxt = 0
+    while nxt < n or held:
+        now = time.perf_counter() - t0
+        # release the device factors of admitted requests
+        for k in list(held):
+            if rb.rttda_server_poll(srv, ids[k])[0] != rb.REQ_PENDING:
+                del held[k]
+        if full:
+            torch.cuda.empty_cache()
+        while nxt < n and arrivals[nxt] <= now and (not full or len(held) < args.serving_pending):
+            (q, mol) = make(nxt)
+            if full:
+                torch.cuda.synchronize()
+            ids[nxt] = rb.rttda_server_submit(srv, q)
+            sub_t[nxt] = time.perf_counter() - t0
+            if full:
+                held[nxt] = (q, mol)
+            nxt += 1
+        time.sleep(0.005)
     for rid in ids:
-        rb.rttda_server_wait(srv, rid, 3600.0)
+        rb.rttda_server_wait(srv, rid, 7200.0)
     wall = time.perf_counter() - t0
     st = rb.rttda_server_stats_get(srv)
-    states = [rb.rttda_server_poll(srv, rid)[0] for rid in ids]
+    polls = [rb.rttda_server_poll(srv, rid) for rid in ids]
     rb.rttda_server_destroy(srv)
+    # time to spectrum from the arrival: host wait before submission plus
+    # the server's submit -> spectrum time
+    tts = np.array([(sub_t[k] - arrivals[k]) + polls[k][4] for k in range(n) if polls[k][0] == rb.REQ_DONE])
     line = {"mode": "serving", "metric": "time-to-spectrum p50/p99 and trajectory-steps/s (continuous batching)",
             "requests": n, "arrival_rate_per_s": args.serving_rate, "precision": args.prec,
-            "workload": ("scaled serving trace: nocc U[16,48], nvirt U[64,192] with nvirt >= 4 nocc, naux = 4 nvirt, "
-                         "kick or sin^2 pulse (E0 log-uniform 1e-3..5e-2), 200-2000 RK4 steps, dt 0.05"),
-            "completed": st["completed"], "failed": st["failed"], "all_done": all(x == rb.REQ_DONE for x in states),
-            "p50_time_to_spectrum_s": st["p50_latency_s"], "p99_time_to_spectrum_s": st["p99_latency_s"],
-            "mean_time_to_spectrum_s": st["mean_latency_s"],
+            "grouping": bool(args.serving_grouping),
+            "workload": (("serving workload sizes: nocc U[16,192], nvirt U[64,1024] with nvirt >= 4 nocc, naux = 4 nvirt, "
+                          "factors drawn on the GPU" if full else
+                          "small molecules: nocc U[16,48], nvirt U[64,192] with nvirt >= 4 nocc, naux = 4 nvirt") +
+                         f"; kick or sin^2 pulse (E0 log-uniform 1e-3..5e-2); {args.serving_steps_min}-"
+                         f"{args.serving_steps_max} RK4 steps of {DT} au"),
+            "completed": st["completed"], "failed": st["failed"],
+            "all_done": all(p[0] == rb.REQ_DONE for p in polls),
+            "p50_time_to_spectrum_s": float(np.percentile(tts, 50)) if len(tts) else None,
+            "p99_time_to_spectrum_s": float(np.percentile(tts, 99)) if len(tts) else None,
+            "mean_time_to_spectrum_s": float(np.mean(tts)) if len(tts) else None,
+            "server_p50_submit_to_spectrum_s": st["p50_latency_s"], "server_p99_submit_to_spectrum_s": st["p99_latency_s"],
             "trajectory_steps_per_s": st["trajectory_steps"] / max(st["busy_seconds"], 1e-9),
             "trajectory_steps": st["trajectory_steps"], "busy_seconds": st["busy_seconds"], "wall_seconds": wall,
-            "max_concurrent": st["max_concurrent"], "slots": args.serving_slots,
+            "max_concurrent": st["max_concurrent"], "grouped_requests": st["grouped"], "slots": args.serving_slots,
             "budget_gb": args.serving_budget_gb, "chunk_steps": args.serving_chunk}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_group_probe(args):
+    """Throughput of S identical small requests submitted at once (kick,
+    BF16), served with the grouped step and with one handle each: the
+    launch-bound regime the grouped step is for."""
+    import torch
+    from paper_2601_16949_b300 import binding as rb
+    from paper_2601_16949_b300 import synth
+    torch.cuda.set_device(0)
+    spec = dict(gamma=1e-3, wmin=0.1, wmax=3.0, nfreq=256)
+    out = []
+    for (o, v) in ((16, 64), (32, 128), (48, 192)):
+        P = 4 * v
+        for S in (1, 16):
+            reqs = [rb.make_request(synth.molecule(o, v, P, seed=2000 + k), CX, "bf16",
+                                    dict(kind=rb.KICK, E0=KAPPA, direction=(0.0, 0.0, 1.0)), DT,
+                                    args.probe_steps, **spec) for k in range(S)]
+            for g in (1, 0):
+                srv = rb.rttda_server_create(64 << 30, S, args.probe_steps)
+                rb.rttda_server_set_grouping(srv, bool(g))
+                t0 = time.perf_counter()
+                ids = [rb.rttda_server_submit(srv, q) for q in reqs]
+                for rid in ids:
+                    rb.rttda_server_wait(srv, rid, 600.0)
+                wall = time.perf_counter() - t0
+                st = rb.rttda_server_stats_get(srv)
+                rb.rttda_server_destroy(srv)
+                out.append({"nocc": o, "nvirt": v, "naux": P, "requests": S, "grouping": g,
+                            "steps_per_request": args.probe_steps, "completed": st["completed"],
+                            "traj_steps_per_s": st["trajectory_steps"] / wall, "wall_s": wall,
+                            "us_per_step_per_request": wall / args.probe_steps * 1e6 / S})
+                print(json.dumps(out[-1]), flush=True)
     return 0
 
 
@@ -860,6 +935,15 @@ def main():
     ap.add_argument("--serving-budget-gb", type=float, default=64.0)
     ap.add_argument("--serving-chunk", type=int, default=200)
     ap.add_argument("--serving-seed", type=int, default=5)
+    ap.add_argument("--group-probe", action="store_true",
+                    help="throughput of identical small requests, grouped step against one handle each")
+    ap.add_argument("--probe-steps", type=int, default=1000)
+    ap.add_argument("--serving-sizes", default="small", choices=["small", "full"])
+    ap.add_argument("--serving-steps-min", type=int, default=200)
+    ap.add_argument("--serving-steps-max", type=int, default=2000)
+    ap.add_argument("--serving-grouping", type=int, default=1, help="1: small BF16 requests stepped together")
+    ap.add_argument("--serving-pending", type=int, default=2,
+                    help="full sizes: most requests with device factors waiting in the server")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=3)
@@ -898,6 +982,8 @@ def main():
         return run_accuracy(args)
     if args.serving:
         return run_serving(args)
+    if args.group_probe:
+        return run_group_probe(args)
     return run_gpu(args)
 
 

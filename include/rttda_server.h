@@ -10,9 +10,9 @@
  * keeps its factors and amplitudes resident on the GPU, and advances every
  * active request in chunks of RK4 steps on its own CUDA stream, so the work
  * of different requests overlaps on the device.  Small requests in the BF16
- * precision (nocc <= 64, nvirt <= 256, naux <= 2048) are instead stepped
- * together: one persistent kernel per chunk advances every such active
- * request at once (see rttda_server_set_grouping).  A finished request's
+ * precision (see rttda_server_set_grouping) are instead stepped together:
+ * one persistent kernel per chunk advances every such active request at
+ * once.  A finished request's
  * dipole trace is turned into a spectrum on the GPU; its memory is then
  * released and the next request is admitted.
  *
@@ -44,6 +44,12 @@ typedef struct {
   long nsteps;         /* >= 1 */
   double gamma, wmin, wmax;
   long nfreq;          /* >= 1 */
+  int factors_on_device;  /* 0: the eight arrays are host memory, copied by
+                             rttda_server_submit.  1: they are device memory of
+                             the server's GPU (e.g. factors drawn there), not
+                             copied; they must stay valid until the request
+                             leaves RTTDA_REQ_PENDING (rttda_server_poll
+                             reports any other state), and may be freed then. */
 } rttda_request;
 
 typedef enum {
@@ -63,6 +69,7 @@ typedef struct {
   double mean_latency_s;
   double busy_seconds;         /* first submit -> last completion            */
   size_t bytes_in_use, bytes_budget;
+  long grouped;                /* requests admitted to the grouped step      */
 } rttda_server_stats;
 
 /* Start a server on the current CUDA device.
@@ -97,8 +104,9 @@ rttda_status rttda_server_wait(rttda_server_t s, long id, double timeout_s);
 rttda_status rttda_server_cancel(rttda_server_t s, long id);
 
 /* Grouped stepping of small BF16 requests (on by default).  With enable != 0
- * every admitted request with prec = RTTDA_BF16, nocc <= 64, nvirt <= 256
- * and naux <= 2048 is advanced, chunk by chunk, by one persistent
+ * every admitted request with prec = RTTDA_BF16, nocc <= 64, nvirt <= 256,
+ * naux <= 2048 and nocc * nvirt^2 * naux <= 3e8 (the sizes whose step is
+ * launch-bound on its own) is advanced, chunk by chunk, by one persistent
  * cooperative kernel that steps all such active requests together (about
  * forty launches per RK4 step of each request become one launch per chunk
  * of the group).  Its numerics are those of the BF16 path (BF16 factors and

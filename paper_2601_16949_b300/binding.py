@@ -45,14 +45,14 @@ class rttda_request(ct.Structure):
                                                         "mu_vv", "mu_0ov")] + \
                [("c_x", ct.c_double), ("prec", ct.c_int), ("pulse", rttda_pulse), ("dt", ct.c_double),
                 ("nsteps", ct.c_long), ("gamma", ct.c_double), ("wmin", ct.c_double), ("wmax", ct.c_double),
-                ("nfreq", ct.c_long)]
+                ("nfreq", ct.c_long), ("factors_on_device", ct.c_int)]
 
 
 class rttda_server_stats(ct.Structure):
     _fields_ = [(n, ct.c_long) for n in ("submitted", "completed", "failed", "cancelled", "pending", "active")] + \
                [("max_concurrent", ct.c_int), ("trajectory_steps", ct.c_double), ("p50_latency_s", ct.c_double),
                 ("p99_latency_s", ct.c_double), ("mean_latency_s", ct.c_double), ("busy_seconds", ct.c_double),
-                ("bytes_in_use", ct.c_size_t), ("bytes_budget", ct.c_size_t)]
+                ("bytes_in_use", ct.c_size_t), ("bytes_budget", ct.c_size_t), ("grouped", ct.c_long)]
 
 
 class rttda_plan_info(ct.Structure):
@@ -387,12 +387,23 @@ def rttda_server_create(hbm_budget, max_active, chunk_steps):
 
 
 def make_request(mol, c_x, prec, pulse, dt, nsteps, gamma, wmin, wmax, nfreq):
-    """Build an rttda_request; the returned tuple keeps the arrays alive."""
-    arrs = [_f64(mol[k]) for k in ("eps_occ", "eps_virt", "B_ov", "B_oo", "B_vv", "mu_oo", "mu_vv", "mu_0ov")]
+    """Build an rttda_request; the returned tuple keeps the arrays alive.
+    A molecule of torch CUDA tensors (float64, contiguous) makes a request
+    with factors_on_device = 1: the tensors must stay alive until the request
+    is no longer pending."""
+    names = ("eps_occ", "eps_virt", "B_ov", "B_oo", "B_vv", "mu_oo", "mu_vv", "mu_0ov")
     q = rttda_request()
     q.nocc, q.nvirt, q.naux = mol["nocc"], mol["nvirt"], mol["naux"]
-    for name, a in zip(("eps_occ", "eps_virt", "B_ov", "B_oo", "B_vv", "mu_oo", "mu_vv", "mu_0ov"), arrs):
-        setattr(q, name, _ptr(a))
+    if getattr(mol["B_vv"], "is_cuda", False):
+        arrs = [mol[k] for k in names]
+        for name, a in zip(names, arrs):
+            setattr(q, name, ct.cast(ct.c_void_p(a.data_ptr()), ct.POINTER(ct.c_double)))
+        q.factors_on_device = 1
+    else:
+        arrs = [_f64(mol[k]) for k in names]
+        for name, a in zip(names, arrs):
+            setattr(q, name, _ptr(a))
+        q.factors_on_device = 0
     q.c_x = float(c_x)
     q.prec = PRECISIONS.get(prec, prec) if isinstance(prec, str) else int(prec)
     q.pulse = make_pulses([pulse])[0]

@@ -44,6 +44,8 @@
 #include <algorithm>
 #include <memory>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -58,13 +60,15 @@ namespace grp {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per barrier wait
-constexpr int kMainBM = 64, kMainBN = 64, kKC = 32;          // main contraction tile, K chunk
+constexpr int kMainBM = 64, kMainBN = 64, kKC = 64;          // main contraction tile, K chunk
 constexpr int kLd = kKC + 8;                                 // padded smem row (bf16): conflict-free fragments
-constexpr long long kMainK = 8192;                           // K elements per main-contraction unit (split-K)
-constexpr int kZP = 4;                                       // P values per Z-build unit
+constexpr long long kMainK = 1024;                           // K elements per main-contraction unit (split-K)
+constexpr int kMainStages = 3;                               // cp.async pipeline depth of the main contraction
+constexpr int kZP = kThreads / 32;                           // P values per Z-build unit (one per warp)
 constexpr int kC1Rows = 8;                                   // P rows per Coulomb pass-1 unit
 constexpr int kRowsPerUnit = 128;                            // amplitude rows per combine unit (2 columns)
-constexpr size_t kSmemBytes = 48 * 1024;
+constexpr size_t kSmemBytes = 64 * 1024;
+constexpr int kMaxPhaseTicks = 4096;
 
 // ---------------------------------------------------------------------------
 // Device helpers
@@ -123,6 +127,8 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, int src_bytes) 
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// all but the newest kMainStages - 2 commit groups complete
+__device__ __forceinline__ void cp_wait_stages() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
@@ -184,7 +190,7 @@ enum Phase : int {
 __device__ __forceinline__ int field_units(const Req& r) { return ((r.o + 7) / 8) * ((r.v + 31) / 32); }
 __device__ __forceinline__ int row_units(const Req& r) { return (r.N + kRowsPerUnit - 1) / kRowsPerUnit; }
 __device__ __forceinline__ int c1_units(const Req& r) { return (r.P + kC1Rows - 1) / kC1Rows; }
-__device__ __forceinline__ int c2_units(const Req& r) { return (r.ov + kThreads - 1) / kThreads; }
+__device__ __forceinline__ int c2_units(const Req& r) { return (r.ov + kThreads / 8 - 1) / (kThreads / 8); }
 __device__ __forceinline__ int z_units(const Req& r) { return 2 * ((r.P + kZP - 1) / kZP); }
 __device__ __forceinline__ int main_units(const Req& r) {
   return r.S * ((2 * r.o + kMainBM - 1) / kMainBM) * ((r.v + kMainBN - 1) / kMainBN);
@@ -235,7 +241,10 @@ __device__ int unit_count(const Req& r, int ph, int k, int stage) {
 // ---------------------------------------------------------------------------
 // Field product rows F_ia = sum_b X_ib mu_ab - sum_j mu_ji X_ja + m_ia X_0
 // (both columns) for an 8 x 32 block of (i, a); TC = float (FP32 stages) or
-// df32 (the step's start).  The same order of operations as k_field_small.
+// df32 (the step's start).  The same order of operations as k_field_small
+// (b ascending, then j ascending, then the ground term); the operands come
+// from shared-memory tiles: the block's 8 rows of X, mu_vv in 32 x 32 tiles
+// and the X rows of 16 values of j at a time.
 template <typename TM, typename TC>
 __device__ void field_unit(const Req& r, int u, const double* X, const TM* moo, const TM* mvv, const TM* m0,
                            uint8_t* smem) {
@@ -245,6 +254,13 @@ __device__ void field_unit(const Req& r, int u, const double* X, const TM* moo, 
   const int i = i0 + ty, a = a0 + tx;
   const int v = r.v, o = r.o;
   TC* xs = reinterpret_cast<TC*>(smem);  // [2][8][v]
+  TC* mt = xs + 2 * 8 * v;               // [32][32]: mu_vv[b0 + bb][a0 + aa]
+  TC* xj = mt + 32 * 32;                 // [2][16][32]: X[(j0 + jj, a0 + aa)]
+  TC* mo_s = xj + 2 * 16 * 32;           // [o][8]: mu_oo[j][i0 + ii]
+  for (int e = threadIdx.x; e < o * 8; e += kThreads) {
+    const int j = e >> 3, ii = e & 7;
+    mo_s[e] = i0 + ii < o ? cvt<TC>(moo[(size_t)j * o + i0 + ii]) : TC(0);
+  }
   for (int e = threadIdx.x; e < 8 * v; e += kThreads) {
     const int ii = e / v, b = e - ii * v;
     const bool ok = i0 + ii < o;
@@ -252,22 +268,41 @@ __device__ void field_unit(const Req& r, int u, const double* X, const TM* moo, 
     xs[e] = ok ? (TC)ldx(X + row * 2) : TC(0);
     xs[8 * v + e] = ok ? (TC)ldx(X + row * 2 + 1) : TC(0);
   }
-  __syncthreads();
   TC fr = TC(0), fi = TC(0);
-  if (a < v) {
-    for (int b = 0; b < v; ++b) {
-      const TC mv = cvt<TC>(mvv[(size_t)b * v + a]);
-      fr = fma(xs[ty * v + b], mv, fr);
-      fi = fma(xs[8 * v + ty * v + b], mv, fi);
+  for (int b0 = 0; b0 < v; b0 += 32) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 32; e += kThreads) {
+      const int bb = e >> 5, aa = e & 31;
+      mt[e] = (b0 + bb < v && a0 + aa < v) ? cvt<TC>(mvv[(size_t)(b0 + bb) * v + a0 + aa]) : TC(0);
+    }
+    __syncthreads();
+    const int nb = min(32, v - b0);
+    for (int bb = 0; bb < nb; ++bb) {
+      const TC mv = mt[bb * 32 + tx];
+      fr = fma(xs[ty * v + b0 + bb], mv, fr);
+      fi = fma(xs[8 * v + ty * v + b0 + bb], mv, fi);
+    }
+  }
+  for (int j0 = 0; j0 < o; j0 += 16) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * 32; e += kThreads) {
+      const int jj = e >> 5, aa = e & 31;
+      const bool ok = j0 + jj < o && a0 + aa < v;
+      const size_t row = 1 + (size_t)(j0 + jj) * v + a0 + aa;
+      xj[e] = ok ? (TC)ldx(X + row * 2) : TC(0);
+      xj[512 + e] = ok ? (TC)ldx(X + row * 2 + 1) : TC(0);
+    }
+    __syncthreads();
+    if (i < o) {
+      const int nj = min(16, o - j0);
+      for (int jj = 0; jj < nj; ++jj) {
+        const TC mo = mo_s[(j0 + jj) * 8 + ty];
+        fr = fma(-mo, xj[jj * 32 + tx], fr);
+        fi = fma(-mo, xj[512 + jj * 32 + tx], fi);
+      }
     }
   }
   if (a < v && i < o) {
-    for (int j = 0; j < o; ++j) {
-      const TC mo = cvt<TC>(moo[(size_t)j * o + i]);
-      const size_t row = 1 + (size_t)j * v + a;
-      fr = fma(-mo, (TC)ldx(X + row * 2), fr);
-      fi = fma(-mo, (TC)ldx(X + row * 2 + 1), fi);
-    }
     const TC mz = cvt<TC>(m0[(size_t)i * v + a]);
     fr = fma(mz, (TC)ldx(X), fr);
     fi = fma(mz, (TC)ldx(X + 1), fi);
@@ -300,6 +335,7 @@ __device__ void c1_unit(const Req& r, int u, const double* X, uint8_t* smem) {
   float s[2 * kC1Rows];
 #pragma unroll
   for (int k = 0; k < 2 * kC1Rows; ++k) s[k] = 0.f;
+#pragma unroll 4
   for (int ia = threadIdx.x; ia < r.ov; ia += kThreads) {
     const float x0 = (float)ldx(X + (size_t)(1 + ia) * 2), x1 = (float)ldx(X + (size_t)(1 + ia) * 2 + 1);
 #pragma unroll
@@ -319,77 +355,98 @@ __device__ void c1_unit(const Req& r, int u, const double* X, uint8_t* smem) {
     }
 }
 
-// Coulomb pass 2: J[ia][col] = 2 sum_p B^p_ia w[p][col] for 256 rows ia.
+// Coulomb pass 2: J[ia][col] = 2 sum_p B^p_ia w[p][col] for 32 rows ia; eight
+// threads per row sum the p of one residue mod 8 each, and the eight sums are
+// added in a fixed tree ((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7)).
 __device__ void c2_unit(const Req& r, int u, uint8_t* smem) {
   float* ws = reinterpret_cast<float*>(smem);
   for (int e = threadIdx.x; e < 2 * r.P; e += kThreads) ws[e] = ldx(r.w + e);
   __syncthreads();
-  const int ia = u * kThreads + threadIdx.x;
+  const int lane8 = threadIdx.x & 7;
+  const int ia = u * (kThreads / 8) + (threadIdx.x >> 3);
+  float j0 = 0.f, j1 = 0.f;
   if (ia < r.ov) {
-    float j0 = 0.f, j1 = 0.f;
-    for (int p = 0; p < r.P; ++p) {
+#pragma unroll 4
+    for (int p = lane8; p < r.P; p += 8) {
       const float b = __bfloat162float(r.Bov[(size_t)p * r.ov + ia]);
       j0 = fmaf(b, ws[2 * p], j0);
       j1 = fmaf(b, ws[2 * p + 1], j1);
     }
+  }
+  // fixed tree within each group of eight lanes
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) {
+    j0 += __shfl_down_sync(0xffffffffu, j0, off);
+    j1 += __shfl_down_sync(0xffffffffu, j1, off);
+  }
+  if (ia < r.ov && lane8 == 0) {
     r.J[(size_t)ia * 2] = 2.f * j0;
     r.J[(size_t)ia * 2 + 1] = 2.f * j1;
   }
   __syncthreads();
 }
 
-// Exchange intermediate for up to kZP values of P and one column:
-// Z^P[(col, i)][b] = sum_j B^P_ij X_(j,b),col  (M = i, N = b, K = j), BF16
-// operands from shared memory, FP32 accumulate, stored as BF16.
+// Exchange intermediate for kZP values of P (one per warp) and one column:
+// Z^P[(col, i)][b] = sum_j B^P_ij X_(j,b),col  (M = i, N = b, K = j).  The
+// column's X^T tile is staged in shared memory once per unit; each warp reads
+// its P's B_oo fragments straight from L2 and runs its MMAs without CTA-wide
+// synchronisation; BF16 operands, FP32 accumulate, stored as BF16.
 __device__ void z_unit(const Req& r, int u, uint8_t* smem) {
   const int col = u & 1, pg = u >> 1;
   const int op = r.op, vp = r.vp, o = r.o, M = 2 * r.o;
   const int ld = op + 8;
   __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(smem);  // [vp][ld]: X^T of this column
-  __nv_bfloat16* bs = xs + (size_t)vp * ld;                    // [op][ld]: B^P_oo
   const int cpr = op / 8;                                      // 16-byte chunks per row
   for (int e = threadIdx.x; e < vp * cpr; e += kThreads) {
     const int b = e / cpr, c = e - b * cpr;
     cp16(xs + (size_t)b * ld + 8 * c, r.Xt + ((size_t)col * vp + b) * op + 8 * c, 16);
   }
+  cp_commit();
+  cp_wait0();
+  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
-  const int mt = op / 16, nt = vp / 8, ks = op / 16;
-  for (int P = pg * kZP; P < min(r.P, pg * kZP + kZP); ++P) {
-    for (int e = threadIdx.x; e < op * cpr; e += kThreads) {
-      const int i = e / cpr, c = e - i * cpr;
-      const bool ok = i < o;
-      cp16(bs + (size_t)i * ld + 8 * c, r.Boo + ((size_t)P * o + (ok ? i : 0)) * op + 8 * c, ok ? 16 : 0);
-    }
-    cp_commit();
-    cp_wait0();
-    __syncthreads();
-    for (int t = warp; t < mt * nt; t += kWarps) {
-      const int mi = t / nt, ni = t - mi * nt;
-      float d[4] = {0.f, 0.f, 0.f, 0.f};
-      const __nv_bfloat16* ar = bs + (size_t)(mi * 16 + g) * ld + 2 * tg;
-      const __nv_bfloat16* br = xs + (size_t)(ni * 8 + g) * ld + 2 * tg;
-      for (int k = 0; k < ks; ++k) {
-        const int k0 = k * 16;
-        mma16816(d, lds32(ar + k0), lds32(ar + 8 * ld + k0), lds32(ar + k0 + 8), lds32(ar + 8 * ld + k0 + 8),
-                 lds32(br + k0), lds32(br + k0 + 8));
-      }
-      const int b = ni * 8 + 2 * tg;
+  const int P = pg * kZP + warp;
+  if (P < r.P) {
+    const int mt = op / 16, nt = vp / 8, ks = op / 16;
+    for (int mi = 0; mi < mt; ++mi) {
+      // A fragments of rows mi*16.. for every k step (zero past nocc)
+      uint32_t af[4][4];
       const int i_lo = mi * 16 + g, i_hi = i_lo + 8;
-      const __nv_bfloat162 lo = __floats2bfloat162_rn(d[0], d[1]);
-      const __nv_bfloat162 hi = __floats2bfloat162_rn(d[2], d[3]);
-      if (i_lo < o)
-        *reinterpret_cast<__nv_bfloat162*>(r.Z + ((size_t)P * M + col * o + i_lo) * vp + b) = lo;
-      if (i_hi < o)
-        *reinterpret_cast<__nv_bfloat162*>(r.Z + ((size_t)P * M + col * o + i_hi) * vp + b) = hi;
+      const uint32_t* rlo = reinterpret_cast<const uint32_t*>(r.Boo + ((size_t)P * o + min(i_lo, o - 1)) * op);
+      const uint32_t* rhi = reinterpret_cast<const uint32_t*>(r.Boo + ((size_t)P * o + min(i_hi, o - 1)) * op);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (k < ks) {
+          const int w0 = (k * 16 + 2 * tg) / 2, w1 = w0 + 4;
+          af[k][0] = i_lo < o ? rlo[w0] : 0u;
+          af[k][1] = i_hi < o ? rhi[w0] : 0u;
+          af[k][2] = i_lo < o ? rlo[w1] : 0u;
+          af[k][3] = i_hi < o ? rhi[w1] : 0u;
+        }
+      }
+      for (int ni = 0; ni < nt; ++ni) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        const __nv_bfloat16* br = xs + (size_t)(ni * 8 + g) * ld + 2 * tg;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < ks) mma16816(d, af[k][0], af[k][1], af[k][2], af[k][3], lds32(br + k * 16), lds32(br + k * 16 + 8));
+        const int b = ni * 8 + 2 * tg;
+        if (i_lo < o)
+          *reinterpret_cast<__nv_bfloat162*>(r.Z + ((size_t)P * M + col * o + i_lo) * vp + b) =
+              __floats2bfloat162_rn(d[0], d[1]);
+        if (i_hi < o)
+          *reinterpret_cast<__nv_bfloat162*>(r.Z + ((size_t)P * M + col * o + i_hi) * vp + b) =
+              __floats2bfloat162_rn(d[2], d[3]);
+      }
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
 // Exchange main contraction, one 64 x 64 tile of K_(col,i),a over the K
 // chunks of split s: K = (P, b) in chunks of 32 (never across two P), A = Z
-// rows, B = B_vv rows (B^P_ab symmetric, stored [P][a][b]).  Double-buffered
-// cp.async tiles; 8 warps as 2 (rows) x 4 (columns), each 32 x 16.
+// rows, B = B_vv rows (B^P_ab symmetric, stored [P][a][b]).  A four-stage
+// cp.async ring of tiles; 8 warps as 2 (rows) x 4 (columns), each 32 x 16.
 __device__ void main_unit(const Req& r, int u, uint8_t* smem) {
   const int M = 2 * r.o, vp = r.vp;
   const int ntn = (r.v + kMainBN - 1) / kMainBN, ntm = (M + kMainBM - 1) / kMainBM;
@@ -399,17 +456,20 @@ __device__ void main_unit(const Req& r, int u, uint8_t* smem) {
   const int KT = r.P * vt;
   const int per = (KT + r.S - 1) / r.S;
   const int kc0 = s * per, kc1 = min(KT, kc0 + per);
-  __nv_bfloat16* as = reinterpret_cast<__nv_bfloat16*>(smem);  // [2][64][kLd]
-  __nv_bfloat16* bsh = as + 2 * kMainBM * kLd;                  // [2][64][kLd]
-  const int row = threadIdx.x >> 2, ch = threadIdx.x & 3;       // 64 rows x 4 chunks of 8
+  __nv_bfloat16* as = reinterpret_cast<__nv_bfloat16*>(smem);  // [kMainStages][64][kLd]
+  __nv_bfloat16* bsh = as + kMainStages * kMainBM * kLd;        // [kMainStages][64][kLd]
   auto load = [&](int kc, int buf) {
-    const int P = kc / vt, b0 = (kc - P * vt) * kKC + 8 * ch;
-    const bool okA = m0 + row < M, okB = n0 + row < r.v;
-    cp16(as + ((size_t)buf * kMainBM + row) * kLd + 8 * ch,
-         r.Z + ((size_t)P * M + (okA ? m0 + row : 0)) * vp + b0, okA ? 16 : 0);
-    cp16(bsh + ((size_t)buf * kMainBN + row) * kLd + 8 * ch,
-         r.Bvv + ((size_t)P * vp + (okB ? n0 + row : 0)) * vp + b0, okB ? 16 : 0);
-    cp_commit();
+    const int P = kc / vt, kb = (kc - P * vt) * kKC;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // 64 rows x 8 chunks of 8 per operand
+      const int e = threadIdx.x + h * kThreads, row = e >> 3, ch = e & 7;
+      const int b0 = kb + 8 * ch;
+      const bool okA = m0 + row < M, okB = n0 + row < r.v;
+      cp16(as + ((size_t)buf * kMainBM + row) * kLd + 8 * ch,
+           r.Z + ((size_t)P * M + (okA ? m0 + row : 0)) * vp + b0, okA ? 16 : 0);
+      cp16(bsh + ((size_t)buf * kMainBN + row) * kLd + 8 * ch,
+           r.Bvv + ((size_t)P * vp + (okB ? n0 + row : 0)) * vp + b0, okB ? 16 : 0);
+    }
   };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
   const int wm = warp >> 2, wn = warp & 3;
@@ -420,16 +480,23 @@ __device__ void main_unit(const Req& r, int u, uint8_t* smem) {
     for (int y = 0; y < 2; ++y)
 #pragma unroll
       for (int z = 0; z < 4; ++z) acc[x][y][z] = 0.f;
-  if (kc0 < kc1) load(kc0, 0);
+  // pipeline: chunks kc0 .. kc0 + kMainStages - 2 in flight before the first
+  // is consumed; one commit group per chunk (empty groups past the end keep
+  // the group count uniform)
+#pragma unroll
+  for (int q = 0; q < kMainStages - 1; ++q) {
+    if (kc0 + q < kc1) load(kc0 + q, q);
+    cp_commit();
+  }
   for (int kc = kc0; kc < kc1; ++kc) {
-    const int buf = (kc - kc0) & 1;
-    if (kc + 1 < kc1) {
-      load(kc + 1, buf ^ 1);
-      cp_wait1();
-    } else {
-      cp_wait0();
-    }
+    const int buf = (kc - kc0) % kMainStages;
+    cp_wait_stages();
     __syncthreads();
+    {
+      const int nk = kc + kMainStages - 1;
+      if (nk < kc1) load(nk, (nk - kc0) % kMainStages);
+      cp_commit();
+    }
     const __nv_bfloat16* A = as + (size_t)buf * kMainBM * kLd;
     const __nv_bfloat16* B = bsh + (size_t)buf * kMainBN * kLd;
 #pragma unroll
@@ -455,8 +522,9 @@ __device__ void main_unit(const Req& r, int u, uint8_t* smem) {
         for (int in = 0; in < 2; ++in)
           mma16816(acc[im][in], af[im][0], af[im][1], af[im][2], af[im][3], bf[in][0], bf[in][1]);
     }
-    __syncthreads();
   }
+  cp_wait0();
+  __syncthreads();
   float* out = r.Kp + (size_t)s * M * r.v;
 #pragma unroll
   for (int im = 0; im < 2; ++im)
@@ -653,11 +721,18 @@ __device__ void run_phase(const Table& tb, int ph, int k, int stage, uint8_t* sm
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_group_chunk(const Table* __restrict__ tbp) {
+__global__ void __launch_bounds__(kThreads, 3) k_group_chunk(const Table* __restrict__ tbp) {
   extern __shared__ __align__(16) uint8_t smem[];
   const Table& tb = *tbp;
   Barrier* bar = tb.bar;
   const unsigned nb = gridDim.x;
+  // optional phase clock: CTA 0 records %globaltimer after every barrier
+  int tick = 0;
+  auto grid_barrier = [&](Barrier* b, unsigned n) {
+    const bool ok = grp::grid_barrier(b, n);
+    if (tb.phase_ns && blockIdx.x == 0 && threadIdx.x == 0 && tick < kMaxPhaseTicks) tb.phase_ns[tick++] = gtimer();
+    return ok;
+  };
   // kick of the requests starting in this chunk (exact exp(i kappa M_d)|0>
   // by its Taylor series, every term's field product in double-float)
   if (tb.kick_terms > 0) {
@@ -730,12 +805,17 @@ double fro_host(const double* a, size_t n) {
 }  // namespace
 
 bool group_eligible(const rttda_request& q) {
-  return q.prec == RTTDA_BF16 && q.nocc <= grp::kMaxO && q.nvirt <= grp::kMaxV && q.naux <= grp::kMaxP;
+  // small BF16 requests whose step is launch-bound: exchange work
+  // nocc nvirt^2 naux multiply-adds per column at most kMaxWork (measured:
+  // grouped steps beat one handle per request up to about nocc 32, nvirt 128,
+  // naux 512, and lose beyond)
+  return q.prec == RTTDA_BF16 && q.nocc <= grp::kMaxO && q.nvirt <= grp::kMaxV && q.naux <= grp::kMaxP &&
+         (double)q.nocc * q.nvirt * q.nvirt * q.naux <= grp::kMaxWork;
 }
 
 size_t group_estimate_bytes(const rttda_request& q) {
   const long long o = q.nocc, v = q.nvirt, P = q.naux;
-  const long long op = cdivl(o, 16) * 16, vp = cdivl(v, 32) * 32, ov = o * v, N = 1 + ov;
+  const long long op = cdivl(o, 16) * 16, vp = cdivl(v, grp::kKC) * grp::kKC, ov = o * v, N = 1 + ov;
   const long long KT = P * (vp / grp::kKC);
   const long long S = std::max<long long>(1, cdivl(KT * grp::kKC, grp::kMainK));
   size_t b = 0;
@@ -759,7 +839,7 @@ rttda_status group_admit(const rttda_request& q, cudaStream_t s, GroupReq** out)
   r.v = v;
   r.P = P;
   r.op = (int)cdivl(o, 16) * 16;
-  r.vp = (int)cdivl(v, 32) * 32;
+  r.vp = (int)cdivl(v, grp::kKC) * grp::kKC;
   r.ov = o * v;
   r.N = 1 + o * v;
   const long long KT = (long long)P * (r.vp / kKC);
@@ -788,11 +868,17 @@ rttda_status group_admit(const rttda_request& q, cudaStream_t s, GroupReq** out)
   // x = kappa sum_x |d_x| (|m_x| + |mu_vv,x| + |mu_oo,x|) on |kappa M_d|
   if (p.kind == RTTDA_KICK) {
     r.kappa = p.E0;
+    // host copies of the dipole blocks (the sources may be host or device)
+    std::vector<double> hm0((size_t)3 * o * v), hmv((size_t)3 * v * v), hmo((size_t)3 * o * o);
+    if (cudaMemcpy(hm0.data(), q.mu_0ov, 8 * hm0.size(), cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(hmv.data(), q.mu_vv, 8 * hmv.size(), cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(hmo.data(), q.mu_oo, 8 * hmo.size(), cudaMemcpyDefault) != cudaSuccess)
+      return set_error(RTTDA_E_CUDA, "grouped request: reading the dipole blocks failed");
     double b = 0.0;
     for (int x = 0; x < 3; ++x)
-      b += std::fabs(dir[x]) * (fro_host(q.mu_0ov + (size_t)x * o * v, (size_t)o * v) +
-                                fro_host(q.mu_vv + (size_t)x * v * v, (size_t)v * v) +
-                                fro_host(q.mu_oo + (size_t)x * o * o, (size_t)o * o));
+      b += std::fabs(dir[x]) * (fro_host(hm0.data() + (size_t)x * o * v, (size_t)o * v) +
+                                fro_host(hmv.data() + (size_t)x * v * v, (size_t)v * v) +
+                                fro_host(hmo.data() + (size_t)x * o * o, (size_t)o * o));
     const double xmax = std::fabs(p.E0) * b;
     int K = 0;
     double term = 1.0;
@@ -844,7 +930,7 @@ rttda_status group_admit(const rttda_request& q, cudaStream_t s, GroupReq** out)
   }
   cudaError_t e = cudaSuccess;
   auto up = [&](double* dst, const double* src, size_t n) {
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, 8 * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, 8 * n, cudaMemcpyDefault, s);  // host or device source
   };
   up(eo, q.eps_occ, o);
   up(ev, q.eps_virt, v);
@@ -927,7 +1013,16 @@ rttda_status group_runner_init(GroupRunner* g) {
   if (e != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("grouped step: ") + cudaGetErrorString(e));
   if (!coop || occ < 1) return set_error(RTTDA_E_CUDA, "grouped step: cooperative launch unavailable");
   g->grid = nsm * occ;
+  // diagnostics: RTTDA_GROUP_PHASE_CLOCK=<file> appends, after every chunk,
+  // the device clock (ns) of each grid barrier relative to the first
+  const char* pc = std::getenv("RTTDA_GROUP_PHASE_CLOCK");
+  if (pc && *pc) {
+    if ((e = cudaMalloc((void**)&g->phase_ns, 8 * kMaxPhaseTicks)) != cudaSuccess)
+      return set_error(RTTDA_E_CUDA, std::string("grouped step: ") + cudaGetErrorString(e));
+    g->phase_file = pc;
+  }
   if ((e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&g->upload, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaMalloc((void**)&g->d_table, sizeof(Table))) != cudaSuccess ||
       (e = cudaMalloc((void**)&g->d_bar, sizeof(Barrier))) != cudaSuccess ||
       (e = cudaMallocHost((void**)&g->h_table, sizeof(Table))) != cudaSuccess ||
@@ -942,9 +1037,12 @@ void group_runner_free(GroupRunner* g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   if (g->d_table) cudaFree(g->d_table);
   if (g->d_bar) cudaFree(g->d_bar);
+  if (g->phase_ns) cudaFree(g->phase_ns);
   if (g->h_table) cudaFreeHost(g->h_table);
+  if (g->upload) cudaStreamSynchronize(g->upload);
   if (g->ev) cudaEventDestroy(g->ev);
   if (g->stream) cudaStreamDestroy(g->stream);
+  if (g->upload) cudaStreamDestroy(g->upload);
   *g = GroupRunner{};
 }
 
@@ -968,8 +1066,10 @@ rttda_status group_launch(GroupRunner* g, const std::vector<GroupReq*>& reqs, co
     t->max_steps = std::max(t->max_steps, r.nsteps);
     t->kick_terms = std::max(t->kick_terms, r.kick_terms);
   }
+  t->phase_ns = g->phase_ns;
   cudaError_t e = cudaMemcpyAsync(g->d_table, t, sizeof(Table), cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_bar, 0, sizeof(Barrier), g->stream);
+  if (e == cudaSuccess && g->phase_ns) e = cudaMemsetAsync(g->phase_ns, 0, 8 * kMaxPhaseTicks, g->stream);
   if (e == cudaSuccess) {
     const Table* arg = g->d_table;
     void* args[] = {(void*)&arg};
@@ -987,6 +1087,16 @@ rttda_status group_status(GroupRunner* g) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("grouped step: ") + cudaGetErrorString(e));
   if (b.err) return set_error(RTTDA_E_TIMEOUT, "grouped step: a grid barrier wait ran out");
+  if (g->phase_ns) {
+    std::vector<unsigned long long> t(grp::kMaxPhaseTicks);
+    if (cudaMemcpy(t.data(), g->phase_ns, 8 * t.size(), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      if (FILE* f = std::fopen(g->phase_file, "a")) {
+        for (size_t k = 1; k < t.size() && t[k]; ++k) std::fprintf(f, "%llu ", t[k] - t[k - 1]);
+        std::fprintf(f, "\n");
+        std::fclose(f);
+      }
+    }
+  }
   return RTTDA_OK;
 }
 

@@ -14,6 +14,7 @@ namespace grp {
 
 // size limits of the grouped path (small molecules, launch-bound otherwise)
 constexpr int kMaxO = 64, kMaxV = 256, kMaxP = 2048;
+constexpr double kMaxWork = 3e8;  // nocc nvirt^2 naux
 
 // one request of a group, as the kernel reads it (device pointers)
 struct Req {
@@ -52,6 +53,7 @@ constexpr int kMaxGroup = 64;
 struct Table {
   int nreq, max_steps, kick_terms;
   Barrier* bar;
+  unsigned long long* phase_ns;  // optional: %globaltimer after every barrier (CTA 0), else NULL
   Req req[kMaxGroup];
 };
 
@@ -68,17 +70,20 @@ struct GroupReq {
 // Group state of a server: table buffers, barrier, stream.
 struct GroupRunner {
   cudaStream_t stream = nullptr;
+  cudaStream_t upload = nullptr;  // admissions: never waits for a running chunk
   grp::Table* d_table = nullptr;
   grp::Table* h_table = nullptr;  // pinned
   grp::Barrier* d_bar = nullptr;
   int grid = 0;
   cudaEvent_t ev = nullptr;
+  unsigned long long* phase_ns = nullptr;  // device clock of every barrier of the last chunk, or NULL
+  const char* phase_file = nullptr;        // diagnostics: where group_status appends those clocks
 };
 
 bool group_eligible(const rttda_request& q);
 size_t group_estimate_bytes(const rttda_request& q);
-// Allocate a grouped request's device state and upload its molecule (host
-// arrays of q, copied before return).
+// Allocate a grouped request's device state and upload its molecule (the
+// arrays of q, host or device memory, are copied before return).
 rttda_status group_admit(const rttda_request& q, cudaStream_t s, GroupReq** out);
 void group_release(GroupReq* g, cudaStream_t s);
 rttda_status group_runner_init(GroupRunner* g);

@@ -84,7 +84,7 @@ struct rttda_server {
   std::vector<Request*> grp_batch;
 
   // statistics
-  long submitted = 0, completed = 0, failed = 0, cancelled = 0;
+  long submitted = 0, completed = 0, failed = 0, cancelled = 0, grouped = 0;
   int max_concurrent = 0;
   double traj_steps = 0.0, first_submit = -1.0, last_done = 0.0;
   std::vector<double> latencies;
@@ -163,7 +163,8 @@ bool rttda_server::admit_one() {
     pending.pop_front();
     used += need;
     r->bytes = need;
-    r->state = RTTDA_REQ_ACTIVE;
+    // the state stays PENDING until the molecule has been copied: a caller
+    // with device factors may free them once the request leaves PENDING
   }
   const rttda_request& q = r->req;
   rttda_status st = RTTDA_OK;
@@ -173,18 +174,13 @@ bool rttda_server::admit_one() {
       st = rttda::group_runner_init(&grp);
       grp_ready = st == RTTDA_OK;
     }
-    rttda_request hq = q;  // the owned host copies
-    hq.eps_occ = r->eps_o.data();
-    hq.eps_virt = r->eps_v.data();
-    hq.B_ov = r->Bov.data();
-    hq.B_oo = r->Boo.data();
-    hq.B_vv = r->Bvv.data();
-    hq.mu_oo = r->moo.data();
-    hq.mu_vv = r->mvv.data();
-    hq.mu_0ov = r->m0.data();
-    if (st == RTTDA_OK) st = rttda::group_admit(hq, grp.stream, &r->g);
-    if (st == RTTDA_OK && cudaMallocAsync((void**)&r->dev, 2 * (size_t)q.nfreq * sizeof(double), grp.stream) !=
-                              cudaSuccess)
+    // r->req points at the owned host copies, or at the caller's device arrays
+    // uploads on the group's admission stream (group_admit synchronises it),
+    // so admitting never waits for the chunk running on the group stream
+    if (st == RTTDA_OK) st = rttda::group_admit(q, grp.upload, &r->g);
+    if (st == RTTDA_OK && (cudaMallocAsync((void**)&r->dev, 2 * (size_t)q.nfreq * sizeof(double), grp.upload) !=
+                               cudaSuccess ||
+                           cudaStreamSynchronize(grp.upload) != cudaSuccess))
       st = RTTDA_E_OOM;
     if (st != RTTDA_OK) {
       r->error = rttda_last_error();
@@ -196,10 +192,16 @@ bool rttda_server::admit_one() {
     std::vector<double>().swap(r->Bvv);
     active.push_back(r);
     max_concurrent = std::max(max_concurrent, (int)active.size());
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      r->state = RTTDA_REQ_ACTIVE;  // group_admit has copied the molecule
+      ++grouped;
+    }
     return true;
   }
-  st = rttda_create(q.nocc, q.nvirt, q.naux, r->eps_o.data(), r->eps_v.data(), r->Bov.data(), r->Boo.data(),
-                    r->Bvv.data(), r->moo.data(), r->mvv.data(), r->m0.data(), q.c_x, q.prec, &r->h);
+  // host copies or the caller's device arrays (the copies inside accept both)
+  st = rttda_create(q.nocc, q.nvirt, q.naux, q.eps_occ, q.eps_virt, q.B_ov, q.B_oo, q.B_vv, q.mu_oo, q.mu_vv,
+                    q.mu_0ov, q.c_x, q.prec, &r->h);
   if (st == RTTDA_OK) st = rttda_set_field(r->h, &q.pulse, 1);
   if (st == RTTDA_OK) {
     const size_t n = 2 * (size_t)(q.nsteps + 1) + 2 * (size_t)q.nfreq;
@@ -213,12 +215,17 @@ bool rttda_server::admit_one() {
     release(r, RTTDA_REQ_FAILED);
     return true;
   }
-  // the factors now live on the device
+  // the factors now live on the device (rttda_set_field synchronised the
+  // handle's stream, so every copy from the caller's arrays has completed)
   std::vector<double>().swap(r->Bov);
   std::vector<double>().swap(r->Boo);
   std::vector<double>().swap(r->Bvv);
   active.push_back(r);
   max_concurrent = std::max(max_concurrent, (int)active.size());
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    r->state = RTTDA_REQ_ACTIVE;
+  }
   return true;
 }
 
@@ -429,14 +436,25 @@ rttda_status rttda_server_submit(rttda_server_t s, const rttda_request* q, long*
   auto r = std::make_unique<Request>();
   const size_t o = q->nocc, v = q->nvirt, P = q->naux;
   r->req = *q;
-  r->eps_o.assign(q->eps_occ, q->eps_occ + o);
-  r->eps_v.assign(q->eps_virt, q->eps_virt + v);
-  r->Bov.assign(q->B_ov, q->B_ov + P * o * v);
-  r->Boo.assign(q->B_oo, q->B_oo + P * o * o);
-  r->Bvv.assign(q->B_vv, q->B_vv + P * v * v);
-  r->moo.assign(q->mu_oo, q->mu_oo + 3 * o * o);
-  r->mvv.assign(q->mu_vv, q->mu_vv + 3 * v * v);
-  r->m0.assign(q->mu_0ov, q->mu_0ov + 3 * o * v);
+  if (!q->factors_on_device) {
+    // host arrays: owned copies until admission
+    r->eps_o.assign(q->eps_occ, q->eps_occ + o);
+    r->eps_v.assign(q->eps_virt, q->eps_virt + v);
+    r->Bov.assign(q->B_ov, q->B_ov + P * o * v);
+    r->Boo.assign(q->B_oo, q->B_oo + P * o * o);
+    r->Bvv.assign(q->B_vv, q->B_vv + P * v * v);
+    r->moo.assign(q->mu_oo, q->mu_oo + 3 * o * o);
+    r->mvv.assign(q->mu_vv, q->mu_vv + 3 * v * v);
+    r->m0.assign(q->mu_0ov, q->mu_0ov + 3 * o * v);
+    r->req.eps_occ = r->eps_o.data();
+    r->req.eps_virt = r->eps_v.data();
+    r->req.B_ov = r->Bov.data();
+    r->req.B_oo = r->Boo.data();
+    r->req.B_vv = r->Bvv.data();
+    r->req.mu_oo = r->moo.data();
+    r->req.mu_vv = r->mvv.data();
+    r->req.mu_0ov = r->m0.data();
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
@@ -539,6 +557,7 @@ rttda_status rttda_server_stats_get(rttda_server_t s, rttda_server_stats* st) {
   st->busy_seconds = s->first_submit >= 0 ? s->last_done - s->first_submit : 0.0;
   st->bytes_in_use = s->used;
   st->bytes_budget = s->budget;
+  st->grouped = s->grouped;
   return RTTDA_OK;
 }
 

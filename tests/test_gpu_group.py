@@ -71,6 +71,7 @@ def mixed(rb):
 def test_grouped_requests_match_the_oracle(rb, mixed):
     out, stats = mixed
     assert stats["completed"] == len(CASES) and stats["max_concurrent"] >= 2 and stats["bytes_in_use"] == 0
+    assert stats["grouped"] == len(CASES)   # every case went through the grouped step
     for (S, dip), case in zip(out, CASES):
         o, v, P, pulse, nsteps, seed = case
         mol = synth.molecule(o, v, P, seed=seed)
@@ -115,7 +116,8 @@ def test_grouped_results_do_not_depend_on_the_chunk_size(rb, mixed):
 
 def test_grouped_path_agrees_with_the_handle_path(rb, mixed):
     out, _ = mixed
-    handles, _ = _serve(rb, CASES, grouping=False)
+    handles, hstats = _serve(rb, CASES, grouping=False)
+    assert hstats["grouped"] == 0
     for k, case in enumerate(CASES):
         dg, dh = out[k][1], handles[k][1]
         scale = np.max(np.abs(dh - dh[0]))
@@ -137,3 +139,27 @@ def test_cancel_grouped_request_releases_its_memory(rb):
     st = rb.rttda_server_stats_get(srv)
     assert st["cancelled"] == 1 and st["completed"] == 1 and st["bytes_in_use"] == 0
     rb.rttda_server_destroy(srv)
+
+
+@pytest.mark.parametrize("grouping", [True, False])
+def test_device_factor_requests_equal_host_factor_requests(rb, grouping):
+    """factors_on_device = 1: the server reads the caller's GPU arrays at
+    admission (grouped path and handle path) and gives bitwise the same
+    result as the same factors passed from the host."""
+    o, v, P, nsteps = 7, 90, 56, 120
+    pulse = dict(kind=4, E0=0.02, omega=0.8, duration=5.0, direction=(0, 1, 0))
+    mol_dev = synth.molecule_device(o, v, P, seed=31)
+    mol_host = {k: (x.cpu().numpy() if hasattr(x, "cpu") else x) for k, x in mol_dev.items()}
+    out = []
+    for mol in (mol_dev, mol_host):
+        srv = rb.rttda_server_create(32 << 30, 2, 50)
+        rb.rttda_server_set_grouping(srv, grouping)
+        q = rb.make_request(mol, CX, "bf16", pulse, DT, nsteps, **SPEC)
+        assert q[0].factors_on_device == (1 if mol is mol_dev else 0)
+        rid = rb.rttda_server_submit(srv, q)
+        rb.rttda_server_wait(srv, rid, 120.0)
+        st, S, om, dip, lat = rb.rttda_server_poll(srv, rid, SPEC["nfreq"], nsteps)
+        assert st == rb.REQ_DONE, rb.rttda_last_error()
+        rb.rttda_server_destroy(srv)
+        out.append(dip)
+    assert np.array_equal(out[0], out[1])
