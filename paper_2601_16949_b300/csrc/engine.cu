@@ -140,6 +140,7 @@ struct rttda_ctx {
   void* mvvC = nullptr;
   void* m0C = nullptr;
   bool any_field = false, any_kick = false;
+  bool same_dir = false;  // every trajectory of the batch has the same polarisation
   int kick_terms = 0;
 
   // state and scratch
@@ -382,7 +383,7 @@ namespace {
 // --- tensor-core exchange -------------------------------------------------
 // Z = B_oo c (K = nocc, short): pipeline stages with hi/lo Z staging (two
 // planes) or one-plane staging
-constexpr int kZBN = 256, kZStages2 = 2, kZStages1 = 2;
+constexpr int kZBN = 256, kZStages2 = 2, kZStages1 = 2, kZStagesR = 3;
 
 // Persistent launch: one CTA per SM (or per tile if fewer tiles).
 template <int BN, int ST, int BM, int EP>
@@ -479,6 +480,7 @@ void tc_attr() {
 void set_tc_smem_limits() {
   tc_attr<kZBN, kZStages2, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>();
   tc_attr<kZBN, kZStages1, tc::BMODE_PLAIN, tc::EPI_ZONE>();
+  tc_attr<kZBN, kZStagesR, tc::BMODE_PLAIN, tc::EPI_ZRES>();
   tc_attr<128, 7, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<224, 5, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<256, 4, tc::BMODE_VV, tc::EPI_PARTIAL>();
@@ -582,6 +584,10 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s, bool xt_done = f
       prm.err = h->d_err;
       if (h->zplanes > 1)
         tc_launch<kZBN, kZStages2, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
+      else if (prm.kt_total <= tc::kResKT)
+        // the amplitude tile (all of K = nocc) stays resident across a
+        // CTA's run of tiles with the same columns (m-fastest order)
+        tc_launch<kZBN, kZStagesR, tc::BMODE_PLAIN, tc::EPI_ZRES>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
       else
         tc_launch<kZBN, kZStages1, tc::BMODE_PLAIN, tc::EPI_ZONE>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
     }
@@ -804,10 +810,24 @@ void coul_stream_attr() {
 
 constexpr int kF0Chunks = 64;  // most chunks of the ground-row field sum
 
+// kernels of one field product: the rows (one kernel, or two GEMMs for a
+// batch with one polarisation), the ground row's chunks and their sum
+inline int field_launches(const rttda_ctx* h) { return (h->same_dir && 2 * h->T >= 8) ? 4 : 3; }
+
 // F = M_d X (singles rows): the register-tiled kernel when its 32 x 64
 // tiles give at least one block per SM, else one output per thread.
 template <typename TM_, typename TC>
 void launch_field(rttda_ctx* h, const double* X, const TM_* moo, const TM_* mvv, const TM_* m0, cudaStream_t s) {
+  const int C = 2 * h->T;
+  if (h->same_dir && C >= 8) {
+    // one polarisation for the whole batch: two GEMMs over the C columns
+    // (the first trajectory's dipole blocks stand for all)
+    k_field_gemm<TM_, TC, false><<<dim3((unsigned)cdiv(C, 64), (unsigned)cdiv(h->v, 64), h->o), 256, 0, s>>>(
+        h->o, h->v, C, X, mvv, m0, h->F);
+    k_field_gemm<TM_, TC, true><<<dim3((unsigned)cdiv(C, 64), (unsigned)cdiv(h->o, 64), h->v), 256, 0, s>>>(
+        h->o, h->v, C, X, moo, m0, h->F);
+    return;
+  }
   const long long tiled = cdiv(h->v, 64) * cdiv(h->o, 32) * (long long)h->T;
   if (tiled >= kNumSM) {
     dim3 g((unsigned)cdiv(h->v, 64), (unsigned)cdiv(h->o, 32), h->T);
@@ -909,7 +929,7 @@ struct Ops {
 
   static void field(rttda_ctx* h, const double* X, cudaStream_t s) {
     Prof pr(h, RTTDA_KC_FIELD, s);
-    h->launches += 3;  // M_d X rows, ground-row chunks, their sum
+    h->launches += field_launches(h);  // M_d X rows, ground-row chunks, their sum
     if (std::is_same<TC, double>::value) {
       launch_field<double, double>(h, X, h->moo64, h->mvv64, h->m064, s);
       launch_field0<double, double>(h, X, h->m064, s);
@@ -929,7 +949,7 @@ struct Ops {
       return;
     }
     Prof pr(h, RTTDA_KC_FIELD, s);
-    h->launches += 3;
+    h->launches += field_launches(h);
     launch_field<double, df32>(h, X, h->moo64, h->mvv64, h->m064, s);
     launch_field0<double, double>(h, X, h->m064, s);
   }
@@ -998,7 +1018,7 @@ void dispatch(int prec, F&& f) {
 // make them cost as much as a few time steps.
 void enqueue_kick(rttda_ctx* h, cudaStream_t s) {
   Prof pr(h, RTTDA_KC_KICK, s);
-  h->launches += 4 * h->kick_terms;
+  h->launches += (field_launches(h) + 1) * h->kick_terms;
   const long long NT = h->N * h->T;
   cudaMemcpyAsync(h->term, h->Xn, sizeof(double) * NT * 2, cudaMemcpyDeviceToDevice, s);
   for (int k = 1; k <= h->kick_terms; ++k) {
@@ -2183,6 +2203,9 @@ rttda_status rttda_set_field(rttda_t h, const rttda_pulse* pulses, int ntraj) {
   h->any_field = any_field;
   h->any_kick = any_kick;
   h->kick_terms = K;
+  h->same_dir = true;
+  for (int t = 1; t < ntraj; ++t)
+    for (int x = 0; x < 3; ++x) h->same_dir = h->same_dir && dirs[3 * t + x] == dirs[x];
   CKS(dalloc(&h->d_pulses, ntraj));
   CKS(dalloc(&h->d_kappa, ntraj));
   CKS(dalloc(&h->d_dirs, 3 * ntraj));

@@ -612,6 +612,99 @@ __global__ void __launch_bounds__(256) k_field_small(int o, int v, int T, const 
   }
 }
 
+// Field product for a batch whose trajectories all share one polarisation
+// (one set of dipole blocks): over the C = 2T real columns it is two GEMMs
+// with contiguous operands,
+//   k_field_vv:  F_(i,a),col  = sum_b mu_ba X_(i,b),col + m_ia X_0,col
+//                (per occupied i: M = a, N = col, K = b)
+//   k_field_oo:  F_(i,a),col -= sum_j mu_ji X_(j,a),col
+//                (per virtual a: M = i, N = col, K = j)
+// 64 x 64 output tiles, 256 threads with 4 x 4 register tiles (4 rows, 4
+// consecutive columns), K in steps of 16 staged in shared memory with the
+// next step's global loads in flight.  TC = float, or df32 for the step's
+// start (the observables).  grid (ceil(C/64), ceil(v/64), o) and
+// (ceil(C/64), ceil(o/64), v).
+template <typename TM, typename TC, bool OO>
+__global__ void __launch_bounds__(256) k_field_gemm(int o, int v, int C, const double* __restrict__ X,
+                                                    const TM* __restrict__ mu, const TM* __restrict__ m0,
+                                                    double* __restrict__ F) {
+  constexpr int BK = 16;
+  __shared__ TC As[2][BK][64];
+  __shared__ TC Bs[2][BK][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int c0 = blockIdx.x * 64, m0r = blockIdx.y * 64, z = blockIdx.z;
+  // OO: rows i, K = j, batch a; else rows a, K = b, batch i
+  const int M = OO ? o : v, K = OO ? o : v;
+  const int lda = OO ? o : v;
+  const size_t bstride = OO ? (size_t)v * C : (size_t)C;
+  const double* Bz = OO ? X + (size_t)(1 + z) * C : X + (size_t)(1 + (size_t)z * v) * C;
+  TC acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = TC(0);
+  TC ra[4], rb[4];
+  auto gload = [&](int k0) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int e = threadIdx.x + 256 * l, kk = e >> 6, mm = e & 63;
+      const int k = k0 + kk;
+      ra[l] = (k < K && m0r + mm < M) ? cvt<TC>(mu[(size_t)k * lda + m0r + mm]) : TC(0);
+      rb[l] = (k < K && c0 + mm < C) ? (TC)Bz[(size_t)k * bstride + c0 + mm] : TC(0);
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int e = threadIdx.x + 256 * l;
+      As[buf][e >> 6][e & 63] = ra[l];
+      Bs[buf][e >> 6][e & 63] = rb[l];
+    }
+  };
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const bool more = k0 + BK < K;
+    if (more) gload(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TC a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[buf][kk][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[buf][kk][tx * 4 + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    if (more) {
+      sstore(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int m = m0r + ty * 4 + r;
+    if (m >= M) continue;
+    const int i = OO ? m : z, a = OO ? z : m;
+    const size_t row = 1 + (size_t)i * v + a;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int col = c0 + tx * 4 + c;
+      if (col >= C) continue;
+      if (OO) {
+        F[row * C + col] -= (double)acc[r][c];
+      } else {
+        F[row * C + col] = (double)fma(cvt<TC>(m0[(size_t)i * v + a]), (TC)X[col], acc[r][c]);
+      }
+    }
+  }
+}
+
 // Ground row of the field product: F_0 = sum_ia m_ia X_ia (Hermitian
 // partner of Eq. (19b)).  Two passes with a fixed order: block (g, t) sums the
 // rows of chunk g (part[(t G + g) 2 + re/im], accumulated in TC), then one

@@ -44,7 +44,13 @@ enum : int { BMODE_PLAIN = 0,  // B[plane][n][k], 3-D map (k, n, plane)
 // epilogue kinds
 enum : int { EPI_PARTIAL = 0,  // out[split][m][n] FP32
              EPI_ZSPLIT = 1,   // Z as BF16 hi/lo planes (see Params)
-             EPI_ZONE = 2 };   // Z as one BF16 plane
+             EPI_ZONE = 2,     // Z as one BF16 plane
+             EPI_ZRES = 3 };   // EPI_ZONE with the B operand resident (K of at most kResKT tiles)
+
+// EPI_ZRES: the whole K extent of the B tile (at most kResKT K tiles) stays
+// in shared memory while a CTA walks its tiles m-fastest, so a B tile is
+// loaded once per run of tiles with the same n0 instead of once per tile.
+constexpr int kResKT = 2;
 
 struct Params {
   int M, N;              // logical output extents
@@ -273,7 +279,7 @@ constexpr int kStageRowWords = 20;
 constexpr int kZGroupBytes = 32 * 128;
 template <int EPI>
 constexpr int zstage_bytes_per_warp() {
-  return EPI == 1 ? 4 * kZGroupBytes : EPI == 2 ? 2 * kZGroupBytes : 0;
+  return EPI == 1 ? 4 * kZGroupBytes : (EPI == 2 || EPI == 3) ? 2 * kZGroupBytes : 0;
 }
 static_assert(2 * 32 * kStageRowWords * 4 <= 2 * kZGroupBytes, "manual staging must fit");
 
@@ -299,13 +305,19 @@ struct Cfg {
 // products of the tile from one stage); the other kinds one plane each.
 template <int EPI>
 constexpr int stage_a_planes() {
-  return EPI == 2 ? 2 : 1;
+  return (EPI == 2 || EPI == 3) ? 2 : 1;
+}
+
+// bytes of one pipeline stage: with EPI_ZRES the A planes only
+template <int BN, int EPI>
+constexpr int stage_bytes() {
+  return EPI == 3 ? 2 * kABytes : Cfg<BN, stage_a_planes<EPI>()>::kStageBytes;
 }
 
 template <int BN, int STAGES, int EPI = 0>
 constexpr size_t smem_bytes() {
-  return (size_t)STAGES * Cfg<BN, stage_a_planes<EPI>()>::kStageBytes + 1024 /*alignment slack*/ +
-         256 /*barriers*/ + (size_t)kEpiWarps * zstage_bytes_per_warp<EPI>();
+  return (size_t)STAGES * stage_bytes<BN, EPI>() + (EPI == 3 ? (size_t)kResKT * BN * 128 : 0) +
+         1024 /*alignment slack*/ + 256 /*barriers*/ + (size_t)kEpiWarps * zstage_bytes_per_warp<EPI>();
 }
 
 // Tile t -> (split, m tile, n tile), n fastest so that consecutive tiles of a
@@ -332,19 +344,25 @@ __global__ void __launch_bounds__(kThreads, 1)
               const __grid_constant__ CUtensorMap tmZ, const Params p) {
   // MERGED: a stage holds A hi, A lo and B hi of one K tile and the MMA warp
   // issues every product of the tile from it (products (hi,hi), (lo,hi),
-  // i.e. nprod <= 2 with alo); otherwise one stage per product
-  constexpr bool MERGED = EPI == EPI_ZONE;
+  // i.e. nprod <= 2 with alo); otherwise one stage per product.  BRES: the
+  // B tile (all K tiles) is resident and stages hold the A planes only.
+  constexpr bool BRES = EPI == EPI_ZRES;
+  constexpr bool MERGED = EPI == EPI_ZONE || BRES;
   using CF = Cfg<BN, stage_a_planes<EPI>()>;
+  constexpr int kStage = stage_bytes<BN, EPI>();
   constexpr int kStgWarp = zstage_bytes_per_warp<EPI>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  // [stages][Z staging (1024-aligned)][barriers]
-  uint8_t* zstage = smem + STAGES * CF::kStageBytes;
+  // [stages][resident B (BRES)][Z staging (1024-aligned)][barriers]
+  uint8_t* bres = smem + STAGES * kStage;
+  uint8_t* zstage = bres + (BRES ? kResKT * CF::kBBytes : 0);
   uint64_t* full = reinterpret_cast<uint64_t*>(zstage + kEpiWarps * kStgWarp);
   uint64_t* empty = full + STAGES;
   uint64_t* accf = empty + STAGES;  // [2] accumulator ready (MMA -> epilogue)
   uint64_t* acce = accf + 2;        // [2] accumulator drained (epilogue -> MMA)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  uint64_t* bfull = acce + 2;       // resident B loaded (BRES)
+  uint64_t* bempty = bfull + 1;     // resident B no longer read by MMAs (BRES)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bempty + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_n = (p.N + BN - 1) / BN;
@@ -360,6 +378,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], kEpiWarps);  // one arrive per epilogue warp
     }
+    mbar_init(bfull, 1);
+    mbar_init(bempty, 1);
     mbar_fence_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, CF::kTmemCols);
@@ -367,17 +387,41 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // tile t -> coordinates: n fastest, or (BRES, one split) m fastest, so that
+  // a CTA's consecutive tiles (t, t + grid, ...) share n0 for long runs
+  auto coord = [&](int t) {
+    if constexpr (BRES) {
+      TileCoord c;
+      c.m0 = (t % tiles_m) * kBM;
+      c.n0 = (t / tiles_m) * BN;
+      c.split = 0;
+      return c;
+    } else {
+      return tile_coord(t, tiles_n, tiles_m, BN);
+    }
+  };
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      int it = 0;
+      int it = 0, bl = 0, cur_n = -1;
       bool alive = true;
       for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
-        const TileCoord tc = tile_coord(t, tiles_n, tiles_m, BN);
+        const TileCoord tc = coord(t);
         const int kr0 = tc.split * p.kt_per_split;
         const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
         const int niter = max(0, kr1 - kr0) * (MERGED ? 1 : p.nprod);
+        if (BRES && tc.n0 != cur_n) {
+          // a new B tile: once the MMAs reading the previous one are done
+          if (bl > 0 && !mbar_wait(bempty, (uint32_t)(bl - 1) & 1u, p.err, ERR_WAIT_EMPTY)) {
+            alive = false;
+            break;
+          }
+          mbar_expect_tx(bfull, (uint32_t)(p.kt_total * CF::kBBytes));
+          for (int k = 0; k < p.kt_total; ++k) tma_load_3d(bres + k * CF::kBBytes, &tmB, bfull, k * kBK, tc.n0, 0);
+          cur_n = tc.n0;
+          ++bl;
+        }
         for (int j = 0; j < niter; ++j, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -387,7 +431,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (MERGED) {
             const int kr = kr0 + j, na = p.nprod >= 2 ? 2 : 1;
-            uint8_t* st = smem + s * CF::kStageBytes;
+            uint8_t* st = smem + s * kStage;
+            if (BRES) {
+              mbar_expect_tx(&full[s], (uint32_t)(na * kABytes));
+              for (int a = 0; a < na; ++a) tma_load_3d(st + a * kABytes, &tmA, &full[s], kr * kBK, tc.m0, a);
+              continue;
+            }
             mbar_expect_tx(&full[s], (uint32_t)(na * kABytes + CF::kBBytes));
             for (int a = 0; a < na; ++a) tma_load_3d(st + a * kABytes, &tmA, &full[s], kr * kBK, tc.m0, a);
             tma_load_3d(st + 2 * kABytes, &tmB, &full[s], kr * kBK, tc.n0, 0);
@@ -398,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // alo the second product is (lo,hi)
           const int pa = (pr == 2 || (pr == 1 && p.alo)) ? 1 : 0;
           const int pb = (pr == 1 && !p.alo) ? 1 : 0;
-          uint8_t* sA = smem + s * CF::kStageBytes;
+          uint8_t* sA = smem + s * kStage;
           uint8_t* sB = sA + kABytes;
           mbar_expect_tx(&full[s], CF::kStageBytes);
           if (BMODE == BMODE_PLAIN)
@@ -414,15 +463,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       drain_loads(full, it, STAGES);
+      if (BRES && bl > 0) mbar_wait(bfull, (uint32_t)(bl - 1) & 1u, nullptr, 0);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
       constexpr uint32_t idesc = idesc_bf16(kBM, BN);
-      int it = 0, tcount = 0;
+      int it = 0, tcount = 0, bl = 0, cur_n = -1;
       bool alive = true;
       for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x, ++tcount) {
-        const TileCoord tc = tile_coord(t, tiles_n, tiles_m, BN);
+        const TileCoord tc = coord(t);
         const int kr0 = tc.split * p.kt_per_split;
         const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
         const int niter = max(0, kr1 - kr0) * (MERGED ? 1 : p.nprod);
@@ -430,6 +480,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
         if (!mbar_wait(&acce[buf], aph ^ 1u, p.err, ERR_WAIT_ACC)) break;
         tc_fence_after();
+        if (BRES && tc.n0 != cur_n) {
+          if (!mbar_wait(bfull, (uint32_t)bl & 1u, p.err, ERR_WAIT_FULL)) break;
+          tc_fence_after();
+          cur_n = tc.n0;
+          ++bl;
+        }
         const uint32_t dcol = tmem + (buf ? CF::kAccCols : 0u);
         for (int j = 0; j < niter; ++j, ++it) {
           const int s = it % STAGES;
@@ -439,9 +495,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t aaddr = smem_u32(smem + s * CF::kStageBytes);
+          const uint32_t aaddr = smem_u32(smem + s * kStage);
           if (MERGED) {
-            const uint64_t bdesc = sdesc_sw128(aaddr + 2 * kABytes);
+            const uint64_t bdesc =
+                sdesc_sw128(BRES ? smem_u32(bres + (kr0 + j) * CF::kBBytes) : aaddr + 2 * kABytes);
             for (int pr = 0; pr < p.nprod; ++pr) {
               const uint64_t adesc = sdesc_sw128(aaddr + pr * kABytes);
 #pragma unroll
@@ -458,6 +515,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           mma_commit(&empty[s]);
         }
         mma_commit(&accf[buf]);
+        if (BRES) {
+          // the resident B is released after the last tile that reads it
+          const int tn = t + (int)gridDim.x;
+          if (tn >= ntiles || coord(tn).n0 != cur_n) mma_commit(bempty);
+        }
       }
     }
   } else {
@@ -471,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int tcount = 0;
     int zcount = 0;  // TMA-stored Z chunks of this warp (staging double buffer)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tcount) {
-      const TileCoord tc = tile_coord(t, tiles_n, tiles_m, BN);
+      const TileCoord tc = coord(t);
       const int kr0 = tc.split * p.kt_per_split;
       const int kr1 = min(p.kt_total, kr0 + p.kt_per_split);
       const bool has_k = kr1 > kr0;

@@ -247,3 +247,46 @@ def test_field_product_on_the_register_tiled_kernel(rb, prec, tol):
         scale = np.abs(A) @ np.abs(c[k]) + abs(E) * (np.abs(Ms[k % 4]) @ np.abs(c[k]))
         assert np.max(np.abs(got[k] - ref) / np.maximum(scale, 1e-300)) < tol, (prec, k)
     prop.close()
+
+
+# A batch whose trajectories all share one polarisation takes the field
+# product as two GEMMs over its 2T columns (k_field_gemm): sigma and a
+# propagation against the oracle, ragged against the 64 x 64 tiles.
+ONE_DIR = [dict(kind=1, E0=0.03, omega=0.7, direction=(0, 0.6, 0.8)),
+           dict(kind=2, E0=0.05, omega=0.9, t0=2.0, fwhm=1.7, direction=(0, 0.6, 0.8)),
+           dict(kind=4, E0=0.05, omega=1.1, duration=4.0, direction=(0, 0.6, 0.8)),
+           dict(kind=3, E0=0.04, omega=0.6, t0=1.5, fwhm=2.5, beta=0.3, direction=(0, 0.6, 0.8)),
+           dict(kind=1, E0=0.02, omega=0.4, direction=(0, 0.6, 0.8))]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp64oz", 2e-12), ("fp32", 2e-6)])
+@pytest.mark.parametrize("shape", [(5, 37, 19), (70, 66, 40)])
+def test_sigma_one_polarisation_batch_matches_oracle(rb, prec, tol, shape):
+    mol = synth.molecule(*shape, seed=14)
+    prop = rb.Propagator(mol, 0.2, prec)
+    prop.set_field(ONE_DIR)
+    c = synth.random_state(prop.n, len(ONE_DIR), seed=15)
+    for t in (0.4, 2.3):
+        got = _sigma_gpu(rb, prop, c, t)
+        ref = oracle_sigma(mol, 0.2, ONE_DIR, c, t)
+        err = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)
+        assert np.all(err < tol), (prec, shape, t, err)
+    prop.close()
+
+
+@pytest.mark.parametrize("prec,dip_tol", [("fp64", 1e-12), ("bf16", 3e-4)])
+def test_one_polarisation_batch_propagation_matches_oracle(rb, prec, dip_tol):
+    """The double-float field product of each step's start (the dipole) in
+    the GEMM form; the FP64 path to 1e-12."""
+    mol = synth.molecule(6, 50, 36, seed=16)
+    pulses = ONE_DIR[:4]
+    prop = rb.Propagator(mol, 0.2, prec)
+    prop.set_field(pulses)
+    _, dip, nrm = prop.propagate(0.05, 160)
+    prop.close()
+    refs = oracle_runs(mol, 0.2, pulses, 0.05, 160)
+    for t, ref in enumerate(refs):
+        d = ref.dipole - ref.dipole[0]
+        rel = np.max(np.abs(dip[t] - ref.dipole)) / np.max(np.abs(d))
+        assert rel < dip_tol, (prec, t, rel)
+        assert np.max(np.abs(nrm[t] - ref.norm)) < 1e-9
