@@ -177,6 +177,8 @@ struct rttda_ctx {
   int wide_mb = 0;                   // >0: main contraction on the wide-M kernel with this many 128-row blocks
   int wide_kb = 32;                  // K tile width of the wide-M kernel (32 or 64 BF16)
   bool wide_tr = false;              // wide kernel with the contraction transposed (rows a)
+  int z_hint = 1;                    // Z stores evict-first in L2 (RTTDA_ZHINT)
+  int z_run = 4;                     // Z-build tiles per CTA and column run in a slab, 0: no slabs (RTTDA_ZRUN)
   int integrator = RTTDA_INT_RK4;    // rttda_integrator
   // projectors (Eq. (22)) and the overlaps of the last propagation
   int nproj = 0;
@@ -581,6 +583,8 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s, bool xt_done = f
       prm.vp = vp;
       prm.zrows = C * o;
       prm.ztma = (o % 32 == 0) ? 1 : 0;
+      prm.zhint = h->z_hint;
+      prm.zrun = h->z_run;
       prm.err = h->d_err;
       if (h->zplanes > 1)
         tc_launch<kZBN, kZStages2, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
@@ -1902,6 +1906,8 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
   CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
   AllocStream as(h->stream);
   dispatch(h->prec, [&](auto ops) { decltype(ops)::set_smem_limits(); });
+  if (const char* e = std::getenv("RTTDA_ZHINT")) h->z_hint = std::atoi(e) != 0;
+  if (const char* e = std::getenv("RTTDA_ZRUN")) h->z_run = std::max(0, std::atoi(e));
   const size_t o = h->o, v = h->v, P = h->P;
   const size_t chunk = (size_t)1 << 26;  // elements per staging pass
   const size_t stage_n = std::min(chunk, std::max({P * o * v, P * o * o, P * v * v}));

@@ -71,6 +71,12 @@ struct Params {
   int o, vp;
   int zrows;             // C * o rows per K tile
   int ztma;              // 1: store Z chunks with TMA (nocc % 32 == 0)
+  int zhint;             // 1: Z stores under the L2 evict-first policy
+  // EPI_ZRES tile order: slabs of gridDim.x * zrun row tiles; inside a slab
+  // the columns advance slowest, so each CTA runs zrun tiles per resident B
+  // tile and the slab's A rows stay in L2 across all column tiles
+  // (0: one slab of all rows)
+  int zrun;
   int* err;
 };
 
@@ -166,6 +172,23 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void*
           reinterpret_cast<uint64_t>(map)),
       "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
+}
+// The same store with an L2 cache policy (createpolicy).
+__device__ __forceinline__ void tma_store_4d_hint(const CUtensorMap* map, const void* src, int c0, int c1, int c2,
+                                                  int c3, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%2, %3, %4, %5}], [%1], %6;" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "l"(policy)
+      : "memory");
+}
+// L2 policy under which the lines a kernel writes are the first to be
+// evicted: a write stream (Z) then leaves the operands it is computed from
+// in L2.
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
@@ -389,11 +412,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
   // tile t -> coordinates: n fastest, or (BRES, one split) m fastest, so that
   // a CTA's consecutive tiles (t, t + grid, ...) share n0 for long runs
+  const int slab_w = (BRES && p.zrun > 0) ? min(tiles_m, (int)gridDim.x * p.zrun) : tiles_m;
+  const int slab_full = (tiles_m / slab_w) * slab_w * tiles_n;  // tiles in full slabs
   auto coord = [&](int t) {
     if constexpr (BRES) {
       TileCoord c;
-      c.m0 = (t % tiles_m) * kBM;
-      c.n0 = (t / tiles_m) * BN;
+      int m, n;
+      if (t < slab_full) {
+        const int s = t / (slab_w * tiles_n), rem = t - s * slab_w * tiles_n;
+        n = rem / slab_w;
+        m = s * slab_w + rem % slab_w;
+      } else {  // the last, narrower slab
+        const int rem = t - slab_full, w = tiles_m - (tiles_m / slab_w) * slab_w;
+        n = rem / w;
+        m = (tiles_m / slab_w) * slab_w + rem % w;
+      }
+      c.m0 = m * kBM;
+      c.n0 = n * BN;
       c.split = 0;
       return c;
     } else {
@@ -616,8 +651,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0 && n < p.N && mb < p.M && ok) {
               const int col = n / p.vp, b = n - col * p.vp;
               const int kt = Pb * vt + (b >> 6);
-              tma_store_4d(&tmZ, wst + (zb * ZPL) * kZGroupBytes, 0, col * p.o + ib, kt, 0);
-              if (two) tma_store_4d(&tmZ, wst + (zb * ZPL + 1) * kZGroupBytes, 0, col * p.o + ib, kt, 1);
+              if (p.zhint) {
+                const uint64_t pol = l2_policy_evict_first();
+                tma_store_4d_hint(&tmZ, wst + (zb * ZPL) * kZGroupBytes, 0, col * p.o + ib, kt, 0, pol);
+                if (two) tma_store_4d_hint(&tmZ, wst + (zb * ZPL + 1) * kZGroupBytes, 0, col * p.o + ib, kt, 1, pol);
+              } else {
+                tma_store_4d(&tmZ, wst + (zb * ZPL) * kZGroupBytes, 0, col * p.o + ib, kt, 0);
+                if (two) tma_store_4d(&tmZ, wst + (zb * ZPL + 1) * kZGroupBytes, 0, col * p.o + ib, kt, 1);
+              }
             }
             if (lane == 0) bulk_commit();
           }

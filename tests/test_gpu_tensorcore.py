@@ -4,7 +4,7 @@ import pytest
 
 from oracle import rttda_oracle as orc
 from paper_2601_16949_b300 import synth
-from tests._util import oracle_runs, oracle_sigma, to_ri, unit
+from tests._util import oracle_pulse, oracle_runs, oracle_sigma, to_ri, unit
 
 pytestmark = pytest.mark.gpu
 
@@ -234,3 +234,44 @@ def test_transposed_plan_for_one_trajectory(rb, prec, monkeypatch):
     for plan, got in outs.items():
         assert np.max(np.abs(got - outs["160,3,32"])) <= 2e-5 * scale, plan
         assert np.max(np.abs(got - ref)) <= tol * scale, plan
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x2"])
+def test_z_build_tile_order_and_l2_policy_do_not_change_sigma(rb, prec, monkeypatch):
+    """The one-plane Z build visits its tiles in slabs of row tiles
+    (RTTDA_ZRUN tiles per CTA and column run; 0 = one slab) and stores Z
+    under an L2 evict-first policy (RTTDA_ZHINT).  Neither changes any
+    arithmetic: sigma is bitwise the same for every setting, here with
+    768 row tiles (several slabs, the last one narrower) and a ragged last
+    column tile, and it matches the oracle's rows of A and M_d."""
+    mol = synth.molecule(64, 64, 1536, seed=5)
+    c_x, t = 0.2, 0.9
+    c = synth.random_state(1 + 64 * 64, len(PULSES), seed=8)
+    out = {}
+    for hint, run in ((1, 4), (0, 0), (1, 1), (0, 7)):
+        monkeypatch.setenv("RTTDA_ZHINT", str(hint))
+        monkeypatch.setenv("RTTDA_ZRUN", str(run))
+        prop = rb.Propagator(mol, c_x, prec)
+        prop.set_field(PULSES)
+        out[(hint, run)] = _sigma_gpu(rb, prop, c, t)
+        prop.close()
+    base = out[(1, 4)]
+    for k, v in out.items():
+        assert np.array_equal(v, base), k
+    n = 1 + 64 * 64
+    rows = np.concatenate([[0, 1, n - 1], np.random.default_rng(3).choice(np.arange(2, n - 1), 13, replace=False)])
+    Arows = orc.A_rows(mol, c_x, rows)
+    m0 = dict(mol)
+    m0["eps_occ"] = np.zeros_like(mol["eps_occ"])
+    m0["eps_virt"] = np.zeros_like(mol["eps_virt"])
+    A2rows = orc.A_rows(m0, c_x, rows)
+    tol = {"bf16": 2e-2, "bf16x2": 3e-3}[prec]
+    for k, pk in enumerate(PULSES):
+        d = unit(pk["direction"])
+        Mrows = orc.M_rows(*orc.dipole_along(mol, d), rows)
+        E = orc.field(oracle_pulse(pk), t)
+        ref = Arows @ c[k] - E * (Mrows @ c[k])
+        s2e = np.abs(A2rows) @ np.abs(c[k])
+        sall = np.abs(Arows) @ np.abs(c[k]) + abs(E) * (np.abs(Mrows) @ np.abs(c[k]))
+        err = np.abs(base[k, rows] - ref)
+        assert np.all(err <= tol * s2e + 2e-6 * sall), (prec, k, np.max(err / np.maximum(s2e, 1e-300)))
