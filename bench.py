@@ -393,12 +393,12 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 
 
 def profiled_traffic(prec: str, cls: str, plan: dict):
-    """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
-    launch of a kernel class, from the committed ncu summary table
-    profiles/dram_traffic.txt, for this workload, precision and plan; None
-    when the table has no capture of exactly this kernel and plan."""
-    if not os.path.exists(TRAFFIC_FILE):
-        return None
+    """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per sigma
+    build of a kernel class's main kernel, from the committed ncu summary
+    table profiles/dram_traffic.txt, for this workload, precision and plan;
+    None when the table has no capture of exactly this kernel and plan."""
+    if not os.path.exists(TRAFFIC_FILE) or plan.get("z_chunk") != NAUX:
+        return None  # the table's captures are of the unchunked exchange
     want = [NAME, str(NAUX), prec, cls, str(plan.get("main_kernel")), str(plan.get("main_bn")),
             str(plan.get("main_mb")), str(plan.get("main_kb")), str(plan.get("main_splits"))]
     for line in open(TRAFFIC_FILE):
@@ -491,7 +491,11 @@ def roofline(prec: str, cls: str, prof_entry, T: int, peaks: dict, nsigma: int, 
         out["hardware_tflops"] = hw_flop / sec / 1e12
     tr = profiled_traffic(prec, cls, plan)
     if tr is not None:
-        out["traffic"] = tr["bytes"] * out["launches_per_sigma"]
+        # the table holds the captured kernel's bytes per sigma build (one
+        # launch per stage with the exchange unchunked); the class's other
+        # launches (the BF16 amplitude planes before the Z build) are not
+        # counted
+        out["traffic"] = tr["bytes"]
         out["traffic_source"] = tr["source"] + " (ncu dram__bytes_read.sum + dram__bytes_write.sum, this plan)"
         out["traffic_over_algorithmic"] = out["traffic"] / byts
     return out
