@@ -963,10 +963,22 @@ struct Ops {
     Prof pr(h, RTTDA_KC_COMBINE, s);
     h->launches += 1;
     const int C = 2 * h->T;
-    k_combine<TC><<<blocks_for(h->N * 2 * h->T, 256), 256, 0, s>>>(
-        mode, stage, h->N, h->o, h->v, h->T, h->eps_o, h->eps_v, h->cx, (const TC*)h->Jpart, h->SJ,
-        (const TC*)h->Kpart, h->SK, (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn, Xin,
-        Xnext, h->acc, sig_out, step_ctr);
+    // column tile: all C columns when C <= 32 (C is even), else 32
+    const int cc = C >= 32 ? 32 : C > 8 ? 16 : C > 4 ? 8 : C > 2 ? 4 : 2;
+    const dim3 grid((unsigned)cdiv(h->N, kCombineTile / cc), (unsigned)cdiv(C, cc));
+    auto go = [&](auto kern) {
+      kern<<<grid, 256, 0, s>>>(mode, stage, h->N, h->o, h->v, h->T, h->eps_o, h->eps_v, h->cx,
+                                (const TC*)h->Jpart, h->SJ, (const TC*)h->Kpart, h->SK,
+                                (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn, Xin, Xnext,
+                                h->acc, sig_out, step_ctr);
+    };
+    switch (cc) {
+      case 2: go(k_combine<TC, 2>); break;
+      case 4: go(k_combine<TC, 4>); break;
+      case 8: go(k_combine<TC, 8>); break;
+      case 16: go(k_combine<TC, 16>); break;
+      default: go(k_combine<TC, 32>); break;
+    }
   }
 
   // split-operator sub-step on the stage input X (in place); see k_sso_update
@@ -975,10 +987,22 @@ struct Ops {
     Prof pr(h, RTTDA_KC_COMBINE, s);
     h->launches += 1;
     const int C = 2 * h->T;
-    k_sso_update<TC><<<blocks_for(h->N * h->T, 256), 256, 0, s>>>(
-        mode, stage, h->N, h->o, h->v, h->T, h->eps_o, h->eps_v, h->cx, (const TC*)h->Jpart, h->SJ,
-        (const TC*)h->Kpart, h->SK, (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn, X,
-        step_ctr);
+    // trajectory tile: all T when T <= 32, else 32
+    const int ct = h->T >= 32 ? 32 : h->T > 8 ? 16 : h->T > 4 ? 8 : h->T > 2 ? 4 : h->T > 1 ? 2 : 1;
+    const dim3 grid((unsigned)cdiv(h->N, kCombineTile / ct), (unsigned)cdiv(h->T, ct));
+    auto go = [&](auto kern) {
+      kern<<<grid, 256, 0, s>>>(mode, stage, h->N, h->o, h->v, h->T, h->eps_o, h->eps_v, h->cx,
+                                (const TC*)h->Jpart, h->SJ, (const TC*)h->Kpart, h->SK,
+                                (long long)C * h->o * h->v, h->F, h->E, use_field ? 1 : 0, dt, h->Xn, X, step_ctr);
+    };
+    switch (ct) {
+      case 1: go(k_sso_update<TC, 1>); break;
+      case 2: go(k_sso_update<TC, 2>); break;
+      case 4: go(k_sso_update<TC, 4>); break;
+      case 8: go(k_sso_update<TC, 8>); break;
+      case 16: go(k_sso_update<TC, 16>); break;
+      default: go(k_sso_update<TC, 32>); break;
+    }
   }
 
   static void set_smem_limits() {

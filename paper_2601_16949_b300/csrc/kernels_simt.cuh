@@ -756,7 +756,7 @@ __global__ void k_efield(int T, const PulseDev* __restrict__ pulses, const long 
 }
 
 // ---------------------------------------------------------------------------
-// sigma assembly and RK4 stage update (one thread per amplitude row n).
+// sigma assembly and RK4 stage update.
 //   sigma_n = (e_a - e_i) X_n + J_n - c_x K_n - E_t F_n      (n = ia)
 //   sigma_0 = -E_t F_0                                        (A_00 = 0)
 //   k = -i sigma
@@ -766,9 +766,17 @@ __global__ void k_efield(int T, const PulseDev* __restrict__ pulses, const long 
 //   s=2: acc += 2k;    Xs = Xn + dt k
 //   s=3: Xn += dt/6 (acc + k);  Xs = Xn
 // mode 1: write sigma to sig_out (same layout as X).
-// Kpart is the exchange partial sum laid out [s][(col*o + i)][a].
+// Kpart is the exchange partial sum laid out [s][(col*o + i)][a], i.e.
+// contiguous along n for a fixed column, while X, F, acc and Jpart hold the
+// C = 2T columns of a row contiguously.  A CTA takes a tile of R rows by CC
+// columns (R CC = 1024): it first sums the exchange partials with threads
+// running along n (coalesced along a) into shared memory, then assembles
+// and updates the tile with threads running along the columns (coalesced
+// along col).  The arithmetic per element is the same in both layouts.
 // ---------------------------------------------------------------------------
-template <typename TC>
+constexpr int kCombineTile = 1024;  // elements per CTA tile
+
+template <typename TC, int CC>
 __global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long N, int o, int v, int T,
                                                  const double* __restrict__ eps_o,
                                                  const double* __restrict__ eps_v, double cx,
@@ -779,58 +787,76 @@ __global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long 
                                                  const double* __restrict__ Xs, double* __restrict__ Xs_next,
                                                  double* __restrict__ acc, double* __restrict__ sig_out,
                                                  long long* __restrict__ step_ctr) {
+  constexpr int R = kCombineTile / CC;
+  static_assert(R * CC == kCombineTile && kCombineTile % 256 == 0, "tile of 1024 elements");
+  __shared__ double ksum_s[CC][R + 1];
   // step_ctr (the last stage of a step): advance the step counter; nothing in
   // this kernel reads it and everything of the step before it already has.
-  if (step_ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
-  // one thread per (trajectory t, part q, row n), n fastest.  Xs is this
-  // stage's input and is only read; the next stage's input goes to Xs_next.  sigma_q is the
-  // real (q = 0) or imaginary (q = 1) part; k = -i sigma swaps them, so the
-  // thread updates the other part of k: k_re = sigma_im, k_im = -sigma_re.
-  // N * 2T < 2^31 (checked by the host): 32-bit index arithmetic
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n32 = (int)N;
-  if (e >= n32 * 2 * T) return;
-  const int n = e % n32;
-  const int tq = e / n32, t = tq >> 1, q = tq & 1;
-  const int C = 2 * T, col = 2 * t + q;
+  if (step_ctr != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *step_ctr += 1;
+  const int C = 2 * T;
+  const long long n0 = (long long)blockIdx.x * R;
+  const int c0 = blockIdx.y * CC;
   const long long ov = N - 1;
-  const size_t idx = (size_t)n * C + col;
-  double sg = 0.0;
-  if (n > 0) {
-    const int i = (n - 1) / v, a = (n - 1) - i * v;
-    // split-K partial sums in a fixed order: eight loads in flight, four
-    // accumulators (partial p goes to accumulator p % 4)
-    const TC* jp = Jpart + (size_t)(n - 1) * C + col;
-    const double jsum = sum_partials(jp, (size_t)ov * C, SJ);
-    const TC* kp = Kpart + ((size_t)col * o + i) * v + a;
-    const double ksum = sum_partials(kp, (size_t)Kstride, SK);
-    sg = (eps_v[a] - eps_o[i]) * Xs[idx] + jsum - cx * ksum;
+  // pass 1: exchange partial sums, threads along n.  Split-K partials are
+  // summed in a fixed order (eight loads in flight, partial p into
+  // accumulator p % 4).
+#pragma unroll
+  for (int k = 0; k < kCombineTile / 256; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    const int r = e % R, c = e / R;
+    const long long n = n0 + r;
+    const int col = c0 + c;
+    double ks = 0.0;
+    if (n >= 1 && n < N && col < C) {
+      const int i = (int)((n - 1) / v), a = (int)(n - 1) - i * v;
+      ks = sum_partials(Kpart + ((size_t)col * o + i) * v + a, (size_t)Kstride, SK);
+    }
+    ksum_s[c][r] = ks;
   }
-  if (use_field) sg -= E[stage * T + t] * F[idx];
-  if (mode == 1) {
-    sig_out[idx] = sg;
-    return;
-  }
-  // this thread's sigma part feeds the other component of k
-  const size_t kidx = (size_t)n * C + 2 * t + (1 - q);
-  const double kv = q == 0 ? -sg : sg;  // k_im = -sigma_re ; k_re = sigma_im
-  switch (stage) {
-    case 0:
-      acc[kidx] = kv;
-      Xs_next[kidx] = Xn[kidx] + 0.5 * dt * kv;
-      break;
-    case 1:
-      acc[kidx] += 2.0 * kv;
-      Xs_next[kidx] = Xn[kidx] + 0.5 * dt * kv;
-      break;
-    case 2:
-      acc[kidx] += 2.0 * kv;
-      Xs_next[kidx] = Xn[kidx] + dt * kv;
-      break;
-    default: {
-      const double x = Xn[kidx] + (dt / 6.0) * (acc[kidx] + kv);
-      Xn[kidx] = x;
-      Xs_next[kidx] = x;
+  __syncthreads();
+  // pass 2: assembly and update, threads along the columns.  The thread of
+  // column col (trajectory t, part q) updates the other part of k: k = -i
+  // sigma gives k_re = sigma_im, k_im = -sigma_re.
+#pragma unroll
+  for (int k = 0; k < kCombineTile / 256; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    const int c = e % CC, r = e / CC;
+    const long long n = n0 + r;
+    const int col = c0 + c;
+    if (n >= N || col >= C) continue;
+    const int t = col >> 1, q = col & 1;
+    const size_t idx = (size_t)n * C + col;
+    double sg = 0.0;
+    if (n > 0) {
+      const int i = (int)((n - 1) / v), a = (int)(n - 1) - i * v;
+      const double jsum = sum_partials(Jpart + (size_t)(n - 1) * C + col, (size_t)ov * C, SJ);
+      sg = (eps_v[a] - eps_o[i]) * Xs[idx] + jsum - cx * ksum_s[c][r];
+    }
+    if (use_field) sg -= E[stage * T + t] * F[idx];
+    if (mode == 1) {
+      sig_out[idx] = sg;
+      continue;
+    }
+    const size_t kidx = (size_t)n * C + (col ^ 1);
+    const double kv = q == 0 ? -sg : sg;  // k_im = -sigma_re ; k_re = sigma_im
+    switch (stage) {
+      case 0:
+        acc[kidx] = kv;
+        Xs_next[kidx] = Xn[kidx] + 0.5 * dt * kv;
+        break;
+      case 1:
+        acc[kidx] += 2.0 * kv;
+        Xs_next[kidx] = Xn[kidx] + 0.5 * dt * kv;
+        break;
+      case 2:
+        acc[kidx] += 2.0 * kv;
+        Xs_next[kidx] = Xn[kidx] + dt * kv;
+        break;
+      default: {
+        const double x = Xn[kidx] + (dt / 6.0) * (acc[kidx] + kv);
+        Xn[kidx] = x;
+        Xs_next[kidx] = x;
+      }
     }
   }
 }
@@ -847,9 +873,10 @@ __global__ void __launch_bounds__(256) k_combine(int mode, int stage, long long 
 //                              p <- p_{n+1} - dt/2 H q     (next step's first half)
 // The two half steps of mode 2 are separate roundings, so a propagation
 // that stops at step n and resumes from Xn with mode 0 reproduces it bit for
-// bit.  One thread per (trajectory t, row n), n fastest; N * T < 2^31.
+// bit.  One thread per (trajectory t, row n), in tiles of R rows by CT
+// trajectories as in k_combine.
 // ---------------------------------------------------------------------------
-template <typename TC>
+template <typename TC, int CT>
 __global__ void __launch_bounds__(256) k_sso_update(int mode, int stage, long long N, int o, int v, int T,
                                                     const double* __restrict__ eps_o,
                                                     const double* __restrict__ eps_v, double cx,
@@ -858,34 +885,59 @@ __global__ void __launch_bounds__(256) k_sso_update(int mode, int stage, long lo
                                                     const double* __restrict__ F, const double* __restrict__ E,
                                                     int use_field, double dt, double* __restrict__ Xn,
                                                     double* __restrict__ X, long long* __restrict__ step_ctr) {
+  constexpr int R = kCombineTile / CT;
+  static_assert(R * CT == kCombineTile, "tile of 1024 elements");
+  __shared__ double ksum_s[CT][R + 1];
   // step_ctr: as in k_combine, for the last sub-step of a step
-  if (step_ctr != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n32 = (int)N;
-  if (e >= n32 * T) return;
-  const int n = e % n32, t = e / n32;
-  const int C = 2 * T, qc = mode == 1 ? 1 : 0, col = 2 * t + qc;
+  if (step_ctr != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *step_ctr += 1;
+  const int C = 2 * T, qc = mode == 1 ? 1 : 0;
+  const long long n0 = (long long)blockIdx.x * R;
+  const int t0 = blockIdx.y * CT;
   const long long ov = N - 1;
-  const size_t iq = (size_t)n * C + 2 * t, ip = iq + 1, idx = iq + qc;
-  double sg = 0.0;
-  if (n > 0) {
-    const int i = (n - 1) / v, a = (n - 1) - i * v;
-    const double jsum = sum_partials(Jpart + (size_t)(n - 1) * C + col, (size_t)ov * C, SJ);
-    const double ksum = sum_partials(Kpart + ((size_t)col * o + i) * v + a, (size_t)Kstride, SK);
-    sg = (eps_v[a] - eps_o[i]) * X[idx] + jsum - cx * ksum;
+  // pass 1: exchange partial sums of column 2t + qc, threads along n
+#pragma unroll
+  for (int k = 0; k < kCombineTile / 256; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    const int r = e % R, c = e / R;
+    const long long n = n0 + r;
+    const int t = t0 + c;
+    double ks = 0.0;
+    if (n >= 1 && n < N && t < T) {
+      const int i = (int)((n - 1) / v), a = (int)(n - 1) - i * v;
+      ks = sum_partials(Kpart + ((size_t)(2 * t + qc) * o + i) * v + a, (size_t)Kstride, SK);
+    }
+    ksum_s[c][r] = ks;
   }
-  if (use_field) sg -= E[stage * T + t] * F[idx];
-  const double h = 0.5 * dt;
-  if (mode == 0) {
-    X[ip] = X[ip] - h * sg;
-  } else if (mode == 1) {
-    const double q1 = X[iq] + dt * sg;
-    X[iq] = q1;
-    Xn[iq] = q1;
-  } else {
-    const double p1 = X[ip] - h * sg;
-    Xn[ip] = p1;
-    X[ip] = p1 - h * sg;
+  __syncthreads();
+  // pass 2: one thread per (row, trajectory), threads along the trajectories
+#pragma unroll
+  for (int k = 0; k < kCombineTile / 256; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    const int c = e % CT, r = e / CT;
+    const long long n = n0 + r;
+    const int t = t0 + c;
+    if (n >= N || t >= T) continue;
+    const int col = 2 * t + qc;
+    const size_t iq = (size_t)n * C + 2 * t, ip = iq + 1, idx = iq + qc;
+    double sg = 0.0;
+    if (n > 0) {
+      const int i = (int)((n - 1) / v), a = (int)(n - 1) - i * v;
+      const double jsum = sum_partials(Jpart + (size_t)(n - 1) * C + col, (size_t)ov * C, SJ);
+      sg = (eps_v[a] - eps_o[i]) * X[idx] + jsum - cx * ksum_s[c][r];
+    }
+    if (use_field) sg -= E[stage * T + t] * F[idx];
+    const double h = 0.5 * dt;
+    if (mode == 0) {
+      X[ip] = X[ip] - h * sg;
+    } else if (mode == 1) {
+      const double q1 = X[iq] + dt * sg;
+      X[iq] = q1;
+      Xn[iq] = q1;
+    } else {
+      const double p1 = X[ip] - h * sg;
+      Xn[ip] = p1;
+      X[ip] = p1 - h * sg;
+    }
   }
 }
 
