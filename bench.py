@@ -824,9 +824,21 @@ def run_serving(args):
                          omega=float(rng.uniform(0.4, 2.5)), duration=0.8 * steps * DT, direction=(0.0, 0.0, 1.0))
         shapes.append((o, v, 4 * v, steps, pulse))
 
+    # The server's threads capture step graphs while this thread draws the
+    # next molecules, so this thread synchronises only its own stream: a
+    # device-wide synchronisation (or a cudaFree that implies one) would
+    # invalidate a capture in flight, and the library would then run that
+    # chunk without its graph.
+    gen = torch.cuda.Stream()
+
     def make(k):
         o, v, P, steps, pulse = shapes[k]
-        mol = synth.molecule_device(o, v, P, seed=1000 + k) if full else synth.molecule(o, v, P, seed=1000 + k)
+        if not full:
+            mol = synth.molecule(o, v, P, seed=1000 + k)
+        else:
+            with torch.cuda.stream(gen):
+                mol = synth.molecule_device(o, v, P, seed=1000 + k)
+            gen.synchronize()
         return rb.make_request(mol, CX, args.prec, pulse, DT, steps, **spec), mol
 
     # small molecules are drawn before the clock starts (host numpy takes up
@@ -844,12 +856,8 @@ def run_serving(args):
         for k in list(held):
             if rb.rttda_server_poll(srv, ids[k])[0] != rb.REQ_PENDING:
                 del held[k]
-        if full:
-            torch.cuda.empty_cache()
         while nxt < n and arrivals[nxt] <= now and (not full or len(held) < args.serving_pending):
             (q, mol) = make(nxt) if full else pre[nxt]
-            if full:
-                torch.cuda.synchronize()
             ids[nxt] = rb.rttda_server_submit(srv, q)
             sub_t[nxt] = time.perf_counter() - t0
             if full:

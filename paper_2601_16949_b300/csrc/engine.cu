@@ -177,6 +177,8 @@ struct rttda_ctx {
   int wide_mb = 0;                   // >0: main contraction on the wide-M kernel with this many 128-row blocks
   int wide_kb = 32;                  // K tile width of the wide-M kernel (32 or 64 BF16)
   bool wide_tr = false;              // wide kernel with the contraction transposed (rows a)
+  long capture_fallbacks = 0;        // propagation calls whose step-graph capture was invalidated
+  bool break_capture = false;        // test hook (RTTDA_TEST_BREAK_CAPTURE): invalidate every capture
   int z_hint = 1;                    // Z stores evict-first in L2 (RTTDA_ZHINT)
   int z_run = 4;                     // Z-build tiles per CTA and column run in a slab, 0: no slabs (RTTDA_ZRUN)
   int integrator = RTTDA_INT_RK4;    // rttda_integrator
@@ -1189,9 +1191,19 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     dispatch(h->prec, step);
     h->launches_per_step = h->launches - l0;
-    h->launches = l0 + h->launches_per_step * nsteps;
+    if (h->break_capture) cudaStreamSynchronize(s);  // test hook: invalidates the capture
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
-    if (ce != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    if (ce != cudaSuccess) {
+      // The capture was invalidated, e.g. by a device-wide synchronisation
+      // that another thread of the process issued meanwhile.  None of the
+      // captured work ran: enqueue the same steps as direct launches.
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      h->launches = l0;
+      for (long k = 0; k < nsteps; ++k) dispatch(h->prec, step);
+      ++h->capture_fallbacks;
+    } else {
+    h->launches = l0 + h->launches_per_step * nsteps;
     // Keep the executable step graph of the handle and give it this call's
     // parameters with cudaGraphExecUpdate (launches in flight keep theirs);
     // a new one is instantiated only when the update is refused (a different
@@ -1229,6 +1241,7 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
       cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+    }
   }
   if (dip) {
     dispatch(h->prec, [&](auto ops) { decltype(ops)::field_obs(h, h->Xn, s); });
@@ -1251,15 +1264,17 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
 // TMA tensor maps (driver entry point; no link-time dependency on libcuda)
 // ---------------------------------------------------------------------------
 static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // looked up once (function-local static: thread-safe initialisation, so
+  // handles created on several threads, as the server does, share it)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* ptr = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -1931,6 +1946,7 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
   AllocStream as(h->stream);
   dispatch(h->prec, [&](auto ops) { decltype(ops)::set_smem_limits(); });
   if (const char* e = std::getenv("RTTDA_ZHINT")) h->z_hint = std::atoi(e) != 0;
+  if (const char* e = std::getenv("RTTDA_TEST_BREAK_CAPTURE")) h->break_capture = std::atoi(e) != 0;
   if (const char* e = std::getenv("RTTDA_ZRUN")) h->z_run = std::max(0, std::atoi(e));
   const size_t o = h->o, v = h->v, P = h->P;
   const size_t chunk = (size_t)1 << 26;  // elements per staging pass

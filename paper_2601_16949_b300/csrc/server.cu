@@ -2,7 +2,10 @@
 //
 // One scheduler thread owns every admitted request's handle.  Per loop it
 //   1. admits pending requests in arrival order while their estimated
-//      footprint fits the budget and an active slot is free;
+//      footprint fits the budget and an active slot is free (a request that
+//      needs its own handle is handed to the creator thread, which casts its
+//      factors and plans its contraction while the scheduler keeps stepping
+//      the others, and hands it back once the handle exists);
 //   2. enqueues the next chunk of RK4 steps of every idle active request on
 //      that request's own stream (the chunks of different requests overlap
 //      on the GPU);
@@ -76,6 +79,15 @@ struct rttda_server {
   std::atomic<bool> stop{false};
   std::thread worker;
 
+  // handle creation (seconds for a large molecule: factor casts, the tile
+  // plan's timed candidates) runs on its own thread so that the scheduler
+  // keeps launching the other requests' chunks meanwhile
+  std::thread creator;
+  std::condition_variable create_cv;
+  std::deque<Request*> to_create;  // admitted, handle not created yet (under mu)
+  std::vector<Request*> created;   // handle ready, not yet taken by the scheduler (under mu)
+  int creating = 0;                // requests admitted but not yet active (under mu)
+
   // grouped step of the small BF16 requests (one persistent kernel per chunk
   // for all of them); touched by the scheduler only, except `grouping`
   rttda::GroupRunner grp;
@@ -91,6 +103,8 @@ struct rttda_server {
 
   void run();
   bool admit_one();
+  void create_loop();
+  rttda_status create_handle(Request* r);
   void release(Request* r, int final_state);
 };
 
@@ -136,9 +150,10 @@ void rttda_server::release(Request* r, int final_state) {
 // (or removed because it was cancelled / can never fit).
 bool rttda_server::admit_one() {
   Request* r = nullptr;
+  bool to_group = false;
   {
     std::lock_guard<std::mutex> lk(mu);
-    if (pending.empty() || (int)active.size() >= max_active) return false;
+    if (pending.empty() || (int)active.size() + creating >= max_active) return false;
     r = reqs[pending.front()].get();
     if (r->cancel) {
       pending.pop_front();
@@ -148,11 +163,12 @@ bool rttda_server::admit_one() {
       return true;
     }
     const rttda_request& q = r->req;
-    const bool grouped = grouping.load() && rttda::group_eligible(q);
-    const size_t need = grouped ? rttda::group_estimate_bytes(q)
+    to_group = grouping.load() && rttda::group_eligible(q);
+    const size_t need = to_group ? rttda::group_estimate_bytes(q)
                                 : rttda::estimate_bytes(q.nocc, q.nvirt, q.naux, 1, q.prec, q.nsteps);
     if (used + need > budget) {
-      if (!active.empty()) return false;  // wait for memory to free up
+      // wait for memory to free up, unless nothing else holds any
+      if (!active.empty() || creating > 0) return false;
       pending.pop_front();
       r->state = RTTDA_REQ_FAILED;
       r->error = "request footprint " + std::to_string(need) + " B exceeds the server budget";
@@ -165,10 +181,18 @@ bool rttda_server::admit_one() {
     r->bytes = need;
     // the state stays PENDING until the molecule has been copied: a caller
     // with device factors may free them once the request leaves PENDING
+    if (!to_group) {
+      ++creating;
+      to_create.push_back(r);
+    }
+  }
+  if (!to_group) {
+    create_cv.notify_one();
+    return true;
   }
   const rttda_request& q = r->req;
   rttda_status st = RTTDA_OK;
-  if (grouping.load() && rttda::group_eligible(q)) {
+  {
     // small BF16 request: stepped with the others in the grouped kernel
     if (!grp_ready) {
       st = rttda::group_runner_init(&grp);
@@ -199,40 +223,81 @@ bool rttda_server::admit_one() {
     }
     return true;
   }
-  // host copies or the caller's device arrays (the copies inside accept both)
-  st = rttda_create(q.nocc, q.nvirt, q.naux, q.eps_occ, q.eps_virt, q.B_ov, q.B_oo, q.B_vv, q.mu_oo, q.mu_vv,
-                    q.mu_0ov, q.c_x, q.prec, &r->h);
+}
+
+// The request's own handle, its field, its trace buffer and its event
+// (creator thread).  The molecule is copied from the owned host copies or
+// from the caller's device arrays (the copies inside accept both).
+rttda_status rttda_server::create_handle(Request* r) {
+  const rttda_request& q = r->req;
+  rttda_status st = rttda_create(q.nocc, q.nvirt, q.naux, q.eps_occ, q.eps_virt, q.B_ov, q.B_oo, q.B_vv, q.mu_oo,
+                                 q.mu_vv, q.mu_0ov, q.c_x, q.prec, &r->h);
   if (st == RTTDA_OK) st = rttda_set_field(r->h, &q.pulse, 1);
   if (st == RTTDA_OK) {
     const size_t n = 2 * (size_t)(q.nsteps + 1) + 2 * (size_t)q.nfreq;
     cudaStream_t hs = rttda::handle_stream(r->h);
     if (cudaMallocAsync((void**)&r->dev, n * sizeof(double), hs) != cudaSuccess ||
-        cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamSynchronize(hs) != cudaSuccess)
       st = RTTDA_E_OOM;
   }
-  if (st != RTTDA_OK) {
-    r->error = rttda_last_error();
-    release(r, RTTDA_REQ_FAILED);
-    return true;
-  }
+  if (st != RTTDA_OK) return st;
   // the factors now live on the device (rttda_set_field synchronised the
   // handle's stream, so every copy from the caller's arrays has completed)
   std::vector<double>().swap(r->Bov);
   std::vector<double>().swap(r->Boo);
   std::vector<double>().swap(r->Bvv);
-  active.push_back(r);
-  max_concurrent = std::max(max_concurrent, (int)active.size());
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    r->state = RTTDA_REQ_ACTIVE;
+  return RTTDA_OK;
+}
+
+// Creator thread: builds the handles of admitted requests in admission
+// order.  A request cancelled before its turn (or left at shutdown) is
+// released without a handle; a finished one is handed to the scheduler.
+void rttda_server::create_loop() {
+  cudaSetDevice(device);
+  while (true) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      create_cv.wait(lk, [&] { return stop.load() || !to_create.empty(); });
+      if (to_create.empty()) return;  // stopping, nothing left
+      r = to_create.front();
+      to_create.pop_front();
+    }
+    rttda_status st = RTTDA_OK;
+    const bool skip = r->cancel || stop.load();
+    if (!skip) st = create_handle(r);
+    if (skip || st != RTTDA_OK) {
+      if (!skip) r->error = rttda_last_error();
+      release(r, skip ? RTTDA_REQ_CANCELLED : RTTDA_REQ_FAILED);
+      std::lock_guard<std::mutex> lk(mu);
+      --creating;
+      continue;
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      r->state = RTTDA_REQ_ACTIVE;
+      created.push_back(r);
+    }
+    cv.notify_all();
   }
-  return true;
 }
 
 void rttda_server::run() {
   cudaSetDevice(device);
   while (!stop.load()) {
     bool progressed = false;
+    {
+      // requests whose handles the creator thread has finished
+      std::lock_guard<std::mutex> lk(mu);
+      if (!created.empty()) {
+        active.insert(active.end(), created.begin(), created.end());
+        creating -= (int)created.size();
+        created.clear();
+        max_concurrent = std::max(max_concurrent, (int)active.size());
+        progressed = true;
+      }
+    }
     while (admit_one()) progressed = true;
     // enqueue the next chunk of every idle request
     for (Request* r : active) {
@@ -419,6 +484,7 @@ rttda_status rttda_server_create(size_t hbm_budget, int max_active, long chunk_s
   s->chunk = chunk_steps;
   s->t0 = clk::now();
   s->worker = std::thread([s] { s->run(); });
+  s->creator = std::thread([s] { s->create_loop(); });
   *out = s;
   return RTTDA_OK;
 }
@@ -565,7 +631,12 @@ void rttda_server_destroy(rttda_server_t s) {
   if (!s) return;
   s->stop.store(true);
   s->cv.notify_all();
+  s->create_cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  if (s->creator.joinable()) s->creator.join();
+  // handles finished after the scheduler stopped
+  for (Request* r : s->created) s->release(r, RTTDA_REQ_CANCELLED);
+  s->created.clear();
   delete s;
 }
 

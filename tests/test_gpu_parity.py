@@ -291,3 +291,25 @@ def test_one_polarisation_batch_propagation_matches_oracle(rb, prec, dip_tol, no
         rel = np.max(np.abs(dip[t] - ref.dipole)) / np.max(np.abs(d))
         assert rel < dip_tol, (prec, t, rel)
         assert np.max(np.abs(nrm[t] - ref.norm)) < norm_tol, (prec, t)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_invalidated_step_graph_capture_runs_the_steps_directly(rb, prec, monkeypatch):
+    """A propagation call captures its step into a CUDA graph.  When the
+    capture is invalidated (another thread of the process synchronising the
+    device meanwhile; here forced by a test hook that makes the capturing
+    thread itself break the capture rules, an API error and nothing on the
+    GPU), none of the captured work ran and the call enqueues the same
+    steps as direct launches: the results are bitwise those of the graph."""
+    mol = synth.molecule(7, 40, 30, seed=23)
+    pulses = [dict(kind=4, E0=0.03, omega=0.8, duration=5.0, direction=(0, 0, 1)),
+              dict(kind=0, E0=1e-3, direction=(1, 0, 0))]
+    out = []
+    for brk in ("0", "1"):
+        monkeypatch.setenv("RTTDA_TEST_BREAK_CAPTURE", brk)
+        prop = rb.Propagator(mol, 0.2, prec)
+        prop.set_field(pulses)
+        out.append(prop.propagate(0.05, 60))
+        prop.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)

@@ -129,3 +129,31 @@ def test_request_larger_than_budget_fails_cleanly(rb):
     assert rb.rttda_server_poll(srv, rid)[0] == rb.REQ_FAILED
     assert "budget" in rb.rttda_last_error()
     rb.rttda_server_destroy(srv)
+
+
+def test_cancel_and_destroy_while_handles_are_being_created(rb):
+    """Handles are created on the server's creator thread while the
+    scheduler steps the active requests.  Requests cancelled right after
+    submission (before or during their handle's creation) end CANCELLED and
+    give their memory back; the others still complete; destroying the server
+    with requests queued for creation returns (nothing left behind)."""
+    srv = rb.rttda_server_create(32 << 30, 3, 50)
+    reqs = [_request(rb, c) for c in CASES[:4]]
+    ids = [rb.rttda_server_submit(srv, q) for _, q in reqs]
+    for k in (1, 3):
+        rb.rttda_server_cancel(srv, ids[k])
+    for rid in ids:
+        rb.rttda_server_wait(srv, rid, 300.0)
+    states = [rb.rttda_server_poll(srv, rid)[0] for rid in ids]
+    assert states[0] == rb.REQ_DONE and states[2] == rb.REQ_DONE, states
+    assert states[1] in (rb.REQ_CANCELLED, rb.REQ_DONE) and states[3] in (rb.REQ_CANCELLED, rb.REQ_DONE), states
+    st = rb.rttda_server_stats_get(srv)
+    assert st["bytes_in_use"] == 0 and st["completed"] + st["cancelled"] == 4
+    rb.rttda_server_destroy(srv)
+    # destroy with work still queued: returns without waiting for it
+    srv = rb.rttda_server_create(32 << 30, 2, 50)
+    for _, q in [_request(rb, c) for c in CASES]:
+        rb.rttda_server_submit(srv, q)
+    t0 = time.time()
+    rb.rttda_server_destroy(srv)
+    assert time.time() - t0 < 120.0
