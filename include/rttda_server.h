@@ -16,7 +16,16 @@
  * dipole trace is turned into a spectrum on the GPU; its memory is then
  * released and the next request is admitted.
  *
- * Conventions are those of rttda.h.  All functions are thread-safe.
+ * Handles of admitted requests are created on a second server thread, so
+ * the scheduler keeps stepping the other requests meanwhile.
+ *
+ * Conventions are those of rttda.h.  All functions are thread-safe.  The
+ * server captures CUDA graphs on its own threads: while it runs, other
+ * threads of the process should synchronise their own streams, not the
+ * whole device.  A device-wide synchronisation during a capture fails in the
+ * calling thread (cudaErrorStreamCaptureUnsupported); the server runs the
+ * chunk whose capture it invalidated as direct launches, with the same
+ * results.
  */
 #ifndef RTTDA_SERVER_H
 #define RTTDA_SERVER_H
