@@ -400,11 +400,12 @@ def profiled_traffic(prec: str, cls: str, plan: dict):
     if not os.path.exists(TRAFFIC_FILE) or plan.get("z_chunk") != NAUX:
         return None  # the table's captures are of the unchunked exchange
     want = [NAME, str(NAUX), prec, cls, str(plan.get("main_kernel")), str(plan.get("main_bn")),
-            str(plan.get("main_mb")), str(plan.get("main_kb")), str(plan.get("main_splits"))]
+            str(plan.get("main_mb")), str(plan.get("main_kb")), str(plan.get("main_splits")),
+            str(plan.get("main_cluster")), str(plan.get("main_grid"))]
     for line in open(TRAFFIC_FILE):
         f = line.split("#", 1)[0].split()
-        if len(f) >= 11 and f[:9] == want:
-            return {"bytes": float(f[9]), "source": f"profiles/{f[10]}"}
+        if len(f) >= 13 and f[:11] == want:
+            return {"bytes": float(f[11]), "source": f"profiles/{f[12]}"}
     return None
 
 

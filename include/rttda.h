@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define RTTDA_ABI_VERSION 1
+#define RTTDA_ABI_VERSION 2
 
 typedef struct rttda_ctx* rttda_t;
 typedef struct rttda_server* rttda_server_t;
@@ -388,6 +388,8 @@ rttda_status rttda_set_integrator(rttda_t h, int integrator);
  * main_kernel 4, "BN,2,32,t" (an unknown candidate there makes
  * rttda_set_field fail with RTTDA_E_ARG).
  * RTTDA_ZCHUNK=n caps z_chunk at n values of P (all precisions).
+ * RTTDA_WIDE_CLUSTER=2 or 4 runs main_kernel 2 (BN 192, MB 2, KB 64) in
+ * clusters of that many CTAs (main_cluster) when the columns allow it.
  * Errors: RTTDA_E_ARG (NULL), RTTDA_E_STATE (no batch yet). */
 typedef struct {
   int prec, ntraj;
@@ -396,6 +398,8 @@ typedef struct {
   int coulomb_kernel;
   int tuned, ncand;
   double tune_ms[8];
+  int main_cluster;  /* main_kernel 2: CTAs per thread-block cluster that share each Z tile (TMA multicast), 1: none */
+  int main_grid;     /* main_kernel 2: CTAs of the main contraction's launch */
 } rttda_plan_info;
 rttda_status rttda_plan(rttda_t h, rttda_plan_info* out);
 

@@ -58,7 +58,7 @@ class rttda_server_stats(ct.Structure):
 class rttda_plan_info(ct.Structure):
     _fields_ = [(n, ct.c_int) for n in ("prec", "ntraj", "main_kernel", "main_bn", "main_mb", "main_kb",
                                         "main_splits", "z_chunk", "coulomb_kernel", "tuned", "ncand")] + \
-               [("tune_ms", ct.c_double * 8)]
+               [("tune_ms", ct.c_double * 8), ("main_cluster", ct.c_int), ("main_grid", ct.c_int)]
 
 
 REQ_PENDING, REQ_ACTIVE, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)

@@ -249,6 +249,36 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// Cluster forms (thread-block clusters of the main contraction).
+// The commit arrives on the barrier at the same shared-memory offset in every
+// CTA of `mask` once this CTA's prior MMAs have completed.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+// A tile load delivered to the same shared-memory offset (and completing on
+// the barrier at the same offset) in every CTA of `mask`.
+__device__ __forceinline__ void tma_load_4d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                               int c2, int c3, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2], %7;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of every CTA of the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
                "r"(ncols));
@@ -780,11 +810,22 @@ constexpr size_t wide_smem_bytes() {
   return (size_t)STAGES * WideCfg<BN, MB, NBP, KB, TR>::kStageBytes + 1024 + 256;
 }
 
-template <int BN, int MB, int NBP, int STAGES, int KB, bool TR = false>
+// CL > 1 (not TR): the kernel runs in clusters of CL CTAs that take CL
+// consecutive column tiles of the same rows and K range (launch with a grid
+// that is a multiple of CL, and tiles_n a multiple of CL).  Each CTA loads
+// 128/CL rows of every A (Z) block and multicasts them to the whole cluster,
+// so a Z tile leaves L2 once per cluster instead of once per CTA and the
+// cluster's CTAs advance through K together.  tmA is then the map of
+// 128/CL-row boxes.  A stage is refilled only when every CTA of the
+// cluster has released it: each CTA's MMA commit arrives on the stage's
+// empty barrier in all CL CTAs.
+template <int BN, int MB, int NBP, int STAGES, int KB, bool TR = false, int CL = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_wide(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p) {
+  static_assert(CL == 1 || (!TR && (CL == 2 || CL == 4)), "clusters of 2 or 4, not transposed");
   using CF = WideCfg<BN, MB, NBP, KB, TR>;
   constexpr int TM = kBM * MB;  // rows per tile
+  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * CF::kStageBytes);
@@ -801,7 +842,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);  // one commit per CTA of the cluster
     }
     mbar_init(accf, 1);
     mbar_init(acce, kEpiWarps);
@@ -810,6 +851,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tmem_alloc(tmem_slot, CF::kTmemCols);
   tc_fence_before();
   __syncthreads();
+  // the cluster's barriers are initialised before any CTA multicasts into them
+  if constexpr (CL > 1) cluster_sync();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -848,8 +891,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tma_load_4d(st + (q * MB + b) * CF::kABlock, &tmA, &full[s], b0, m0 + b * kBM, P, q);
             tma_load_4d(st + MB * NBP * CF::kABlock, &tmB, &full[s], zx, n0, zt, 0);
           } else {
+            if constexpr (CL > 1) {
+              // this CTA's 128/CL rows of every A block, to the whole cluster
+              constexpr int RS = kBM / CL;
+              const int rk = (int)cluster_rank();
 #pragma unroll
-            for (int b = 0; b < MB; ++b) tma_load_4d(st + b * CF::kABlock, &tmA, &full[s], zx, m0 + b * kBM, zt, 0);
+              for (int b = 0; b < MB; ++b)
+                tma_load_4d_mc(st + b * CF::kABlock + rk * RS * CF::kRowBytes, &tmA, &full[s], zx,
+                               m0 + b * kBM + rk * RS, zt, 0, kMask);
+            } else {
+#pragma unroll
+              for (int b = 0; b < MB; ++b)
+                tma_load_4d(st + b * CF::kABlock, &tmA, &full[s], zx, m0 + b * kBM, zt, 0);
+            }
 #pragma unroll
             for (int q = 0; q < NBP; ++q)
               tma_load_4d(st + MB * CF::kABlock + q * CF::kBBytes, &tmB, &full[s], b0, n0, P, q);
@@ -857,6 +911,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       drain_loads(full, it, STAGES);
+      if constexpr (CL > 1) {
+        // every CTA of the cluster has released the last stages, so no
+        // commit of another CTA is still on its way to this CTA's barriers
+        for (int j = max(0, it - STAGES); j < it; ++j)
+          mbar_wait(&empty[j % STAGES], (uint32_t)(j / STAGES) & 1u, nullptr, 0);
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -891,7 +951,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                          (kr > kr0 || q > 0 || k > 0) ? 1u : 0u);
             }
           }
-          mma_commit(&empty[s]);
+          if constexpr (CL > 1)
+            mma_commit_mc(&empty[s], kMask);
+          else
+            mma_commit(&empty[s]);
         }
         mma_commit(accf);
       }
@@ -939,6 +1002,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  // no CTA leaves while another CTA of its cluster may still write to it
+  if constexpr (CL > 1) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, CF::kTmemCols);

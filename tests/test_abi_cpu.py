@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(rb):
 
 
 def test_abi_version(rb):
-    assert rb.rttda_abi_version() == 1
+    assert rb.rttda_abi_version() == 2
 
 
 def test_create_rejects_bad_sizes_without_gpu(rb):
