@@ -846,7 +846,7 @@ def run_serving(args):
     # to half a second each); the large ones on the GPU at arrival
     pre = None if full else [make(k) for k in range(n)]
     srv = rb.rttda_server_create(int(args.serving_budget_gb * (1 << 30)), args.serving_slots, args.serving_chunk)
-    rb.rttda_server_set_grouping(srv, bool(args.serving_grouping))
+    rb.rttda_server_set_grouping(srv, args.serving_grouping)
     ids, sub_t = [None] * n, [0.0] * n
     held = {}   # request index -> its device molecule, until admitted
     t0 = time.perf_counter()
@@ -876,7 +876,7 @@ def run_serving(args):
     tts = np.array([(sub_t[k] - arrivals[k]) + polls[k][4] for k in range(n) if polls[k][0] == rb.REQ_DONE])
     line = {"mode": "serving", "metric": "time-to-spectrum p50/p99 and trajectory-steps/s (continuous batching)",
             "requests": n, "arrival_rate_per_s": args.serving_rate, "precision": args.prec,
-            "grouping": bool(args.serving_grouping),
+            "grouping": {0: "off", 1: "by work", 2: "every eligible request"}[args.serving_grouping],
             "workload": (("serving workload sizes: nocc U[16,192], nvirt U[64,1024] with nvirt >= 4 nocc, naux = 4 nvirt, "
                           "factors drawn on the GPU" if full else
                           "small molecules: nocc U[16,48], nvirt U[64,192] with nvirt >= 4 nocc, naux = 4 nvirt") +
@@ -914,7 +914,7 @@ def run_group_probe(args):
                                     args.probe_steps, **spec) for k in range(S)]
             for g in (1, 0):
                 srv = rb.rttda_server_create(64 << 30, S, args.probe_steps)
-                rb.rttda_server_set_grouping(srv, bool(g))
+                rb.rttda_server_set_grouping(srv, 2 if g else 0)
                 t0 = time.perf_counter()
                 ids = [rb.rttda_server_submit(srv, q) for q in reqs]
                 for rid in ids:
@@ -961,7 +961,8 @@ def main():
     ap.add_argument("--serving-sizes", default="small", choices=["small", "full"])
     ap.add_argument("--serving-steps-min", type=int, default=200)
     ap.add_argument("--serving-steps-max", type=int, default=2000)
-    ap.add_argument("--serving-grouping", type=int, default=1, help="1: small BF16 requests stepped together")
+    ap.add_argument("--serving-grouping", type=int, default=1, choices=(0, 1, 2),
+                    help="grouped step of small BF16 requests: 0 off, 1 by work (default), 2 every eligible request")
     ap.add_argument("--serving-pending", type=int, default=2,
                     help="full sizes: most requests with device factors waiting in the server")
     ap.add_argument("--fp64-steps", type=int, default=2)

@@ -112,22 +112,29 @@ rttda_status rttda_server_wait(rttda_server_t s, long id, double timeout_s);
  * Errors: RTTDA_E_ARG (NULL s, unknown id). */
 rttda_status rttda_server_cancel(rttda_server_t s, long id);
 
-/* Grouped stepping of small BF16 requests (on by default).  With enable != 0
- * every admitted request with prec = RTTDA_BF16, nocc <= 64, nvirt <= 256,
- * naux <= 2048 and nocc * nvirt^2 * naux <= 3e8 (the sizes whose step is
- * launch-bound on its own) is advanced, chunk by chunk, by one persistent
- * cooperative kernel that steps all such active requests together (about
- * forty launches per RK4 step of each request become one launch per chunk
- * of the group).  Its numerics are those of the BF16 path (BF16 factors and
- * contraction inputs, FP32 accumulation on the warp-level tensor-core
- * instructions, FP64 state, FP64-accurate dipole expectation); a request's
- * results are bitwise the same whichever requests share its group, but not
+/* Grouped stepping of small BF16 requests.  A grouped request is advanced,
+ * chunk by chunk, by one persistent cooperative kernel that steps all such
+ * active requests together (about forty launches per RK4 step of each
+ * request become one launch per chunk of the group); its grid takes a share
+ * of the SMs in proportion to the group's work, so requests on their own
+ * handles keep running beside it.  The kernel takes requests with prec =
+ * RTTDA_BF16, nocc <= 64, nvirt <= 256, naux <= 2048 and nocc * nvirt^2 *
+ * naux <= 3e8.  Modes (`enable`):
+ *   0  no grouping: every request gets its own handle;
+ *   1  (default) by work: such a request is grouped when its nocc nvirt^2
+ *      naux is at most 6e7 and the summed nocc nvirt^2 naux of the grouped
+ *      requests stays at most 4e8 (the regime where the grouped step was
+ *      measured faster than one handle per request); the others get handles;
+ *   2  every request within the kernel's limits is grouped.
+ * Numerics are those of the BF16 path (BF16 factors and contraction inputs,
+ * FP32 accumulation on the warp-level tensor-core instructions, FP64 state,
+ * FP64-accurate dipole expectation); a request's results are bitwise the
+ * same whichever requests share its group and whatever the grid, but not
  * bitwise equal to a plain rttda_propagate in the BF16 precision, whose
- * contractions sum in another order.  With enable = 0 they get handles like
- * every other request.  Applies to requests admitted afterwards.  The
- * serving pattern of the workload (Sec. 2.2 propagation served as
- * continuous batching) has no counterpart in the paper.
- * Errors: RTTDA_E_ARG (NULL s). */
+ * contractions sum in another order.  Applies to requests admitted
+ * afterwards.  The serving pattern of the workload (Sec. 2.2 propagation
+ * served as continuous batching) has no counterpart in the paper.
+ * Errors: RTTDA_E_ARG (NULL s, mode not 0, 1 or 2). */
 rttda_status rttda_server_set_grouping(rttda_server_t s, int enable);
 
 /* Counters and latency percentiles of the requests so far (the serving

@@ -439,8 +439,9 @@ def rttda_server_cancel(srv, rid) -> None:
     _check(lib.rttda_server_cancel(srv, int(rid)), "rttda_server_cancel")
 
 
-def rttda_server_set_grouping(srv, enable: bool) -> None:
-    _check(lib.rttda_server_set_grouping(srv, int(bool(enable))), "rttda_server_set_grouping")
+def rttda_server_set_grouping(srv, mode) -> None:
+    """0: off, 1 (or True): by work (the default), 2: every eligible request."""
+    _check(lib.rttda_server_set_grouping(srv, int(mode)), "rttda_server_set_grouping")
 
 
 def rttda_server_stats_get(srv) -> dict:

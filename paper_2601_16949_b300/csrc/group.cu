@@ -804,6 +804,8 @@ double fro_host(const double* a, size_t n) {
 
 }  // namespace
 
+double group_work(const rttda_request& q) { return (double)q.nocc * q.nvirt * q.nvirt * q.naux; }
+
 bool group_eligible(const rttda_request& q) {
   // small BF16 requests whose step is launch-bound: exchange work
   // nocc nvirt^2 naux multiply-adds per column at most kMaxWork (measured:
@@ -1013,6 +1015,7 @@ rttda_status group_runner_init(GroupRunner* g) {
   if (e != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("grouped step: ") + cudaGetErrorString(e));
   if (!coop || occ < 1) return set_error(RTTDA_E_CUDA, "grouped step: cooperative launch unavailable");
   g->grid = nsm * occ;
+  g->nsm = nsm;
   // diagnostics: RTTDA_GROUP_PHASE_CLOCK=<file> appends, after every chunk,
   // the device clock (ns) of each grid barrier relative to the first
   const char* pc = std::getenv("RTTDA_GROUP_PHASE_CLOCK");
@@ -1067,14 +1070,23 @@ rttda_status group_launch(GroupRunner* g, const std::vector<GroupReq*>& reqs, co
     t->kick_terms = std::max(t->kick_terms, r.kick_terms);
   }
   t->phase_ns = g->phase_ns;
+  // Grid sized by the group's work: a small group takes a share of the SMs
+  // (at least 16) and leaves the rest to the requests stepped on their own
+  // handles, which run concurrently on other streams; a group of half the
+  // work cap or more takes all of them.  Results do not depend on the grid
+  // (the CTAs only take work units in turn; every sum has a fixed order).
+  double work = 0.0;
+  for (int k = 0; k < t->nreq; ++k) work += (double)t->req[k].o * t->req[k].v * t->req[k].v * t->req[k].P;
+  const int occ = std::max(1, g->grid / std::max(1, g->nsm));
+  const int nsm = std::min(g->nsm, std::max(16, (int)std::ceil(2.0 * g->nsm * work / kMaxGroupWork)));
+  const unsigned grid = (unsigned)std::min(g->grid, nsm * occ);
   cudaError_t e = cudaMemcpyAsync(g->d_table, t, sizeof(Table), cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_bar, 0, sizeof(Barrier), g->stream);
   if (e == cudaSuccess && g->phase_ns) e = cudaMemsetAsync(g->phase_ns, 0, 8 * kMaxPhaseTicks, g->stream);
   if (e == cudaSuccess) {
     const Table* arg = g->d_table;
     void* args[] = {(void*)&arg};
-    e = cudaLaunchCooperativeKernel((void*)k_group_chunk, dim3(g->grid), dim3(kThreads), args, kSmemBytes,
-                                    g->stream);
+    e = cudaLaunchCooperativeKernel((void*)k_group_chunk, dim3(grid), dim3(kThreads), args, kSmemBytes, g->stream);
   }
   if (e == cudaSuccess) e = cudaEventRecord(g->ev, g->stream);
   if (e != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("grouped step: launch: ") + cudaGetErrorString(e));

@@ -14,7 +14,19 @@ namespace grp {
 
 // size limits of the grouped path (small molecules, launch-bound otherwise)
 constexpr int kMaxO = 64, kMaxV = 256, kMaxP = 2048;
-constexpr double kMaxWork = 3e8;  // nocc nvirt^2 naux
+constexpr double kMaxWork = 3e8;  // nocc nvirt^2 naux of one request the grouped step takes at all
+// routed to the grouped step by default (rttda_server_set_grouping mode 1):
+// one request's nocc nvirt^2 naux at most this (measured: the grouped step
+// wins for many requests of (16, 64, 256), 1.7e7 each, and on a trace of
+// molecules up to (48, 192, 768) grouping requests up to 3e8 lost 5 % of
+// the throughput to one handle per request)
+constexpr double kAutoWork = 6e7;
+// summed nocc nvirt^2 naux of the requests in the grouped step at once: the
+// grouped kernel wins while the group's step is launch- or latency-bound
+// (measured: 16 requests of (16, 64, 256), 2.7e8 in total, and one of
+// (32, 128, 512), 2.7e8) and loses to one tcgen05 handle per request
+// beyond (16 of (32, 128, 512), 4.3e9 in total)
+constexpr double kMaxGroupWork = 4e8;
 
 // one request of a group, as the kernel reads it (device pointers)
 struct Req {
@@ -74,13 +86,15 @@ struct GroupRunner {
   grp::Table* d_table = nullptr;
   grp::Table* h_table = nullptr;  // pinned
   grp::Barrier* d_bar = nullptr;
-  int grid = 0;
+  int grid = 0;  // largest co-resident grid (SMs x CTAs per SM)
+  int nsm = 0;
   cudaEvent_t ev = nullptr;
   unsigned long long* phase_ns = nullptr;  // device clock of every barrier of the last chunk, or NULL
   const char* phase_file = nullptr;        // diagnostics: where group_status appends those clocks
 };
 
-bool group_eligible(const rttda_request& q);
+bool group_eligible(const rttda_request& q);  // within the grouped kernel's limits
+double group_work(const rttda_request& q);  // nocc nvirt^2 naux
 size_t group_estimate_bytes(const rttda_request& q);
 // Allocate a grouped request's device state and upload its molecule (the
 // arrays of q, host or device memory, are copied before return).

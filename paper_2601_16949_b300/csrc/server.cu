@@ -53,6 +53,7 @@ struct Request {
   rttda::GroupReq* g = nullptr;  // grouped request (small BF16): no handle
   double* dev = nullptr;  // handle: [dip nsteps+1][nrm nsteps+1][omega nfreq][S nfreq]; grouped: [omega][S]
   size_t bytes = 0;
+  double gwork = 0.0;  // grouped: its share of the group's work (nocc nvirt^2 naux)
   long done_steps = 0, inflight = 0;
   cudaEvent_t ev = nullptr;
   std::vector<double> spectrum, omega, dipole;
@@ -91,8 +92,9 @@ struct rttda_server {
   // grouped step of the small BF16 requests (one persistent kernel per chunk
   // for all of them); touched by the scheduler only, except `grouping`
   rttda::GroupRunner grp;
-  std::atomic<bool> grouping{true};
+  std::atomic<int> grouping{1};  // rttda_server_set_grouping mode: 0 off, 1 by work, 2 every eligible request
   bool grp_ready = false, grp_busy = false;
+  double grp_work = 0.0;  // summed work of the admitted grouped requests (under mu)
   std::vector<Request*> grp_batch;
 
   // statistics
@@ -132,6 +134,8 @@ void rttda_server::release(Request* r, int final_state) {
   std::lock_guard<std::mutex> lk(mu);
   used -= r->bytes;
   r->bytes = 0;
+  grp_work -= r->gwork;
+  r->gwork = 0.0;
   r->state = final_state;
   r->t_done = seconds_since(t0);
   if (final_state == RTTDA_REQ_DONE) {
@@ -163,7 +167,11 @@ bool rttda_server::admit_one() {
       return true;
     }
     const rttda_request& q = r->req;
-    to_group = grouping.load() && rttda::group_eligible(q);
+    const int gm = grouping.load();
+    if (gm != 0 && rttda::group_eligible(q)) {
+      const double w = rttda::group_work(q);
+      to_group = gm == 2 || (w <= rttda::grp::kAutoWork && grp_work + w <= rttda::grp::kMaxGroupWork);
+    }
     const size_t need = to_group ? rttda::group_estimate_bytes(q)
                                 : rttda::estimate_bytes(q.nocc, q.nvirt, q.naux, 1, q.prec, q.nsteps);
     if (used + need > budget) {
@@ -179,6 +187,10 @@ bool rttda_server::admit_one() {
     pending.pop_front();
     used += need;
     r->bytes = need;
+    if (to_group) {
+      r->gwork = rttda::group_work(q);
+      grp_work += r->gwork;
+    }
     // the state stays PENDING until the molecule has been copied: a caller
     // with device factors may free them once the request leaves PENDING
     if (!to_group) {
@@ -587,7 +599,8 @@ rttda_status rttda_server_cancel(rttda_server_t s, long id) {
 rttda_status rttda_server_set_grouping(rttda_server_t s, int enable) {
   rttda::g_last_error.clear();
   if (!s) return rttda::set_error(RTTDA_E_ARG, "rttda_server_set_grouping: NULL server");
-  s->grouping.store(enable != 0);
+  if (enable < 0 || enable > 2) return rttda::set_error(RTTDA_E_ARG, "rttda_server_set_grouping: mode must be 0, 1 or 2");
+  s->grouping.store(enable);
   return RTTDA_OK;
 }
 

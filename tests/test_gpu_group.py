@@ -49,7 +49,7 @@ def _request(rb, case):
 
 def _serve(rb, cases, grouping=True, chunk=64, max_active=8):
     srv = rb.rttda_server_create(32 << 30, max_active, chunk)
-    rb.rttda_server_set_grouping(srv, grouping)
+    rb.rttda_server_set_grouping(srv, 2 if grouping else 0)
     reqs = [_request(rb, c) for c in cases]
     ids = [rb.rttda_server_submit(srv, q) for _, q in reqs]
     out = []
@@ -153,7 +153,7 @@ def test_device_factor_requests_equal_host_factor_requests(rb, grouping):
     out = []
     for mol in (mol_dev, mol_host):
         srv = rb.rttda_server_create(32 << 30, 2, 50)
-        rb.rttda_server_set_grouping(srv, grouping)
+        rb.rttda_server_set_grouping(srv, 2 if grouping else 0)
         q = rb.make_request(mol, CX, "bf16", pulse, DT, nsteps, **SPEC)
         assert q[0].factors_on_device == (1 if mol is mol_dev else 0)
         rid = rb.rttda_server_submit(srv, q)
@@ -163,3 +163,22 @@ def test_device_factor_requests_equal_host_factor_requests(rb, grouping):
         rb.rttda_server_destroy(srv)
         out.append(dip)
     assert np.array_equal(out[0], out[1])
+
+
+def test_grouping_by_work_routes_small_requests_only(rb):
+    """Mode 1 (the default) groups a request only while it and the group are
+    small in nocc nvirt^2 naux; the others get handles.  Results do not
+    depend on the route beyond the BF16 tolerance, and a mode outside 0-2
+    is refused."""
+    small = (8, 64, 48, dict(kind=0, E0=1e-3, direction=(0, 0, 1)), 120, 1)       # 1.6e6
+    large = (20, 130, 260, dict(kind=0, E0=2e-3, direction=(0, 1, 0)), 120, 5)    # 8.8e7 > 6e7
+    srv = rb.rttda_server_create(32 << 30, 4, 40)
+    reqs = [_request(rb, c) for c in (small, large)]
+    ids = [rb.rttda_server_submit(srv, q) for _, q in reqs]
+    for rid in ids:
+        rb.rttda_server_wait(srv, rid, 300.0)
+    assert [rb.rttda_server_poll(srv, rid)[0] for rid in ids] == [rb.REQ_DONE] * 2
+    assert rb.rttda_server_stats_get(srv)["grouped"] == 1
+    with pytest.raises(Exception):
+        rb.rttda_server_set_grouping(srv, 3)
+    rb.rttda_server_destroy(srv)
