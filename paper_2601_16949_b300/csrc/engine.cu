@@ -417,75 +417,87 @@ void wide_attr() {
                        (int)tc::wide_smem_bytes<BN, MB, NBP, ST, KB, TR>());
 }
 
-// Clustered wide-M main contraction (BN 192, two 128-row blocks, K tile 64):
-// clusters of CL CTAs over CL consecutive column tiles share every Z tile by
-// TMA multicast.  `a` is the map of 128/CL-row Z boxes; `grid` a multiple
-// of CL that is co-resident (wide_cluster_grid).
-template <int NBP, int CL>
-void wide_cluster_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s,
-                         int grid) {
-  constexpr int ST = NBP == 2 ? 2 : 4;
+// Clustered wide-M main contraction (BN 192, two 128-row blocks, K tile KB
+// of 64 or 32): clusters of CL CTAs over CL consecutive column tiles share
+// every Z tile by TMA multicast.  `a` is the map of 128/CL-row Z boxes;
+// `grid` a multiple of CL that is co-resident (wide_cluster_capacity).
+// Stages as in the plain plans: K tile 64 holds 4 (one B_vv plane) or 2
+// (two planes), K tile 32 holds 8 or 5.
+template <int NBP, int KB>
+constexpr int wide_cluster_stages() {
+  return KB == 64 ? (NBP == 2 ? 2 : 4) : (NBP == 2 ? 5 : 8);
+}
+
+template <int NBP, int KB, int CL>
+cudaLaunchConfig_t wide_cluster_config(cudaLaunchAttribute* at, int grid, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(tc::kThreads);
-  cfg.dynamicSmemBytes = tc::wide_smem_bytes<192, 2, NBP, ST, 64>();
+  cfg.dynamicSmemBytes = tc::wide_smem_bytes<192, 2, NBP, wide_cluster_stages<NBP, KB>(), KB>();
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = CL;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, tc::k_tc_wide<192, 2, NBP, ST, 64, false, CL>, a, b, prm);
+  return cfg;
 }
 
-template <int NBP, int CL>
-void wide_cluster_attr() {
-  constexpr int ST = NBP == 2 ? 2 : 4;
-  cudaFuncSetAttribute(tc::k_tc_wide<192, 2, NBP, ST, 64, false, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)tc::wide_smem_bytes<192, 2, NBP, ST, 64>());
+template <int NBP, int KB, int CL>
+void wide_cluster_launch(const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm, cudaStream_t s,
+                         int grid) {
+  cudaLaunchAttribute at[1];
+  const cudaLaunchConfig_t cfg = wide_cluster_config<NBP, KB, CL>(at, grid, s);
+  cudaLaunchKernelEx(&cfg, tc::k_tc_wide<192, 2, NBP, wide_cluster_stages<NBP, KB>(), KB, false, CL>, a, b, prm);
 }
 
 // CTAs of the clustered kernel that can be resident at once (a multiple of
 // CL; clusters must fit inside one GPC), 0 if none.
-template <int NBP, int CL>
+template <int NBP, int KB, int CL>
 int wide_cluster_capacity() {
-  constexpr int ST = NBP == 2 ? 2 : 4;
-  wide_cluster_attr<NBP, CL>();
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)(CL * 64));
-  cfg.blockDim = dim3(tc::kThreads);
-  cfg.dynamicSmemBytes = tc::wide_smem_bytes<192, 2, NBP, ST, 64>();
+  constexpr int ST = wide_cluster_stages<NBP, KB>();
+  auto kern = tc::k_tc_wide<192, 2, NBP, ST, KB, false, CL>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::wide_smem_bytes<192, 2, NBP, ST, KB>());
   cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CL;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
+  const cudaLaunchConfig_t cfg = wide_cluster_config<NBP, KB, CL>(at, CL * 64, nullptr);
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, (void*)tc::k_tc_wide<192, 2, NBP, ST, 64, false, CL>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, (void*)kern, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return n * CL;
 }
 
-int wide_cluster_capacity(int nbp, int cl) {
-  if (nbp == 2) return cl == 4 ? wide_cluster_capacity<2, 4>() : wide_cluster_capacity<2, 2>();
-  return cl == 4 ? wide_cluster_capacity<1, 4>() : wide_cluster_capacity<1, 2>();
+template <int KB>
+int wide_cluster_capacity_kb(int nbp, int cl) {
+  if (nbp == 2) return cl == 4 ? wide_cluster_capacity<2, KB, 4>() : wide_cluster_capacity<2, KB, 2>();
+  return cl == 4 ? wide_cluster_capacity<1, KB, 4>() : wide_cluster_capacity<1, KB, 2>();
 }
 
-void wide_cluster_dispatch(int nbp, int cl, const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm,
-                           cudaStream_t s, int grid) {
+int wide_cluster_capacity(int nbp, int kb, int cl) {
+  return kb == 32 ? wide_cluster_capacity_kb<32>(nbp, cl) : wide_cluster_capacity_kb<64>(nbp, cl);
+}
+
+template <int KB>
+void wide_cluster_dispatch_kb(int nbp, int cl, const CUtensorMap& a, const CUtensorMap& b, const tc::Params& prm,
+                              cudaStream_t s, int grid) {
   if (nbp == 2) {
-    if (cl == 4) wide_cluster_launch<2, 4>(a, b, prm, s, grid);
-    else wide_cluster_launch<2, 2>(a, b, prm, s, grid);
+    if (cl == 4) wide_cluster_launch<2, KB, 4>(a, b, prm, s, grid);
+    else wide_cluster_launch<2, KB, 2>(a, b, prm, s, grid);
   } else {
-    if (cl == 4) wide_cluster_launch<1, 4>(a, b, prm, s, grid);
-    else wide_cluster_launch<1, 2>(a, b, prm, s, grid);
+    if (cl == 4) wide_cluster_launch<1, KB, 4>(a, b, prm, s, grid);
+    else wide_cluster_launch<1, KB, 2>(a, b, prm, s, grid);
   }
+}
+
+void wide_cluster_dispatch(int nbp, int kb, int cl, const CUtensorMap& a, const CUtensorMap& b,
+                           const tc::Params& prm, cudaStream_t s, int grid) {
+  if (kb == 32)
+    wide_cluster_dispatch_kb<32>(nbp, cl, a, b, prm, s, grid);
+  else
+    wide_cluster_dispatch_kb<64>(nbp, cl, a, b, prm, s, grid);
 }
 
 // Transposed wide configurations (rows a in two 128-row blocks, columns
@@ -694,7 +706,7 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s, bool xt_done = f
       if (h->wide_mb) {
         // wide-M tiles: MB accumulators share each B tile; both B planes per stage
         if (h->wide_cl > 1)
-          wide_cluster_dispatch(h->nprod_main, h->wide_cl, h->tmMAc[c], h->tmMB[c], prm, s, h->wide_grid);
+          wide_cluster_dispatch(h->nprod_main, h->wide_kb, h->wide_cl, h->tmMAc[c], h->tmMB[c], prm, s, h->wide_grid);
         else
           wide_dispatch(h->tc_bn, h->wide_mb, h->nprod_main, h->wide_kb, h->tmMA[c], h->tmMB[c], prm, s,
                         h->wide_tr);
@@ -1747,7 +1759,7 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   const int best = h->tc_bn;
   // Clustered main contraction: clusters of 4 CTAs over 4 column tiles share
   // every Z tile by TMA multicast when the plan is the wide-M tile with BN
-  // 192, K tile 64 and a multiple of 4 column tiles, and Z dominates the
+  // 192 (K tile 64 or 32) and a multiple of 4 column tiles, and Z dominates the
   // operand bytes (Z is C o / v times B_vv; here at least twice).  Measured
   // under the power cap: on the batched field scan (Z 10.7 x B_vv) the
   // kernel's DRAM reads drop from 68 to 55 GB per launch, the SM clock
@@ -1760,10 +1772,10 @@ static rttda_status alloc_tc(rttda_ctx* h, int C) {
   {
     int cl = M >= 2LL * v ? 4 : 1;
     if (const char* e = std::getenv("RTTDA_WIDE_CLUSTER")) cl = std::atoi(e);
-    if ((cl == 2 || cl == 4) && h->wide_mb == 2 && !h->wide_tr && best == 192 && kb == 64 &&
+    if ((cl == 2 || cl == 4) && h->wide_mb == 2 && !h->wide_tr && best == 192 && (kb == 64 || kb == 32) &&
         cdiv(v, best) % cl == 0 && (h->nprod_main == 1 || h->nprod_main == 2)) {
       const long long tmn = cdiv(v, best) * cdiv(M, 2LL * tc::kBM);
-      const int cap = wide_cluster_capacity(h->nprod_main, cl);
+      const int cap = wide_cluster_capacity(h->nprod_main, kb, cl);
       if (cap >= cl) {
         // fewer CTAs than SMs: keep the plan's split count unless its last
         // wave leaves more than a tenth of the launch idle, then choose the

@@ -279,8 +279,9 @@ def test_z_build_tile_order_and_l2_policy_do_not_change_sigma(rb, prec, monkeypa
 
 @pytest.mark.parametrize("prec", ["bf16", "bf16x2"])
 @pytest.mark.parametrize("cl", [2, 4])
-def test_clustered_main_contraction_is_bitwise_the_plain_one(rb, prec, cl, monkeypatch):
-    """The wide-M main contraction in clusters of 2 or 4 CTAs (RTTDA_WIDE_CLUSTER;
+@pytest.mark.parametrize("kb", [64, 32])
+def test_clustered_main_contraction_is_bitwise_the_plain_one(rb, prec, cl, kb, monkeypatch):
+    """The wide-M main contraction, K tile 64 or 32, in clusters of 2 or 4 CTAs (RTTDA_WIDE_CLUSTER;
     4 is the default where the plan allows it, 1 turns clusters off):
     each CTA loads 128/CL rows of every Z tile and multicasts them to the
     cluster, and a stage is refilled only after every CTA of the cluster has
@@ -288,23 +289,27 @@ def test_clustered_main_contraction_is_bitwise_the_plain_one(rb, prec, cl, monke
     of the plain kernel, so sigma and a short propagation are bitwise the
     same (four column tiles of 192, one row block, split-K), and sigma
     matches the oracle's rows."""
-    mol = synth.molecule(32, 768, 40, seed=9)
+    # naux such that the plan's split-K count gives at most 132 units, so the
+    # clustered grid keeps it (a re-chosen count would sum in another order)
+    mol = synth.molecule(32, 768, 40 if kb == 64 else 20, seed=9)
     pulses = [dict(kind=4, E0=0.01 * (k + 1), omega=0.6, duration=6.0, direction=(0, 0, 1)) for k in range(4)]
-    monkeypatch.setenv("RTTDA_WIDE_PLAN", "192,2,64")
+    monkeypatch.setenv("RTTDA_WIDE_PLAN", f"192,2,{kb}")
     n = 1 + 32 * 768
     c = synth.random_state(n, len(pulses), seed=5)
-    res = {}
+    res, splits = {}, {}
     for clu in (1, cl):
         monkeypatch.setenv("RTTDA_WIDE_CLUSTER", str(clu))
         prop = rb.Propagator(mol, 0.2, prec)
         prop.set_field(pulses)
         plan = rb.rttda_plan(prop.h)
-        assert (plan["main_kernel"], plan["main_bn"], plan["main_mb"], plan["main_kb"]) == (2, 192, 2, 64), plan
+        assert (plan["main_kernel"], plan["main_bn"], plan["main_mb"], plan["main_kb"]) == (2, 192, 2, kb), plan
         assert plan["main_cluster"] == clu and plan["main_grid"] % clu == 0, plan
+        splits[clu] = plan["main_splits"]
         sig = _sigma_gpu(rb, prop, c, 2.5)
         _, dip, nrm = prop.propagate(0.05, 6, c0=c)
         prop.close()
         res[clu] = (sig, dip, nrm)
+    assert splits[1] == splits[cl], splits
     for a, b in zip(res[1], res[cl]):
         assert np.array_equal(a, b)
     rows = np.concatenate([[0, 1, n - 1], np.random.default_rng(4).choice(np.arange(2, n - 1), 9, replace=False)])
