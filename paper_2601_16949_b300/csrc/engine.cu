@@ -138,6 +138,12 @@ struct rttda_ctx {
   double* m064 = nullptr;
   void* mooC = nullptr;
   void* mvvC = nullptr;
+  // one-polarisation batches in the FP32 modes: the field GEMMs' operands
+  // in their arithmetic types (the stage input cast per call into Xfc; the
+  // first trajectory's FP64 dipole blocks as double-float pairs)
+  void* Xfc = nullptr;     // [N][C] float or df32
+  void* moo_df = nullptr;  // [o][o] df32
+  void* mvv_df = nullptr;  // [v][v] df32
   void* m0C = nullptr;
   bool any_field = false, any_kick = false;
   bool same_dir = false;  // every trajectory of the batch has the same polarisation
@@ -309,13 +315,15 @@ rttda_ctx::~rttda_ctx() {
 }
 
 void rttda_ctx::free_batch() {
-  void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xn, Xs, Xs2, acc, F, E, term,
+  void* ps[] = {d_pulses, d_kappa, d_dirs, moo64, mvv64, m064, mooC, mvvC, m0C, Xfc, moo_df, mvv_df,
+                Xn, Xs, Xs2, acc, F, E, term,
                 obs_part, Xq, d_step, w, Jpart, Zt, Kpart, h_io, Xt, Zk, Xc, Wt, wpart_tc, Xf, f0_part,
                 oz_x, oz_ex, oz_zi, oz_z, oz_ez, oz_xc, oz_exc, oz_wpart, oz_w, oz_ew};
   for (void* p : ps) dfree(p);
   d_pulses = nullptr;
   d_kappa = d_dirs = moo64 = mvv64 = m064 = nullptr;
   mooC = mvvC = m0C = nullptr;
+  Xfc = moo_df = mvv_df = nullptr;
   Xn = Xs = Xs2 = acc = F = E = term = obs_part = Xq = nullptr;
   d_step = nullptr;
   w = Jpart = Zt = Kpart = nullptr;
@@ -909,7 +917,12 @@ constexpr int kF0Chunks = 64;  // most chunks of the ground-row field sum
 
 // kernels of one field product: the rows (one kernel, or two GEMMs for a
 // batch with one polarisation), the ground row's chunks and their sum
-inline int field_launches(const rttda_ctx* h) { return (h->same_dir && 2 * h->T >= 8) ? 4 : 3; }
+// launches of one field product: M_d X rows (two GEMMs, after the cast of
+// the stage input when its operands are pre-converted), ground-row chunks,
+// their sum
+inline int field_launches(const rttda_ctx* h) {
+  return (h->same_dir && 2 * h->T >= 8) ? (h->Xfc ? 5 : 4) : 3;
+}
 
 // F = M_d X (singles rows): the register-tiled kernel when its 32 x 64
 // tiles give at least one block per SM, else one output per thread.
@@ -919,10 +932,25 @@ void launch_field(rttda_ctx* h, const double* X, const TM_* moo, const TM_* mvv,
   if (h->same_dir && C >= 8) {
     // one polarisation for the whole batch: two GEMMs over the C columns
     // (the first trajectory's dipole blocks stand for all)
-    k_field_gemm<TM_, TC, false><<<dim3((unsigned)cdiv(C, 64), (unsigned)cdiv(h->v, 64), h->o), 256, 0, s>>>(
-        h->o, h->v, C, X, mvv, m0, h->F);
-    k_field_gemm<TM_, TC, true><<<dim3((unsigned)cdiv(C, 64), (unsigned)cdiv(h->o, 64), h->v), 256, 0, s>>>(
-        h->o, h->v, C, X, moo, m0, h->F);
+    const dim3 gvv((unsigned)cdiv(C, 64), (unsigned)cdiv(h->v, 64), h->o);
+    const dim3 goo((unsigned)cdiv(C, 64), (unsigned)cdiv(h->o, 64), h->v);
+    if constexpr (!std::is_same<TC, double>::value) {
+      if (h->Xfc) {
+        // operands in the arithmetic's type: the stage input cast once here,
+        // the dipole blocks (float, or df32 pairs of the FP64 blocks) at
+        // rttda_set_field
+        const long long n = h->N * C;
+        k_to_type<TC><<<blocks_for(n, 256), 256, 0, s>>>(n, X, (TC*)h->Xfc);
+        const TC* xf = (const TC*)h->Xfc;
+        const TC* mv = std::is_same<TC, df32>::value ? (const TC*)h->mvv_df : (const TC*)(const void*)mvv;
+        const TC* mo = std::is_same<TC, df32>::value ? (const TC*)h->moo_df : (const TC*)(const void*)moo;
+        k_field_gemm<TC, TC, false, TC, TM_><<<gvv, 256, 0, s>>>(h->o, h->v, C, xf, mv, m0, h->F);
+        k_field_gemm<TC, TC, true, TC, TM_><<<goo, 256, 0, s>>>(h->o, h->v, C, xf, mo, m0, h->F);
+        return;
+      }
+    }
+    k_field_gemm<TM_, TC, false><<<gvv, 256, 0, s>>>(h->o, h->v, C, X, mvv, m0, h->F);
+    k_field_gemm<TM_, TC, true><<<goo, 256, 0, s>>>(h->o, h->v, C, X, moo, m0, h->F);
     return;
   }
   const long long tiled = cdiv(h->v, 64) * cdiv(h->o, 32) * (long long)h->T;
@@ -2411,6 +2439,14 @@ rttda_status rttda_set_field(rttda_t h, const rttda_pulse* pulses, int ntraj) {
     k_dipole_dir<float><<<blocks_for(loo * ntraj, 256), 256, 0, s>>>(loo, ntraj, h->d_dirs, h->mu_oo, (float*)h->mooC);
     k_dipole_dir<float><<<blocks_for(lvv * ntraj, 256), 256, 0, s>>>(lvv, ntraj, h->d_dirs, h->mu_vv, (float*)h->mvvC);
     k_dipole_dir<float><<<blocks_for(lov * ntraj, 256), 256, 0, s>>>(lov, ntraj, h->d_dirs, h->mu_0, (float*)h->m0C);
+    if (h->same_dir && 2 * ntraj >= 8) {
+      // the field GEMMs' operands in their arithmetic types (launch_field)
+      CKS(dalloc_bytes(&h->Xfc, (size_t)h->N * 2 * ntraj * sizeof(df32)));
+      CKS(dalloc_bytes(&h->moo_df, (size_t)loo * sizeof(df32)));
+      CKS(dalloc_bytes(&h->mvv_df, (size_t)lvv * sizeof(df32)));
+      k_to_type<df32><<<blocks_for(loo, 256), 256, 0, s>>>(loo, h->moo64, (df32*)h->moo_df);
+      k_to_type<df32><<<blocks_for(lvv, 256), 256, 0, s>>>(lvv, h->mvv64, (df32*)h->mvv_df);
+    }
   }
   CKS(h->alloc_batch());
   CK(cudaGetLastError());

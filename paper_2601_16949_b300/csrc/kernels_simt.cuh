@@ -623,10 +623,14 @@ __global__ void __launch_bounds__(256) k_field_small(int o, int v, int T, const 
 // consecutive columns), K in steps of 16 staged in shared memory with the
 // next step's global loads in flight.  TC = float, or df32 for the step's
 // start (the observables).  grid (ceil(C/64), ceil(v/64), o) and
-// (ceil(C/64), ceil(o/64), v).
-template <typename TM, typename TC, bool OO>
-__global__ void __launch_bounds__(256) k_field_gemm(int o, int v, int C, const double* __restrict__ X,
-                                                    const TM* __restrict__ mu, const TM* __restrict__ m0,
+// (ceil(C/64), ceil(o/64), v).  TM is the dipole block's element type, T0
+// that of the ground-row vector m, TX that of the amplitudes: with TM = TX =
+// TC the operands arrive already in the arithmetic's type (k_to_type), and
+// the loads convert nothing (B300's conversions from FP64 run on the slow
+// FP64 pipe).
+template <typename TM, typename TC, bool OO, typename TX = double, typename T0 = TM>
+__global__ void __launch_bounds__(256) k_field_gemm(int o, int v, int C, const TX* __restrict__ X,
+                                                    const TM* __restrict__ mu, const T0* __restrict__ m0,
                                                     double* __restrict__ F) {
   constexpr int BK = 16;
   __shared__ TC As[2][BK][64];
@@ -637,7 +641,7 @@ __global__ void __launch_bounds__(256) k_field_gemm(int o, int v, int C, const d
   const int M = OO ? o : v, K = OO ? o : v;
   const int lda = OO ? o : v;
   const size_t bstride = OO ? (size_t)v * C : (size_t)C;
-  const double* Bz = OO ? X + (size_t)(1 + z) * C : X + (size_t)(1 + (size_t)z * v) * C;
+  const TX* Bz = OO ? X + (size_t)(1 + z) * C : X + (size_t)(1 + (size_t)z * v) * C;
   TC acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -650,7 +654,7 @@ __global__ void __launch_bounds__(256) k_field_gemm(int o, int v, int C, const d
       const int e = threadIdx.x + 256 * l, kk = e >> 6, mm = e & 63;
       const int k = k0 + kk;
       ra[l] = (k < K && m0r + mm < M) ? cvt<TC>(mu[(size_t)k * lda + m0r + mm]) : TC(0);
-      rb[l] = (k < K && c0 + mm < C) ? (TC)Bz[(size_t)k * bstride + c0 + mm] : TC(0);
+      rb[l] = (k < K && c0 + mm < C) ? cvt<TC>(Bz[(size_t)k * bstride + c0 + mm]) : TC(0);
     }
   };
   auto sstore = [&](int buf) {
@@ -699,10 +703,18 @@ __global__ void __launch_bounds__(256) k_field_gemm(int o, int v, int C, const d
       if (OO) {
         F[row * C + col] -= (double)acc[r][c];
       } else {
-        F[row * C + col] = (double)fma(cvt<TC>(m0[(size_t)i * v + a]), (TC)X[col], acc[r][c]);
+        F[row * C + col] = (double)fma(cvt<TC>(m0[(size_t)i * v + a]), cvt<TC>(X[col]), acc[r][c]);
       }
     }
   }
+}
+
+// out[e] = x[e] in type T (float, or df32: hi = rn(x), lo = rn(x - hi), the
+// conversion the field kernels make of every operand they load).
+template <typename T>
+__global__ void __launch_bounds__(256) k_to_type(long long n, const double* __restrict__ x, T* __restrict__ out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = cvt<T>(x[e]);
 }
 
 // Ground row of the field product: F_0 = sum_ia m_ia X_ia (Hermitian
