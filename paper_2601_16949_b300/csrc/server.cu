@@ -227,9 +227,9 @@ bool rttda_server::admit_one() {
     std::vector<double>().swap(r->Boo);
     std::vector<double>().swap(r->Bvv);
     active.push_back(r);
-    max_concurrent = std::max(max_concurrent, (int)active.size());
     {
       std::lock_guard<std::mutex> lk(mu);
+      max_concurrent = std::max(max_concurrent, (int)active.size());
       r->state = RTTDA_REQ_ACTIVE;  // group_admit has copied the molecule
       ++grouped;
     }
