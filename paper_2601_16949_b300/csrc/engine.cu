@@ -1322,44 +1322,44 @@ rttda_status run_steps(rttda_ctx* h, double t_call, double dt, long nsteps, doub
       for (long k = 0; k < nsteps; ++k) dispatch(h->prec, step);
       ++h->capture_fallbacks;
     } else {
-    h->launches = l0 + h->launches_per_step * nsteps;
-    // Keep the executable step graph of the handle and give it this call's
-    // parameters with cudaGraphExecUpdate (launches in flight keep theirs);
-    // a new one is instantiated only when the update is refused (a different
-    // topology).  With an instantiation per call, the steps of concurrent
-    // handles (the server's requests) were measured not to overlap at all;
-    // instantiation allocates device memory, which keeps commands of
-    // different streams from running concurrently.  RTTDA_GRAPH_CACHE=0
-    // instantiates per call.
-    const char* gc = std::getenv("RTTDA_GRAPH_CACHE");
-    const bool keep = !(gc && std::atoi(gc) == 0);
-    if (keep && h->step_exec) {
-      cudaGraphExecUpdateResultInfo info{};
-      if (cudaGraphExecUpdate(h->step_exec, graph, &info) == cudaSuccess) {
-        exec = h->step_exec;
-      } else {
-        cudaGetLastError();
-        cudaGraphExecDestroy(h->step_exec);
+      h->launches = l0 + h->launches_per_step * nsteps;
+      // Keep the executable step graph of the handle and give it this call's
+      // parameters with cudaGraphExecUpdate (launches in flight keep theirs);
+      // a new one is instantiated only when the update is refused (a different
+      // topology).  With an instantiation per call, the steps of concurrent
+      // handles (the server's requests) were measured not to overlap at all;
+      // instantiation allocates device memory, which keeps commands of
+      // different streams from running concurrently.  RTTDA_GRAPH_CACHE=0
+      // instantiates per call.
+      const char* gc = std::getenv("RTTDA_GRAPH_CACHE");
+      const bool keep = !(gc && std::atoi(gc) == 0);
+      if (keep && h->step_exec) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(h->step_exec, graph, &info) == cudaSuccess) {
+          exec = h->step_exec;
+        } else {
+          cudaGetLastError();
+          cudaGraphExecDestroy(h->step_exec);
+        }
+        h->step_exec = nullptr;
       }
-      h->step_exec = nullptr;
-    }
-    if (!exec) {
-      ce = cudaGraphInstantiate(&exec, graph, 0);
-      if (ce != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        return set_error(RTTDA_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+      if (!exec) {
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (ce != cudaSuccess) {
+          cudaGraphDestroy(graph);
+          return set_error(RTTDA_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        }
       }
-    }
-    for (long k = 0; k < nsteps; ++k) {
-      ce = cudaGraphLaunch(exec, s);
-      if (ce != cudaSuccess) break;
-    }
-    if (keep && ce == cudaSuccess)
-      h->step_exec = exec;
-    else
-      cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+      for (long k = 0; k < nsteps; ++k) {
+        ce = cudaGraphLaunch(exec, s);
+        if (ce != cudaSuccess) break;
+      }
+      if (keep && ce == cudaSuccess)
+        h->step_exec = exec;
+      else
+        cudaGraphExecDestroy(exec);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return set_error(RTTDA_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
     }
   }
   if (dip) {
