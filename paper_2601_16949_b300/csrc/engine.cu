@@ -188,6 +188,7 @@ struct rttda_ctx {
   long capture_fallbacks = 0;        // propagation calls whose step-graph capture was invalidated
   bool break_capture = false;        // test hook (RTTDA_TEST_BREAK_CAPTURE): invalidate every capture
   int z_hint = 1;                    // Z stores evict-first in L2 (RTTDA_ZHINT)
+  int z_res1 = 1;                    // one-plane stages for the one-product Z build (RTTDA_ZRES1)
   int z_run = 4;                     // Z-build tiles per CTA and column run in a slab, 0: no slabs (RTTDA_ZRUN)
   int integrator = RTTDA_INT_RK4;    // rttda_integrator
   // projectors (Eq. (22)) and the overlaps of the last propagation
@@ -399,7 +400,7 @@ namespace {
 // --- tensor-core exchange -------------------------------------------------
 // Z = B_oo c (K = nocc, short): pipeline stages with hi/lo Z staging (two
 // planes) or one-plane staging
-constexpr int kZBN = 256, kZStages2 = 2, kZStages1 = 2, kZStagesR = 3;
+constexpr int kZBN = 256, kZStages2 = 2, kZStages1 = 2, kZStagesR = 3, kZStagesR1 = 6;
 
 // Persistent launch: one CTA per SM (or per tile if fewer tiles).
 template <int BN, int ST, int BM, int EP>
@@ -580,6 +581,7 @@ void set_tc_smem_limits() {
   tc_attr<kZBN, kZStages2, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>();
   tc_attr<kZBN, kZStages1, tc::BMODE_PLAIN, tc::EPI_ZONE>();
   tc_attr<kZBN, kZStagesR, tc::BMODE_PLAIN, tc::EPI_ZRES>();
+  tc_attr<kZBN, kZStagesR1, tc::BMODE_PLAIN, tc::EPI_ZRES1>();
   tc_attr<128, 7, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<224, 5, tc::BMODE_VV, tc::EPI_PARTIAL>();
   tc_attr<256, 4, tc::BMODE_VV, tc::EPI_PARTIAL>();
@@ -685,12 +687,18 @@ void exchange_tc(rttda_ctx* h, const double* X, cudaStream_t s, bool xt_done = f
       prm.err = h->d_err;
       if (h->zplanes > 1)
         tc_launch<kZBN, kZStages2, tc::BMODE_PLAIN, tc::EPI_ZSPLIT>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
-      else if (prm.kt_total <= tc::kResKT)
+      else if (prm.kt_total <= tc::kResKT) {
         // the amplitude tile (all of K = nocc) stays resident across a
-        // CTA's run of tiles with the same columns (m-fastest order)
-        tc_launch<kZBN, kZStagesR, tc::BMODE_PLAIN, tc::EPI_ZRES>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
-      else
+        // CTA's run of tiles with the same columns (m-fastest order); one
+        // product (plain BF16) needs one A plane per stage, so twice the
+        // stages fit
+        if (prm.nprod == 1 && h->z_res1)
+          tc_launch<kZBN, kZStagesR1, tc::BMODE_PLAIN, tc::EPI_ZRES1>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
+        else
+          tc_launch<kZBN, kZStagesR, tc::BMODE_PLAIN, tc::EPI_ZRES>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
+      } else {
         tc_launch<kZBN, kZStages1, tc::BMODE_PLAIN, tc::EPI_ZONE>(h->tmZA[c], h->tmZB, prm, s, &h->tmZS[c]);
+      }
     }
     {
       // K_(col,i),a (+)= sum_{P in chunk, b} Z^P_(col,i),b B^P_ab   (split-K)
@@ -2108,6 +2116,7 @@ static rttda_status create_impl(rttda_ctx* h, const double* eps_occ, const doubl
   AllocStream as(h->stream);
   dispatch(h->prec, [&](auto ops) { decltype(ops)::set_smem_limits(); });
   if (const char* e = std::getenv("RTTDA_ZHINT")) h->z_hint = std::atoi(e) != 0;
+  if (const char* e = std::getenv("RTTDA_ZRES1")) h->z_res1 = std::atoi(e) != 0;
   if (const char* e = std::getenv("RTTDA_TEST_BREAK_CAPTURE")) h->break_capture = std::atoi(e) != 0;
   if (const char* e = std::getenv("RTTDA_ZRUN")) h->z_run = std::max(0, std::atoi(e));
   const size_t o = h->o, v = h->v, P = h->P;

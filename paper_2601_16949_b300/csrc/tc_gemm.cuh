@@ -45,7 +45,8 @@ enum : int { BMODE_PLAIN = 0,  // B[plane][n][k], 3-D map (k, n, plane)
 enum : int { EPI_PARTIAL = 0,  // out[split][m][n] FP32
              EPI_ZSPLIT = 1,   // Z as BF16 hi/lo planes (see Params)
              EPI_ZONE = 2,     // Z as one BF16 plane
-             EPI_ZRES = 3 };   // EPI_ZONE with the B operand resident (K of at most kResKT tiles)
+             EPI_ZRES = 3,     // EPI_ZONE with the B operand resident (K of at most kResKT tiles)
+             EPI_ZRES1 = 4 };  // EPI_ZRES with one A plane per stage (one product: plain BF16)
 
 // EPI_ZRES: the whole K extent of the B tile (at most kResKT K tiles) stays
 // in shared memory while a CTA walks its tiles m-fastest, so a B tile is
@@ -332,7 +333,7 @@ constexpr int kStageRowWords = 20;
 constexpr int kZGroupBytes = 32 * 128;
 template <int EPI>
 constexpr int zstage_bytes_per_warp() {
-  return EPI == 1 ? 4 * kZGroupBytes : (EPI == 2 || EPI == 3) ? 2 * kZGroupBytes : 0;
+  return EPI == 1 ? 4 * kZGroupBytes : (EPI == 2 || EPI == 3 || EPI == 4) ? 2 * kZGroupBytes : 0;
 }
 static_assert(2 * 32 * kStageRowWords * 4 <= 2 * kZGroupBytes, "manual staging must fit");
 
@@ -358,18 +359,18 @@ struct Cfg {
 // products of the tile from one stage); the other kinds one plane each.
 template <int EPI>
 constexpr int stage_a_planes() {
-  return (EPI == 2 || EPI == 3) ? 2 : 1;
+  return (EPI == 2 || EPI == 3) ? 2 : 1;  // EPI_ZRES1: one
 }
 
 // bytes of one pipeline stage: with EPI_ZRES the A planes only
 template <int BN, int EPI>
 constexpr int stage_bytes() {
-  return EPI == 3 ? 2 * kABytes : Cfg<BN, stage_a_planes<EPI>()>::kStageBytes;
+  return EPI == 3 ? 2 * kABytes : EPI == 4 ? kABytes : Cfg<BN, stage_a_planes<EPI>()>::kStageBytes;
 }
 
 template <int BN, int STAGES, int EPI = 0>
 constexpr size_t smem_bytes() {
-  return (size_t)STAGES * stage_bytes<BN, EPI>() + (EPI == 3 ? (size_t)kResKT * BN * 128 : 0) +
+  return (size_t)STAGES * stage_bytes<BN, EPI>() + ((EPI == 3 || EPI == 4) ? (size_t)kResKT * BN * 128 : 0) +
          1024 /*alignment slack*/ + 256 /*barriers*/ + (size_t)kEpiWarps * zstage_bytes_per_warp<EPI>();
 }
 
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // issues every product of the tile from it (products (hi,hi), (lo,hi),
   // i.e. nprod <= 2 with alo); otherwise one stage per product.  BRES: the
   // B tile (all K tiles) is resident and stages hold the A planes only.
-  constexpr bool BRES = EPI == EPI_ZRES;
+  constexpr bool BRES = EPI == EPI_ZRES || EPI == EPI_ZRES1;
   constexpr bool MERGED = EPI == EPI_ZONE || BRES;
   using CF = Cfg<BN, stage_a_planes<EPI>()>;
   constexpr int kStage = stage_bytes<BN, EPI>();
